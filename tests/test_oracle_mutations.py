@@ -1,0 +1,85 @@
+"""Planted mistakes in the oracle must fail at least one pin.
+
+Each case replaces one oracle function (on the CPU, via monkeypatch) by a
+plausible wrong variant and checks that the pin comparisons of
+test_oracle_pins.py no longer hold.
+"""
+import numpy as np
+import pytest
+
+from oracle import grids, gw
+import pin_forms as PF
+from test_oracle_pins import generic_inputs, rel, small_workload
+
+
+def _pol_variant(mirror=True, sign=+1, s_factor=1.0):
+    def pol(V, G, nk3, spin_factor=2.0, q_list=None, t_list=None):
+        nk, naux, ntau = V.shape[0], V.shape[2], G.shape[1]
+        out = np.zeros((nk, ntau, naux, naux), complex)
+        for q in range(nk):
+            for t in range(ntau):
+                for k in range(nk):
+                    kq = gw.k_shift(nk3, k, q, sign)
+                    gm = G[k, ntau - 1 - t] if mirror else G[k, t]
+                    out[q, t] += np.einsum("Qda,cd,ab,Pbc->QP", V[k, kq], gm, G[kq, t], V[kq, k])
+                out[q, t] *= -(spin_factor * s_factor / nk)
+        return out
+    return pol
+
+
+def _sig_variant(conj_right=False, transpose_p=False, sign=-1):
+    def sig(V, G, Pt, nk3, k_list=None, t_list=None):
+        nk, nao, ntau = V.shape[0], V.shape[3], G.shape[1]
+        out = np.zeros((nk, ntau, nao, nao), complex)
+        for k in range(nk):
+            for t in range(ntau):
+                for q in range(nk):
+                    kmq = gw.k_shift(nk3, k, q, sign)
+                    vr = V[kmq, k].conj() if conj_right else V[kmq, k]
+                    p = Pt[q, t].T if transpose_p else Pt[q, t]
+                    out[k, t] += np.einsum("Qia,ab,QP,Pbj->ij", V[k, kmq], G[kmq, t], p, vr)
+                out[k, t] *= -1.0 / nk
+        return out
+    return sig
+
+
+def _pins_hold():
+    """The pole-form, brute-force and scalar pins, as booleans."""
+    ok = []
+    nk3 = (3, 1, 1)
+    w = small_workload(nk3=nk3, nao=2, naux=3, ntau=10, beta=5.0)
+    h, v, g = generic_inputs(w, rng_seed=7)
+    tau = PF.np.array(grids.chebyshev_nodes(w.ntau, w.beta))
+    ok.append(rel(gw.polarization(v, g, nk3, 2.0), PF.pole_form_p0_tau(h, v, nk3, w.beta, 0.0, tau, 2.0)) < 1e-13)
+    r = gw.sigma_eval(v, g, nk3, w.beta, 2.0)
+    _, F, B = grids.transform_matrices(w.ntau, w.beta, 0)
+    ok.append(rel(r["Sig"], PF.brute_force_sigma(v, g, nk3, F, B, 2.0)) < 1e-12)
+    beta, eps, vv = 10.0, 0.3, 0.7
+    hh = np.array([[[eps]]], complex)
+    v1 = np.full((1, 1, 1, 1, 1), vv, complex)
+    g1 = PF.np.array(__import__("paper_2406_18479_gb300.inputs", fromlist=["g0_tau"]).g0_tau(
+        hh, 0.0, beta, grids.chebyshev_nodes(20, beta)))
+    r1 = gw.sigma_eval(v1, g1, (1, 1, 1), beta, 2.0)
+    f = PF.fermi(np.array([eps]), beta)[0]
+    c = -2.0 * vv * vv * f * (1 - f)
+    ok.append(rel(r1["Sig"], -vv * vv * g1 * c / (1 - beta * c)) < 1e-10)
+    return ok
+
+
+def test_unmutated_pins_hold():
+    assert all(_pins_hold())
+
+
+@pytest.mark.parametrize("name,target,variant", [
+    ("G(tau) for G(beta-tau) in P0", "polarization", _pol_variant(mirror=False)),
+    ("k-q for k+q in P0", "polarization", _pol_variant(sign=-1)),
+    ("spin factor dropped", "polarization", _pol_variant(s_factor=0.5)),
+    ("conjugated right V in Sigma", "self_energy", _sig_variant(conj_right=True)),
+    ("transposed P~ in Sigma", "self_energy", _sig_variant(transpose_p=True)),
+    ("k+q for k-q in Sigma", "self_energy", _sig_variant(sign=+1)),
+    ("(I+P0)^-1 P0 in the aux Dyson", "aux_dyson",
+     lambda P0w: np.linalg.solve(np.eye(P0w.shape[-1]) + P0w, P0w)),
+])
+def test_planted_mistake_is_caught(monkeypatch, name, target, variant):
+    monkeypatch.setattr(gw, target, variant)
+    assert not all(_pins_hold()), name
