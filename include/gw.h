@@ -1,0 +1,191 @@
+/*
+ * gw.h -- C ABI of the GB300 (sm_103a) GW self-energy library.
+ *
+ * The library evaluates the dynamical GW self-energy of fully self-consistent
+ * finite-temperature GW with density-fitted Coulomb integrals
+ * (arXiv 2406.18479, Sec. 2.3, Eqs. tilde_P0_tau, P0t_to_P0w, tilde_P_omega,
+ * tilde_W_DF2, sigma_gw) and the Dyson update of G (Sec. 2.5, Eq. dyson).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Complex numbers are interleaved (re, im) doubles (gw_c128). All arrays are
+ * row-major and dense:
+ *   V    [nk][nk][naux][nao][nao]   V[k1][k2][Q][i][j] = V_{k1 i, k2 j}(Q)   (Eq. CoulombDF)
+ *   G    [nk][ntau][nao][nao]       G^k_ij(tau_t), tau_t first-kind Chebyshev nodes on [0, beta]
+ *   H    [nk][nao][nao]
+ *   P0t, Pt   [nk][ntau][naux][naux]      bosonic, indexed by q
+ *   P0w, Pw   [nk][nw_b][naux][naux]      nw_b = gw_sample_count(ntau, 0)
+ *   Sig  [nk][ntau][nao][nao]
+ * k is the flat index (n1*N2 + n2)*N3 + n3 of the Gamma-centred mesh
+ * k = 2 pi (n1/N1, n2/N2, n3/N3); k +- q is taken modulo the mesh.
+ *
+ * Pointers named *_dev are device pointers owned by the caller (for example
+ * torch tensors); the library never frees them and reads or writes them only
+ * on the context's stream, so results are valid in stream order. Pointers
+ * named *_host are host memory, read or written synchronously. The library
+ * owns its own workspaces, allocated in gw_create.
+ *
+ * Every call returns a gw_status. On failure the call leaves its outputs
+ * undefined and gw_last_error() returns a thread-local message. Nothing is
+ * thrown across the ABI.
+ */
+#ifndef GW_GB300_H
+#define GW_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } gw_c128;
+
+typedef enum {
+  GW_OK = 0,
+  GW_EINVAL = 1,        /* bad argument (null pointer, size out of range) */
+  GW_ENOMEM = 2,        /* workspace does not fit the budget or cudaMalloc failed */
+  GW_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+  GW_ETIMEOUT = 4,      /* host-side wait ran out of time */
+  GW_EDEVTIMEOUT = 5,   /* a device-side bounded wait gave up; the kernel returned early */
+  GW_ENOTFINITE = 6,    /* a non-finite value was found where the call checks for one */
+  GW_ENOTCONV = 7,      /* iteration limit reached without convergence */
+  GW_EAGAIN = 8,        /* result not ready yet */
+  GW_ENOTIMPL = 9       /* not implemented for this configuration */
+} gw_status;
+
+typedef enum {
+  GW_FP64 = 0,          /* every contraction in FP64 */
+  GW_MIXED_BF16X3 = 1,  /* V.G.V contractions on tcgen05 tensor cores with 3 bf16 limbs
+                           per FP32-rounded operand and FP32 accumulation; transforms,
+                           Dyson solves and the Sigma accumulation stay FP64 */
+  GW_MIXED_FP16S = 2    /* as above with one fp16 limb and a power-of-two scale per tile */
+} gw_precision;
+
+typedef struct {
+  int nk[3];            /* k-mesh N1, N2, N3 (1,1,1 for a molecule) */
+  int nao;              /* orbitals, 1..512 */
+  int naux;             /* auxiliary functions, 1..4096 */
+  int ntau;             /* Chebyshev tau nodes, 1..512 */
+  double beta;          /* inverse temperature (1/Ha), > 0 */
+  double mu;            /* chemical potential (Ha), used by gw_dyson_G */
+  double spin_factor;   /* spin sum of Eq. tilde_P0_tau: 2 for spin-restricted G */
+  int precision;        /* gw_precision */
+  int tau_chunk;        /* tau nodes per batch in the contractions; 0 = automatic */
+} gw_config;
+
+/* Library version string. */
+const char* gw_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* gw_last_error(void);
+
+/*
+ * Number of sampled Matsubara frequencies for an ntau-node grid: ntau, or ntau+1
+ * where the parity differs from that of a set symmetric under w -> -w (odd for
+ * bosons, stat = 0; even for fermions, stat = 1). Returns -1 on bad input.
+ */
+int gw_sample_count(int ntau, int stat);
+
+/*
+ * Host-only grid builder for the Fourier integral of Eq. P0t_to_P0w (bosonic,
+ * w_n = 2 n pi / beta, Sec. 2.3) or of G and Sigma (fermionic,
+ * w_n = (2n+1) pi / beta, Eq. dyson). Writes, for nw = gw_sample_count(ntau, stat):
+ *   tau_host[ntau]      Chebyshev nodes (beta/2)(1 - cos(pi (j + 1/2)/ntau))
+ *   idx_host[nw]        sampled Matsubara indices n (ascending, symmetric in w)
+ *   F_host[nw][ntau]    X(i w_n) = sum_t F_nt X(tau_t) for the Chebyshev interpolant
+ *   B_host[ntau][nw]    least-squares left inverse of F (B F = I)
+ * Any output pointer may be NULL. Needs no GPU.
+ */
+int gw_grid_build(int ntau, double beta, int stat, double* tau_host, int64_t* idx_host,
+                  gw_c128* F_host, gw_c128* B_host);
+
+typedef struct gw_ctx gw_ctx;
+
+/*
+ * Creates a context for one problem size on the current CUDA device, bound to
+ * cuda_stream (a cudaStream_t; NULL = the legacy default stream). Builds the
+ * bosonic and fermionic grids and allocates every workspace. *out is NULL on
+ * failure.
+ */
+int gw_create(gw_ctx** out, const gw_config* cfg, void* cuda_stream);
+
+/* Synchronizes the context's stream and frees its workspaces. NULL is a no-op. */
+int gw_destroy(gw_ctx* ctx);
+
+/* Bytes of device memory the context owns. */
+size_t gw_workspace_bytes(const gw_ctx* ctx);
+
+/*
+ * Borrows the Coulomb factor V (layout above, Eq. CoulombDF). The caller keeps
+ * V_dev alive and unchanged until gw_destroy or the next gw_set_coulomb. In the
+ * mixed precisions this call also converts V into its limb planes (a device
+ * workspace).
+ */
+int gw_set_coulomb(gw_ctx* ctx, const gw_c128* V_dev);
+
+/*
+ * Step (a), Eq. tilde_P0_tau (Sec. 2.3):
+ *   P0^q_QQ'(tau) = -(s/N_k) sum_k sum_abcd V^{k,k+q}_da(Q) G^k_cd(beta - tau)
+ *                                          G^{k+q}_ab(tau) V^{k+q,k}_bc(Q'),
+ * where G(beta - tau_t) is the mirrored node G[ntau-1-t] and s = spin_factor.
+ * Reads G_dev, writes P0t_dev.
+ */
+int gw_polarization(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* P0t_dev);
+
+/*
+ * Grid transforms along the time axis of a batch of nbatch blocks:
+ *   to_matsubara:  out[b][n][e] = sum_t F_nt in[b][t][e]   (in: [nbatch][ntau][nelem])
+ *   to_tau:        out[b][t][e] = sum_n B_tn in[b][n][e]   (in: [nbatch][nw][nelem])
+ * stat = 0 bosonic (Eq. P0t_to_P0w), 1 fermionic (Eq. dyson).
+ */
+int gw_to_matsubara(gw_ctx* ctx, int stat, const gw_c128* in_dev, gw_c128* out_dev,
+                    int nbatch, long long nelem);
+int gw_to_tau(gw_ctx* ctx, int stat, const gw_c128* in_dev, gw_c128* out_dev,
+              int nbatch, long long nelem);
+
+/*
+ * Step (c), Eq. tilde_P_omega: Pw = (I - P0w)^{-1} P0w for every (q, n), by
+ * Gauss-Jordan inversion with partial pivoting, Pw = (I - P0w)^{-1} - I.
+ * P0w_dev and Pw_dev may be the same buffer.
+ */
+int gw_aux_dyson(gw_ctx* ctx, const gw_c128* P0w_dev, gw_c128* Pw_dev);
+
+/* Steps (b)+(c)+back-transform: Pt = B (I - F P0t)^{-1} (F P0t). */
+int gw_screened_interaction(gw_ctx* ctx, const gw_c128* P0t_dev, gw_c128* Pt_dev);
+
+/*
+ * Step (d), Eqs. sigma_gw and tilde_W_DF2 (Sec. 2.3):
+ *   Sigma^k_ij(tau) = -(1/N_k) sum_q sum_QQ'ab V^{k,k-q}_ia(Q) G^{k-q}_ab(tau)
+ *                                             P~^q_QQ'(tau) V^{k-q,k}_bj(Q').
+ * W~ is never formed. Overwrites Sig_dev.
+ */
+int gw_self_energy(gw_ctx* ctx, const gw_c128* G_dev, const gw_c128* Pt_dev, gw_c128* Sig_dev);
+
+/* One self-energy evaluation, steps (a)-(d), with P0 and P~ in context workspaces. */
+int gw_sigma_eval(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* Sig_dev);
+
+/*
+ * Dyson equation, Eq. dyson (Sec. 2.5) with S = I and Sigma^inf = 0:
+ *   G^k(i w_n) = [(i w_n + mu) I - H^k - Sigma^k(i w_n)]^{-1},
+ * with Sigma(i w) = F^f Sigma(tau) and G(tau) = B^f G(i w) on the fermionic grid.
+ * Reads H_dev [nk][nao][nao] and Sig_dev, writes G_dev.
+ */
+int gw_dyson_G(gw_ctx* ctx, const gw_c128* H_dev, const gw_c128* Sig_dev, gw_c128* G_dev);
+
+/*
+ * Iteration mixing (Sec. 5.3): Sig_inout <- alpha Sig_new + (1 - alpha) Sig_inout, and
+ * *max_abs_diff_host = max |Sig_inout(after) - Sig_inout(before)| over all elements.
+ * Synchronizes the stream to return the norm. Returns GW_ENOTFINITE if the
+ * mixed self-energy holds a NaN or infinity.
+ */
+int gw_mix(gw_ctx* ctx, const gw_c128* Sig_new_dev, gw_c128* Sig_inout_dev, double alpha,
+           double* max_abs_diff_host);
+
+/* Waits for all work queued on the context's stream. */
+int gw_synchronize(gw_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GW_GB300_H */

@@ -11,8 +11,8 @@ here from its definition:
   is represented by its Chebyshev interpolant through those nodes.
 * F (i Omega <- tau): F = T C, with T_nl = int_0^beta T_l(x(tau)) e^{i w_n tau} dtau
   (Eq. P0t_to_P0w applied to each Chebyshev polynomial) and C the map from
-  node values to Chebyshev coefficients. T is evaluated by Gauss-Legendre
-  quadrature with enough points to integrate the oscillation exactly to
+  node values to Chebyshev coefficients. T is evaluated by composite
+  Gauss-Legendre quadrature fine enough to integrate the oscillation to
   rounding.
 * B (tau <- i Omega) = the least-squares left inverse of F (F^{-1} when
   square): values at the sampled frequencies determine the interpolant, so
@@ -91,10 +91,16 @@ def _unit_transform(ntau: int, stat: int):
     l = np.arange(ntau)
     t_nodes = np.cos(np.outer(np.arccos(np.clip(x_nodes, -1, 1)), l))   # [t][l]
     c = np.linalg.inv(t_nodes)                              # [l][t]
-    # T_nl = int_0^1 T_l(2 tau - 1) e^{i w_n tau} dtau, Gauss-Legendre in x on [-1, 1]
-    nq = ntau + int(np.ceil(np.max(np.abs(w)) / 2.0)) + 64
-    xq, wq = np.polynomial.legendre.leggauss(nq)
-    tl_q = np.cos(np.outer(np.arccos(xq), l))               # [q][l]
+    # T_nl = int_0^1 T_l(2 tau - 1) e^{i w_n tau} dtau, in x = 2 tau - 1 on [-1, 1]:
+    # composite 24-point Gauss-Legendre on panels x_p = -cos(pi p / P), which are
+    # graded like the Chebyshev polynomials and span a few radians of phase each.
+    panels = int(np.ceil((np.max(np.abs(w)) / 2.0 + ntau) / 2.0)) + 8
+    edges = -np.cos(np.pi * np.arange(panels + 1) / panels)
+    g, gwt = np.polynomial.legendre.leggauss(24)
+    lo, hi = edges[:-1], edges[1:]
+    xq = (0.5 * (hi - lo)[:, None] * (g[None, :] + 1.0) + lo[:, None]).ravel()
+    wq = (0.5 * (hi - lo)[:, None] * gwt[None, :]).ravel()
+    tl_q = np.cos(np.outer(np.arccos(np.clip(xq, -1.0, 1.0)), l))   # [q][l]
     phase = np.exp(1j * np.outer(w, 0.5 * (xq + 1.0)))      # [n][q]
     t_nl = 0.5 * (phase * wq) @ tl_q                        # [n][l]
     f = t_nl @ c                                            # [n][t]

@@ -1,0 +1,451 @@
+// C ABI of the GW self-energy library: context, grids, k-mesh gather tables
+// and the FP64 stages (arXiv 2406.18479, Sec. 2.3 and Eq. dyson).
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gw_internal.h"
+#include "gw_mixed.h"
+
+namespace gwi {
+
+static thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+}  // namespace gwi
+
+using namespace gwi;
+
+struct gw_ctx {
+  gw_config cfg{};
+  cudaStream_t stream = nullptr;
+  int nk = 0, nao = 0, naux = 0, ntau = 0, nwb = 0, nwf = 0, nt = 1;
+  long long nao2 = 0, naux2 = 0, pair = 0;
+  double2 *Fb = nullptr, *Bb = nullptr, *Ff = nullptr, *Bf = nullptr;
+  double* wf = nullptr;                   // fermionic frequencies (device)
+  long long* tabs = nullptr;              // 6 tables [nq][nk]
+  long long *tab_kkpq = nullptr, *tab_kpqk = nullptr, *tab_gkpq = nullptr;
+  long long *tab_kkmq = nullptr, *tab_kmqk = nullptr, *tab_gkmq = nullptr;
+  double2* work = nullptr;                // contraction intermediates, nt * 2 * nk * pair
+  double2 *P0t = nullptr, *Pw = nullptr, *Pt = nullptr;
+  double2* dyson_ws = nullptr;            // nk * nwf * nao2
+  int* status = nullptr;                  // device flags: [0] singular matrix
+  double* maxdiff = nullptr;
+  int* nonfinite = nullptr;
+  const double2* V = nullptr;
+  size_t bytes = 0;
+  MixedState* mixed = nullptr;
+};
+
+namespace {
+
+int kshift(const int nk3[3], int k, int q, int sign) {
+  const int k1 = k / (nk3[1] * nk3[2]), k2 = (k / nk3[2]) % nk3[1], k3 = k % nk3[2];
+  const int q1 = q / (nk3[1] * nk3[2]), q2 = (q / nk3[2]) % nk3[1], q3 = q % nk3[2];
+  const int a = ((k1 + sign * q1) % nk3[0] + nk3[0]) % nk3[0];
+  const int b = ((k2 + sign * q2) % nk3[1] + nk3[1]) % nk3[1];
+  const int c = ((k3 + sign * q3) % nk3[2] + nk3[2]) % nk3[2];
+  return (a * nk3[1] + b) * nk3[2] + c;
+}
+
+template <class T>
+int dev_alloc(gw_ctx* c, T** p, size_t count) {
+  if (count == 0) count = 1;
+  const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(GW_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+  }
+  c->bytes += count * sizeof(T);
+  return GW_OK;
+}
+
+int cuda_check(const char* what) {
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define GW_TRY(x)                 \
+  do {                            \
+    const int _rc = (x);          \
+    if (_rc != GW_OK) return _rc; \
+  } while (0)
+
+void free_ctx(gw_ctx* c) {
+  if (!c) return;
+  mixed_destroy(c->mixed);
+  void* ptrs[] = {c->Fb, c->Bb, c->Ff, c->Bf, c->wf, c->tabs, c->work, c->P0t, c->Pw,
+                  c->Pt, c->dyson_ws, c->status, c->maxdiff, c->nonfinite};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete c;
+}
+
+int upload_grid(gw_ctx* c, int stat, double2** F, double2** B, int* nw_out) {
+  const int nw = sample_count(c->ntau, stat);
+  std::vector<gw_c128> hF((size_t)nw * c->ntau), hB((size_t)c->ntau * nw);
+  std::vector<int64_t> idx(nw);
+  GW_TRY(grid_build(c->ntau, c->cfg.beta, stat, nullptr, idx.data(), hF.data(), hB.data()));
+  GW_TRY(dev_alloc(c, F, hF.size()));
+  GW_TRY(dev_alloc(c, B, hB.size()));
+  cudaMemcpy(*F, hF.data(), hF.size() * sizeof(double2), cudaMemcpyHostToDevice);
+  cudaMemcpy(*B, hB.data(), hB.size() * sizeof(double2), cudaMemcpyHostToDevice);
+  if (stat == 1) {
+    std::vector<double> w(nw);
+    for (int n = 0; n < nw; ++n) w[n] = (2.0 * (double)idx[n] + 1.0) * M_PI / c->cfg.beta;
+    GW_TRY(dev_alloc(c, &c->wf, nw));
+    cudaMemcpy(c->wf, w.data(), nw * sizeof(double), cudaMemcpyHostToDevice);
+  }
+  *nw_out = nw;
+  return cuda_check("grid upload");
+}
+
+// ---- FP64 stages ------------------------------------------------------------------------
+
+int polarization_fp64(gw_ctx* c, const double2* G, double2* P0t) {
+  const int nk = c->nk, nao = c->nao, naux = c->naux, ntau = c->ntau;
+  const long long nao2 = c->nao2, pair = c->pair;
+  for (int q = 0; q < nk; ++q) {
+    for (int t0 = 0; t0 < ntau; t0 += c->nt) {
+      const int nt = std::min(c->nt, ntau - t0);
+      double2* Abuf = c->work;
+      double2* Bbuf = c->work + (long long)c->nt * nk * pair;
+      {  // A^Q_{db}(k,t) = sum_a V^{k,k+q}_da(Q) G^{k+q}_ab(t)
+        ZGemm g;
+        g.M = naux * nao; g.N = nao; g.K = nao; g.nbatch = nt * nk; g.bin = nk;
+        g.A = c->V; g.va.rs_in = nao; g.va.ks_in = 1; g.ba.tab = c->tab_kkpq + (long long)q * nk;
+        g.B = G + (long long)t0 * nao2; g.vb.rs_in = 1; g.vb.ks_in = nao;
+        g.bb.tab = c->tab_gkpq + (long long)q * nk; g.bb.bs_out = nao2;
+        g.C = Abuf; g.vc.rs_in = nao; g.vc.ks_in = 1; g.bc.bs_in = pair; g.bc.bs_out = (long long)nk * pair;
+        GW_TRY(zgemm_fp64(g, c->stream));
+      }
+      {  // B^{Q'}_{bd}(k,t) = sum_c V^{k+q,k}_bc(Q') G^k_cd(beta - t), stored as [Q'][d][b]
+        ZGemm g;
+        g.M = naux * nao; g.N = nao; g.K = nao; g.nbatch = nt * nk; g.bin = nk;
+        g.A = c->V; g.va.rs_in = nao; g.va.ks_in = 1; g.ba.tab = c->tab_kpqk + (long long)q * nk;
+        g.B = G + (long long)(ntau - 1 - t0) * nao2; g.vb.rs_in = 1; g.vb.ks_in = nao;
+        g.bb.bs_in = (long long)ntau * nao2; g.bb.bs_out = -nao2;
+        g.C = Bbuf; g.vc.rin = nao; g.vc.rs_in = 1; g.vc.rs_out = nao2; g.vc.ks_in = nao;
+        g.bc.bs_in = pair; g.bc.bs_out = (long long)nk * pair;
+        GW_TRY(zgemm_fp64(g, c->stream));
+      }
+      {  // P0^q_QQ'(t) = -(s/N_k) sum_{k,d,b} A^Q_{db} B^{Q'}_{bd}
+        ZGemm g;
+        g.M = naux; g.N = naux; g.K = nk * (int)nao2; g.nbatch = nt;
+        g.A = Abuf; g.va.rs_in = nao2; g.va.kin = (int)nao2; g.va.ks_in = 1; g.va.ks_out = pair;
+        g.ba.bs_in = (long long)nk * pair;
+        g.B = Bbuf; g.vb = g.va; g.bb = g.ba;
+        g.C = P0t + ((long long)q * ntau + t0) * c->naux2; g.vc.rs_in = naux; g.vc.ks_in = 1;
+        g.bc.bs_in = c->naux2;
+        g.alpha = -c->cfg.spin_factor / nk;
+        GW_TRY(zgemm_fp64(g, c->stream));
+      }
+    }
+  }
+  return GW_OK;
+}
+
+int self_energy_fp64(gw_ctx* c, const double2* G, const double2* Pt, double2* Sig) {
+  const int nk = c->nk, nao = c->nao, naux = c->naux, ntau = c->ntau;
+  const long long nao2 = c->nao2, pair = c->pair;
+  if (cudaMemsetAsync(Sig, 0, (size_t)nk * ntau * nao2 * sizeof(double2), c->stream) != cudaSuccess)
+    return cuda_check("memset Sigma");
+  for (int q = 0; q < nk; ++q) {
+    for (int t0 = 0; t0 < ntau; t0 += c->nt) {
+      const int nt = std::min(c->nt, ntau - t0);
+      double2* Rbuf = c->work;
+      double2* Zbuf = c->work + (long long)c->nt * nk * pair;
+      {  // R^Q_{bj}(k,t) = sum_Q' P~^q_QQ'(t) V^{k-q,k}_bj(Q')
+        ZGemm g;
+        g.M = naux; g.N = (int)nao2; g.K = naux; g.nbatch = nt * nk; g.bin = nk;
+        g.A = Pt + ((long long)q * ntau + t0) * c->naux2; g.va.rs_in = naux; g.va.ks_in = 1;
+        g.ba.bs_out = c->naux2;
+        g.B = c->V; g.vb.rs_in = 1; g.vb.ks_in = nao2; g.bb.tab = c->tab_kmqk + (long long)q * nk;
+        g.C = Rbuf; g.vc.rs_in = nao2; g.vc.ks_in = 1; g.bc.bs_in = pair; g.bc.bs_out = (long long)nk * pair;
+        GW_TRY(zgemm_fp64(g, c->stream));
+      }
+      {  // Z^Q_{ib}(k,t) = sum_a V^{k,k-q}_ia(Q) G^{k-q}_ab(t)
+        ZGemm g;
+        g.M = naux * nao; g.N = nao; g.K = nao; g.nbatch = nt * nk; g.bin = nk;
+        g.A = c->V; g.va.rs_in = nao; g.va.ks_in = 1; g.ba.tab = c->tab_kkmq + (long long)q * nk;
+        g.B = G + (long long)t0 * nao2; g.vb.rs_in = 1; g.vb.ks_in = nao;
+        g.bb.tab = c->tab_gkmq + (long long)q * nk; g.bb.bs_out = nao2;
+        g.C = Zbuf; g.vc.rs_in = nao; g.vc.ks_in = 1; g.bc.bs_in = pair; g.bc.bs_out = (long long)nk * pair;
+        GW_TRY(zgemm_fp64(g, c->stream));
+      }
+      {  // Sigma^k_ij(t) += -(1/N_k) sum_{Q,b} Z^Q_{ib} R^Q_{bj}
+        ZGemm g;
+        g.M = nao; g.N = nao; g.K = naux * nao; g.nbatch = nt * nk; g.bin = nk;
+        g.A = Zbuf; g.va.rs_in = nao; g.va.kin = nao; g.va.ks_in = 1; g.va.ks_out = nao2;
+        g.ba.bs_in = pair; g.ba.bs_out = (long long)nk * pair;
+        g.B = Rbuf; g.vb.rs_in = 1; g.vb.kin = nao; g.vb.ks_in = nao; g.vb.ks_out = nao2;
+        g.bb = g.ba;
+        g.C = Sig + (long long)t0 * nao2; g.vc.rs_in = nao; g.vc.ks_in = 1;
+        g.bc.bs_in = (long long)ntau * nao2; g.bc.bs_out = nao2;
+        g.alpha = -1.0 / nk;
+        g.accumulate = 1;
+        GW_TRY(zgemm_fp64(g, c->stream));
+      }
+    }
+  }
+  return GW_OK;
+}
+
+int transform(gw_ctx* c, int stat, bool forward, const double2* in, double2* out, int nbatch,
+              long long nelem) {
+  const int nw = stat == 0 ? c->nwb : c->nwf;
+  const int nin = forward ? c->ntau : nw, nout = forward ? nw : c->ntau;
+  const double2* Mtx = forward ? (stat == 0 ? c->Fb : c->Ff) : (stat == 0 ? c->Bb : c->Bf);
+  if (nelem > (1LL << 30)) return fail(GW_EINVAL, "transform: nelem %lld too large", nelem);
+  for (int b0 = 0; b0 < nbatch; b0 += 65535) {
+    const int nb = std::min(65535, nbatch - b0);
+    ZGemm g;
+    g.M = nout; g.N = (int)nelem; g.K = nin; g.nbatch = nb;
+    g.A = Mtx; g.va.rs_in = nin; g.va.ks_in = 1;
+    g.B = in + (long long)b0 * nin * nelem; g.vb.rs_in = 1; g.vb.ks_in = nelem; g.bb.bs_in = nin * nelem;
+    g.C = out + (long long)b0 * nout * nelem; g.vc.rs_in = nelem; g.vc.ks_in = 1; g.bc.bs_in = nout * nelem;
+    GW_TRY(zgemm_fp64(g, c->stream));
+  }
+  return GW_OK;
+}
+
+int aux_dyson(gw_ctx* c, const double2* P0w, double2* Pw) {
+  const long long n2 = c->naux2;
+  const int nb = c->nk * c->nwb;
+  if (Pw != P0w &&
+      cudaMemcpyAsync(Pw, P0w, (size_t)nb * n2 * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream) !=
+          cudaSuccess)
+    return cuda_check("aux_dyson copy");
+  GW_TRY(add_identity_fp64(Pw, c->naux, n2, nb, -1.0, 1.0, c->stream));   // I - P0
+  GW_TRY(batched_inverse_fp64(Pw, c->naux, n2, nb, c->status, c->stream));
+  GW_TRY(add_identity_fp64(Pw, c->naux, n2, nb, 1.0, -1.0, c->stream));   // (I - P0)^-1 - I
+  return GW_OK;
+}
+
+int screened(gw_ctx* c, const double2* P0t, double2* Pt) {
+  GW_TRY(transform(c, 0, true, P0t, c->Pw, c->nk, c->naux2));
+  GW_TRY(aux_dyson(c, c->Pw, c->Pw));
+  GW_TRY(transform(c, 0, false, c->Pw, Pt, c->nk, c->naux2));
+  return GW_OK;
+}
+
+}  // namespace
+
+// ---- ABI ----------------------------------------------------------------------------------
+
+extern "C" {
+
+const char* gw_version(void) { return "gw-gb300 0.1.0 (sm_103a)"; }
+
+const char* gw_last_error(void) { return g_last_error.c_str(); }
+
+int gw_sample_count(int ntau, int stat) { return sample_count(ntau, stat); }
+
+int gw_grid_build(int ntau, double beta, int stat, double* tau_host, int64_t* idx_host, gw_c128* F_host,
+                  gw_c128* B_host) {
+  if (sample_count(ntau, stat) < 0 || !(beta > 0)) return fail(GW_EINVAL, "gw_grid_build: bad arguments");
+  return grid_build(ntau, beta, stat, tau_host, idx_host, F_host, B_host);
+}
+
+int gw_create(gw_ctx** out, const gw_config* cfg, void* cuda_stream) {
+  if (!out || !cfg) return fail(GW_EINVAL, "gw_create: null argument");
+  *out = nullptr;
+  const int nk = cfg->nk[0] * cfg->nk[1] * cfg->nk[2];
+  if (cfg->nk[0] < 1 || cfg->nk[1] < 1 || cfg->nk[2] < 1 || nk > 4096 || cfg->nao < 1 || cfg->nao > 512 ||
+      cfg->naux < 1 || cfg->naux > 4096 || cfg->ntau < 1 || cfg->ntau > 512 || !(cfg->beta > 0) ||
+      cfg->precision < GW_FP64 || cfg->precision > GW_MIXED_FP16S)
+    return fail(GW_EINVAL, "gw_create: configuration out of range");
+  gw_ctx* c = new gw_ctx();
+  c->cfg = *cfg;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->nk = nk;
+  c->nao = cfg->nao;
+  c->naux = cfg->naux;
+  c->ntau = cfg->ntau;
+  c->nao2 = (long long)c->nao * c->nao;
+  c->naux2 = (long long)c->naux * c->naux;
+  c->pair = (long long)c->naux * c->nao2;
+  int rc = GW_OK;
+  do {
+    if ((rc = upload_grid(c, 0, &c->Fb, &c->Bb, &c->nwb)) != GW_OK) break;
+    if ((rc = upload_grid(c, 1, &c->Ff, &c->Bf, &c->nwf)) != GW_OK) break;
+    // k-mesh gather tables (element offsets), [q][k]
+    std::vector<long long> t(6 * (size_t)nk * nk);
+    const long long gk = (long long)c->ntau * c->nao2;
+    for (int q = 0; q < nk; ++q)
+      for (int k = 0; k < nk; ++k) {
+        const int kp = kshift(cfg->nk, k, q, +1), km = kshift(cfg->nk, k, q, -1);
+        const size_t i = (size_t)q * nk + k, s = (size_t)nk * nk;
+        t[0 * s + i] = ((long long)k * nk + kp) * c->pair;
+        t[1 * s + i] = ((long long)kp * nk + k) * c->pair;
+        t[2 * s + i] = (long long)kp * gk;
+        t[3 * s + i] = ((long long)k * nk + km) * c->pair;
+        t[4 * s + i] = ((long long)km * nk + k) * c->pair;
+        t[5 * s + i] = (long long)km * gk;
+      }
+    if ((rc = dev_alloc(c, &c->tabs, t.size())) != GW_OK) break;
+    cudaMemcpy(c->tabs, t.data(), t.size() * sizeof(long long), cudaMemcpyHostToDevice);
+    const size_t s = (size_t)nk * nk;
+    c->tab_kkpq = c->tabs;
+    c->tab_kpqk = c->tabs + s;
+    c->tab_gkpq = c->tabs + 2 * s;
+    c->tab_kkmq = c->tabs + 3 * s;
+    c->tab_kmqk = c->tabs + 4 * s;
+    c->tab_gkmq = c->tabs + 5 * s;
+    // tau chunk: intermediates of 2 * nk * pair complex per tau node, capped at 4 GiB
+    const double per_t = 2.0 * nk * (double)c->pair * sizeof(double2);
+    int nt = cfg->tau_chunk > 0 ? cfg->tau_chunk : (int)std::max(1.0, std::floor(4294967296.0 / per_t));
+    c->nt = std::min(nt, c->ntau);
+    if (cfg->precision == GW_FP64) {
+      if ((rc = dev_alloc(c, &c->work, (size_t)c->nt * 2 * nk * c->pair)) != GW_OK) break;
+    }
+    if ((rc = dev_alloc(c, &c->P0t, (size_t)nk * c->ntau * c->naux2)) != GW_OK) break;
+    if ((rc = dev_alloc(c, &c->Pw, (size_t)nk * c->nwb * c->naux2)) != GW_OK) break;
+    if ((rc = dev_alloc(c, &c->Pt, (size_t)nk * c->ntau * c->naux2)) != GW_OK) break;
+    if ((rc = dev_alloc(c, &c->dyson_ws, (size_t)nk * c->nwf * c->nao2)) != GW_OK) break;
+    if ((rc = dev_alloc(c, &c->status, 4)) != GW_OK) break;
+    if ((rc = dev_alloc(c, &c->maxdiff, 1)) != GW_OK) break;
+    if ((rc = dev_alloc(c, &c->nonfinite, 1)) != GW_OK) break;
+    cudaMemset(c->status, 0, 4 * sizeof(int));
+    if (cfg->precision != GW_FP64) {
+      MixedDims d;
+      d.nk3[0] = cfg->nk[0]; d.nk3[1] = cfg->nk[1]; d.nk3[2] = cfg->nk[2];
+      d.nk = nk; d.nao = c->nao; d.naux = c->naux; d.ntau = c->ntau; d.precision = cfg->precision;
+      d.tau_chunk = cfg->tau_chunk;
+      if ((rc = mixed_create(&c->mixed, d, c->stream, &c->bytes)) != GW_OK) break;
+    }
+    rc = cuda_check("gw_create");
+  } while (false);
+  if (rc != GW_OK) {
+    free_ctx(c);
+    return rc;
+  }
+  *out = c;
+  return GW_OK;
+}
+
+int gw_destroy(gw_ctx* ctx) {
+  if (!ctx) return GW_OK;
+  cudaStreamSynchronize(ctx->stream);
+  free_ctx(ctx);
+  return GW_OK;
+}
+
+size_t gw_workspace_bytes(const gw_ctx* ctx) { return ctx ? ctx->bytes : 0; }
+
+int gw_set_coulomb(gw_ctx* ctx, const gw_c128* V_dev) {
+  if (!ctx || !V_dev) return fail(GW_EINVAL, "gw_set_coulomb: null argument");
+  ctx->V = reinterpret_cast<const double2*>(V_dev);
+  if (ctx->mixed) return mixed_set_coulomb(ctx->mixed, ctx->V, ctx->tabs);
+  return GW_OK;
+}
+
+int gw_polarization(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* P0t_dev) {
+  if (!ctx || !G_dev || !P0t_dev) return fail(GW_EINVAL, "gw_polarization: null argument");
+  if (!ctx->V) return fail(GW_EINVAL, "gw_polarization: call gw_set_coulomb first");
+  const double2* G = reinterpret_cast<const double2*>(G_dev);
+  double2* P = reinterpret_cast<double2*>(P0t_dev);
+  if (ctx->mixed) return mixed_polarization(ctx->mixed, G, P, ctx->cfg.spin_factor);
+  return polarization_fp64(ctx, G, P);
+}
+
+int gw_to_matsubara(gw_ctx* ctx, int stat, const gw_c128* in_dev, gw_c128* out_dev, int nbatch,
+                    long long nelem) {
+  if (!ctx || !in_dev || !out_dev || (stat != 0 && stat != 1) || nbatch < 0 || nelem < 0)
+    return fail(GW_EINVAL, "gw_to_matsubara: bad argument");
+  return transform(ctx, stat, true, reinterpret_cast<const double2*>(in_dev),
+                   reinterpret_cast<double2*>(out_dev), nbatch, nelem);
+}
+
+int gw_to_tau(gw_ctx* ctx, int stat, const gw_c128* in_dev, gw_c128* out_dev, int nbatch, long long nelem) {
+  if (!ctx || !in_dev || !out_dev || (stat != 0 && stat != 1) || nbatch < 0 || nelem < 0)
+    return fail(GW_EINVAL, "gw_to_tau: bad argument");
+  return transform(ctx, stat, false, reinterpret_cast<const double2*>(in_dev),
+                   reinterpret_cast<double2*>(out_dev), nbatch, nelem);
+}
+
+int gw_aux_dyson(gw_ctx* ctx, const gw_c128* P0w_dev, gw_c128* Pw_dev) {
+  if (!ctx || !P0w_dev || !Pw_dev) return fail(GW_EINVAL, "gw_aux_dyson: null argument");
+  return aux_dyson(ctx, reinterpret_cast<const double2*>(P0w_dev), reinterpret_cast<double2*>(Pw_dev));
+}
+
+int gw_screened_interaction(gw_ctx* ctx, const gw_c128* P0t_dev, gw_c128* Pt_dev) {
+  if (!ctx || !P0t_dev || !Pt_dev) return fail(GW_EINVAL, "gw_screened_interaction: null argument");
+  return screened(ctx, reinterpret_cast<const double2*>(P0t_dev), reinterpret_cast<double2*>(Pt_dev));
+}
+
+int gw_self_energy(gw_ctx* ctx, const gw_c128* G_dev, const gw_c128* Pt_dev, gw_c128* Sig_dev) {
+  if (!ctx || !G_dev || !Pt_dev || !Sig_dev) return fail(GW_EINVAL, "gw_self_energy: null argument");
+  if (!ctx->V) return fail(GW_EINVAL, "gw_self_energy: call gw_set_coulomb first");
+  const double2* G = reinterpret_cast<const double2*>(G_dev);
+  const double2* P = reinterpret_cast<const double2*>(Pt_dev);
+  double2* S = reinterpret_cast<double2*>(Sig_dev);
+  if (ctx->mixed) return mixed_self_energy(ctx->mixed, G, P, S);
+  return self_energy_fp64(ctx, G, P, S);
+}
+
+int gw_sigma_eval(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* Sig_dev) {
+  if (!ctx || !G_dev || !Sig_dev) return fail(GW_EINVAL, "gw_sigma_eval: null argument");
+  GW_TRY(gw_polarization(ctx, G_dev, reinterpret_cast<gw_c128*>(ctx->P0t)));
+  GW_TRY(screened(ctx, ctx->P0t, ctx->Pt));
+  return gw_self_energy(ctx, G_dev, reinterpret_cast<const gw_c128*>(ctx->Pt), Sig_dev);
+}
+
+int gw_dyson_G(gw_ctx* ctx, const gw_c128* H_dev, const gw_c128* Sig_dev, gw_c128* G_dev) {
+  if (!ctx || !H_dev || !Sig_dev || !G_dev) return fail(GW_EINVAL, "gw_dyson_G: null argument");
+  const double2* H = reinterpret_cast<const double2*>(H_dev);
+  const double2* S = reinterpret_cast<const double2*>(Sig_dev);
+  double2* G = reinterpret_cast<double2*>(G_dev);
+  GW_TRY(transform(ctx, 1, true, S, ctx->dyson_ws, ctx->nk, ctx->nao2));
+  GW_TRY(build_g_dyson_fp64(ctx->dyson_ws, H, ctx->wf, ctx->cfg.mu, ctx->nk, ctx->nwf, ctx->nao, ctx->stream));
+  GW_TRY(batched_inverse_fp64(ctx->dyson_ws, ctx->nao, ctx->nao2, ctx->nk * ctx->nwf, ctx->status, ctx->stream));
+  GW_TRY(transform(ctx, 1, false, ctx->dyson_ws, G, ctx->nk, ctx->nao2));
+  return GW_OK;
+}
+
+int gw_mix(gw_ctx* ctx, const gw_c128* Sig_new_dev, gw_c128* Sig_inout_dev, double alpha,
+           double* max_abs_diff_host) {
+  if (!ctx || !Sig_new_dev || !Sig_inout_dev) return fail(GW_EINVAL, "gw_mix: null argument");
+  const long long n = (long long)ctx->nk * ctx->ntau * ctx->nao2;
+  cudaMemsetAsync(ctx->maxdiff, 0, sizeof(double), ctx->stream);
+  cudaMemsetAsync(ctx->nonfinite, 0, sizeof(int), ctx->stream);
+  GW_TRY(mix_fp64(reinterpret_cast<const double2*>(Sig_new_dev), reinterpret_cast<double2*>(Sig_inout_dev),
+                  alpha, n, ctx->maxdiff, ctx->nonfinite, ctx->stream));
+  double md = 0;
+  int bad = 0;
+  cudaMemcpyAsync(&md, ctx->maxdiff, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+  cudaMemcpyAsync(&bad, ctx->nonfinite, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check("gw_mix sync");
+  if (max_abs_diff_host) *max_abs_diff_host = md;
+  if (bad) return fail(GW_ENOTFINITE, "gw_mix: non-finite self-energy");
+  return GW_OK;
+}
+
+int gw_synchronize(gw_ctx* ctx) {
+  if (!ctx) return fail(GW_EINVAL, "gw_synchronize: null context");
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check("gw_synchronize");
+  int st[4] = {0, 0, 0, 0};
+  cudaMemcpy(st, ctx->status, sizeof(st), cudaMemcpyDeviceToHost);
+  if (st[0] || st[1] || st[2] || st[3]) {
+    cudaMemset(ctx->status, 0, sizeof(st));
+    if (st[1]) return fail(GW_EDEVTIMEOUT, "a device-side wait gave up (code %d)", st[1]);
+    if (st[0]) return fail(GW_EINVAL, "a Dyson matrix was singular");
+    return fail(GW_ECUDA, "device status %d %d", st[2], st[3]);
+  }
+  return cuda_check("gw_synchronize");
+}
+
+}  // extern "C"

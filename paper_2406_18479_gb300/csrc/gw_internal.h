@@ -1,0 +1,69 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <vector_types.h>
+
+#include "gw.h"
+
+namespace gwi {
+
+// ---- host utilities (grids.cpp, errors in gw_api.cu)
+int sample_count(int ntau, int stat);
+std::vector<int64_t> matsubara_indices(int n, int stat);
+int grid_build(int ntau, double beta, int stat, double* tau, int64_t* idx, gw_c128* F, gw_c128* B);
+int fail(int code, const char* fmt, ...);
+
+// ---- batched complex FP64 GEMM (k_fp64.cu)
+//
+// Operand view: element (r, k) of a matrix sits at
+//   base + (r / rin) * rs_out + (r % rin) * rs_in + (k / kin) * ks_out + (k % kin) * ks_in.
+// Two-level row and k indices express the (k-point, orbital) and (Q, orbital)
+// flattenings of the GW contractions without copies.
+struct ZView {
+  long long rs_in = 0, rs_out = 0;
+  long long ks_in = 0, ks_out = 0;
+  int rin = 1 << 30, kin = 1 << 30;
+};
+
+// Batch index b -> (bo, bi) = (b / bin, b % bin); the operand's offset is
+//   (tab ? tab[bi] : bi * bs_in) + bo * bs_out.
+struct ZBatch {
+  const long long* tab = nullptr;
+  long long bs_in = 0, bs_out = 0;
+};
+
+struct ZGemm {
+  int M = 0, N = 0, K = 0, nbatch = 1, bin = 1 << 30;
+  const double2* A = nullptr;    // A(m, k)
+  const double2* B = nullptr;    // B(n, k)
+  double2* C = nullptr;          // C(m, n): rows per C.rs_*, columns with stride C.ks_in
+  ZView va, vb, vc;
+  ZBatch ba, bb, bc;
+  double alpha = 1.0;            // C = alpha * sum_k A(m,k) B(n,k) (+ C if accumulate)
+  int accumulate = 0;
+};
+
+int zgemm_fp64(const ZGemm& g, void* stream);
+
+// In-place Gauss-Jordan inversion with partial pivoting of nbatch n x n matrices
+// (matrix b at base + b * stride). diag_shift: before inverting, M <- diag_sign*M + shift(b)*I
+// is applied by the callers' build kernels instead; here only the inversion.
+int batched_inverse_fp64(double2* base, int n, long long stride, int nbatch, int* status_dev,
+                         void* stream);
+
+// Aux Dyson pieces: M <- I - M; and after inversion M <- M - I.
+int add_identity_fp64(double2* base, int n, long long stride, int nbatch, double scale_m,
+                      double shift, void* stream);
+
+// G Dyson build: A[k][n] = (i w_n + mu) I - H[k] - Sw[k][n]   (in place over Sw)
+int build_g_dyson_fp64(double2* sw, const double2* H, const double* wn, double mu, int nk, int nw,
+                       int nao, void* stream);
+
+// Sig_inout = alpha*new + (1-alpha)*old; *maxdiff (device double) = max |change|; nonfinite flag
+int mix_fp64(const double2* s_new, double2* s_inout, double alpha, long long n, double* maxdiff_dev,
+             int* nonfinite_dev, void* stream);
+
+}  // namespace gwi

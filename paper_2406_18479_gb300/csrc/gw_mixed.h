@@ -1,0 +1,23 @@
+// Mixed-precision contractions (tcgen05 tensor cores) of the GW path.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+namespace gwi {
+
+struct MixedDims {
+  int nk3[3] = {1, 1, 1};
+  int nk = 1, nao = 0, naux = 0, ntau = 0, precision = 0, tau_chunk = 0;
+};
+
+struct MixedState;
+
+int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, size_t* bytes);
+void mixed_destroy(MixedState* s);
+// tabs: the six [nq][nk] gather tables of the context (element offsets into V and G).
+int mixed_set_coulomb(MixedState* s, const double2* V, const long long* tabs);
+int mixed_polarization(MixedState* s, const double2* G, double2* P0t, double spin_factor);
+int mixed_self_energy(MixedState* s, const double2* G, const double2* Pt, double2* Sig);
+
+}  // namespace gwi

@@ -1,0 +1,333 @@
+// FP64 kernels of the GW self-energy path (the all-FP64 precision and the FP64
+// stages of the mixed precisions).
+//
+// GB300 runs FP64 at about 2 DFMA per clock per SM, so these kernels are bound
+// by the FP64 pipe: a 32x32 output tile per 256-thread block, staged through
+// shared memory, keeps that pipe busy without deeper register blocking.
+#include <cuda_runtime.h>
+
+#include <climits>
+
+#include "gw_internal.h"
+
+namespace gwi {
+
+namespace {
+
+constexpr int TM = 32, TN = 32, TK = 16;
+constexpr long long kInvalid = LLONG_MIN;
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+__device__ __forceinline__ void cmac(double2& acc, double2 a, double2 b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+
+__device__ __forceinline__ long long view_row(const ZView& v, int r) {
+  return (long long)(r / v.rin) * v.rs_out + (long long)(r % v.rin) * v.rs_in;
+}
+
+__device__ __forceinline__ long long view_k(const ZView& v, int k) {
+  return (long long)(k / v.kin) * v.ks_out + (long long)(k % v.kin) * v.ks_in;
+}
+
+__device__ __forceinline__ long long batch_off(const ZBatch& b, int bo, int bi) {
+  return (b.tab ? b.tab[bi] : (long long)bi * b.bs_in) + (long long)bo * b.bs_out;
+}
+
+__global__ void __launch_bounds__(256) zgemm_fp64_kernel(const ZGemm g) {
+  __shared__ double2 As[TK][TM + 1];
+  __shared__ double2 Bs[TK][TN + 1];
+  __shared__ long long rowA[TM], rowB[TN], kA[TK], kB[TK];
+
+  const int b = blockIdx.z;
+  const int bo = b / g.bin, bi = b % g.bin;
+  const double2* A = g.A + batch_off(g.ba, bo, bi);
+  const double2* B = g.B + batch_off(g.bb, bo, bi);
+  double2* C = g.C + batch_off(g.bc, bo, bi);
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+
+  if (tid < TM) {
+    const int r = m0 + tid;
+    rowA[tid] = r < g.M ? view_row(g.va, r) : kInvalid;
+  } else if (tid < TM + TN) {
+    const int r = n0 + tid - TM;
+    rowB[tid - TM] = r < g.N ? view_row(g.vb, r) : kInvalid;
+  }
+  const bool a_kfast = g.va.ks_in == 1;
+  const bool b_kfast = g.vb.ks_in == 1;
+
+  double2 acc[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) acc[i][j] = make_double2(0.0, 0.0);
+
+  for (int k0 = 0; k0 < g.K; k0 += TK) {
+    __syncthreads();
+    if (tid < TK) {
+      const int k = k0 + tid;
+      kA[tid] = k < g.K ? view_k(g.va, k) : kInvalid;
+    } else if (tid < 2 * TK) {
+      const int k = k0 + tid - TK;
+      kB[tid - TK] = k < g.K ? view_k(g.vb, k) : kInvalid;
+    }
+    __syncthreads();
+    for (int e = tid; e < TM * TK; e += 256) {
+      const int mm = a_kfast ? e / TK : e % TM;
+      const int kk = a_kfast ? e % TK : e / TM;
+      const long long ro = rowA[mm], ko = kA[kk];
+      As[kk][mm] = (ro != kInvalid && ko != kInvalid) ? A[ro + ko] : make_double2(0.0, 0.0);
+    }
+    for (int e = tid; e < TN * TK; e += 256) {
+      const int nn = b_kfast ? e / TK : e % TN;
+      const int kk = b_kfast ? e % TK : e / TN;
+      const long long ro = rowB[nn], ko = kB[kk];
+      Bs[kk][nn] = (ro != kInvalid && ko != kInvalid) ? B[ro + ko] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < TK; ++kk) {
+      const double2 a0 = As[kk][2 * ty], a1 = As[kk][2 * ty + 1];
+      const double2 b0 = Bs[kk][2 * tx], b1 = Bs[kk][2 * tx + 1];
+      cmac(acc[0][0], a0, b0);
+      cmac(acc[0][1], a0, b1);
+      cmac(acc[1][0], a1, b0);
+      cmac(acc[1][1], a1, b1);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int m = m0 + 2 * ty + i;
+    if (m >= g.M) continue;
+    const long long ro = view_row(g.vc, m);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int n = n0 + 2 * tx + j;
+      if (n >= g.N) continue;
+      double2* c = C + ro + (long long)n * g.vc.ks_in;
+      double2 v = make_double2(g.alpha * acc[i][j].x, g.alpha * acc[i][j].y);
+      if (g.accumulate) {
+        const double2 old = *c;
+        v.x += old.x;
+        v.y += old.y;
+      }
+      *c = v;
+    }
+  }
+}
+
+// One block per matrix; the matrix stays in global memory (L2), the pivot
+// column and the scaled pivot row in shared memory.
+__global__ void __launch_bounds__(256) gj_inverse_kernel(double2* base, int n, long long stride,
+                                                         int* status) {
+  extern __shared__ double2 sm[];
+  double2* f = sm;
+  double2* row = sm + n;
+  int* piv = reinterpret_cast<int*>(sm + 2 * n);
+  __shared__ double red_v[8];
+  __shared__ int red_i[8];
+  __shared__ int s_p;
+  __shared__ int s_bad;
+  double2* M = base + (long long)blockIdx.x * stride;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_bad = 0;
+
+  for (int j = 0; j < n; ++j) {
+    double best = -1.0;
+    int bi = j;
+    for (int i = j + tid; i < n; i += blockDim.x) {
+      const double2 v = M[(long long)i * n + j];
+      const double a = v.x * v.x + v.y * v.y;
+      if (a > best) { best = a; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_down_sync(0xffffffffu, best, o);
+      const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      double bb = red_v[0];
+      int ii = red_i[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+        if (red_v[w] > bb || (red_v[w] == bb && red_i[w] < ii)) { bb = red_v[w]; ii = red_i[w]; }
+      s_p = ii;
+      if (!(bb > 0.0)) s_bad = 1;
+    }
+    __syncthreads();
+    if (s_bad) break;
+    const int p = s_p;
+    if (p != j) {
+      for (int c = tid; c < n; c += blockDim.x) {
+        const double2 t = M[(long long)j * n + c];
+        M[(long long)j * n + c] = M[(long long)p * n + c];
+        M[(long long)p * n + c] = t;
+      }
+    }
+    if (tid == 0) piv[j] = p;
+    __syncthreads();
+    const double2 pv = M[(long long)j * n + j];
+    const double den = pv.x * pv.x + pv.y * pv.y;
+    const double2 inv = make_double2(pv.x / den, -pv.y / den);
+    for (int c = tid; c < n; c += blockDim.x) {
+      row[c] = (c == j) ? inv : cmul(M[(long long)j * n + c], inv);
+      f[c] = M[(long long)c * n + j];
+    }
+    __syncthreads();
+    for (int c = tid; c < n; c += blockDim.x) M[(long long)j * n + c] = row[c];
+    const long long nn = (long long)n * n;
+    for (long long e = tid; e < nn; e += blockDim.x) {
+      const int i = (int)(e / n), c = (int)(e % n);
+      if (i == j) continue;
+      double2 v = (c == j) ? make_double2(0.0, 0.0) : M[e];
+      const double2 t = cmul(f[i], row[c]);
+      v.x -= t.x;
+      v.y -= t.y;
+      M[e] = v;
+    }
+    __syncthreads();
+  }
+  if (s_bad) {
+    if (tid == 0) atomicExch(status, 1);
+    return;
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    const int p = piv[j];
+    if (p != j) {
+      for (int r = tid; r < n; r += blockDim.x) {
+        const double2 t = M[(long long)r * n + j];
+        M[(long long)r * n + j] = M[(long long)r * n + p];
+        M[(long long)r * n + p] = t;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void add_identity_kernel(double2* base, int n, long long stride, int nbatch,
+                                    double scale_m, double shift) {
+  const long long nn = (long long)n * n;
+  const long long total = nn * nbatch;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long b = e / nn, r = e % nn;
+    double2* p = base + b * stride + r;
+    double2 v = *p;
+    v.x *= scale_m;
+    v.y *= scale_m;
+    if (r / n == r % n) v.x += shift;
+    *p = v;
+  }
+}
+
+__global__ void build_g_dyson_kernel(double2* sw, const double2* H, const double* wn, double mu,
+                                     int nk, int nw, int nao) {
+  const long long nn = (long long)nao * nao;
+  const long long total = nn * nw * nk;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e % nn;
+    const long long kn = e / nn;
+    const int n = (int)(kn % nw), k = (int)(kn / nw);
+    const double2 h = H[(long long)k * nn + r];
+    double2 s = sw[e];
+    double2 v = make_double2(-h.x - s.x, -h.y - s.y);
+    if (r / nao == r % nao) {
+      v.x += mu;
+      v.y += wn[n];
+    }
+    sw[e] = v;
+  }
+}
+
+__global__ void mix_kernel(const double2* s_new, double2* s_inout, double alpha, long long n,
+                           unsigned long long* maxbits, int* nonfinite) {
+  double local = 0.0;
+  int bad = 0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double2 a = s_new[e], o = s_inout[e];
+    const double2 v = make_double2(alpha * a.x + (1.0 - alpha) * o.x, alpha * a.y + (1.0 - alpha) * o.y);
+    if (!isfinite(v.x) || !isfinite(v.y)) bad = 1;
+    const double dx = v.x - o.x, dy = v.y - o.y;
+    const double d = sqrt(dx * dx + dy * dy);
+    if (d > local) local = d;
+    s_inout[e] = v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) local = fmax(local, __shfl_down_sync(0xffffffffu, local, o));
+  if ((threadIdx.x & 31) == 0 && local > 0.0)
+    atomicMax(maxbits, (unsigned long long)__double_as_longlong(local));
+  if (bad) atomicExch(nonfinite, 1);
+}
+
+inline int grid_for(long long total, int block) {
+  long long g = (total + block - 1) / block;
+  if (g > 152LL * 32) g = 152LL * 32;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+}  // namespace
+
+int zgemm_fp64(const ZGemm& g, void* stream) {
+  if (g.M <= 0 || g.N <= 0 || g.nbatch <= 0) return GW_OK;
+  if (g.nbatch > 65535) return fail(GW_EINVAL, "zgemm_fp64: batch %d too large", g.nbatch);
+  dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM, g.nbatch);
+  if (grid.y > 65535) return fail(GW_EINVAL, "zgemm_fp64: M=%d too large", g.M);
+  zgemm_fp64_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(g);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "zgemm_fp64 launch: %s", cudaGetErrorString(e));
+}
+
+int batched_inverse_fp64(double2* base, int n, long long stride, int nbatch, int* status_dev,
+                         void* stream) {
+  if (nbatch <= 0) return GW_OK;
+  const size_t smem = 2 * (size_t)n * sizeof(double2) + (size_t)n * sizeof(int);
+  if (smem > 200 * 1024) return fail(GW_EINVAL, "batched_inverse_fp64: n=%d too large", n);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(gj_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  gj_inverse_kernel<<<nbatch, 256, smem, (cudaStream_t)stream>>>(base, n, stride, status_dev);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "gj_inverse launch: %s", cudaGetErrorString(e));
+}
+
+int add_identity_fp64(double2* base, int n, long long stride, int nbatch, double scale_m,
+                      double shift, void* stream) {
+  const long long total = (long long)n * n * nbatch;
+  add_identity_kernel<<<grid_for(total, 256), 256, 0, (cudaStream_t)stream>>>(base, n, stride, nbatch,
+                                                                              scale_m, shift);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "add_identity launch: %s", cudaGetErrorString(e));
+}
+
+int build_g_dyson_fp64(double2* sw, const double2* H, const double* wn, double mu, int nk, int nw,
+                       int nao, void* stream) {
+  const long long total = (long long)nao * nao * nw * nk;
+  build_g_dyson_kernel<<<grid_for(total, 256), 256, 0, (cudaStream_t)stream>>>(sw, H, wn, mu, nk, nw,
+                                                                               nao);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "build_g_dyson launch: %s", cudaGetErrorString(e));
+}
+
+int mix_fp64(const double2* s_new, double2* s_inout, double alpha, long long n, double* maxdiff_dev,
+             int* nonfinite_dev, void* stream) {
+  mix_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(
+      s_new, s_inout, alpha, n, reinterpret_cast<unsigned long long*>(maxdiff_dev), nonfinite_dev);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "mix launch: %s", cudaGetErrorString(e));
+}
+
+}  // namespace gwi

@@ -1,0 +1,232 @@
+"""Python binding of the C ABI declared in include/gw.h (ctypes).
+
+Argument marshalling only: every step of the GW path runs in the CUDA
+library. Device arrays are torch tensors (complex128, contiguous, on the
+context's device); their data pointers are passed straight through. The
+library must have been built (``python -m paper_2406_18479_gb300.build``);
+loading raises if it is missing, and there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libgw_gb300.so")
+
+GW_OK, GW_EINVAL, GW_ENOMEM, GW_ECUDA, GW_ETIMEOUT, GW_EDEVTIMEOUT = 0, 1, 2, 3, 4, 5
+GW_ENOTFINITE, GW_ENOTCONV, GW_EAGAIN, GW_ENOTIMPL = 6, 7, 8, 9
+GW_FP64, GW_MIXED_BF16X3, GW_MIXED_FP16S = 0, 1, 2
+PRECISIONS = {"fp64": GW_FP64, "bf16x3": GW_MIXED_BF16X3, "fp16s": GW_MIXED_FP16S}
+
+# Every symbol declared in include/gw.h.
+ABI_SYMBOLS = [
+    "gw_version", "gw_last_error", "gw_sample_count", "gw_grid_build", "gw_create", "gw_destroy",
+    "gw_workspace_bytes", "gw_set_coulomb", "gw_polarization", "gw_to_matsubara", "gw_to_tau",
+    "gw_aux_dyson", "gw_screened_interaction", "gw_self_energy", "gw_sigma_eval", "gw_dyson_G",
+    "gw_mix", "gw_synchronize",
+]
+
+
+class GWError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"gw error {code}: {msg}")
+        self.code = code
+
+
+class gw_config(ctypes.Structure):
+    _fields_ = [
+        ("nk", ctypes.c_int * 3), ("nao", ctypes.c_int), ("naux", ctypes.c_int), ("ntau", ctypes.c_int),
+        ("beta", ctypes.c_double), ("mu", ctypes.c_double), ("spin_factor", ctypes.c_double),
+        ("precision", ctypes.c_int), ("tau_chunk", ctypes.c_int),
+    ]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library (loaded once). Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                           "(run python -m paper_2406_18479_gb300.build)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, ll, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_double
+    L.gw_version.restype = ctypes.c_char_p
+    L.gw_last_error.restype = ctypes.c_char_p
+    L.gw_sample_count.argtypes = [i, i]
+    L.gw_grid_build.argtypes = [i, d, i, vp, vp, vp, vp]
+    L.gw_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(gw_config), vp]
+    L.gw_destroy.argtypes = [vp]
+    L.gw_workspace_bytes.argtypes = [vp]
+    L.gw_workspace_bytes.restype = ctypes.c_size_t
+    L.gw_set_coulomb.argtypes = [vp, vp]
+    L.gw_polarization.argtypes = [vp, vp, vp]
+    L.gw_to_matsubara.argtypes = [vp, i, vp, vp, i, ll]
+    L.gw_to_tau.argtypes = [vp, i, vp, vp, i, ll]
+    L.gw_aux_dyson.argtypes = [vp, vp, vp]
+    L.gw_screened_interaction.argtypes = [vp, vp, vp]
+    L.gw_self_energy.argtypes = [vp, vp, vp, vp]
+    L.gw_sigma_eval.argtypes = [vp, vp, vp]
+    L.gw_dyson_G.argtypes = [vp, vp, vp, vp]
+    L.gw_mix.argtypes = [vp, vp, vp, d, ctypes.POINTER(d)]
+    L.gw_synchronize.argtypes = [vp]
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != GW_OK:
+        raise GWError(rc, lib().gw_last_error().decode())
+
+
+def gw_version() -> str:
+    return lib().gw_version().decode()
+
+
+def gw_sample_count(ntau: int, stat: int) -> int:
+    return lib().gw_sample_count(ntau, stat)
+
+
+def gw_grid_build(ntau: int, beta: float, stat: int):
+    """(tau [ntau], idx [nw], F [nw][ntau], B [ntau][nw]) as numpy arrays (host)."""
+    nw = gw_sample_count(ntau, stat)
+    if nw < 0:
+        raise GWError(GW_EINVAL, "bad grid size")
+    tau = np.zeros(ntau)
+    idx = np.zeros(nw, np.int64)
+    F = np.zeros((nw, ntau), np.complex128)
+    B = np.zeros((ntau, nw), np.complex128)
+    _check(lib().gw_grid_build(ntau, float(beta), stat, tau.ctypes.data, idx.ctypes.data,
+                               F.ctypes.data, B.ctypes.data))
+    return tau, idx, F, B
+
+
+def _ptr(t, shape=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dtype != torch.complex128 or not t.is_cuda:
+        raise GWError(GW_EINVAL, "expected a complex128 CUDA tensor")
+    if not t.is_contiguous():
+        raise GWError(GW_EINVAL, "expected a contiguous tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise GWError(GW_EINVAL, f"expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class gw_ctx:
+    """Owner of one gw_ctx* (gw_create ... gw_destroy)."""
+
+    def __init__(self, nk3, nao, naux, ntau, beta, mu=0.0, spin_factor=2.0, precision="fp64",
+                 tau_chunk=0, stream=None):
+        import torch
+        self.nk3 = tuple(int(x) for x in nk3)
+        self.nk = int(np.prod(self.nk3))
+        self.nao, self.naux, self.ntau = int(nao), int(naux), int(ntau)
+        self.beta, self.mu = float(beta), float(mu)
+        self.nwb = gw_sample_count(ntau, 0)
+        self.nwf = gw_sample_count(ntau, 1)
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        cfg = gw_config((ctypes.c_int * 3)(*self.nk3), self.nao, self.naux, self.ntau, self.beta,
+                        self.mu, float(spin_factor), prec, int(tau_chunk))
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check(lib().gw_create(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(self.stream.cuda_stream)))
+        self._h = h
+        self._keep = None
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise GWError(GW_EINVAL, "context destroyed")
+        return self._h
+
+    def shapes(self):
+        nk, nao, naux, ntau = self.nk, self.nao, self.naux, self.ntau
+        return {"V": (nk, nk, naux, nao, nao), "G": (nk, ntau, nao, nao), "H": (nk, nao, nao),
+                "Pt": (nk, ntau, naux, naux), "Pw": (nk, self.nwb, naux, naux),
+                "Sig": (nk, ntau, nao, nao)}
+
+    def workspace_bytes(self) -> int:
+        return int(lib().gw_workspace_bytes(self.handle))
+
+    def destroy(self):
+        if self._h is not None:
+            lib().gw_destroy(self._h)
+            self._h = None
+            self._keep = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def gw_create(nk3, nao, naux, ntau, beta, **kw) -> gw_ctx:
+    return gw_ctx(nk3, nao, naux, ntau, beta, **kw)
+
+
+def gw_destroy(ctx: gw_ctx):
+    ctx.destroy()
+
+
+def gw_set_coulomb(ctx: gw_ctx, V):
+    _check(lib().gw_set_coulomb(ctx.handle, _ptr(V, ctx.shapes()["V"])))
+    ctx._keep = V          # the library borrows V
+
+
+def gw_polarization(ctx: gw_ctx, G, P0t):
+    s = ctx.shapes()
+    _check(lib().gw_polarization(ctx.handle, _ptr(G, s["G"]), _ptr(P0t, s["Pt"])))
+
+
+def gw_to_matsubara(ctx: gw_ctx, stat: int, x, out):
+    nb, nelem = x.shape[0], int(np.prod(x.shape[2:]))
+    _check(lib().gw_to_matsubara(ctx.handle, stat, _ptr(x), _ptr(out), nb, nelem))
+
+
+def gw_to_tau(ctx: gw_ctx, stat: int, x, out):
+    nb, nelem = x.shape[0], int(np.prod(x.shape[2:]))
+    _check(lib().gw_to_tau(ctx.handle, stat, _ptr(x), _ptr(out), nb, nelem))
+
+
+def gw_aux_dyson(ctx: gw_ctx, P0w, Pw):
+    s = ctx.shapes()
+    _check(lib().gw_aux_dyson(ctx.handle, _ptr(P0w, s["Pw"]), _ptr(Pw, s["Pw"])))
+
+
+def gw_screened_interaction(ctx: gw_ctx, P0t, Pt):
+    s = ctx.shapes()
+    _check(lib().gw_screened_interaction(ctx.handle, _ptr(P0t, s["Pt"]), _ptr(Pt, s["Pt"])))
+
+
+def gw_self_energy(ctx: gw_ctx, G, Pt, Sig):
+    s = ctx.shapes()
+    _check(lib().gw_self_energy(ctx.handle, _ptr(G, s["G"]), _ptr(Pt, s["Pt"]), _ptr(Sig, s["Sig"])))
+
+
+def gw_sigma_eval(ctx: gw_ctx, G, Sig):
+    s = ctx.shapes()
+    _check(lib().gw_sigma_eval(ctx.handle, _ptr(G, s["G"]), _ptr(Sig, s["Sig"])))
+
+
+def gw_dyson_G(ctx: gw_ctx, H, Sig, G):
+    s = ctx.shapes()
+    _check(lib().gw_dyson_G(ctx.handle, _ptr(H, s["H"]), _ptr(Sig, s["Sig"]), _ptr(G, s["G"])))
+
+
+def gw_mix(ctx: gw_ctx, Sig_new, Sig_inout, alpha: float) -> float:
+    s = ctx.shapes()
+    d = ctypes.c_double(0.0)
+    _check(lib().gw_mix(ctx.handle, _ptr(Sig_new, s["Sig"]), _ptr(Sig_inout, s["Sig"]), float(alpha),
+                        ctypes.byref(d)))
+    return d.value
+
+
+def gw_synchronize(ctx: gw_ctx):
+    _check(lib().gw_synchronize(ctx.handle))
