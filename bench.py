@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Benchmark: GW self-energy evaluations per second on one GB300.
+
+One step is one self-energy evaluation -- P0(tau) (Eq. tilde_P0_tau), the
+tau -> i Omega transform, the auxiliary Dyson equation (Eq. tilde_P_omega),
+the transform back, and Sigma(tau) (Eqs. sigma_gw, tilde_W_DF2) -- over every
+k and tau of the Si-like 3x3x3 solid (nk=27, nao=26, naux=200, ntau=100,
+beta=100), with V, G and all workspaces resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|fp16s|fp64]
+    python bench.py --impl reference      # the FP64 CPU oracle on a bounded sample
+
+Under torchrun (N > 1) every rank evaluates its own seeded system (weak
+scaling, no collective on the data path); the time is the maximum over ranks.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("GW Σ evals/s & TFLOP/s vs peak, mixed vs FP64 at max|ΔΣ|≤1e-6 Ha; p50/p99")
+UNIT = "sigma_evals/s"
+WORKLOAD = "solid_3x3x3_nao26"
+FP64_PEAK_TFLOPS = 1.25      # GB300 nominal FP64 (no FP64 tensor path is faster on this part)
+
+
+def algorithmic_flops(nk, nao, naux, ntau, nwb):
+    """Real flops of one evaluation, 8 per complex multiply-add (Eqs. tilde_P0_tau ... sigma_gw)."""
+    contraction = 8.0 * nk * nk * ntau * (2.0 * naux * nao ** 3 + naux ** 2 * nao ** 2)   # each of P0, Sigma
+    transforms = 2 * 8.0 * nk * nwb * ntau * naux ** 2
+    dyson = 8.0 * nk * nwb * naux ** 3 + 2.0 * nk * nwb * naux ** 2
+    return 2 * contraction + transforms + dyson
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9 and p[1].replace(".", "").isdigit():
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+def oracle_sample(w, h, v, g, budget_s=15.0):
+    """Time the FP64 CPU oracle on whole units of each stage and extrapolate one evaluation.
+
+    Units: P0 for one (q, tau); Sigma for one (k, tau); one aux Dyson solve (q, Omega);
+    the transforms for one q. The loop repeats units until budget_s is spent.
+    """
+    from oracle import grids, gw as O
+    nk, ntau = w.nk, w.ntau
+    m, F, B = grids.transform_matrices(ntau, w.beta, 0)
+    nwb = len(m)
+    rng = np.random.default_rng(0)
+    t_p0 = t_sig = t_dys = t_tr = 0.0
+    n_p0 = n_sig = n_dys = n_tr = 0
+    start = time.perf_counter()
+    pt_fake = None
+    while True:
+        t0 = time.perf_counter()
+        q, t = int(rng.integers(nk)), int(rng.integers(ntau))
+        p0 = O.polarization(v, g, w.nk3, 2.0, q_list=[q], t_list=[t])
+        t_p0 += time.perf_counter() - t0
+        n_p0 += 1
+        if pt_fake is None:
+            pt_fake = np.broadcast_to(p0[0, 0], (nk, ntau) + p0.shape[2:]).copy()
+        t0 = time.perf_counter()
+        O.self_energy(v, g, pt_fake, w.nk3, k_list=[int(rng.integers(nk))], t_list=[t])
+        t_sig += time.perf_counter() - t0
+        n_sig += 1
+        t0 = time.perf_counter()
+        O.aux_dyson(pt_fake[:1, :1])
+        t_dys += time.perf_counter() - t0
+        n_dys += 1
+        if n_tr == 0 or time.perf_counter() - start < budget_s / 2:
+            t0 = time.perf_counter()
+            O.to_tau(O.to_matsubara(pt_fake[:1], F), B)
+            t_tr += time.perf_counter() - t0
+            n_tr += 1
+        if time.perf_counter() - start > budget_s:
+            break
+    per_eval = (t_p0 / n_p0) * nk * ntau + (t_sig / n_sig) * nk * ntau + (t_dys / n_dys) * nk * nwb \
+        + (t_tr / n_tr) * nk
+    sample = (f"{n_p0} P0 (q,tau) units, {n_sig} Sigma (k,tau) units, {n_dys} aux Dyson solves, "
+              f"{n_tr} transform pairs in {time.perf_counter() - start:.1f} s; extrapolated to "
+              f"{nk * ntau} + {nk * ntau} + {nk * nwb} + {nk} units per evaluation")
+    return 1.0 / per_eval, sample, time.perf_counter() - start
+
+
+def blas_threads():
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count()
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if its source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, rec["source"])
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return rec["dram_bytes_per_launch"] if sha == rec["source_sha256"] else None
+
+
+def run_reference(args, rank):
+    from paper_2406_18479_gb300 import inputs as I
+    if rank != 0:
+        return
+    w = I.WORKLOADS[args.workload]
+    h, v, g = I.make_inputs(w)
+    vals = []
+    sample = ""
+    for _ in range(args.warmup):
+        oracle_sample(w, h, v, g, budget_s=2.0)
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        val, sample, _ = oracle_sample(w, h, v, g, budget_s=args.ref_budget)
+        vals.append(val)
+    wall = time.perf_counter() - t_all
+    value = float(np.median(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic (seeded)",
+        "config": {"workload": w.name, "nk": w.nk, "nao": w.nao, "naux": w.naux, "ntau": w.ntau,
+                   "beta": w.beta, "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                         "sample": sample + "; numpy loops, BLAS threads as reported"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "wall_s": wall,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2406_18479_gb300 import gw, inputs as I
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    base = I.WORKLOADS[args.workload]
+    w = I.Workload(base.name, base.nk3, base.nao, base.naux, base.ntau, base.nomega, base.beta, base.mu,
+                   base.decay, base.seed + rank, base.solid)
+    h, v, g = I.make_inputs(w)
+    V = torch.from_numpy(v).cuda()
+    G = torch.from_numpy(g).cuda()
+    ctx = gw.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision=args.precision)
+    Sig = torch.empty(ctx.shapes()["Sig"], dtype=torch.complex128, device="cuda")
+    gw.gw_set_coulomb(ctx, V)
+    stream = ctx.stream
+    for _ in range(args.warmup):
+        gw.gw_sigma_eval(ctx, G, Sig)
+    gw.gw_synchronize(ctx)
+
+    # ---- device-resident timed region
+    gw.gw_profile_enable(ctx, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            gw.gw_sigma_eval(ctx, G, Sig)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = gw.gw_launch_count(ctx)
+    prof = gw.gw_profile_read(ctx)
+    gw.gw_profile_enable(ctx, False)
+    gw.gw_synchronize(ctx)
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+
+    # ---- end to end through the public API with host buffers (pinned)
+    G_host = torch.from_numpy(g).pin_memory()
+    S_host = torch.empty(Sig.shape, dtype=Sig.dtype).pin_memory()
+    k_e2e = max(1, args.steps)
+    barrier()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        f0.record(stream)
+        for _ in range(k_e2e):
+            G.copy_(G_host, non_blocking=True)
+            gw.gw_sigma_eval(ctx, G, Sig)
+            S_host.copy_(Sig, non_blocking=True)
+        f1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = f0.elapsed_time(f1)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # ---- optional FP64 comparison (one evaluation) for the mixed precisions
+    fp64 = None
+    if args.precision != "fp64" and args.fp64_compare:
+        c64 = gw.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision="fp64")
+        S64 = torch.empty_like(Sig)
+        gw.gw_set_coulomb(c64, V)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(c64.stream)
+        gw.gw_sigma_eval(c64, G, S64)
+        a1.record(c64.stream)
+        torch.cuda.synchronize()
+        ms64 = a0.elapsed_time(a1)
+        gw.gw_sigma_eval(ctx, G, Sig)
+        torch.cuda.synchronize()
+        dsig = float((Sig - S64).abs().max().item())
+        fp64 = {"ms_per_eval": ms64, "speedup_mixed_over_fp64": ms64 / (t_max / args.steps),
+                "max_abs_dSigma_Ha": dsig, "max_abs_Sigma_Ha": float(S64.abs().max().item())}
+        c64.destroy()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    nwb = gw.gw_sample_count(w.ntau, 0)
+    flops = algorithmic_flops(w.nk, w.nao, w.naux, w.ntau, nwb)
+    steps = args.steps
+    value = world * steps / (t_max / 1e3)
+    peaks, peak_src = measured_peaks()
+    # dominant kernel by device time
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    dname, d = dom
+    per_launch_ms = d["ms"] / d["launches"]
+    if dname.endswith("_tc"):
+        bound, unit = "tensor", "TFLOP/s"
+        achieved = d["flops"] / d["launches"] / (per_launch_ms * 1e-3) / 1e12
+        peak = peaks["bf16_tflops_sustained"]
+        peak_note = f"bf16 dense sustained ({peak_src})"
+    elif dname in ("limb_convert", "elementwise", "reduce"):
+        bound, unit = "hbm", "GB/s"
+        achieved = d["bytes"] / d["launches"] / (per_launch_ms * 1e-3) / 1e9
+        peak = peaks["hbm_gbs"]
+        peak_note = f"HBM copy ({peak_src})"
+    else:
+        bound, unit = "alu", "TFLOP/s"
+        achieved = d["flops"] / d["launches"] / (per_launch_ms * 1e-3) / 1e12
+        peak = FP64_PEAK_TFLOPS
+        peak_note = "FP64 pipe, GB300 nominal 1.25 TFLOP/s (cuBLAS ZGEMM measured 1.10)"
+    traffic = ncu_traffic(dname)
+    clocks = clk.summary()
+    kernels = {k: {"launches": x["launches"], "ms": round(x["ms"], 3),
+                   "share": round(x["ms"] / sum(y["ms"] for y in prof.values()), 4)} for k, x in prof.items()}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": t_max / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "c128 (f64)", "bf16x3": "bf16x3 limbs, f32 accumulate, f64 transforms/Dyson",
+                  "fp16s": "fp16 scaled, f32 accumulate, f64 transforms/Dyson"}[args.precision],
+        "data": "synthetic (seeded H(k), V, G0 shaped like the paper's Si example)",
+        "config": {"workload": w.name, "nk": w.nk, "nao": w.nao, "naux": w.naux, "ntau": w.ntau,
+                   "nomega": nwb, "beta": w.beta, "precision": args.precision,
+                   "l2": "inputs larger than L2 (V 1.58 GB, P 1.73 GB per pass)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "tflops_algorithmic": flops * world * steps / (t_max / 1e3) / 1e12,
+        "roofline": {"kernel": dname, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_note},
+        "kernels": kernels,
+        "gpu_launches": launches,
+        "e2e": {"value": world * k_e2e / (e2e_ms / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": int(G.numel() * 16), "d2h_bytes_per_step": int(Sig.numel() * 16)},
+        "clocks": clocks,
+    }
+    if fp64 is not None:
+        line["fp64"] = fp64
+    if world == 1 and not args.no_cpu_baseline:
+        val, sample, spent = oracle_sample(w, h, v, g, budget_s=args.ref_budget)
+        line["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
+                                "sample": sample}
+    print(json.dumps(line), flush=True)
+    ctx.destroy()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=None)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["bf16x3", "fp16s", "fp64"], default=None)
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--fp64-compare", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.precision is None:
+        args.precision = "fp64"
+    if args.steps is None:
+        args.steps = 2 if args.precision == "fp64" else 10
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -182,6 +182,20 @@ int gw_dyson_G(gw_ctx* ctx, const gw_c128* H_dev, const gw_c128* Sig_dev, gw_c12
 int gw_mix(gw_ctx* ctx, const gw_c128* Sig_new_dev, gw_c128* Sig_inout_dev, double alpha,
            double* max_abs_diff_host);
 
+/*
+ * Kernel accounting. Every kernel launch of a context is counted. With
+ * profiling on, CUDA events on the context's stream also bracket each launch,
+ * and each kernel class ("slot") accumulates its device time and its
+ * algorithmic flops and bytes. gw_profile_enable resets all counters.
+ * gw_profile_read synchronizes the recorded events; name receives the slot's
+ * kernel name (at most name_cap bytes with the terminator).
+ */
+int gw_profile_enable(gw_ctx* ctx, int on);
+long long gw_launch_count(const gw_ctx* ctx);
+int gw_profile_slots(void);
+int gw_profile_read(gw_ctx* ctx, int slot, char* name, int name_cap, long long* launches,
+                    double* total_ms, double* flops, double* bytes);
+
 /* Waits for all work queued on the context's stream. */
 int gw_synchronize(gw_ctx* ctx);
 

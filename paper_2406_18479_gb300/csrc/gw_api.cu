@@ -25,6 +25,91 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+struct Prof {
+  bool on = false;
+  long long launches = 0;
+  long long slot_launches[SLOT_COUNT] = {};
+  double slot_flops[SLOT_COUNT] = {}, slot_bytes[SLOT_COUNT] = {}, slot_ms[SLOT_COUNT] = {};
+  cudaEvent_t open[SLOT_COUNT] = {};
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[SLOT_COUNT];
+  std::vector<cudaEvent_t> pool;
+
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void drain() {
+    for (int s = 0; s < SLOT_COUNT; ++s) {
+      for (auto& pr : pending[s]) {
+        float ms = 0.f;
+        cudaEventSynchronize(pr.second);
+        cudaEventElapsedTime(&ms, pr.first, pr.second);
+        slot_ms[s] += ms;
+        pool.push_back(pr.first);
+        pool.push_back(pr.second);
+      }
+      pending[s].clear();
+    }
+  }
+  void reset() {
+    drain();
+    for (int s = 0; s < SLOT_COUNT; ++s) {
+      slot_launches[s] = 0;
+      slot_flops[s] = slot_bytes[s] = slot_ms[s] = 0.0;
+    }
+    launches = 0;
+  }
+  ~Prof() {
+    drain();
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
+static thread_local Prof* t_prof = nullptr;
+
+const char* prof_slot_name(int slot) {
+  static const char* names[SLOT_COUNT] = {
+      "vg_fp64", "p0_gemm_fp64", "r_gemm_fp64", "sigma_gemm_fp64", "transform_fp64", "inverse_fp64",
+      "elementwise", "limb_convert", "vg_mixed", "p0_gemm_tc", "r_gemm_tc", "sigma_mixed", "reduce"};
+  return (slot >= 0 && slot < SLOT_COUNT) ? names[slot] : "";
+}
+
+void prof_begin(int slot, cudaStream_t s) {
+  Prof* p = t_prof;
+  if (!p) return;
+  p->launches++;
+  p->slot_launches[slot]++;
+  if (p->on) {
+    p->open[slot] = p->get();
+    cudaEventRecord(p->open[slot], s);
+  }
+}
+
+void prof_end(int slot, cudaStream_t s, double flops, double bytes) {
+  Prof* p = t_prof;
+  if (!p) return;
+  p->slot_flops[slot] += flops;
+  p->slot_bytes[slot] += bytes;
+  if (p->on && p->open[slot]) {
+    cudaEvent_t e = p->get();
+    cudaEventRecord(e, s);
+    p->pending[slot].push_back({p->open[slot], e});
+    p->open[slot] = nullptr;
+  }
+}
+
+struct ProfScope {
+  Prof* saved;
+  explicit ProfScope(Prof* p) : saved(t_prof) { t_prof = p; }
+  ~ProfScope() { t_prof = saved; }
+};
+
 }  // namespace gwi
 
 using namespace gwi;
@@ -48,6 +133,7 @@ struct gw_ctx {
   const double2* V = nullptr;
   size_t bytes = 0;
   MixedState* mixed = nullptr;
+  Prof prof;
 };
 
 namespace {
@@ -130,6 +216,7 @@ int polarization_fp64(gw_ctx* c, const double2* G, double2* P0t) {
         g.B = G + (long long)t0 * nao2; g.vb.rs_in = 1; g.vb.ks_in = nao;
         g.bb.tab = c->tab_gkpq + (long long)q * nk; g.bb.bs_out = nao2;
         g.C = Abuf; g.vc.rs_in = nao; g.vc.ks_in = 1; g.bc.bs_in = pair; g.bc.bs_out = (long long)nk * pair;
+        g.slot = SLOT_VG_FP64;
         GW_TRY(zgemm_fp64(g, c->stream));
       }
       {  // B^{Q'}_{bd}(k,t) = sum_c V^{k+q,k}_bc(Q') G^k_cd(beta - t), stored as [Q'][d][b]
@@ -140,6 +227,7 @@ int polarization_fp64(gw_ctx* c, const double2* G, double2* P0t) {
         g.bb.bs_in = (long long)ntau * nao2; g.bb.bs_out = -nao2;
         g.C = Bbuf; g.vc.rin = nao; g.vc.rs_in = 1; g.vc.rs_out = nao2; g.vc.ks_in = nao;
         g.bc.bs_in = pair; g.bc.bs_out = (long long)nk * pair;
+        g.slot = SLOT_VG_FP64;
         GW_TRY(zgemm_fp64(g, c->stream));
       }
       {  // P0^q_QQ'(t) = -(s/N_k) sum_{k,d,b} A^Q_{db} B^{Q'}_{bd}
@@ -151,6 +239,7 @@ int polarization_fp64(gw_ctx* c, const double2* G, double2* P0t) {
         g.C = P0t + ((long long)q * ntau + t0) * c->naux2; g.vc.rs_in = naux; g.vc.ks_in = 1;
         g.bc.bs_in = c->naux2;
         g.alpha = -c->cfg.spin_factor / nk;
+        g.slot = SLOT_P0_FP64;
         GW_TRY(zgemm_fp64(g, c->stream));
       }
     }
@@ -175,6 +264,7 @@ int self_energy_fp64(gw_ctx* c, const double2* G, const double2* Pt, double2* Si
         g.ba.bs_out = c->naux2;
         g.B = c->V; g.vb.rs_in = 1; g.vb.ks_in = nao2; g.bb.tab = c->tab_kmqk + (long long)q * nk;
         g.C = Rbuf; g.vc.rs_in = nao2; g.vc.ks_in = 1; g.bc.bs_in = pair; g.bc.bs_out = (long long)nk * pair;
+        g.slot = SLOT_R_FP64;
         GW_TRY(zgemm_fp64(g, c->stream));
       }
       {  // Z^Q_{ib}(k,t) = sum_a V^{k,k-q}_ia(Q) G^{k-q}_ab(t)
@@ -184,6 +274,7 @@ int self_energy_fp64(gw_ctx* c, const double2* G, const double2* Pt, double2* Si
         g.B = G + (long long)t0 * nao2; g.vb.rs_in = 1; g.vb.ks_in = nao;
         g.bb.tab = c->tab_gkmq + (long long)q * nk; g.bb.bs_out = nao2;
         g.C = Zbuf; g.vc.rs_in = nao; g.vc.ks_in = 1; g.bc.bs_in = pair; g.bc.bs_out = (long long)nk * pair;
+        g.slot = SLOT_VG_FP64;
         GW_TRY(zgemm_fp64(g, c->stream));
       }
       {  // Sigma^k_ij(t) += -(1/N_k) sum_{Q,b} Z^Q_{ib} R^Q_{bj}
@@ -197,6 +288,7 @@ int self_energy_fp64(gw_ctx* c, const double2* G, const double2* Pt, double2* Si
         g.bc.bs_in = (long long)ntau * nao2; g.bc.bs_out = nao2;
         g.alpha = -1.0 / nk;
         g.accumulate = 1;
+        g.slot = SLOT_SIGMA_FP64;
         GW_TRY(zgemm_fp64(g, c->stream));
       }
     }
@@ -217,6 +309,7 @@ int transform(gw_ctx* c, int stat, bool forward, const double2* in, double2* out
     g.A = Mtx; g.va.rs_in = nin; g.va.ks_in = 1;
     g.B = in + (long long)b0 * nin * nelem; g.vb.rs_in = 1; g.vb.ks_in = nelem; g.bb.bs_in = nin * nelem;
     g.C = out + (long long)b0 * nout * nelem; g.vc.rs_in = nelem; g.vc.ks_in = 1; g.bc.bs_in = nout * nelem;
+    g.slot = SLOT_TRANSFORM_FP64;
     GW_TRY(zgemm_fp64(g, c->stream));
   }
   return GW_OK;
@@ -325,7 +418,7 @@ int gw_create(gw_ctx** out, const gw_config* cfg, void* cuda_stream) {
       d.nk3[0] = cfg->nk[0]; d.nk3[1] = cfg->nk[1]; d.nk3[2] = cfg->nk[2];
       d.nk = nk; d.nao = c->nao; d.naux = c->naux; d.ntau = c->ntau; d.precision = cfg->precision;
       d.tau_chunk = cfg->tau_chunk;
-      if ((rc = mixed_create(&c->mixed, d, c->stream, &c->bytes)) != GW_OK) break;
+      if ((rc = mixed_create(&c->mixed, d, c->stream, c->status, &c->bytes)) != GW_OK) break;
     }
     rc = cuda_check("gw_create");
   } while (false);
@@ -347,13 +440,15 @@ int gw_destroy(gw_ctx* ctx) {
 size_t gw_workspace_bytes(const gw_ctx* ctx) { return ctx ? ctx->bytes : 0; }
 
 int gw_set_coulomb(gw_ctx* ctx, const gw_c128* V_dev) {
+  ProfScope _ps(ctx ? &ctx->prof : nullptr);
   if (!ctx || !V_dev) return fail(GW_EINVAL, "gw_set_coulomb: null argument");
   ctx->V = reinterpret_cast<const double2*>(V_dev);
-  if (ctx->mixed) return mixed_set_coulomb(ctx->mixed, ctx->V, ctx->tabs);
+  if (ctx->mixed) return mixed_set_coulomb(ctx->mixed, ctx->V);
   return GW_OK;
 }
 
 int gw_polarization(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* P0t_dev) {
+  ProfScope _ps(ctx ? &ctx->prof : nullptr);
   if (!ctx || !G_dev || !P0t_dev) return fail(GW_EINVAL, "gw_polarization: null argument");
   if (!ctx->V) return fail(GW_EINVAL, "gw_polarization: call gw_set_coulomb first");
   const double2* G = reinterpret_cast<const double2*>(G_dev);
@@ -366,11 +461,13 @@ int gw_to_matsubara(gw_ctx* ctx, int stat, const gw_c128* in_dev, gw_c128* out_d
                     long long nelem) {
   if (!ctx || !in_dev || !out_dev || (stat != 0 && stat != 1) || nbatch < 0 || nelem < 0)
     return fail(GW_EINVAL, "gw_to_matsubara: bad argument");
+  ProfScope _ps(ctx ? &ctx->prof : nullptr);
   return transform(ctx, stat, true, reinterpret_cast<const double2*>(in_dev),
                    reinterpret_cast<double2*>(out_dev), nbatch, nelem);
 }
 
 int gw_to_tau(gw_ctx* ctx, int stat, const gw_c128* in_dev, gw_c128* out_dev, int nbatch, long long nelem) {
+  ProfScope _ps(ctx ? &ctx->prof : nullptr);
   if (!ctx || !in_dev || !out_dev || (stat != 0 && stat != 1) || nbatch < 0 || nelem < 0)
     return fail(GW_EINVAL, "gw_to_tau: bad argument");
   return transform(ctx, stat, false, reinterpret_cast<const double2*>(in_dev),
@@ -378,16 +475,19 @@ int gw_to_tau(gw_ctx* ctx, int stat, const gw_c128* in_dev, gw_c128* out_dev, in
 }
 
 int gw_aux_dyson(gw_ctx* ctx, const gw_c128* P0w_dev, gw_c128* Pw_dev) {
+  ProfScope _ps(ctx ? &ctx->prof : nullptr);
   if (!ctx || !P0w_dev || !Pw_dev) return fail(GW_EINVAL, "gw_aux_dyson: null argument");
   return aux_dyson(ctx, reinterpret_cast<const double2*>(P0w_dev), reinterpret_cast<double2*>(Pw_dev));
 }
 
 int gw_screened_interaction(gw_ctx* ctx, const gw_c128* P0t_dev, gw_c128* Pt_dev) {
+  ProfScope _ps(ctx ? &ctx->prof : nullptr);
   if (!ctx || !P0t_dev || !Pt_dev) return fail(GW_EINVAL, "gw_screened_interaction: null argument");
   return screened(ctx, reinterpret_cast<const double2*>(P0t_dev), reinterpret_cast<double2*>(Pt_dev));
 }
 
 int gw_self_energy(gw_ctx* ctx, const gw_c128* G_dev, const gw_c128* Pt_dev, gw_c128* Sig_dev) {
+  ProfScope _ps(ctx ? &ctx->prof : nullptr);
   if (!ctx || !G_dev || !Pt_dev || !Sig_dev) return fail(GW_EINVAL, "gw_self_energy: null argument");
   if (!ctx->V) return fail(GW_EINVAL, "gw_self_energy: call gw_set_coulomb first");
   const double2* G = reinterpret_cast<const double2*>(G_dev);
@@ -398,6 +498,7 @@ int gw_self_energy(gw_ctx* ctx, const gw_c128* G_dev, const gw_c128* Pt_dev, gw_
 }
 
 int gw_sigma_eval(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* Sig_dev) {
+  ProfScope _ps(ctx ? &ctx->prof : nullptr);
   if (!ctx || !G_dev || !Sig_dev) return fail(GW_EINVAL, "gw_sigma_eval: null argument");
   GW_TRY(gw_polarization(ctx, G_dev, reinterpret_cast<gw_c128*>(ctx->P0t)));
   GW_TRY(screened(ctx, ctx->P0t, ctx->Pt));
@@ -405,6 +506,7 @@ int gw_sigma_eval(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* Sig_dev) {
 }
 
 int gw_dyson_G(gw_ctx* ctx, const gw_c128* H_dev, const gw_c128* Sig_dev, gw_c128* G_dev) {
+  ProfScope _ps(ctx ? &ctx->prof : nullptr);
   if (!ctx || !H_dev || !Sig_dev || !G_dev) return fail(GW_EINVAL, "gw_dyson_G: null argument");
   const double2* H = reinterpret_cast<const double2*>(H_dev);
   const double2* S = reinterpret_cast<const double2*>(Sig_dev);
@@ -418,6 +520,7 @@ int gw_dyson_G(gw_ctx* ctx, const gw_c128* H_dev, const gw_c128* Sig_dev, gw_c12
 
 int gw_mix(gw_ctx* ctx, const gw_c128* Sig_new_dev, gw_c128* Sig_inout_dev, double alpha,
            double* max_abs_diff_host) {
+  ProfScope _ps(ctx ? &ctx->prof : nullptr);
   if (!ctx || !Sig_new_dev || !Sig_inout_dev) return fail(GW_EINVAL, "gw_mix: null argument");
   const long long n = (long long)ctx->nk * ctx->ntau * ctx->nao2;
   cudaMemsetAsync(ctx->maxdiff, 0, sizeof(double), ctx->stream);
@@ -431,6 +534,32 @@ int gw_mix(gw_ctx* ctx, const gw_c128* Sig_new_dev, gw_c128* Sig_inout_dev, doub
   if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check("gw_mix sync");
   if (max_abs_diff_host) *max_abs_diff_host = md;
   if (bad) return fail(GW_ENOTFINITE, "gw_mix: non-finite self-energy");
+  return GW_OK;
+}
+
+int gw_profile_enable(gw_ctx* ctx, int on) {
+  if (!ctx) return fail(GW_EINVAL, "gw_profile_enable: null context");
+  ctx->prof.reset();
+  ctx->prof.on = on != 0;
+  return GW_OK;
+}
+
+long long gw_launch_count(const gw_ctx* ctx) { return ctx ? ctx->prof.launches : -1; }
+
+int gw_profile_slots(void) { return SLOT_COUNT; }
+
+int gw_profile_read(gw_ctx* ctx, int slot, char* name, int name_cap, long long* launches, double* total_ms,
+                    double* flops, double* bytes) {
+  if (!ctx || slot < 0 || slot >= SLOT_COUNT) return fail(GW_EINVAL, "gw_profile_read: bad argument");
+  ctx->prof.drain();
+  if (name && name_cap > 0) {
+    std::strncpy(name, prof_slot_name(slot), (size_t)name_cap - 1);
+    name[name_cap - 1] = 0;
+  }
+  if (launches) *launches = ctx->prof.slot_launches[slot];
+  if (total_ms) *total_ms = ctx->prof.slot_ms[slot];
+  if (flops) *flops = ctx->prof.slot_flops[slot];
+  if (bytes) *bytes = ctx->prof.slot_bytes[slot];
   return GW_OK;
 }
 

@@ -4,6 +4,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
 #include <vector_types.h>
 
 #include "gw.h"
@@ -15,6 +16,21 @@ int sample_count(int ntau, int stat);
 std::vector<int64_t> matsubara_indices(int n, int stat);
 int grid_build(int ntau, double beta, int stat, double* tau, int64_t* idx, gw_c128* F, gw_c128* B);
 int fail(int code, const char* fmt, ...);
+
+// ---- kernel timing and launch counting (gw_api.cu)
+//
+// Every kernel launch goes through prof_begin/prof_end with a slot naming the
+// kernel. The launch counter always runs; when the context's profiling is on,
+// CUDA events on the launching stream bracket each launch and the slot
+// accumulates its algorithmic flops and bytes.
+enum ProfSlot {
+  SLOT_VG_FP64 = 0, SLOT_P0_FP64, SLOT_R_FP64, SLOT_SIGMA_FP64, SLOT_TRANSFORM_FP64, SLOT_INVERSE_FP64,
+  SLOT_ELEMENTWISE, SLOT_LIMBS, SLOT_VG_MIXED, SLOT_P0_TC, SLOT_R_TC, SLOT_SIGMA_MIXED, SLOT_REDUCE,
+  SLOT_COUNT
+};
+const char* prof_slot_name(int slot);
+void prof_begin(int slot, cudaStream_t s);
+void prof_end(int slot, cudaStream_t s, double flops, double bytes);
 
 // ---- batched complex FP64 GEMM (k_fp64.cu)
 //
@@ -44,6 +60,7 @@ struct ZGemm {
   ZBatch ba, bb, bc;
   double alpha = 1.0;            // C = alpha * sum_k A(m,k) B(n,k) (+ C if accumulate)
   int accumulate = 0;
+  int slot = SLOT_VG_FP64;       // profiling slot of this launch
 };
 
 int zgemm_fp64(const ZGemm& g, void* stream);

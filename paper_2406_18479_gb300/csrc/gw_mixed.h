@@ -13,10 +13,10 @@ struct MixedDims {
 
 struct MixedState;
 
-int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, size_t* bytes);
+// status: the context's device status words (status[1] receives device-side wait failures).
+int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int* status, size_t* bytes);
 void mixed_destroy(MixedState* s);
-// tabs: the six [nq][nk] gather tables of the context (element offsets into V and G).
-int mixed_set_coulomb(MixedState* s, const double2* V, const long long* tabs);
+int mixed_set_coulomb(MixedState* s, const double2* V);
 int mixed_polarization(MixedState* s, const double2* G, double2* P0t, double spin_factor);
 int mixed_self_energy(MixedState* s, const double2* G, const double2* Pt, double2* Sig);
 

@@ -284,7 +284,10 @@ int zgemm_fp64(const ZGemm& g, void* stream) {
   if (g.nbatch > 65535) return fail(GW_EINVAL, "zgemm_fp64: batch %d too large", g.nbatch);
   dim3 grid((g.N + TN - 1) / TN, (g.M + TM - 1) / TM, g.nbatch);
   if (grid.y > 65535) return fail(GW_EINVAL, "zgemm_fp64: M=%d too large", g.M);
+  prof_begin(g.slot, (cudaStream_t)stream);
   zgemm_fp64_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(g);
+  prof_end(g.slot, (cudaStream_t)stream, 8.0 * g.M * (double)g.N * g.K * g.nbatch,
+           16.0 * ((double)g.M * g.K + (double)g.N * g.K + (double)g.M * g.N) * g.nbatch);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "zgemm_fp64 launch: %s", cudaGetErrorString(e));
 }
@@ -299,7 +302,10 @@ int batched_inverse_fp64(double2* base, int n, long long stride, int nbatch, int
     cudaFuncSetAttribute(gj_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     attr_set = true;
   }
+  prof_begin(SLOT_INVERSE_FP64, (cudaStream_t)stream);
   gj_inverse_kernel<<<nbatch, 256, smem, (cudaStream_t)stream>>>(base, n, stride, status_dev);
+  prof_end(SLOT_INVERSE_FP64, (cudaStream_t)stream, 8.0 * (double)n * n * n * nbatch,
+           32.0 * (double)n * n * nbatch);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "gj_inverse launch: %s", cudaGetErrorString(e));
 }
@@ -307,8 +313,10 @@ int batched_inverse_fp64(double2* base, int n, long long stride, int nbatch, int
 int add_identity_fp64(double2* base, int n, long long stride, int nbatch, double scale_m,
                       double shift, void* stream) {
   const long long total = (long long)n * n * nbatch;
+  prof_begin(SLOT_ELEMENTWISE, (cudaStream_t)stream);
   add_identity_kernel<<<grid_for(total, 256), 256, 0, (cudaStream_t)stream>>>(base, n, stride, nbatch,
                                                                               scale_m, shift);
+  prof_end(SLOT_ELEMENTWISE, (cudaStream_t)stream, 2.0 * total, 32.0 * total);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "add_identity launch: %s", cudaGetErrorString(e));
 }
@@ -316,16 +324,20 @@ int add_identity_fp64(double2* base, int n, long long stride, int nbatch, double
 int build_g_dyson_fp64(double2* sw, const double2* H, const double* wn, double mu, int nk, int nw,
                        int nao, void* stream) {
   const long long total = (long long)nao * nao * nw * nk;
+  prof_begin(SLOT_ELEMENTWISE, (cudaStream_t)stream);
   build_g_dyson_kernel<<<grid_for(total, 256), 256, 0, (cudaStream_t)stream>>>(sw, H, wn, mu, nk, nw,
                                                                                nao);
+  prof_end(SLOT_ELEMENTWISE, (cudaStream_t)stream, 4.0 * total, 32.0 * total);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "build_g_dyson launch: %s", cudaGetErrorString(e));
 }
 
 int mix_fp64(const double2* s_new, double2* s_inout, double alpha, long long n, double* maxdiff_dev,
              int* nonfinite_dev, void* stream) {
+  prof_begin(SLOT_ELEMENTWISE, (cudaStream_t)stream);
   mix_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(
       s_new, s_inout, alpha, n, reinterpret_cast<unsigned long long*>(maxdiff_dev), nonfinite_dev);
+  prof_end(SLOT_ELEMENTWISE, (cudaStream_t)stream, 8.0 * n, 48.0 * n);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "mix launch: %s", cudaGetErrorString(e));
 }

@@ -1,21 +1,874 @@
-// Mixed-precision contractions: not built yet in this file revision.
+// Mixed-precision contractions of the GW path on tcgen05 tensor cores.
+//
+// Every V.G.V contraction (Eqs. tilde_P0_tau and sigma_gw) is a complex GEMM
+// C = sum_k A(m,k) B(n,k). Each operand is split, per row and per chunk of at
+// most 512 k-values, into four bf16 slices that share one power-of-two
+// alignment 2^E (E from the chunk's largest |re|, |im|):
+//     x = 2^E (s0 + s1 + s2 + s3) + O(2^(E-32)),   s_i = integer_i * 2^-(8i+7), |integer_i| <= 128.
+// Products of leading slices are integers times one common quantum, so their
+// sum over a chunk (at most 2*512 terms of at most 2^14) is exact in the FP32
+// accumulator. Products of lower order (i + j = 1..3) go to a second FP32
+// accumulator whose rounding is 2^-8 smaller in scale; products with i+j > 3
+// are dropped (2^-32 relative). After each chunk the four accumulators
+// (main/correction x re/im) are added in FP64 into the output. Complex
+// products use four real MMAs per slice pair (the A-imaginary one negated by
+// the instruction descriptor).
+//
+// Kernels
+//   slice_kernel   FP64 complex view -> 8 bf16 planes [slice*2 + re/im][row][Kpad]
+//   oz_gemm_kernel persistent tcgen05 GEMM over plane tiles loaded by TMA
+//                  (SWIZZLE_32B K-major, one 16-wide k-step per pipeline stage)
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "gw_internal.h"
 #include "gw_mixed.h"
 
 namespace gwi {
 
-struct MixedState {
-  MixedDims d;
+namespace {
+
+#ifndef GW_TRY_INTERNAL
+#define GW_TRY_INTERNAL(x)        \
+  do {                            \
+    const int _rc = (x);          \
+    if (_rc != GW_OK) return _rc; \
+  } while (0)
+#endif
+
+constexpr int kPlanes = 8;     // 4 slices x (re, im)
+constexpr int kBM = 128;       // rows of an MMA tile (TMEM lanes)
+constexpr int kStepK = 16;     // k per MMA (kind::f16)
+constexpr int kMaxChunk = 512; // k per exact-accumulation chunk
+
+// ------------------------------------------------------------------------------------------------
+// slicer
+
+struct SliceJob {
+  const double2* src = nullptr;
+  ZView v;                 // row and k view of one batch entry
+  ZBatch b;                // per-batch source offset
+  int bin = 1 << 30;
+  int rows = 0, K = 0, Kc = 0, Kpad = 0, nbatch = 1;
+  __nv_bfloat16* dst = nullptr;
+  long long plane_stride = 0;   // elements between planes (= total rows * Kpad)
+  long long dst_row0 = 0;       // first destination row of batch 0
+  long long dst_rows_per_batch = 0;
 };
 
-int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t, size_t*) {
-  *out = nullptr;
-  (void)d;
-  return fail(GW_ENOTIMPL, "mixed precision is not available in this build");
+__device__ __forceinline__ long long s_view_row(const ZView& v, int r) {
+  return (long long)(r / v.rin) * v.rs_out + (long long)(r % v.rin) * v.rs_in;
 }
-void mixed_destroy(MixedState* s) { delete s; }
-int mixed_set_coulomb(MixedState*, const double2*, const long long*) { return fail(GW_ENOTIMPL, "mixed"); }
-int mixed_polarization(MixedState*, const double2*, double2*, double) { return fail(GW_ENOTIMPL, "mixed"); }
-int mixed_self_energy(MixedState*, const double2*, const double2*, double2*) { return fail(GW_ENOTIMPL, "mixed"); }
+__device__ __forceinline__ long long s_view_k(const ZView& v, int k) {
+  return (long long)(k / v.kin) * v.ks_out + (long long)(k % v.kin) * v.ks_in;
+}
+
+// One warp per (batch, row, chunk).
+__global__ void __launch_bounds__(256) slice_kernel(const SliceJob j) {
+  const long long warp_global = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int nchunk = j.Kpad / j.Kc;
+  const long long total = (long long)j.nbatch * j.rows * nchunk;
+  if (warp_global >= total) return;
+  const int c = (int)(warp_global % nchunk);
+  const long long br = warp_global / nchunk;
+  const int r = (int)(br % j.rows);
+  const int b = (int)(br / j.rows);
+  const int bo = b / j.bin, bi = b % j.bin;
+  const double2* src = j.src + (j.b.tab ? j.b.tab[bi] : (long long)bi * j.b.bs_in) + (long long)bo * j.b.bs_out +
+                       s_view_row(j.v, r);
+  constexpr int kPer = kMaxChunk / 32;
+  double2 x[kPer];
+  double m = 0.0;
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int e = lane + 32 * u;
+    const int k = c * j.Kc + e;
+    double2 val = make_double2(0.0, 0.0);
+    if (e < j.Kc && k < j.K) val = src[s_view_k(j.v, k)];
+    x[u] = val;
+    m = fmax(m, fmax(fabs(val.x), fabs(val.y)));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  int E = 0;
+  if (m > 0.0) frexp(m, &E);             // m = f 2^E, f in [0.5, 1): |x| / 2^E < 1
+  const long long row = j.dst_row0 + (long long)b * j.dst_rows_per_batch + r;
+  __nv_bfloat16* out = j.dst + row * j.Kpad + (long long)c * j.Kc;
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int e = lane + 32 * u;
+    if (e >= j.Kc) break;
+    double tr = (m > 0.0) ? ldexp(x[u].x, -E) : 0.0;
+    double ti = (m > 0.0) ? ldexp(x[u].y, -E) : 0.0;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int sh = 8 * s + 7;
+      const double qr = rint(ldexp(tr, sh)), qi = rint(ldexp(ti, sh));
+      tr -= ldexp(qr, -sh);
+      ti -= ldexp(qi, -sh);
+      // integer * 2^(E - sh) is exact in float and in bf16 (|integer| <= 128)
+      out[(long long)(2 * s) * j.plane_stride + e] = __float2bfloat16_rn((float)ldexp(qr, E - sh));
+      out[(long long)(2 * s + 1) * j.plane_stride + e] = __float2bfloat16_rn((float)ldexp(qi, E - sh));
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// tcgen05 GEMM
+
+struct OzParams {
+  int M = 0, N = 0, nsteps = 0, steps_per_chunk = 0;
+  int mtiles = 0, ntiles = 0, nbatch = 1, bin = 1 << 30;
+  long long a_row0 = 0, b_row0 = 0;   // constant first plane row of A and B
+  const long long* a_tab = nullptr;   // A row base per inner batch index
+  long long a_bs_in = 0, a_bs_out = 0;
+  const long long* b_tab = nullptr;
+  long long b_bs_in = 0, b_bs_out = 0;
+  double2* C = nullptr;
+  ZView vc;                           // rows via rin/rs_*, columns via kin/ks_*
+  ZBatch bc;
+  double alpha = 1.0;
+  int accumulate = 0;
+  int* status = nullptr;              // status[1] <- error code of a device-side wait that gave up
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.b32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t globaltimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+constexpr uint64_t kWaitLimitNs = 4000000000ull;   // 4 s: far beyond any legitimate wait
+
+// Bounded wait. Returns false when the CTA is aborting or the limit passed (and then raises abort).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status,
+                                          int code) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = globaltimer();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (globaltimer() - t0 > kWaitLimitNs) {
+      *abort_flag = 1;
+      atomicExch(status + 1, code);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major, 32-byte swizzle: 8-row atoms of 32 bytes,
+// stride between 8-row groups 256 bytes; version 1 (bits 46-47); layout type 6.
+__device__ __forceinline__ uint64_t sw32_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(256 >> 4) << 32;        // stride byte offset
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)6 << 61;
+  return d;
+}
+
+// Instruction descriptor for kind::f16: D f32, A and B bf16, both K-major, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n, bool neg_a) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((neg_a ? 1u : 0u) << 13) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(kBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+template <int BN>
+struct OzShape {
+  static constexpr int kStages = BN >= 128 ? 3 : (BN >= 64 ? 4 : 5);   // <= 205 KB of stages
+  static constexpr int kATile = kBM * kStepK;     // bf16 elements per plane tile
+  static constexpr int kBTile = BN * kStepK;
+  static constexpr int kStageElems = kPlanes * (kATile + kBTile);
+  static constexpr uint32_t kStageBytes = kStageElems * 2;
+  static constexpr int kTmemCols = 4 * BN <= 32 ? 32 : (4 * BN <= 64 ? 64 : (4 * BN <= 128 ? 128 : (4 * BN <= 256 ? 256 : 512)));
+  static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + 256;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(192, 1)
+    oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const OzParams p) {
+  using S = OzShape<BN>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __nv_bfloat16* tiles = reinterpret_cast<__nv_bfloat16*>(smem);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)S::kStages * S::kStageBytes);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + S::kStages;
+  uint64_t* acc_full = bars + 2 * S::kStages;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* drain_bar = acc_full + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 3);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S::kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, 4);
+    mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(S::kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int tiles_per_batch = p.mtiles * p.ntiles;
+  const int total_tiles = p.nbatch * tiles_per_batch;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      uint32_t step = 0;
+      for (int tile = blockIdx.x; tile < total_tiles && !*abort_flag; tile += gridDim.x) {
+        const int b = tile / tiles_per_batch, mt = (tile % tiles_per_batch) / p.ntiles, nt = tile % p.ntiles;
+        const int bo = b / p.bin, bi = b % p.bin;
+        const int arow = (int)(p.a_row0 + (p.a_tab ? p.a_tab[bi] : bi * p.a_bs_in) + bo * p.a_bs_out) + mt * kBM;
+        const int brow = (int)(p.b_row0 + (p.b_tab ? p.b_tab[bi] : bi * p.b_bs_in) + bo * p.b_bs_out) + nt * BN;
+        for (int s = 0; s < p.nsteps; ++s, ++step) {
+          const int st = step % S::kStages;
+          const uint32_t ph = (step / S::kStages) & 1;
+          if (!mbar_wait(&empty[st], ph ^ 1, abort_flag, p.status, 11)) break;
+          mbar_expect_tx(&full[st], S::kStageBytes);
+          __nv_bfloat16* sa = tiles + (size_t)st * S::kStageElems;
+          __nv_bfloat16* sb = sa + kPlanes * S::kATile;
+#pragma unroll
+          for (int pl = 0; pl < kPlanes; ++pl) tma_load_3d(sa + pl * S::kATile, &tmA, s * kStepK, arow, pl, &full[st]);
+#pragma unroll
+          for (int pl = 0; pl < kPlanes; ++pl) tma_load_3d(sb + pl * S::kBTile, &tmB, s * kStepK, brow, pl, &full[st]);
+        }
+      }
+      if (*abort_flag) {
+        // let every issued copy land before the CTA exits (bounded)
+        const uint64_t t0 = globaltimer();
+        for (int k = 0; k < S::kStages && step > 0; ++k) {
+          const uint32_t st2 = (step - 1 - k) % S::kStages;
+          const uint32_t ph2 = ((step - 1 - k) / S::kStages) & 1;
+          while (!mbar_try(&full[st2], ph2) && globaltimer() - t0 < kWaitLimitNs) {
+          }
+          if (step - 1 - k == 0) break;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer
+      uint32_t step = 0, chunk = 0;
+      const uint32_t id_pos = idesc_bf16(BN, false), id_neg = idesc_bf16(BN, true);
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < total_tiles && ok; tile += gridDim.x) {
+        for (int s = 0; s < p.nsteps && ok; ++s, ++step) {
+          const bool chunk_start = (s % p.steps_per_chunk) == 0;
+          if (chunk_start) {
+            if (!mbar_wait(acc_empty, (chunk & 1) ^ 1, abort_flag, p.status, 12)) { ok = false; break; }
+            tc_fence_after();
+          }
+          const int st = step % S::kStages;
+          const uint32_t ph = (step / S::kStages) & 1;
+          if (!mbar_wait(&full[st], ph, abort_flag, p.status, 13)) { ok = false; break; }
+          tc_fence_after();
+          const __nv_bfloat16* sa = tiles + (size_t)st * S::kStageElems;
+          const __nv_bfloat16* sb = sa + kPlanes * S::kATile;
+          // products (i, j) with i + j <= 3; (0,0) to the main accumulators, the rest to the corrections
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) {
+              if (i + jj > 3) continue;
+              const int acc = (i + jj == 0) ? 0 : 1;
+              const uint32_t d_re = tmem + (uint32_t)((2 * acc) * BN);
+              const uint32_t d_im = tmem + (uint32_t)((2 * acc + 1) * BN);
+              // first write of this accumulator pair in the chunk: (0,0) for main, (0,1) for corrections
+              const bool first = chunk_start && ((acc == 0) || (i == 0 && jj == 1));
+              const uint64_t ar = sw32_desc(smem_u32(sa + (2 * i) * S::kATile));
+              const uint64_t ai = sw32_desc(smem_u32(sa + (2 * i + 1) * S::kATile));
+              const uint64_t br = sw32_desc(smem_u32(sb + (2 * jj) * S::kBTile));
+              const uint64_t bim = sw32_desc(smem_u32(sb + (2 * jj + 1) * S::kBTile));
+              mma_bf16(d_re, ar, br, id_pos, first ? 0u : 1u);
+              mma_bf16(d_re, ai, bim, id_neg, 1u);
+              mma_bf16(d_im, ar, bim, id_pos, first ? 0u : 1u);
+              mma_bf16(d_im, ai, br, id_pos, 1u);
+            }
+          }
+          mma_commit(&empty[st]);
+          if ((s % p.steps_per_chunk) == p.steps_per_chunk - 1 || s == p.nsteps - 1) {
+            mma_commit(acc_full);
+            ++chunk;
+          }
+        }
+      }
+      // wait for the last MMAs before the TMEM is released
+      mma_commit(drain_bar);
+      const uint64_t t0 = globaltimer();
+      while (!mbar_try(drain_bar, 0) && globaltimer() - t0 < kWaitLimitNs) {
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5, TMEM lane quarter = warp % 4
+    const int quarter = warp & 3;
+    uint32_t chunk = 0;
+    for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+      const int b = tile / tiles_per_batch, mt = (tile % tiles_per_batch) / p.ntiles, nt = tile % p.ntiles;
+      const int bo = b / p.bin, bi = b % p.bin;
+      double2* C = p.C + (p.bc.tab ? p.bc.tab[bi] : (long long)bi * p.bc.bs_in) + (long long)bo * p.bc.bs_out;
+      const int row = mt * kBM + quarter * 32 + lane;
+      const bool row_ok = row < p.M;
+      const long long roff = row_ok ? s_view_row(p.vc, row) : 0;
+      const int nchunks = (p.nsteps + p.steps_per_chunk - 1) / p.steps_per_chunk;
+      bool ok = true;
+      for (int c = 0; c < nchunks; ++c, ++chunk) {
+        if (!mbar_wait(acc_full, chunk & 1, abort_flag, p.status, 14)) { ok = false; break; }
+        tc_fence_after();
+        const bool overwrite = (c == 0) && !p.accumulate;
+#pragma unroll 1
+        for (int cb = 0; cb < BN; cb += 16) {
+          float mr[16], cr[16], mi[16], ci[16];
+          const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cb;
+          tmem_ld16(lane_addr + 0 * BN, mr);
+          tmem_ld16(lane_addr + 2 * BN, cr);
+          tmem_ld16(lane_addr + 1 * BN, mi);
+          tmem_ld16(lane_addr + 3 * BN, ci);
+          tmem_wait_ld();
+          if (row_ok) {
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+              const int n = nt * BN + cb + u;
+              if (n < p.N) {
+                double2* dst = C + roff + (long long)(n / p.vc.kin) * p.vc.ks_out + (long long)(n % p.vc.kin) * p.vc.ks_in;
+                const double re = p.alpha * ((double)mr[u] + (double)cr[u]);
+                const double im = p.alpha * ((double)mi[u] + (double)ci[u]);
+                if (overwrite) {
+                  *dst = make_double2(re, im);
+                } else {
+                  double2 o = *dst;
+                  o.x += re;
+                  o.y += im;
+                  *dst = o;
+                }
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acc_empty);
+      }
+      if (!ok) break;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::kTmemCols));
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// host side
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  }
+  return fn;
+}
+
+// Planes buffer: [8][rows][Kpad] bf16.
+struct Planes {
+  __nv_bfloat16* ptr = nullptr;
+  long long rows = 0;
+  int Kpad = 0, Kc = 0;
+  long long plane_stride() const { return rows * Kpad; }
+};
+
+int make_map(const Planes& P, int box_rows, CUtensorMap* map) {
+  auto enc = encode_fn();
+  if (!enc) return fail(GW_ECUDA, "cuTensorMapEncodeTiled is not available");
+  cuuint64_t dims[3] = {(cuuint64_t)P.Kpad, (cuuint64_t)P.rows, (cuuint64_t)kPlanes};
+  cuuint64_t strides[2] = {(cuuint64_t)P.Kpad * 2, (cuuint64_t)P.rows * P.Kpad * 2};
+  cuuint32_t box[3] = {(cuuint32_t)kStepK, (cuuint32_t)box_rows, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)P.ptr, dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(GW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return GW_OK;
+}
+
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// chunk length and padded K for a contraction of length K
+inline void chunking(int K, int* Kc, int* Kpad) {
+  if (K <= kMaxChunk) {
+    *Kc = round_up(std::max(K, 1), kStepK);
+    *Kpad = *Kc;
+  } else {
+    *Kc = kMaxChunk;
+    *Kpad = round_up(K, kMaxChunk);
+  }
+}
+
+int launch_slice(const SliceJob& j, cudaStream_t st) {
+  const int nchunk = j.Kpad / j.Kc;
+  const long long warps = (long long)j.nbatch * j.rows * nchunk;
+  if (warps == 0) return GW_OK;
+  const long long blocks = (warps + 7) / 8;
+  if (blocks > 2147483647LL) return fail(GW_EINVAL, "slice: too many rows");
+  prof_begin(SLOT_LIMBS, st);
+  slice_kernel<<<(unsigned)blocks, 256, 0, st>>>(j);
+  prof_end(SLOT_LIMBS, st, 0.0, (double)warps * j.Kc * (16.0 + 16.0));
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "slice launch: %s", cudaGetErrorString(e));
+}
+
+int g_num_sms = 0;
+
+template <int BN>
+int launch_oz(const Planes& A, const Planes& B, OzParams p, int slot, cudaStream_t st) {
+  using S = OzShape<BN>;
+  if (A.Kpad != B.Kpad || A.Kc != B.Kc) return fail(GW_EINVAL, "oz_gemm: operand chunking differs");
+  p.nsteps = A.Kpad / kStepK;
+  p.steps_per_chunk = A.Kc / kStepK;
+  p.mtiles = (p.M + kBM - 1) / kBM;
+  p.ntiles = (p.N + BN - 1) / BN;
+  const long long total = (long long)p.nbatch * p.mtiles * p.ntiles;
+  if (total == 0) return GW_OK;
+  if (total > 2147483647LL) return fail(GW_EINVAL, "oz_gemm: too many tiles");
+  CUtensorMap ma, mb;
+  GW_TRY_INTERNAL(make_map(A, kBM, &ma));
+  GW_TRY_INTERNAL(make_map(B, BN, &mb));
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(oz_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
+    attr = true;
+  }
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int grid = (int)std::min<long long>(total, g_num_sms);
+  prof_begin(slot, st);
+  oz_gemm_kernel<BN><<<grid, 192, S::kSmem, st>>>(ma, mb, p);
+  // executed bf16 tensor flops: 10 slice products x 4 real products per complex multiply-add
+  prof_end(slot, st, 2.0 * 40.0 * (double)total * kBM * BN * (double)p.nsteps * kStepK,
+           (double)total * p.nsteps * S::kStageBytes);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "oz_gemm launch: %s", cudaGetErrorString(e));
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+// the mixed stages
+
+// Plane-row tables, [kTabs][nq][nk]: first plane row of each operand block.
+enum { T_VKKPQ = 0, T_VKPQK, T_GKPQ, T_GK, T_VKKMQ, T_GKMQ, T_VCOL_KMQK, kTabs };
+
+struct MixedState {
+  MixedDims d;
+  cudaStream_t stream = nullptr;
+  int nt = 1;                   // tau nodes per batch
+  long long nao2 = 0, naux2 = 0, pair = 0;
+  const double2* V = nullptr;
+  Planes vrow, vcol, gf, gm;    // V rows (Q,i) over orbitals; V rows (b,j) over Q'; G^T forward / mirrored tau
+  __nv_bfloat16* xs_mem = nullptr;   // operand planes for the batched GEMMs (two buffers)
+  __nv_bfloat16* ys_mem = nullptr;
+  Planes ps;                    // P~ planes
+  double2 *x64 = nullptr, *y64 = nullptr;   // FP64 intermediates, nt * nk * pair each
+  long long* rowtabs = nullptr;
+  int* status = nullptr;
+  int Kc_vg = 0, Kpad_vg = 0, Kc_p0 = 0, Kpad_p0 = 0, Kc_r = 0, Kpad_r = 0, Kc_s = 0, Kpad_s = 0;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+template <class T>
+int m_alloc(MixedState* s, T** p, size_t count, size_t* bytes) {
+  if (count == 0) count = 1;
+  if (cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T)) != cudaSuccess) {
+    *p = nullptr;
+    return fail(GW_ENOMEM, "mixed workspace: cudaMalloc of %zu bytes failed", count * sizeof(T));
+  }
+  s->allocs.push_back(*p);
+  *bytes += count * sizeof(T);
+  return GW_OK;
+}
+
+int alloc_planes(MixedState* s, Planes* P, long long rows, int Kc, int Kpad, size_t* bytes) {
+  P->rows = rows;
+  P->Kc = Kc;
+  P->Kpad = Kpad;
+  return m_alloc(s, &P->ptr, (size_t)kPlanes * rows * Kpad, bytes);
+}
+
+Planes view(__nv_bfloat16* mem, long long rows, int Kc, int Kpad) {
+  Planes P;
+  P.ptr = mem;
+  P.rows = rows;
+  P.Kc = Kc;
+  P.Kpad = Kpad;
+  return P;
+}
+
+int kshift3(const int nk3[3], int k, int q, int sign) {
+  const int k1 = k / (nk3[1] * nk3[2]), k2 = (k / nk3[2]) % nk3[1], k3 = k % nk3[2];
+  const int q1 = q / (nk3[1] * nk3[2]), q2 = (q / nk3[2]) % nk3[1], q3 = q % nk3[2];
+  const int a = ((k1 + sign * q1) % nk3[0] + nk3[0]) % nk3[0];
+  const int b = ((k2 + sign * q2) % nk3[1] + nk3[1]) % nk3[1];
+  const int c = ((k3 + sign * q3) % nk3[2] + nk3[2]) % nk3[2];
+  return (a * nk3[1] + b) * nk3[2] + c;
+}
+
+const long long* tab(const MixedState* s, int which, int q) {
+  return s->rowtabs + ((size_t)which * s->d.nk + q) * s->d.nk;
+}
+
+// Slice a batch of FP64 matrices into planes (rows x K, per-row chunk alignment).
+int slice(MixedState* s, const double2* src, const ZView& v, long long b_in, long long b_out, int bin, int nbatch,
+          int rows, int K, const Planes& P, long long dst_rows_per_batch) {
+  SliceJob j;
+  j.src = src;
+  j.v = v;
+  j.b.bs_in = b_in;
+  j.b.bs_out = b_out;
+  j.bin = bin;
+  j.rows = rows;
+  j.K = K;
+  j.Kc = P.Kc;
+  j.Kpad = P.Kpad;
+  j.nbatch = nbatch;
+  j.dst = P.ptr;
+  j.plane_stride = P.plane_stride();
+  j.dst_rows_per_batch = dst_rows_per_batch;
+  return launch_slice(j, s->stream);
+}
+
+int slice_g(MixedState* s, const double2* G) {
+  const int nk = s->d.nk, ntau = s->d.ntau, nao = s->d.nao;
+  for (int mir = 0; mir < 2; ++mir) {
+    ZView v;
+    v.rin = nao;
+    v.rs_in = 1;                                   // b (or d)
+    v.rs_out = mir ? -s->nao2 : s->nao2;           // tau, or mirrored tau
+    v.ks_in = nao;                                 // a (or c)
+    const double2* src = G + (mir ? (long long)(ntau - 1) * s->nao2 : 0);
+    GW_TRY_INTERNAL(slice(s, src, v, (long long)ntau * s->nao2, 0, 1 << 30, nk, ntau * nao, nao, mir ? s->gm : s->gf,
+                          (long long)ntau * nao));
+  }
+  return GW_OK;
+}
+
+// out[t][k][Q][i][b] = sum_a V^{pair(k)}_ia(Q) G^{kg(k)}_ab(t) for t in [t0, t0+nt) (A and Z), or, with
+// transposed, out[t][k][Q'][d][b] = sum_c V^{pair(k)}_bc(Q') G^{kg(k)}_cd(beta - t) (the B operand of P0).
+int vg_gemm(MixedState* s, int pair_tab, int g_tab, const Planes& Gp, int q, int t0, int nt, bool transposed,
+            double2* out) {
+  const int nk = s->d.nk, nao = s->d.nao, naux = s->d.naux;
+  OzParams p;
+  p.M = naux * nao;
+  p.N = nt * nao;
+  p.nbatch = nk;
+  p.a_tab = tab(s, pair_tab, q);
+  p.b_tab = tab(s, g_tab, q);
+  p.b_row0 = (long long)t0 * nao;
+  p.C = out;
+  p.bc.bs_in = s->pair;
+  if (!transposed) {
+    p.vc.rs_in = nao;
+    p.vc.kin = nao;
+    p.vc.ks_in = 1;
+    p.vc.ks_out = (long long)nk * s->pair;
+  } else {
+    p.vc.rin = nao;
+    p.vc.rs_in = 1;
+    p.vc.rs_out = s->nao2;
+    p.vc.kin = nao;
+    p.vc.ks_in = nao;
+    p.vc.ks_out = (long long)nk * s->pair;
+  }
+  p.status = s->status;
+  return launch_oz<128>(s->vrow, Gp, p, SLOT_VG_MIXED, s->stream);
+}
+
+int polarization_chunk(MixedState* s, const double2* G, double2* P0t, double spin, int q, int t0, int nt) {
+  const int nk = s->d.nk, nao = s->d.nao, naux = s->d.naux, ntau = s->d.ntau;
+  GW_TRY_INTERNAL(vg_gemm(s, T_VKKPQ, T_GKPQ, s->gf, q, t0, nt, false, s->x64));
+  GW_TRY_INTERNAL(vg_gemm(s, T_VKPQK, T_GK, s->gm, q, t0, nt, true, s->y64));
+  const Planes xs = view(s->xs_mem, (long long)nt * naux, s->Kc_p0, s->Kpad_p0);
+  const Planes ys = view(s->ys_mem, (long long)nt * naux, s->Kc_p0, s->Kpad_p0);
+  ZView v;                                 // rows Q, k = (k, d, b)
+  v.rs_in = s->nao2;
+  v.kin = (int)s->nao2;
+  v.ks_in = 1;
+  v.ks_out = s->pair;
+  GW_TRY_INTERNAL(slice(s, s->x64, v, (long long)nk * s->pair, 0, 1 << 30, nt, naux, nk * (int)s->nao2, xs, naux));
+  GW_TRY_INTERNAL(slice(s, s->y64, v, (long long)nk * s->pair, 0, 1 << 30, nt, naux, nk * (int)s->nao2, ys, naux));
+  OzParams p;
+  p.M = naux;
+  p.N = naux;
+  p.nbatch = nt;
+  p.a_bs_in = naux;
+  p.b_bs_in = naux;
+  p.C = P0t + ((long long)q * ntau + t0) * s->naux2;
+  p.bc.bs_in = s->naux2;
+  p.vc.rs_in = naux;
+  p.vc.ks_in = 1;
+  p.alpha = -spin / nk;
+  p.status = s->status;
+  (void)nao;
+  return launch_oz<128>(xs, ys, p, SLOT_P0_TC, s->stream);
+}
+
+int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double2* Sig, int q, int t0, int nt) {
+  const int nk = s->d.nk, nao = s->d.nao, naux = s->d.naux, ntau = s->d.ntau;
+  {  // P~ planes: rows Q over Q'
+    ZView v;
+    v.rs_in = naux;
+    v.ks_in = 1;
+    GW_TRY_INTERNAL(slice(s, Pt + ((long long)q * ntau + t0) * s->naux2, v, s->naux2, 0, 1 << 30, nt, naux, naux,
+                          s->ps, naux));
+  }
+  {  // R^Q_{(b,j)}(k,t) = sum_Q' P~_QQ'(t) V^{k-q,k}_bj(Q')  -> y64[t][k][Q][(b,j)]
+    OzParams p;
+    p.M = naux;
+    p.N = (int)s->nao2;
+    p.nbatch = nt * nk;
+    p.bin = nk;
+    p.a_bs_out = naux;                      // rows t * naux
+    p.b_tab = tab(s, T_VCOL_KMQK, q);
+    p.C = s->y64;
+    p.bc.bs_in = s->pair;
+    p.bc.bs_out = (long long)nk * s->pair;
+    p.vc.rs_in = s->nao2;
+    p.vc.ks_in = 1;
+    p.status = s->status;
+    GW_TRY_INTERNAL(launch_oz<128>(s->ps, s->vcol, p, SLOT_R_TC, s->stream));
+  }
+  // Z^Q_{ib}(k,t) = sum_a V^{k,k-q}_ia(Q) G^{k-q}_ab(t) -> x64[t][k][Q][i][b]
+  GW_TRY_INTERNAL(vg_gemm(s, T_VKKMQ, T_GKMQ, s->gf, q, t0, nt, false, s->x64));
+  const Planes xs = view(s->xs_mem, (long long)nt * nk * nao, s->Kc_s, s->Kpad_s);
+  const Planes ys = view(s->ys_mem, (long long)nt * nk * nao, s->Kc_s, s->Kpad_s);
+  {
+    ZView vz;                               // rows i, k = (Q, b)
+    vz.rs_in = nao;
+    vz.kin = nao;
+    vz.ks_out = s->nao2;
+    vz.ks_in = 1;
+    GW_TRY_INTERNAL(slice(s, s->x64, vz, s->pair, 0, 1 << 30, nt * nk, nao, naux * nao, xs, nao));
+    ZView vr;                               // rows j, k = (Q, b)
+    vr.rs_in = 1;
+    vr.kin = nao;
+    vr.ks_out = s->nao2;
+    vr.ks_in = nao;
+    GW_TRY_INTERNAL(slice(s, s->y64, vr, s->pair, 0, 1 << 30, nt * nk, nao, naux * nao, ys, nao));
+  }
+  OzParams p;                               // Sigma^k_ij(t) += -(1/N_k) sum_{Q,b} Z_{Q,i,b} R_{Q,b,j}
+  p.M = nao;
+  p.N = nao;
+  p.nbatch = nt * nk;
+  p.bin = nk;
+  p.a_bs_in = nao;
+  p.a_bs_out = (long long)nk * nao;
+  p.b_bs_in = nao;
+  p.b_bs_out = (long long)nk * nao;
+  p.C = Sig + (long long)t0 * s->nao2;
+  p.bc.bs_in = (long long)ntau * s->nao2;
+  p.bc.bs_out = s->nao2;
+  p.vc.rs_in = nao;
+  p.vc.ks_in = 1;
+  p.alpha = -1.0 / nk;
+  p.accumulate = 1;
+  p.status = s->status;
+  return launch_oz<32>(xs, ys, p, SLOT_SIGMA_MIXED, s->stream);
+}
+
+}  // namespace
+
+int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int* status, size_t* bytes) {
+  *out = nullptr;
+  if (!encode_fn()) return fail(GW_ECUDA, "cuTensorMapEncodeTiled entry point not found");
+  if (d.nao > 512 || d.naux > 4096) return fail(GW_EINVAL, "mixed: nao <= 512 and naux <= 4096 required");
+  MixedState* s = new MixedState();
+  s->d = d;
+  s->stream = stream;
+  s->status = status;
+  s->nao2 = (long long)d.nao * d.nao;
+  s->naux2 = (long long)d.naux * d.naux;
+  s->pair = (long long)d.naux * s->nao2;
+  const int nk = d.nk, nao = d.nao, naux = d.naux, ntau = d.ntau;
+  chunking(nao, &s->Kc_vg, &s->Kpad_vg);
+  chunking(nk * (int)s->nao2, &s->Kc_p0, &s->Kpad_p0);
+  chunking(naux, &s->Kc_r, &s->Kpad_r);
+  chunking(naux * nao, &s->Kc_s, &s->Kpad_s);
+  // tau batch: FP64 intermediates plus operand planes per tau node, capped at 6 GiB
+  const double per_t = 2.0 * nk * (double)s->pair * 16.0 +
+                       2.0 * std::max((double)naux * s->Kpad_p0, (double)nk * nao * s->Kpad_s) * kPlanes * 2.0 +
+                       (double)naux * s->Kpad_r * kPlanes * 2.0;
+  int nt = d.tau_chunk > 0 ? d.tau_chunk : (int)std::max(1.0, std::floor(6442450944.0 / per_t));
+  s->nt = std::min(nt, ntau);
+  int rc = GW_OK;
+  do {
+    if ((rc = alloc_planes(s, &s->vrow, (long long)nk * nk * naux * nao, s->Kc_vg, s->Kpad_vg, bytes))) break;
+    if ((rc = alloc_planes(s, &s->vcol, (long long)nk * nk * s->nao2, s->Kc_r, s->Kpad_r, bytes))) break;
+    if ((rc = alloc_planes(s, &s->gf, (long long)nk * ntau * nao, s->Kc_vg, s->Kpad_vg, bytes))) break;
+    if ((rc = alloc_planes(s, &s->gm, (long long)nk * ntau * nao, s->Kc_vg, s->Kpad_vg, bytes))) break;
+    if ((rc = alloc_planes(s, &s->ps, (long long)s->nt * naux, s->Kc_r, s->Kpad_r, bytes))) break;
+    const size_t xs_elems =
+        (size_t)kPlanes * std::max((size_t)s->nt * naux * s->Kpad_p0, (size_t)s->nt * nk * nao * s->Kpad_s);
+    if ((rc = m_alloc(s, &s->xs_mem, xs_elems, bytes))) break;
+    if ((rc = m_alloc(s, &s->ys_mem, xs_elems, bytes))) break;
+    if ((rc = m_alloc(s, &s->x64, (size_t)s->nt * nk * s->pair, bytes))) break;
+    if ((rc = m_alloc(s, &s->y64, (size_t)s->nt * nk * s->pair, bytes))) break;
+    std::vector<long long> t((size_t)kTabs * nk * nk);
+    const long long vrows = (long long)naux * nao;
+    for (int q = 0; q < nk; ++q)
+      for (int k = 0; k < nk; ++k) {
+        const int kp = kshift3(d.nk3, k, q, +1), km = kshift3(d.nk3, k, q, -1);
+        auto at = [&](int w) -> long long& { return t[((size_t)w * nk + q) * nk + k]; };
+        at(T_VKKPQ) = ((long long)k * nk + kp) * vrows;
+        at(T_VKPQK) = ((long long)kp * nk + k) * vrows;
+        at(T_GKPQ) = (long long)kp * ntau * nao;
+        at(T_GK) = (long long)k * ntau * nao;
+        at(T_VKKMQ) = ((long long)k * nk + km) * vrows;
+        at(T_GKMQ) = (long long)km * ntau * nao;
+        at(T_VCOL_KMQK) = ((long long)km * nk + k) * s->nao2;
+      }
+    if ((rc = m_alloc(s, &s->rowtabs, t.size(), bytes))) break;
+    cudaMemcpy(s->rowtabs, t.data(), t.size() * sizeof(long long), cudaMemcpyHostToDevice);
+  } while (false);
+  if (rc != GW_OK) {
+    mixed_destroy(s);
+    return rc;
+  }
+  *out = s;
+  return GW_OK;
+}
+
+void mixed_destroy(MixedState* s) {
+  if (!s) return;
+  for (void* p : s->allocs) cudaFree(p);
+  delete s;
+}
+
+int mixed_set_coulomb(MixedState* s, const double2* V) {
+  s->V = V;
+  const int nk = s->d.nk, nao = s->d.nao, naux = s->d.naux;
+  ZView vr;                                 // rows (Q, i) over orbital a
+  vr.rs_in = nao;
+  vr.ks_in = 1;
+  GW_TRY_INTERNAL(slice(s, V, vr, s->pair, 0, 1 << 30, nk * nk, naux * nao, nao, s->vrow, (long long)naux * nao));
+  ZView vc;                                 // rows (b, j) over Q'
+  vc.rs_in = 1;
+  vc.ks_in = s->nao2;
+  GW_TRY_INTERNAL(slice(s, V, vc, s->pair, 0, 1 << 30, nk * nk, (int)s->nao2, naux, s->vcol, s->nao2));
+  return GW_OK;
+}
+
+int mixed_polarization(MixedState* s, const double2* G, double2* P0t, double spin_factor) {
+  GW_TRY_INTERNAL(slice_g(s, G));
+  for (int q = 0; q < s->d.nk; ++q)
+    for (int t0 = 0; t0 < s->d.ntau; t0 += s->nt)
+      GW_TRY_INTERNAL(polarization_chunk(s, G, P0t, spin_factor, q, t0, std::min(s->nt, s->d.ntau - t0)));
+  return GW_OK;
+}
+
+int mixed_self_energy(MixedState* s, const double2* G, const double2* Pt, double2* Sig) {
+  if (cudaMemsetAsync(Sig, 0, (size_t)s->d.nk * s->d.ntau * s->nao2 * sizeof(double2), s->stream) != cudaSuccess)
+    return fail(GW_ECUDA, "memset Sigma");
+  GW_TRY_INTERNAL(slice_g(s, G));
+  for (int q = 0; q < s->d.nk; ++q)
+    for (int t0 = 0; t0 < s->d.ntau; t0 += s->nt)
+      GW_TRY_INTERNAL(self_energy_chunk(s, G, Pt, Sig, q, t0, std::min(s->nt, s->d.ntau - t0)));
+  return GW_OK;
+}
 
 }  // namespace gwi

@@ -26,7 +26,8 @@ ABI_SYMBOLS = [
     "gw_version", "gw_last_error", "gw_sample_count", "gw_grid_build", "gw_create", "gw_destroy",
     "gw_workspace_bytes", "gw_set_coulomb", "gw_polarization", "gw_to_matsubara", "gw_to_tau",
     "gw_aux_dyson", "gw_screened_interaction", "gw_self_energy", "gw_sigma_eval", "gw_dyson_G",
-    "gw_mix", "gw_synchronize",
+    "gw_mix", "gw_synchronize", "gw_profile_enable", "gw_launch_count", "gw_profile_slots",
+    "gw_profile_read",
 ]
 
 
@@ -76,6 +77,11 @@ def lib():
     L.gw_dyson_G.argtypes = [vp, vp, vp, vp]
     L.gw_mix.argtypes = [vp, vp, vp, d, ctypes.POINTER(d)]
     L.gw_synchronize.argtypes = [vp]
+    L.gw_profile_enable.argtypes = [vp, i]
+    L.gw_launch_count.argtypes = [vp]
+    L.gw_launch_count.restype = ctypes.c_longlong
+    L.gw_profile_read.argtypes = [vp, i, ctypes.c_char_p, i, ctypes.POINTER(ll), ctypes.POINTER(d),
+                                  ctypes.POINTER(d), ctypes.POINTER(d)]
     _lib = L
     return L
 
@@ -230,3 +236,26 @@ def gw_mix(ctx: gw_ctx, Sig_new, Sig_inout, alpha: float) -> float:
 
 def gw_synchronize(ctx: gw_ctx):
     _check(lib().gw_synchronize(ctx.handle))
+
+
+def gw_profile_enable(ctx: gw_ctx, on: bool = True):
+    _check(lib().gw_profile_enable(ctx.handle, 1 if on else 0))
+
+
+def gw_launch_count(ctx: gw_ctx) -> int:
+    return int(lib().gw_launch_count(ctx.handle))
+
+
+def gw_profile_read(ctx: gw_ctx) -> dict:
+    """{kernel name: {"launches", "ms", "flops", "bytes"}} for every slot with launches."""
+    out = {}
+    for slot in range(lib().gw_profile_slots()):
+        name = ctypes.create_string_buffer(64)
+        n = ctypes.c_longlong(0)
+        ms, fl, by = ctypes.c_double(0), ctypes.c_double(0), ctypes.c_double(0)
+        _check(lib().gw_profile_read(ctx.handle, slot, name, 64, ctypes.byref(n), ctypes.byref(ms),
+                                     ctypes.byref(fl), ctypes.byref(by)))
+        if n.value:
+            out[name.value.decode()] = {"launches": n.value, "ms": ms.value, "flops": fl.value,
+                                        "bytes": by.value}
+    return out
