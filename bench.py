@@ -368,14 +368,15 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["bf16x3", "fp16s", "fp64"], default=None)
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--fp64-compare", action="store_true")
+    ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false",
+                    help="skip the one FP64 evaluation that gives the mixed/FP64 speed-up and max|dSigma|")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=15.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.precision is None:
-        args.precision = "fp64"
+        args.precision = "bf16x3"
     if args.steps is None:
         args.steps = 2 if args.precision == "fp64" else 10
     rank = int(os.environ.get("RANK", "0"))

@@ -2,20 +2,26 @@
 //
 // Every V.G.V contraction (Eqs. tilde_P0_tau and sigma_gw) is a complex GEMM
 // C = sum_k A(m,k) B(n,k). Each operand is split, per row and per chunk of at
-// most 512 k-values, into four bf16 slices that share one power-of-two
+// most 256 k-values, into four bf16 slices that share one power-of-two
 // alignment 2^E (E from the chunk's largest |re|, |im|):
 //     x = 2^E (s0 + s1 + s2 + s3) + O(2^(E-32)),   s_i = integer_i * 2^-(8i+7), |integer_i| <= 128.
 // Products of leading slices are integers times one common quantum, so their
-// sum over a chunk (at most 2*512 terms of at most 2^14) is exact in the FP32
-// accumulator. Products of lower order (i + j = 1..3) go to a second FP32
-// accumulator whose rounding is 2^-8 smaller in scale; products with i+j > 3
-// are dropped (2^-32 relative). After each chunk the four accumulators
-// (main/correction x re/im) are added in FP64 into the output. Complex
-// products use four real MMAs per slice pair (the A-imaginary one negated by
-// the instruction descriptor).
+// sum over a chunk (at most 2*256 terms of at most 2^14) is exact in the FP32
+// accumulator, and so is the sum of the order-1 products (i + j = 1, at most
+// 4*256 terms of at most 2^14 on a quantum 2^-8 smaller) in a second
+// accumulator. Orders 2 and 3 share a third accumulator, whose FP32 rounding
+// sits 2^-16 below the leading term; products with i + j > 3 are dropped
+// (2^-32 relative). Tensor-core FP32 accumulation rounds toward zero, so only
+// exact partial sums keep the error from growing with the chunk length. After
+// each chunk the six accumulators (three orders x re/im) are combined without
+// rounding into an FP32 pair and added to a double-float running sum (FP64 is
+// about 1/64 of the FP32 rate on this part, so no FP64 instruction runs per
+// chunk); the last chunk writes FP64, or double-float for intermediates that
+// are sliced again. Complex products use four real MMAs per slice pair (the
+// A-imaginary one negated by the instruction descriptor).
 //
 // Kernels
-//   slice_kernel   FP64 complex view -> 8 bf16 planes [slice*2 + re/im][row][Kpad]
+//   slice_kernel   FP64 or double-float complex view -> 8 bf16 planes [slice*2 + re/im][row][Kpad]
 //   oz_gemm_kernel persistent tcgen05 GEMM over plane tiles loaded by TMA
 //                  (SWIZZLE_32B K-major, one 16-wide k-step per pipeline stage)
 #include <cuda.h>
@@ -46,13 +52,19 @@ namespace {
 constexpr int kPlanes = 8;     // 4 slices x (re, im)
 constexpr int kBM = 128;       // rows of an MMA tile (TMEM lanes)
 constexpr int kStepK = 16;     // k per MMA (kind::f16)
-constexpr int kMaxChunk = 512; // k per exact-accumulation chunk
+constexpr int kMaxChunk = 256; // k per exact-accumulation chunk
 
 // ------------------------------------------------------------------------------------------------
 // slicer
 
+// Source elements are FP64 complex (double2) or, for intermediates written by
+// the GEMM epilogue, double-float complex: float4 (re_hi, re_lo, im_hi, im_lo)
+// in the same 16-byte slot. Slicing uses integer arithmetic only: the element
+// scaled to 2^31 / 2^E is rounded to an integer N (|N| <= 2^31) and split into
+// four signed base-256 digits, so no FP64 instruction runs per element.
 struct SliceJob {
   const double2* src = nullptr;
+  int src_df = 0;          // 1: src holds double-float complex values
   ZView v;                 // row and k view of one batch entry
   ZBatch b;                // per-batch source offset
   int bin = 1 << 30;
@@ -70,6 +82,39 @@ __device__ __forceinline__ long long s_view_k(const ZView& v, int k) {
   return (long long)(k / v.kin) * v.ks_out + (long long)(k % v.kin) * v.ks_in;
 }
 
+// round(x * 2^(31 - E)) for an FP64 bit pattern x with |x| < 2^E (round half up on |x|).
+__device__ __forceinline__ long long fixed31_f64(unsigned long long bits, int E) {
+  const int eb = (int)((bits >> 52) & 0x7FF);
+  if (eb == 0) return 0;
+  const long long m = (long long)((bits & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+  const int sh = 1044 + E - eb;          // x = m 2^(eb - 1075); sh >= 22 because |x| < 2^E
+  const long long n = sh >= 62 ? 0 : ((m + (1ll << (sh - 1))) >> sh);
+  return (bits >> 63) ? -n : n;
+}
+
+// round(x * 2^(31 - E)) for an FP32 bit pattern x with |x| < 2^E (shift may be to the left).
+__device__ __forceinline__ long long fixed31_f32(uint32_t bits, int E) {
+  const int eb = (int)((bits >> 23) & 0xFF);
+  if (eb == 0) return 0;
+  const long long m = (long long)((bits & 0x7FFFFFu) | (1u << 23));
+  const int sh = 119 + E - eb;           // x = m 2^(eb - 150); sh >= -7 because |x| < 2^E
+  long long n;
+  if (sh <= 0) n = m << (-sh);
+  else n = sh >= 62 ? 0 : ((m + (1ll << (sh - 1))) >> sh);
+  return (bits >> 31) ? -n : n;
+}
+
+// N (|N| <= 2^31 + 1) -> signed base-256 digits d0..d3, N = d0 2^24 + d1 2^16 + d2 2^8 + d3, |d| <= 128.
+__device__ __forceinline__ void split_digits(long long n, int d[4]) {
+  d[0] = (int)((n + (1ll << 23)) >> 24);
+  n -= (long long)d[0] << 24;
+  d[1] = (int)((n + (1ll << 15)) >> 16);
+  n -= (long long)d[1] << 16;
+  d[2] = (int)((n + (1ll << 7)) >> 8);
+  n -= (long long)d[2] << 8;
+  d[3] = (int)n;
+}
+
 // One warp per (batch, row, chunk).
 __global__ void __launch_bounds__(256) slice_kernel(const SliceJob j) {
   const long long warp_global = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -85,38 +130,68 @@ __global__ void __launch_bounds__(256) slice_kernel(const SliceJob j) {
   const double2* src = j.src + (j.b.tab ? j.b.tab[bi] : (long long)bi * j.b.bs_in) + (long long)bo * j.b.bs_out +
                        s_view_row(j.v, r);
   constexpr int kPer = kMaxChunk / 32;
-  double2 x[kPer];
-  double m = 0.0;
+  // raw bit patterns of (re, im): FP64 bits, or the two FP32 halves of a double-float
+  unsigned long long xr[kPer], xi[kPer];
+  unsigned long long mbits = 0;          // largest |value| as bits (ordered like the values)
 #pragma unroll
   for (int u = 0; u < kPer; ++u) {
     const int e = lane + 32 * u;
     const int k = c * j.Kc + e;
-    double2 val = make_double2(0.0, 0.0);
-    if (e < j.Kc && k < j.K) val = src[s_view_k(j.v, k)];
-    x[u] = val;
-    m = fmax(m, fmax(fabs(val.x), fabs(val.y)));
+    xr[u] = xi[u] = 0;
+    if (e < j.Kc && k < j.K) {
+      const long long off = s_view_k(j.v, k);
+      if (j.src_df) {
+        const float4 f = reinterpret_cast<const float4*>(src)[off];
+        xr[u] = ((unsigned long long)__float_as_uint(f.y) << 32) | __float_as_uint(f.x);
+        xi[u] = ((unsigned long long)__float_as_uint(f.w) << 32) | __float_as_uint(f.z);
+        mbits = max(mbits, (unsigned long long)max(__float_as_uint(f.x) & 0x7FFFFFFFu, __float_as_uint(f.z) & 0x7FFFFFFFu));
+      } else {
+        const double2 d = src[off];
+        xr[u] = (unsigned long long)__double_as_longlong(d.x);
+        xi[u] = (unsigned long long)__double_as_longlong(d.y);
+        mbits = max(mbits, max(xr[u] & 0x7FFFFFFFFFFFFFFFull, xi[u] & 0x7FFFFFFFFFFFFFFFull));
+      }
+    }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int o = 16; o > 0; o >>= 1) mbits = max(mbits, __shfl_xor_sync(0xffffffffu, mbits, o));
+  // E: the chunk maximum m = f 2^E with f in [0.5, 1), so every |x| / 2^E < 1
   int E = 0;
-  if (m > 0.0) frexp(m, &E);             // m = f 2^E, f in [0.5, 1): |x| / 2^E < 1
+  bool zero;
+  if (j.src_df) {
+    const int eb = (int)((mbits >> 23) & 0xFF);
+    zero = eb == 0;
+    E = eb - 126;
+  } else {
+    const int eb = (int)((mbits >> 52) & 0x7FF);
+    zero = eb == 0;
+    E = eb - 1022;
+  }
   const long long row = j.dst_row0 + (long long)b * j.dst_rows_per_batch + r;
   __nv_bfloat16* out = j.dst + row * j.Kpad + (long long)c * j.Kc;
+  float scale[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) scale[s] = ldexpf(1.0f, E - 7 - 8 * s);
 #pragma unroll
   for (int u = 0; u < kPer; ++u) {
     const int e = lane + 32 * u;
     if (e >= j.Kc) break;
-    double tr = (m > 0.0) ? ldexp(x[u].x, -E) : 0.0;
-    double ti = (m > 0.0) ? ldexp(x[u].y, -E) : 0.0;
+    int dr[4], di[4];
+    if (zero) {
+#pragma unroll
+      for (int s = 0; s < 4; ++s) dr[s] = di[s] = 0;
+    } else if (j.src_df) {
+      split_digits(fixed31_f32((uint32_t)xr[u], E) + fixed31_f32((uint32_t)(xr[u] >> 32), E), dr);
+      split_digits(fixed31_f32((uint32_t)xi[u], E) + fixed31_f32((uint32_t)(xi[u] >> 32), E), di);
+    } else {
+      split_digits(fixed31_f64(xr[u], E), dr);
+      split_digits(fixed31_f64(xi[u], E), di);
+    }
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
-      const int sh = 8 * s + 7;
-      const double qr = rint(ldexp(tr, sh)), qi = rint(ldexp(ti, sh));
-      tr -= ldexp(qr, -sh);
-      ti -= ldexp(qi, -sh);
-      // integer * 2^(E - sh) is exact in float and in bf16 (|integer| <= 128)
-      out[(long long)(2 * s) * j.plane_stride + e] = __float2bfloat16_rn((float)ldexp(qr, E - sh));
-      out[(long long)(2 * s + 1) * j.plane_stride + e] = __float2bfloat16_rn((float)ldexp(qi, E - sh));
+      // digit * 2^(E - 7 - 8s) is exact in float and in bf16 (|digit| <= 128)
+      out[(long long)(2 * s) * j.plane_stride + e] = __float2bfloat16_rn((float)dr[s] * scale[s]);
+      out[(long long)(2 * s + 1) * j.plane_stride + e] = __float2bfloat16_rn((float)di[s] * scale[s]);
     }
   }
 }
@@ -137,8 +212,26 @@ struct OzParams {
   ZBatch bc;
   double alpha = 1.0;
   int accumulate = 0;
+  int out_df = 0;                     // 1: write double-float complex (float4) instead of FP64 (alpha 1, no accumulate)
+  float4* ws = nullptr;               // per-CTA running sums across chunks, gridDim.x * 128 * BN
   int* status = nullptr;              // status[1] <- error code of a device-side wait that gave up
 };
+
+// Error-free FP32 sum: s + e = a + b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Double-float addition (hi, lo) + (bh, bl), about 2^-44 relative.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
+  float s, e;
+  two_sum(hi, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(lo, bl));
+  hi = __fadd_rn(s, e);
+  lo = __fsub_rn(e, __fsub_rn(hi, s));
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -247,12 +340,14 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 
 template <int BN>
 struct OzShape {
-  static constexpr int kStages = BN >= 128 ? 3 : (BN >= 64 ? 4 : 5);   // <= 205 KB of stages
+  static constexpr int kStages = BN >= 64 ? 4 : 5;   // <= 213 KB of stages for BN <= 80
   static constexpr int kATile = kBM * kStepK;     // bf16 elements per plane tile
   static constexpr int kBTile = BN * kStepK;
   static constexpr int kStageElems = kPlanes * (kATile + kBTile);
   static constexpr uint32_t kStageBytes = kStageElems * 2;
-  static constexpr int kTmemCols = 4 * BN <= 32 ? 32 : (4 * BN <= 64 ? 64 : (4 * BN <= 128 ? 128 : (4 * BN <= 256 ? 256 : 512)));
+  static constexpr int kAccCols = 6 * BN;        // (order 0, order 1, orders 2-3) x (re, im)
+  static_assert(kAccCols <= 512, "six accumulators of BN columns must fit in TMEM");
+  static constexpr int kTmemCols = kAccCols <= 32 ? 32 : (kAccCols <= 64 ? 64 : (kAccCols <= 128 ? 128 : (kAccCols <= 256 ? 256 : 512)));
   static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + 256;
 };
 
@@ -350,17 +445,17 @@ __global__ void __launch_bounds__(192, 1)
           tc_fence_after();
           const __nv_bfloat16* sa = tiles + (size_t)st * S::kStageElems;
           const __nv_bfloat16* sb = sa + kPlanes * S::kATile;
-          // products (i, j) with i + j <= 3; (0,0) to the main accumulators, the rest to the corrections
+          // products (i, j) with i + j <= 3, accumulated by order: 0, 1, and 2-3
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
               if (i + jj > 3) continue;
-              const int acc = (i + jj == 0) ? 0 : 1;
+              const int acc = (i + jj == 0) ? 0 : (i + jj == 1 ? 1 : 2);
               const uint32_t d_re = tmem + (uint32_t)((2 * acc) * BN);
               const uint32_t d_im = tmem + (uint32_t)((2 * acc + 1) * BN);
-              // first write of this accumulator pair in the chunk: (0,0) for main, (0,1) for corrections
-              const bool first = chunk_start && ((acc == 0) || (i == 0 && jj == 1));
+              // first write of each accumulator pair in a chunk: (0,0), (0,1) and (0,2) in loop order
+              const bool first = chunk_start && i == 0 && jj == acc;
               const uint64_t ar = sw32_desc(smem_u32(sa + (2 * i) * S::kATile));
               const uint64_t ai = sw32_desc(smem_u32(sa + (2 * i + 1) * S::kATile));
               const uint64_t br = sw32_desc(smem_u32(sb + (2 * jj) * S::kBTile));
@@ -400,31 +495,54 @@ __global__ void __launch_bounds__(192, 1)
       for (int c = 0; c < nchunks; ++c, ++chunk) {
         if (!mbar_wait(acc_full, chunk & 1, abort_flag, p.status, 14)) { ok = false; break; }
         tc_fence_after();
-        const bool overwrite = (c == 0) && !p.accumulate;
+        const bool last = c == nchunks - 1;
+        float4* wrow = p.ws + ((size_t)blockIdx.x * kBM + (size_t)(quarter * 32 + lane)) * BN;
 #pragma unroll 1
         for (int cb = 0; cb < BN; cb += 16) {
-          float mr[16], cr[16], mi[16], ci[16];
+          float mr[16], mi[16], ar[16], ai[16], br[16], bi[16];
           const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cb;
           tmem_ld16(lane_addr + 0 * BN, mr);
-          tmem_ld16(lane_addr + 2 * BN, cr);
           tmem_ld16(lane_addr + 1 * BN, mi);
-          tmem_ld16(lane_addr + 3 * BN, ci);
+          tmem_ld16(lane_addr + 2 * BN, ar);
+          tmem_ld16(lane_addr + 3 * BN, ai);
+          tmem_ld16(lane_addr + 4 * BN, br);
+          tmem_ld16(lane_addr + 5 * BN, bi);
           tmem_wait_ld();
           if (row_ok) {
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
               const int n = nt * BN + cb + u;
               if (n < p.N) {
+                // the chunk value: orders 0 and 1 are exact, so their sum is exact as a pair
+                float rh, rl, ih, il;
+                two_sum(mr[u], ar[u], rh, rl);
+                rl = __fadd_rn(rl, br[u]);
+                two_sum(mi[u], ai[u], ih, il);
+                il = __fadd_rn(il, bi[u]);
+                if (nchunks > 1) {
+                  float4* w = wrow + cb + u;
+                  if (c > 0) {
+                    const float4 o = *w;
+                    df_add(rh, rl, o.x, o.y);
+                    df_add(ih, il, o.z, o.w);
+                  }
+                  if (!last) {
+                    *w = make_float4(rh, rl, ih, il);
+                    continue;
+                  }
+                }
                 double2* dst = C + roff + (long long)(n / p.vc.kin) * p.vc.ks_out + (long long)(n % p.vc.kin) * p.vc.ks_in;
-                const double re = p.alpha * ((double)mr[u] + (double)cr[u]);
-                const double im = p.alpha * ((double)mi[u] + (double)ci[u]);
-                if (overwrite) {
-                  *dst = make_double2(re, im);
+                if (p.out_df) {
+                  *reinterpret_cast<float4*>(dst) = make_float4(rh, rl, ih, il);
                 } else {
-                  double2 o = *dst;
-                  o.x += re;
-                  o.y += im;
-                  *dst = o;
+                  double re = p.alpha * ((double)rh + (double)rl);
+                  double im = p.alpha * ((double)ih + (double)il);
+                  if (p.accumulate) {
+                    const double2 o = *dst;
+                    re += o.x;
+                    im += o.y;
+                  }
+                  *dst = make_double2(re, im);
                 }
               }
             }
@@ -559,11 +677,12 @@ struct MixedState {
   int nt = 1;                   // tau nodes per batch
   long long nao2 = 0, naux2 = 0, pair = 0;
   const double2* V = nullptr;
-  Planes vrow, vcol, gf, gm;    // V rows (Q,i) over orbitals; V rows (b,j) over Q'; G^T forward / mirrored tau
+  Planes vrow, vcol, gf, gm;    // V rows (Q,i) over orbitals; V rows (j,b) over Q'; G^T forward / mirrored tau
   __nv_bfloat16* xs_mem = nullptr;   // operand planes for the batched GEMMs (two buffers)
   __nv_bfloat16* ys_mem = nullptr;
   Planes ps;                    // P~ planes
-  double2 *x64 = nullptr, *y64 = nullptr;   // FP64 intermediates, nt * nk * pair each
+  double2 *x64 = nullptr, *y64 = nullptr;   // double-float intermediates (16 B per element), nt * nk * pair each
+  float4* ws = nullptr;                       // per-CTA running sums of the chunked GEMMs
   long long* rowtabs = nullptr;
   int* status = nullptr;
   int Kc_vg = 0, Kpad_vg = 0, Kc_p0 = 0, Kpad_p0 = 0, Kc_r = 0, Kpad_r = 0, Kc_s = 0, Kpad_s = 0;
@@ -613,11 +732,13 @@ const long long* tab(const MixedState* s, int which, int q) {
   return s->rowtabs + ((size_t)which * s->d.nk + q) * s->d.nk;
 }
 
-// Slice a batch of FP64 matrices into planes (rows x K, per-row chunk alignment).
+// Slice a batch of FP64 (or, with src_df, double-float) matrices into planes
+// (rows x K, per-row chunk alignment).
 int slice(MixedState* s, const double2* src, const ZView& v, long long b_in, long long b_out, int bin, int nbatch,
-          int rows, int K, const Planes& P, long long dst_rows_per_batch) {
+          int rows, int K, const Planes& P, long long dst_rows_per_batch, int src_df = 0) {
   SliceJob j;
   j.src = src;
+  j.src_df = src_df;
   j.v = v;
   j.b.bs_in = b_in;
   j.b.bs_out = b_out;
@@ -676,7 +797,9 @@ int vg_gemm(MixedState* s, int pair_tab, int g_tab, const Planes& Gp, int q, int
     p.vc.ks_out = (long long)nk * s->pair;
   }
   p.status = s->status;
-  return launch_oz<128>(s->vrow, Gp, p, SLOT_VG_MIXED, s->stream);
+  p.ws = s->ws;
+  p.out_df = 1;
+  return launch_oz<80>(s->vrow, Gp, p, SLOT_VG_MIXED, s->stream);
 }
 
 int polarization_chunk(MixedState* s, const double2* G, double2* P0t, double spin, int q, int t0, int nt) {
@@ -690,8 +813,8 @@ int polarization_chunk(MixedState* s, const double2* G, double2* P0t, double spi
   v.kin = (int)s->nao2;
   v.ks_in = 1;
   v.ks_out = s->pair;
-  GW_TRY_INTERNAL(slice(s, s->x64, v, (long long)nk * s->pair, 0, 1 << 30, nt, naux, nk * (int)s->nao2, xs, naux));
-  GW_TRY_INTERNAL(slice(s, s->y64, v, (long long)nk * s->pair, 0, 1 << 30, nt, naux, nk * (int)s->nao2, ys, naux));
+  GW_TRY_INTERNAL(slice(s, s->x64, v, (long long)nk * s->pair, 0, 1 << 30, nt, naux, nk * (int)s->nao2, xs, naux, 1));
+  GW_TRY_INTERNAL(slice(s, s->y64, v, (long long)nk * s->pair, 0, 1 << 30, nt, naux, nk * (int)s->nao2, ys, naux, 1));
   OzParams p;
   p.M = naux;
   p.N = naux;
@@ -704,8 +827,9 @@ int polarization_chunk(MixedState* s, const double2* G, double2* P0t, double spi
   p.vc.ks_in = 1;
   p.alpha = -spin / nk;
   p.status = s->status;
+  p.ws = s->ws;
   (void)nao;
-  return launch_oz<128>(xs, ys, p, SLOT_P0_TC, s->stream);
+  return launch_oz<80>(xs, ys, p, SLOT_P0_TC, s->stream);
 }
 
 int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double2* Sig, int q, int t0, int nt) {
@@ -717,7 +841,7 @@ int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double
     GW_TRY_INTERNAL(slice(s, Pt + ((long long)q * ntau + t0) * s->naux2, v, s->naux2, 0, 1 << 30, nt, naux, naux,
                           s->ps, naux));
   }
-  {  // R^Q_{(b,j)}(k,t) = sum_Q' P~_QQ'(t) V^{k-q,k}_bj(Q')  -> y64[t][k][Q][(b,j)]
+  {  // R^Q_{bj}(k,t) = sum_Q' P~_QQ'(t) V^{k-q,k}_bj(Q')  -> y64[t][k][Q][j][b]
     OzParams p;
     p.M = naux;
     p.N = (int)s->nao2;
@@ -731,7 +855,9 @@ int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double
     p.vc.rs_in = s->nao2;
     p.vc.ks_in = 1;
     p.status = s->status;
-    GW_TRY_INTERNAL(launch_oz<128>(s->ps, s->vcol, p, SLOT_R_TC, s->stream));
+    p.ws = s->ws;
+    p.out_df = 1;                           // double-float, sliced again for the Sigma contraction
+    GW_TRY_INTERNAL(launch_oz<80>(s->ps, s->vcol, p, SLOT_R_TC, s->stream));
   }
   // Z^Q_{ib}(k,t) = sum_a V^{k,k-q}_ia(Q) G^{k-q}_ab(t) -> x64[t][k][Q][i][b]
   GW_TRY_INTERNAL(vg_gemm(s, T_VKKMQ, T_GKMQ, s->gf, q, t0, nt, false, s->x64));
@@ -743,13 +869,9 @@ int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double
     vz.kin = nao;
     vz.ks_out = s->nao2;
     vz.ks_in = 1;
-    GW_TRY_INTERNAL(slice(s, s->x64, vz, s->pair, 0, 1 << 30, nt * nk, nao, naux * nao, xs, nao));
-    ZView vr;                               // rows j, k = (Q, b)
-    vr.rs_in = 1;
-    vr.kin = nao;
-    vr.ks_out = s->nao2;
-    vr.ks_in = nao;
-    GW_TRY_INTERNAL(slice(s, s->y64, vr, s->pair, 0, 1 << 30, nt * nk, nao, naux * nao, ys, nao));
+    GW_TRY_INTERNAL(slice(s, s->x64, vz, s->pair, 0, 1 << 30, nt * nk, nao, naux * nao, xs, nao, 1));
+    // R is stored [Q][j][b]: rows j, k = (Q, b), the same view as Z
+    GW_TRY_INTERNAL(slice(s, s->y64, vz, s->pair, 0, 1 << 30, nt * nk, nao, naux * nao, ys, nao, 1));
   }
   OzParams p;                               // Sigma^k_ij(t) += -(1/N_k) sum_{Q,b} Z_{Q,i,b} R_{Q,b,j}
   p.M = nao;
@@ -768,6 +890,7 @@ int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double
   p.alpha = -1.0 / nk;
   p.accumulate = 1;
   p.status = s->status;
+  p.ws = s->ws;
   return launch_oz<32>(xs, ys, p, SLOT_SIGMA_MIXED, s->stream);
 }
 
@@ -808,6 +931,12 @@ int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int*
     if ((rc = m_alloc(s, &s->ys_mem, xs_elems, bytes))) break;
     if ((rc = m_alloc(s, &s->x64, (size_t)s->nt * nk * s->pair, bytes))) break;
     if ((rc = m_alloc(s, &s->y64, (size_t)s->nt * nk * s->pair, bytes))) break;
+    {
+      int dev = 0, sms = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if ((rc = m_alloc(s, &s->ws, (size_t)std::max(sms, 1) * kBM * 80, bytes))) break;
+    }
     std::vector<long long> t((size_t)kTabs * nk * nk);
     const long long vrows = (long long)naux * nao;
     for (int q = 0; q < nk; ++q)
@@ -846,8 +975,10 @@ int mixed_set_coulomb(MixedState* s, const double2* V) {
   vr.rs_in = nao;
   vr.ks_in = 1;
   GW_TRY_INTERNAL(slice(s, V, vr, s->pair, 0, 1 << 30, nk * nk, naux * nao, nao, s->vrow, (long long)naux * nao));
-  ZView vc;                                 // rows (b, j) over Q'
-  vc.rs_in = 1;
+  ZView vc;                                 // rows (j, b) over Q': row j*nao + b reads V[Q'][b][j]
+  vc.rin = nao;
+  vc.rs_in = nao;
+  vc.rs_out = 1;
   vc.ks_in = s->nao2;
   GW_TRY_INTERNAL(slice(s, V, vc, s->pair, 0, 1 << 30, nk * nk, (int)s->nao2, naux, s->vcol, s->nao2));
   return GW_OK;
