@@ -174,6 +174,17 @@ def ncu_traffic(kernel):
     return rec["dram_bytes_per_launch"] if sha == rec["source_sha256"] else None
 
 
+def max_over_ranks(value, dist=None):
+    """The largest value over all ranks (the timing rule for a multi-rank run)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return value
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args, rank):
     from paper_2406_18479_gb300 import inputs as I
     if rank != 0:
@@ -224,7 +235,7 @@ def run_ours(args, rank, world, local_rank):
     h, v, g = I.make_inputs(w)
     V = torch.from_numpy(v).cuda()
     G = torch.from_numpy(g).cuda()
-    ctx = gw.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision=args.precision)
+    ctx = gw.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision=args.precision, tau_chunk=args.tau_chunk)
     Sig = torch.empty(ctx.shapes()["Sig"], dtype=torch.complex128, device="cuda")
     gw.gw_set_coulomb(ctx, V)
     stream = ctx.stream
@@ -249,11 +260,7 @@ def run_ours(args, rank, world, local_rank):
     prof = gw.gw_profile_read(ctx)
     gw.gw_profile_enable(ctx, False)
     gw.gw_synchronize(ctx)
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(ms, dist)
 
     # ---- end to end through the public API with host buffers (pinned)
     G_host = torch.from_numpy(g).pin_memory()
@@ -270,11 +277,7 @@ def run_ours(args, rank, world, local_rank):
             S_host.copy_(Sig, non_blocking=True)
         f1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = f0.elapsed_time(f1)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(f0.elapsed_time(f1), dist)
 
     # ---- optional FP64 comparison (one evaluation) for the mixed precisions
     fp64 = None
@@ -336,7 +339,7 @@ def run_ours(args, rank, world, local_rank):
                   "fp16s": "fp16 scaled, f32 accumulate, f64 transforms/Dyson"}[args.precision],
         "data": "synthetic (seeded H(k), V, G0 shaped like the paper's Si example)",
         "config": {"workload": w.name, "nk": w.nk, "nao": w.nao, "naux": w.naux, "ntau": w.ntau,
-                   "nomega": nwb, "beta": w.beta, "precision": args.precision,
+                   "nomega": nwb, "beta": w.beta, "precision": args.precision, "tau_chunk": args.tau_chunk,
                    "l2": "inputs larger than L2 (V 1.58 GB, P 1.73 GB per pass)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "tflops_algorithmic": flops * world * steps / (t_max / 1e3) / 1e12,
@@ -372,6 +375,7 @@ def main():
                     help="skip the one FP64 evaluation that gives the mixed/FP64 speed-up and max|dSigma|")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=15.0)
+    ap.add_argument("--tau-chunk", type=int, default=0, help="tau nodes per contraction batch (0: automatic)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

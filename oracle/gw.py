@@ -90,24 +90,26 @@ def screened_interaction(P0t, F, B):
     return P0w, Pw, Pt
 
 
-def self_energy(V, G, Pt, nk3, k_list=None, t_list=None):
+def self_energy(V, G, Pt, nk3, k_list=None, t_list=None, q_list=None):
     """GW self-energy, Eqs. (sigma_gw) and (tilde_W_DF2), Sec. 2.3:
 
       Sigma^k_ij(tau) = -(1/N_k) sum_q sum_ab G^{k-q}_ab(tau) W~^{k,k-q,k-q,k}_{iabj}(tau),
       W~_{iabj} = sum_QQ' V^{k,k-q}_ia(Q) P~^q_QQ'(tau) V^{k-q,k}_bj(Q').
 
-    Returns Sig[len(k_list)][len(t_list)][nao][nao].
+    Returns Sig[len(k_list)][len(t_list)][nao][nao]; q_list restricts the sum over q
+    (the contribution of a subset of q, as one rank of a q-sharded run computes it).
     """
     nk = V.shape[0]
     nao = V.shape[3]
     ntau = G.shape[1]
     k_list = range(nk) if k_list is None else k_list
     t_list = range(ntau) if t_list is None else t_list
+    q_list = range(nk) if q_list is None else q_list
     out = np.zeros((len(k_list), len(t_list), nao, nao), complex)
     for ik, k in enumerate(k_list):
         for it, t in enumerate(t_list):
             acc = np.zeros((nao, nao), complex)
-            for q in range(nk):
+            for q in q_list:
                 kmq = k_shift(nk3, k, q, -1)
                 acc += np.einsum("Qia,ab,QP,Pbj->ij", V[k, kmq], G[kmq, t], Pt[q, t], V[kmq, k],
                                  optimize=True)

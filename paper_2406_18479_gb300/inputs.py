@@ -53,6 +53,10 @@ WORKLOADS = {
                                   decay=40.0, seed=1, solid=True),
     "solid_4x4x4_nao52": Workload("solid_4x4x4_nao52", (4, 4, 4), 52, 400, 120, 120, 200.0,
                                   decay=40.0, seed=2, solid=True),
+    # same orbital and auxiliary sizes as the 3x3x3 solid on a 3x3x1 mesh and 25 tau nodes:
+    # a case small enough for full hardware-counter captures
+    "solid_3x3x1_nao26": Workload("solid_3x3x1_nao26", (3, 3, 1), 26, 200, 25, 25, 100.0,
+                                  decay=40.0, seed=6, solid=True),
 }
 
 
