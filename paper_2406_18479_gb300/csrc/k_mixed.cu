@@ -107,15 +107,15 @@ __device__ __forceinline__ long long fixed31_f32(uint32_t bits, int E) {
 // N (|N| <= 2^31 + 1) -> signed base-256 digits d0..d3, N = d0 2^24 + d1 2^16 + d2 2^8 + d3, |d| <= 128.
 __device__ __forceinline__ void split_digits(long long n, int d[4]) {
   d[0] = (int)((n + (1ll << 23)) >> 24);
-  n -= (long long)d[0] << 24;
-  d[1] = (int)((n + (1ll << 15)) >> 16);
-  n -= (long long)d[1] << 16;
-  d[2] = (int)((n + (1ll << 7)) >> 8);
-  n -= (long long)d[2] << 8;
-  d[3] = (int)n;
+  int r = (int)(n - ((long long)d[0] << 24));   // |r| <= 2^23: the rest in 32-bit arithmetic
+  d[1] = (r + (1 << 15)) >> 16;
+  r -= d[1] << 16;
+  d[2] = (r + (1 << 7)) >> 8;
+  d[3] = r - (d[2] << 8);
 }
 
 // One warp per (batch, row, chunk).
+template <bool DF>
 __global__ void __launch_bounds__(256) slice_kernel(const SliceJob j) {
   const long long warp_global = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -129,36 +129,37 @@ __global__ void __launch_bounds__(256) slice_kernel(const SliceJob j) {
   const int bo = b / j.bin, bi = b % j.bin;
   const double2* src = j.src + (j.b.tab ? j.b.tab[bi] : (long long)bi * j.b.bs_in) + (long long)bo * j.b.bs_out +
                        s_view_row(j.v, r);
-  constexpr int kPer = kMaxChunk / 32;
+  // each lane owns element pairs (2 lane + 64 u, +1): bf16x2 stores, half the store instructions
+  constexpr int kPairs = kMaxChunk / 64;
   // raw bit patterns of (re, im): FP64 bits, or the two FP32 halves of a double-float
-  unsigned long long xr[kPer], xi[kPer];
+  unsigned long long xr[2 * kPairs], xi[2 * kPairs];
   unsigned long long mbits = 0;          // largest |value| as bits (ordered like the values)
 #pragma unroll
-  for (int u = 0; u < kPer; ++u) {
-    const int e = lane + 32 * u;
+  for (int v = 0; v < 2 * kPairs; ++v) {
+    const int e = 2 * lane + 64 * (v >> 1) + (v & 1);
     const int k = c * j.Kc + e;
-    xr[u] = xi[u] = 0;
+    xr[v] = xi[v] = 0;
     if (e < j.Kc && k < j.K) {
       const long long off = s_view_k(j.v, k);
-      if (j.src_df) {
+      if (DF) {
         const float4 f = reinterpret_cast<const float4*>(src)[off];
-        xr[u] = ((unsigned long long)__float_as_uint(f.y) << 32) | __float_as_uint(f.x);
-        xi[u] = ((unsigned long long)__float_as_uint(f.w) << 32) | __float_as_uint(f.z);
+        xr[v] = ((unsigned long long)__float_as_uint(f.y) << 32) | __float_as_uint(f.x);
+        xi[v] = ((unsigned long long)__float_as_uint(f.w) << 32) | __float_as_uint(f.z);
         mbits = max(mbits, (unsigned long long)max(__float_as_uint(f.x) & 0x7FFFFFFFu, __float_as_uint(f.z) & 0x7FFFFFFFu));
       } else {
         const double2 d = src[off];
-        xr[u] = (unsigned long long)__double_as_longlong(d.x);
-        xi[u] = (unsigned long long)__double_as_longlong(d.y);
-        mbits = max(mbits, max(xr[u] & 0x7FFFFFFFFFFFFFFFull, xi[u] & 0x7FFFFFFFFFFFFFFFull));
+        xr[v] = (unsigned long long)__double_as_longlong(d.x);
+        xi[v] = (unsigned long long)__double_as_longlong(d.y);
+        mbits = max(mbits, max(xr[v] & 0x7FFFFFFFFFFFFFFFull, xi[v] & 0x7FFFFFFFFFFFFFFFull));
       }
     }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mbits = max(mbits, __shfl_xor_sync(0xffffffffu, mbits, o));
   // E: the chunk maximum m = f 2^E with f in [0.5, 1), so every |x| / 2^E < 1
-  int E = 0;
+  int E;
   bool zero;
-  if (j.src_df) {
+  if (DF) {
     const int eb = (int)((mbits >> 23) & 0xFF);
     zero = eb == 0;
     E = eb - 126;
@@ -173,25 +174,31 @@ __global__ void __launch_bounds__(256) slice_kernel(const SliceJob j) {
 #pragma unroll
   for (int s = 0; s < 4; ++s) scale[s] = ldexpf(1.0f, E - 7 - 8 * s);
 #pragma unroll
-  for (int u = 0; u < kPer; ++u) {
-    const int e = lane + 32 * u;
-    if (e >= j.Kc) break;
-    int dr[4], di[4];
-    if (zero) {
+  for (int u = 0; u < kPairs; ++u) {
+    const int e = 2 * lane + 64 * u;
+    if (e >= j.Kc) break;                // Kc is a multiple of 16, so e + 1 < Kc as well
+    int dr[2][4], di[2][4];
 #pragma unroll
-      for (int s = 0; s < 4; ++s) dr[s] = di[s] = 0;
-    } else if (j.src_df) {
-      split_digits(fixed31_f32((uint32_t)xr[u], E) + fixed31_f32((uint32_t)(xr[u] >> 32), E), dr);
-      split_digits(fixed31_f32((uint32_t)xi[u], E) + fixed31_f32((uint32_t)(xi[u] >> 32), E), di);
-    } else {
-      split_digits(fixed31_f64(xr[u], E), dr);
-      split_digits(fixed31_f64(xi[u], E), di);
+    for (int h = 0; h < 2; ++h) {
+      const int v = 2 * u + h;
+      if (zero) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) dr[h][s] = di[h][s] = 0;
+      } else if (DF) {
+        split_digits(fixed31_f32((uint32_t)xr[v], E) + fixed31_f32((uint32_t)(xr[v] >> 32), E), dr[h]);
+        split_digits(fixed31_f32((uint32_t)xi[v], E) + fixed31_f32((uint32_t)(xi[v] >> 32), E), di[h]);
+      } else {
+        split_digits(fixed31_f64(xr[v], E), dr[h]);
+        split_digits(fixed31_f64(xi[v], E), di[h]);
+      }
     }
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
       // digit * 2^(E - 7 - 8s) is exact in float and in bf16 (|digit| <= 128)
-      out[(long long)(2 * s) * j.plane_stride + e] = __float2bfloat16_rn((float)dr[s] * scale[s]);
-      out[(long long)(2 * s + 1) * j.plane_stride + e] = __float2bfloat16_rn((float)di[s] * scale[s]);
+      *reinterpret_cast<__nv_bfloat162*>(out + (long long)(2 * s) * j.plane_stride + e) =
+          __floats2bfloat162_rn((float)dr[0][s] * scale[s], (float)dr[1][s] * scale[s]);
+      *reinterpret_cast<__nv_bfloat162*>(out + (long long)(2 * s + 1) * j.plane_stride + e) =
+          __floats2bfloat162_rn((float)di[0][s] * scale[s], (float)di[1][s] * scale[s]);
     }
   }
 }
@@ -336,6 +343,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 template <int BN>
@@ -352,7 +368,7 @@ struct OzShape {
 };
 
 template <int BN>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(320, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const OzParams p) {
   using S = OzShape<BN>;
   extern __shared__ uint8_t smem_raw[];
@@ -374,7 +390,7 @@ __global__ void __launch_bounds__(192, 1)
       mbar_init(&empty[s], 1);
     }
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 4);
+    mbar_init(acc_empty, 8);                 // one arrival per epilogue warp
     mbar_init(drain_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -431,6 +447,8 @@ __global__ void __launch_bounds__(192, 1)
       // ---------------- MMA issuer
       uint32_t step = 0, chunk = 0;
       const uint32_t id_pos = idesc_bf16(BN, false), id_neg = idesc_bf16(BN, true);
+      const uint64_t desc_a0 = sw32_desc(smem_u32(tiles));
+      const uint64_t desc_b0 = sw32_desc(smem_u32(tiles + kPlanes * S::kATile));
       bool ok = true;
       for (int tile = blockIdx.x; tile < total_tiles && ok; tile += gridDim.x) {
         for (int s = 0; s < p.nsteps && ok; ++s, ++step) {
@@ -443,8 +461,10 @@ __global__ void __launch_bounds__(192, 1)
           const uint32_t ph = (step / S::kStages) & 1;
           if (!mbar_wait(&full[st], ph, abort_flag, p.status, 13)) { ok = false; break; }
           tc_fence_after();
-          const __nv_bfloat16* sa = tiles + (size_t)st * S::kStageElems;
-          const __nv_bfloat16* sb = sa + kPlanes * S::kATile;
+          // descriptors of this stage: the start-address field (bits 0-13, address >> 4) of the
+          // stage-0 descriptors advanced by the byte offset >> 4 (shared memory < 256 KB: no carry)
+          const uint64_t sa = desc_a0 + (uint64_t)((st * S::kStageBytes) >> 4);
+          const uint64_t sb = desc_b0 + (uint64_t)((st * S::kStageBytes) >> 4);
           // products (i, j) with i + j <= 3, accumulated by order: 0, 1, and 2-3
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
@@ -456,10 +476,10 @@ __global__ void __launch_bounds__(192, 1)
               const uint32_t d_im = tmem + (uint32_t)((2 * acc + 1) * BN);
               // first write of each accumulator pair in a chunk: (0,0), (0,1) and (0,2) in loop order
               const bool first = chunk_start && i == 0 && jj == acc;
-              const uint64_t ar = sw32_desc(smem_u32(sa + (2 * i) * S::kATile));
-              const uint64_t ai = sw32_desc(smem_u32(sa + (2 * i + 1) * S::kATile));
-              const uint64_t br = sw32_desc(smem_u32(sb + (2 * jj) * S::kBTile));
-              const uint64_t bim = sw32_desc(smem_u32(sb + (2 * jj + 1) * S::kBTile));
+              const uint64_t ar = sa + (uint64_t)(((2 * i) * S::kATile * 2) >> 4);
+              const uint64_t ai = sa + (uint64_t)(((2 * i + 1) * S::kATile * 2) >> 4);
+              const uint64_t br = sb + (uint64_t)(((2 * jj) * S::kBTile * 2) >> 4);
+              const uint64_t bim = sb + (uint64_t)(((2 * jj + 1) * S::kBTile * 2) >> 4);
               mma_bf16(d_re, ar, br, id_pos, first ? 0u : 1u);
               mma_bf16(d_re, ai, bim, id_neg, 1u);
               mma_bf16(d_im, ar, bim, id_pos, first ? 0u : 1u);
@@ -480,37 +500,54 @@ __global__ void __launch_bounds__(192, 1)
       }
     }
   } else {
-    // ---------------- epilogue: warps 2..5, TMEM lane quarter = warp % 4
+    // ---------------- epilogue: warps 2..9; TMEM lane quarter = warp % 4, column half = (warp - 2) / 4
     const int quarter = warp & 3;
+    const int half = (warp - 2) >> 2;
+    constexpr int kHalf = BN / 2;
     uint32_t chunk = 0;
     for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
       const int b = tile / tiles_per_batch, mt = (tile % tiles_per_batch) / p.ntiles, nt = tile % p.ntiles;
       const int bo = b / p.bin, bi = b % p.bin;
       double2* C = p.C + (p.bc.tab ? p.bc.tab[bi] : (long long)bi * p.bc.bs_in) + (long long)bo * p.bc.bs_out;
-      const int row = mt * kBM + quarter * 32 + lane;
+      const int lrow = quarter * 32 + lane;           // TMEM lane = row within the tile
+      const int row = mt * kBM + lrow;
       const bool row_ok = row < p.M;
       const long long roff = row_ok ? s_view_row(p.vc, row) : 0;
       const int nchunks = (p.nsteps + p.steps_per_chunk - 1) / p.steps_per_chunk;
+      // running sums, column-major per CTA so that a warp's 32 rows of one column are contiguous
+      float4* wcol = p.ws + (size_t)blockIdx.x * BN * kBM + lrow;
       bool ok = true;
       for (int c = 0; c < nchunks; ++c, ++chunk) {
         if (!mbar_wait(acc_full, chunk & 1, abort_flag, p.status, 14)) { ok = false; break; }
         tc_fence_after();
         const bool last = c == nchunks - 1;
-        float4* wrow = p.ws + ((size_t)blockIdx.x * kBM + (size_t)(quarter * 32 + lane)) * BN;
+        const bool need_prev = nchunks > 1 && c > 0 && row_ok;
 #pragma unroll 1
-        for (int cb = 0; cb < BN; cb += 16) {
-          float mr[16], mi[16], ar[16], ai[16], br[16], bi[16];
+        for (int cb = half * kHalf; cb < (half + 1) * kHalf; cb += 8) {
+          // running sums of the previous chunks, in flight while the accumulators are read
+          float4 prev[8];
+          if (need_prev) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) prev[u] = wcol[(size_t)(cb + u) * kBM];
+          }
+          float mr[8], mi[8], ar[8], ai[8], br[8], bi[8];
           const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cb;
-          tmem_ld16(lane_addr + 0 * BN, mr);
-          tmem_ld16(lane_addr + 1 * BN, mi);
-          tmem_ld16(lane_addr + 2 * BN, ar);
-          tmem_ld16(lane_addr + 3 * BN, ai);
-          tmem_ld16(lane_addr + 4 * BN, br);
-          tmem_ld16(lane_addr + 5 * BN, bi);
+          tmem_ld8(lane_addr + 0 * BN, mr);
+          tmem_ld8(lane_addr + 1 * BN, mi);
+          tmem_ld8(lane_addr + 2 * BN, ar);
+          tmem_ld8(lane_addr + 3 * BN, ai);
+          tmem_ld8(lane_addr + 4 * BN, br);
+          tmem_ld8(lane_addr + 5 * BN, bi);
           tmem_wait_ld();
+          if (cb + 8 >= (half + 1) * kHalf) {
+            // this warp's accumulator columns of the chunk are in registers: release TMEM
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty);
+          }
           if (row_ok) {
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
+            for (int u = 0; u < 8; ++u) {
               const int n = nt * BN + cb + u;
               if (n < p.N) {
                 // the chunk value: orders 0 and 1 are exact, so their sum is exact as a pair
@@ -519,17 +556,13 @@ __global__ void __launch_bounds__(192, 1)
                 rl = __fadd_rn(rl, br[u]);
                 two_sum(mi[u], ai[u], ih, il);
                 il = __fadd_rn(il, bi[u]);
-                if (nchunks > 1) {
-                  float4* w = wrow + cb + u;
-                  if (c > 0) {
-                    const float4 o = *w;
-                    df_add(rh, rl, o.x, o.y);
-                    df_add(ih, il, o.z, o.w);
-                  }
-                  if (!last) {
-                    *w = make_float4(rh, rl, ih, il);
-                    continue;
-                  }
+                if (need_prev) {
+                  df_add(rh, rl, prev[u].x, prev[u].y);
+                  df_add(ih, il, prev[u].z, prev[u].w);
+                }
+                if (nchunks > 1 && !last) {
+                  wcol[(size_t)(cb + u) * kBM] = make_float4(rh, rl, ih, il);
+                  continue;
                 }
                 double2* dst = C + roff + (long long)(n / p.vc.kin) * p.vc.ks_out + (long long)(n % p.vc.kin) * p.vc.ks_in;
                 if (p.out_df) {
@@ -548,9 +581,6 @@ __global__ void __launch_bounds__(192, 1)
             }
           }
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(acc_empty);
       }
       if (!ok) break;
     }
@@ -621,7 +651,10 @@ int launch_slice(const SliceJob& j, cudaStream_t st) {
   const long long blocks = (warps + 7) / 8;
   if (blocks > 2147483647LL) return fail(GW_EINVAL, "slice: too many rows");
   prof_begin(SLOT_LIMBS, st);
-  slice_kernel<<<(unsigned)blocks, 256, 0, st>>>(j);
+  if (j.src_df)
+    slice_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(j);
+  else
+    slice_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(j);
   prof_end(SLOT_LIMBS, st, 0.0, (double)warps * j.Kc * (16.0 + 16.0));
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "slice launch: %s", cudaGetErrorString(e));
@@ -655,7 +688,7 @@ int launch_oz(const Planes& A, const Planes& B, OzParams p, int slot, cudaStream
   }
   const int grid = (int)std::min<long long>(total, g_num_sms);
   prof_begin(slot, st);
-  oz_gemm_kernel<BN><<<grid, 192, S::kSmem, st>>>(ma, mb, p);
+  oz_gemm_kernel<BN><<<grid, 320, S::kSmem, st>>>(ma, mb, p);
   // executed bf16 tensor flops: 10 slice products x 4 real products per complex multiply-add
   prof_end(slot, st, 2.0 * 40.0 * (double)total * kBM * BN * (double)p.nsteps * kStepK,
            (double)total * p.nsteps * S::kStageBytes);
