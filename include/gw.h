@@ -196,6 +196,31 @@ int gw_profile_slots(void);
 int gw_profile_read(gw_ctx* ctx, int slot, char* name, int name_cap, long long* launches,
                     double* total_ms, double* flops, double* bytes);
 
+/*
+ * P0(tau) of gw_polarization (FP64) for callers that cannot allocate device
+ * memory when they call: code inside a CUDA-graph capture, where cudaMalloc
+ * cannot be recorded, or a host whose device memory budget is already handed
+ * out to its own pools. This entry point has no counterpart in the paper; it
+ * is an allocation-free form of step (a).
+ *
+ * Needs no context: sizes, spin factor, V_dev, G_dev and the output P0t_dev
+ * (layouts as above) are passed directly; work is queued on cuda_stream
+ * (a cudaStream_t, NULL = legacy default stream). The V.G intermediates live
+ * in one fixed 64 MiB device array inside the library, which every GPU that
+ * loads the library holds until the process exits. The call rejects, with
+ * GW_EINVAL and a message, problems whose one (tau, k) unit needs more than
+ * that array (2 * naux * nao^2 complex elements > 4 Mi).
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture. All calls share the
+ * one array, so calls whose work overlaps on the GPU (different streams or
+ * threads without ordering) race on it; order them on one stream. Nothing in
+ * the array needs to start at zero; P0t_dev is overwritten.
+ */
+int gw_polarization_noalloc(const int nk3[3], int nao, int naux, int ntau, double spin_factor,
+                            const gw_c128* V_dev, const gw_c128* G_dev, gw_c128* P0t_dev,
+                            void* cuda_stream);
+
 /* Waits for all work queued on the context's stream. */
 int gw_synchronize(gw_ctx* ctx);
 

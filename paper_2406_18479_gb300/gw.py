@@ -27,7 +27,7 @@ ABI_SYMBOLS = [
     "gw_workspace_bytes", "gw_set_coulomb", "gw_polarization", "gw_to_matsubara", "gw_to_tau",
     "gw_aux_dyson", "gw_screened_interaction", "gw_self_energy", "gw_sigma_eval", "gw_dyson_G",
     "gw_mix", "gw_synchronize", "gw_profile_enable", "gw_launch_count", "gw_profile_slots",
-    "gw_profile_read",
+    "gw_profile_read", "gw_polarization_noalloc",
 ]
 
 
@@ -77,6 +77,7 @@ def lib():
     L.gw_dyson_G.argtypes = [vp, vp, vp, vp]
     L.gw_mix.argtypes = [vp, vp, vp, d, ctypes.POINTER(d)]
     L.gw_synchronize.argtypes = [vp]
+    L.gw_polarization_noalloc.argtypes = [ctypes.POINTER(ctypes.c_int), i, i, i, d, vp, vp, vp, vp]
     L.gw_profile_enable.argtypes = [vp, i]
     L.gw_launch_count.argtypes = [vp]
     L.gw_launch_count.restype = ctypes.c_longlong
@@ -259,3 +260,18 @@ def gw_profile_read(ctx: gw_ctx) -> dict:
             out[name.value.decode()] = {"launches": n.value, "ms": ms.value, "flops": fl.value,
                                         "bytes": by.value}
     return out
+
+
+def gw_polarization_noalloc(nk3, nao, naux, ntau, spin_factor, V, G, P0t, stream=None):
+    """P0(tau) without a context or any device allocation (see include/gw.h).
+
+    The first call on a device must come before any stream capture; calls that
+    overlap on the GPU share the library's one scratch array and race.
+    """
+    import torch
+    nk = int(np.prod(nk3))
+    s = stream if stream is not None else torch.cuda.current_stream()
+    arr = (ctypes.c_int * 3)(*[int(x) for x in nk3])
+    _check(lib().gw_polarization_noalloc(arr, int(nao), int(naux), int(ntau), float(spin_factor),
+                                         _ptr(V, (nk, nk, naux, nao, nao)), _ptr(G, (nk, ntau, nao, nao)),
+                                         _ptr(P0t, (nk, ntau, naux, naux)), ctypes.c_void_p(s.cuda_stream)))
