@@ -318,7 +318,7 @@ def run_ours(args, rank, world, local_rank):
         achieved = d["flops"] / d["launches"] / (per_launch_ms * 1e-3) / 1e12
         peak = peaks["bf16_tflops_sustained"]
         peak_note = f"bf16 dense sustained ({peak_src})"
-    elif dname in ("limb_convert", "elementwise", "reduce"):
+    elif dname in ("slice_planes", "elementwise", "reduce"):
         bound, unit = "hbm", "GB/s"
         achieved = d["bytes"] / d["launches"] / (per_launch_ms * 1e-3) / 1e9
         peak = peaks["hbm_gbs"]

@@ -76,7 +76,7 @@ static thread_local Prof* t_prof = nullptr;
 const char* prof_slot_name(int slot) {
   static const char* names[SLOT_COUNT] = {
       "vg_fp64", "p0_gemm_fp64", "r_gemm_fp64", "sigma_gemm_fp64", "transform_fp64", "inverse_fp64",
-      "elementwise", "limb_convert", "vg_mixed", "p0_gemm_tc", "r_gemm_tc", "sigma_mixed", "reduce"};
+      "elementwise", "slice_planes", "vg_gemm_tc", "p0_gemm_tc", "r_gemm_tc", "sigma_gemm_tc", "reduce"};
   return (slot >= 0 && slot < SLOT_COUNT) ? names[slot] : "";
 }
 
@@ -127,6 +127,8 @@ struct gw_ctx {
   double2* work = nullptr;                // contraction intermediates, nt * 2 * nk * pair
   double2 *P0t = nullptr, *Pw = nullptr, *Pt = nullptr;
   double2* dyson_ws = nullptr;            // nk * nwf * nao2
+  std::vector<int> mq;                    // index of -q for every q
+  int* mq_dev = nullptr;
   int* status = nullptr;                  // device flags: [0] singular matrix
   double* maxdiff = nullptr;
   int* nonfinite = nullptr;
@@ -173,7 +175,7 @@ int cuda_check(const char* what) {
 void free_ctx(gw_ctx* c) {
   if (!c) return;
   mixed_destroy(c->mixed);
-  void* ptrs[] = {c->Fb, c->Bb, c->Ff, c->Bf, c->wf, c->tabs, c->work, c->P0t, c->Pw,
+  void* ptrs[] = {c->Fb, c->Bb, c->Ff, c->Bf, c->wf, c->tabs, c->mq_dev, c->work, c->P0t, c->Pw,
                   c->Pt, c->dyson_ws, c->status, c->maxdiff, c->nonfinite};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -201,12 +203,17 @@ int upload_grid(gw_ctx* c, int stat, double2** F, double2** B, int* nw_out) {
 
 // ---- FP64 stages ------------------------------------------------------------------------
 
+// Canonical tau range of q: all nodes if q < -q, the first half if q = -q, none if q > -q;
+// the rest follows from P0^q(beta - tau) = P0^{-q}(tau)^T (mirror_fill).
+int canonical_end(const gw_ctx* c, int q, int T) { return c->mq[q] < q ? 0 : (c->mq[q] == q ? (T + 1) / 2 : T); }
+
 int polarization_fp64(gw_ctx* c, const double2* G, double2* P0t) {
   const int nk = c->nk, nao = c->nao, naux = c->naux, ntau = c->ntau;
   const long long nao2 = c->nao2, pair = c->pair;
   for (int q = 0; q < nk; ++q) {
-    for (int t0 = 0; t0 < ntau; t0 += c->nt) {
-      const int nt = std::min(c->nt, ntau - t0);
+    const int tend = canonical_end(c, q, ntau);
+    for (int t0 = 0; t0 < tend; t0 += c->nt) {
+      const int nt = std::min(c->nt, tend - t0);
       double2* Abuf = c->work;
       double2* Bbuf = c->work + (long long)c->nt * nk * pair;
       {  // A^Q_{db}(k,t) = sum_a V^{k,k+q}_da(Q) G^{k+q}_ab(t)
@@ -315,6 +322,22 @@ int transform(gw_ctx* c, int stat, bool forward, const double2* in, double2* out
   return GW_OK;
 }
 
+// Rows [row0, row0 + nrows) of the transform of the q-th block.
+int transform_q(gw_ctx* c, int stat, bool forward, const double2* in, double2* out, int q, int row0, int nrows,
+                long long nelem) {
+  const int nw = stat == 0 ? c->nwb : c->nwf;
+  const int nin = forward ? c->ntau : nw, nout = forward ? nw : c->ntau;
+  const double2* Mtx = forward ? (stat == 0 ? c->Fb : c->Ff) : (stat == 0 ? c->Bb : c->Bf);
+  if (nrows <= 0) return GW_OK;
+  ZGemm g;
+  g.M = nrows; g.N = (int)nelem; g.K = nin; g.nbatch = 1;
+  g.A = Mtx + (long long)row0 * nin; g.va.rs_in = nin; g.va.ks_in = 1;
+  g.B = in + (long long)q * nin * nelem; g.vb.rs_in = 1; g.vb.ks_in = nelem;
+  g.C = out + ((long long)q * nout + row0) * nelem; g.vc.rs_in = nelem; g.vc.ks_in = 1;
+  g.slot = SLOT_TRANSFORM_FP64;
+  return zgemm_fp64(g, c->stream);
+}
+
 int aux_dyson(gw_ctx* c, const double2* P0w, double2* Pw) {
   const long long n2 = c->naux2;
   const int nb = c->nk * c->nwb;
@@ -333,6 +356,27 @@ int screened(gw_ctx* c, const double2* P0t, double2* Pt) {
   GW_TRY(aux_dyson(c, c->Pw, c->Pw));
   GW_TRY(transform(c, 0, false, c->Pw, Pt, c->nk, c->naux2));
   return GW_OK;
+}
+
+// The same for a P0t that satisfies P0^q(beta - tau) = P0^{-q}(tau)^T exactly (as gw_polarization
+// writes it). Then P0^q(i W_n) = P0^{-q}(-i W_n)^T, the aux Dyson equation commutes with the
+// transpose, and P~ inherits both relations: only canonical (q, n) and (q, t) are computed,
+// the rest is filled by transposition. The frequency samples are symmetric (index j <-> nw-1-j).
+int screened_sym(gw_ctx* c, const double2* P0t, double2* Pt) {
+  const long long n2 = c->naux2;
+  for (int q = 0; q < c->nk; ++q) {
+    if (c->mq[q] < q) continue;
+    GW_TRY(transform_q(c, 0, true, P0t, c->Pw, q, 0, c->nwb, n2));
+    const int nb = canonical_end(c, q, c->nwb);
+    double2* blk = c->Pw + (long long)q * c->nwb * n2;
+    GW_TRY(add_identity_fp64(blk, c->naux, n2, nb, -1.0, 1.0, c->stream));   // I - P0
+    GW_TRY(batched_inverse_fp64(blk, c->naux, n2, nb, c->status, c->stream));
+    GW_TRY(add_identity_fp64(blk, c->naux, n2, nb, 1.0, -1.0, c->stream));   // (I - P0)^-1 - I
+  }
+  GW_TRY(mirror_fill(c->Pw, c->nk, c->nwb, c->naux, c->mq_dev, c->stream));
+  for (int q = 0; q < c->nk; ++q)
+    GW_TRY(transform_q(c, 0, false, c->Pw, Pt, q, 0, canonical_end(c, q, c->ntau), n2));
+  return mirror_fill(Pt, c->nk, c->ntau, c->naux, c->mq_dev, c->stream);
 }
 
 }  // namespace
@@ -398,6 +442,10 @@ int gw_create(gw_ctx** out, const gw_config* cfg, void* cuda_stream) {
     c->tab_kkmq = c->tabs + 3 * s;
     c->tab_kmqk = c->tabs + 4 * s;
     c->tab_gkmq = c->tabs + 5 * s;
+    c->mq.resize(nk);
+    for (int q = 0; q < nk; ++q) c->mq[q] = kshift(cfg->nk, 0, q, -1);
+    if ((rc = dev_alloc(c, &c->mq_dev, nk)) != GW_OK) break;
+    cudaMemcpy(c->mq_dev, c->mq.data(), nk * sizeof(int), cudaMemcpyHostToDevice);
     // tau chunk: intermediates of 2 * nk * pair complex per tau node, capped at 4 GiB
     const double per_t = 2.0 * nk * (double)c->pair * sizeof(double2);
     int nt = cfg->tau_chunk > 0 ? cfg->tau_chunk : (int)std::max(1.0, std::floor(4294967296.0 / per_t));
@@ -418,6 +466,7 @@ int gw_create(gw_ctx** out, const gw_config* cfg, void* cuda_stream) {
       d.nk3[0] = cfg->nk[0]; d.nk3[1] = cfg->nk[1]; d.nk3[2] = cfg->nk[2];
       d.nk = nk; d.nao = c->nao; d.naux = c->naux; d.ntau = c->ntau; d.precision = cfg->precision;
       d.tau_chunk = cfg->tau_chunk;
+      d.mq = c->mq;
       if ((rc = mixed_create(&c->mixed, d, c->stream, c->status, &c->bytes)) != GW_OK) break;
     }
     rc = cuda_check("gw_create");
@@ -453,8 +502,12 @@ int gw_polarization(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* P0t_dev) {
   if (!ctx->V) return fail(GW_EINVAL, "gw_polarization: call gw_set_coulomb first");
   const double2* G = reinterpret_cast<const double2*>(G_dev);
   double2* P = reinterpret_cast<double2*>(P0t_dev);
-  if (ctx->mixed) return mixed_polarization(ctx->mixed, G, P, ctx->cfg.spin_factor);
-  return polarization_fp64(ctx, G, P);
+  // only canonical (q, tau) are contracted; the rest is P0^q(beta - tau) = P0^{-q}(tau)^T
+  if (ctx->mixed)
+    GW_TRY(mixed_polarization(ctx->mixed, G, P, ctx->cfg.spin_factor));
+  else
+    GW_TRY(polarization_fp64(ctx, G, P));
+  return mirror_fill(P, ctx->nk, ctx->ntau, ctx->naux, ctx->mq_dev, ctx->stream);
 }
 
 int gw_to_matsubara(gw_ctx* ctx, int stat, const gw_c128* in_dev, gw_c128* out_dev, int nbatch,
@@ -501,7 +554,7 @@ int gw_sigma_eval(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* Sig_dev) {
   ProfScope _ps(ctx ? &ctx->prof : nullptr);
   if (!ctx || !G_dev || !Sig_dev) return fail(GW_EINVAL, "gw_sigma_eval: null argument");
   GW_TRY(gw_polarization(ctx, G_dev, reinterpret_cast<gw_c128*>(ctx->P0t)));
-  GW_TRY(screened(ctx, ctx->P0t, ctx->Pt));
+  GW_TRY(screened_sym(ctx, ctx->P0t, ctx->Pt));
   return gw_self_energy(ctx, G_dev, reinterpret_cast<const gw_c128*>(ctx->Pt), Sig_dev);
 }
 

@@ -79,6 +79,11 @@ int add_identity_fp64(double2* base, int n, long long stride, int nbatch, double
 int build_g_dyson_fp64(double2* sw, const double2* H, const double* wn, double mu, int nk, int nw,
                        int nao, void* stream);
 
+// Index pairs related by P0^q(beta - tau) = P0^{-q}(tau)^T (and the same for the frequency
+// samples, which are symmetric): X[q][t] <- X[mq[q]][T-1-t]^T for every (q, t) that is not
+// canonical; canonical (q, t): q < mq[q], or q == mq[q] and t <= T-1-t. X is [nk][T][n][n].
+int mirror_fill(double2* X, int nk, int T, int n, const int* mq_dev, void* stream);
+
 // Sig_inout = alpha*new + (1-alpha)*old; *maxdiff (device double) = max |change|; nonfinite flag
 int mix_fp64(const double2* s_new, double2* s_inout, double alpha, long long n, double* maxdiff_dev,
              int* nonfinite_dev, void* stream);

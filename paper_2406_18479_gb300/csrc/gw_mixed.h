@@ -3,12 +3,14 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <vector>
 
 namespace gwi {
 
 struct MixedDims {
   int nk3[3] = {1, 1, 1};
   int nk = 1, nao = 0, naux = 0, ntau = 0, precision = 0, tau_chunk = 0;
+  std::vector<int> mq;    // index of -q for every q
 };
 
 struct MixedState;

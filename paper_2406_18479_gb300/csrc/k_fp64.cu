@@ -270,6 +270,37 @@ __global__ void mix_kernel(const double2* s_new, double2* s_inout, double alpha,
   if (bad) atomicExch(nonfinite, 1);
 }
 
+// X[q][t] = X[mq[q]][T-1-t]^T for the (q, t) that are not canonical, where
+// canonical means q < mq[q], or q == mq[q] and t <= T-1-t. One 32x32 tile per block.
+__global__ void __launch_bounds__(256) mirror_fill_kernel(double2* X, int nk, int T, int n, const int* mq) {
+  __shared__ double2 tile[32][33];
+  const int tiles_1d = (n + 31) / 32;
+  long long b = blockIdx.x;
+  const int tj = (int)(b % tiles_1d);
+  b /= tiles_1d;
+  const int ti = (int)(b % tiles_1d);
+  b /= tiles_1d;
+  const int t = (int)(b % T);
+  const int q = (int)(b / T);
+  const int p = mq[q];
+  const bool canonical = q < p || (q == p && t <= T - 1 - t);
+  if (canonical) return;
+  const long long nn = (long long)n * n;
+  const double2* src = X + ((long long)p * T + (T - 1 - t)) * nn;
+  double2* dst = X + ((long long)q * T + t) * nn;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  // read src rows tj*32.., columns ti*32.. (coalesced), write dst rows ti*32.., columns tj*32..
+  for (int r = ty; r < 32; r += 8) {
+    const int i = tj * 32 + r, j = ti * 32 + tx;
+    if (i < n && j < n) tile[r][tx] = src[(long long)i * n + j];
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int i = ti * 32 + r, j = tj * 32 + tx;
+    if (i < n && j < n) dst[(long long)i * n + j] = tile[tx][r];
+  }
+}
+
 inline int grid_for(long long total, int block) {
   long long g = (total + block - 1) / block;
   if (g > 152LL * 32) g = 152LL * 32;
@@ -330,6 +361,18 @@ int build_g_dyson_fp64(double2* sw, const double2* H, const double* wn, double m
   prof_end(SLOT_ELEMENTWISE, (cudaStream_t)stream, 4.0 * total, 32.0 * total);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "build_g_dyson launch: %s", cudaGetErrorString(e));
+}
+
+int mirror_fill(double2* X, int nk, int T, int n, const int* mq_dev, void* stream) {
+  const long long tiles_1d = (n + 31) / 32;
+  const long long blocks = (long long)nk * T * tiles_1d * tiles_1d;
+  if (blocks == 0) return GW_OK;
+  if (blocks > 2147483647LL) return fail(GW_EINVAL, "mirror_fill: too many blocks");
+  prof_begin(SLOT_ELEMENTWISE, (cudaStream_t)stream);
+  mirror_fill_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(X, nk, T, n, mq_dev);
+  prof_end(SLOT_ELEMENTWISE, (cudaStream_t)stream, 0.0, 16.0 * (double)nk * T * n * n);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "mirror_fill launch: %s", cudaGetErrorString(e));
 }
 
 int mix_fp64(const double2* s_new, double2* s_inout, double alpha, long long n, double* maxdiff_dev,

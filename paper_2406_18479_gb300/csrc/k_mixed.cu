@@ -18,7 +18,7 @@
 // about 1/64 of the FP32 rate on this part, so no FP64 instruction runs per
 // chunk); the last chunk writes FP64, or double-float for intermediates that
 // are sliced again. Complex products use four real MMAs per slice pair (the
-// A-imaginary one negated by the instruction descriptor).
+// B-imaginary operand of the A_im B_im product negated by the instruction descriptor).
 //
 // Kernels
 //   slice_kernel   FP64 or double-float complex view -> 8 bf16 planes [slice*2 + re/im][row][Kpad]
@@ -310,12 +310,13 @@ __device__ __forceinline__ uint64_t sw32_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor for kind::f16: D f32, A and B bf16, both K-major, M = 128.
-__host__ __device__ constexpr uint32_t idesc_bf16(int n, bool neg_a) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((neg_a ? 1u : 0u) << 13) | ((uint32_t)(n >> 3) << 17) |
+// Instruction descriptor for kind::f16: D f32, A and B bf16, both K-major, M = 128; optionally B negated.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n, bool neg_b) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((neg_b ? 1u : 0u) << 14) | ((uint32_t)(n >> 3) << 17) |
          ((uint32_t)(kBM >> 4) << 24);
 }
 
+// D (TMEM) (+)= A (shared memory, descriptor) * B (shared memory, descriptor)^T
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accum) {
   asm volatile(
@@ -363,7 +364,7 @@ struct OzShape {
   static constexpr uint32_t kStageBytes = kStageElems * 2;
   static constexpr int kAccCols = 6 * BN;        // (order 0, order 1, orders 2-3) x (re, im)
   static_assert(kAccCols <= 512, "six accumulators of BN columns must fit in TMEM");
-  static constexpr int kTmemCols = kAccCols <= 32 ? 32 : (kAccCols <= 64 ? 64 : (kAccCols <= 128 ? 128 : (kAccCols <= 256 ? 256 : 512)));
+  static constexpr int kTmemCols = kAccCols <= 128 ? 128 : (kAccCols <= 256 ? 256 : 512);
   static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + 256;
 };
 
@@ -481,7 +482,7 @@ __global__ void __launch_bounds__(320, 1)
               const uint64_t br = sb + (uint64_t)(((2 * jj) * S::kBTile * 2) >> 4);
               const uint64_t bim = sb + (uint64_t)(((2 * jj + 1) * S::kBTile * 2) >> 4);
               mma_bf16(d_re, ar, br, id_pos, first ? 0u : 1u);
-              mma_bf16(d_re, ai, bim, id_neg, 1u);
+              mma_bf16(d_re, ai, bim, id_neg, 1u);             // - A_im B_im (B negated)
               mma_bf16(d_im, ar, bim, id_pos, first ? 0u : 1u);
               mma_bf16(d_im, ai, br, id_pos, 1u);
             }
@@ -1019,9 +1020,13 @@ int mixed_set_coulomb(MixedState* s, const double2* V) {
 
 int mixed_polarization(MixedState* s, const double2* G, double2* P0t, double spin_factor) {
   GW_TRY_INTERNAL(slice_g(s, G));
-  for (int q = 0; q < s->d.nk; ++q)
-    for (int t0 = 0; t0 < s->d.ntau; t0 += s->nt)
-      GW_TRY_INTERNAL(polarization_chunk(s, G, P0t, spin_factor, q, t0, std::min(s->nt, s->d.ntau - t0)));
+  for (int q = 0; q < s->d.nk; ++q) {
+    // canonical tau nodes only (the caller fills P0^q(beta - tau) = P0^{-q}(tau)^T)
+    const int mq = s->d.mq[q];
+    const int tend = mq < q ? 0 : (mq == q ? (s->d.ntau + 1) / 2 : s->d.ntau);
+    for (int t0 = 0; t0 < tend; t0 += s->nt)
+      GW_TRY_INTERNAL(polarization_chunk(s, G, P0t, spin_factor, q, t0, std::min(s->nt, tend - t0)));
+  }
   return GW_OK;
 }
 
