@@ -129,6 +129,8 @@ struct gw_ctx {
   double2* dyson_ws = nullptr;            // nk * nwf * nao2
   std::vector<int> mq;                    // index of -q for every q
   int* mq_dev = nullptr;
+  int* wlist = nullptr;                   // canonical (q, n) matrices of P~(i Omega), as q * nwb + n
+  int nwlist = 0;
   int* status = nullptr;                  // device flags: [0] singular matrix
   double* maxdiff = nullptr;
   int* nonfinite = nullptr;
@@ -175,7 +177,7 @@ int cuda_check(const char* what) {
 void free_ctx(gw_ctx* c) {
   if (!c) return;
   mixed_destroy(c->mixed);
-  void* ptrs[] = {c->Fb, c->Bb, c->Ff, c->Bf, c->wf, c->tabs, c->mq_dev, c->work, c->P0t, c->Pw,
+  void* ptrs[] = {c->Fb, c->Bb, c->Ff, c->Bf, c->wf, c->tabs, c->mq_dev, c->wlist, c->work, c->P0t, c->Pw,
                   c->Pt, c->dyson_ws, c->status, c->maxdiff, c->nonfinite};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -367,12 +369,11 @@ int screened_sym(gw_ctx* c, const double2* P0t, double2* Pt) {
   for (int q = 0; q < c->nk; ++q) {
     if (c->mq[q] < q) continue;
     GW_TRY(transform_q(c, 0, true, P0t, c->Pw, q, 0, c->nwb, n2));
-    const int nb = canonical_end(c, q, c->nwb);
-    double2* blk = c->Pw + (long long)q * c->nwb * n2;
-    GW_TRY(add_identity_fp64(blk, c->naux, n2, nb, -1.0, 1.0, c->stream));   // I - P0
-    GW_TRY(batched_inverse_fp64(blk, c->naux, n2, nb, c->status, c->stream));
-    GW_TRY(add_identity_fp64(blk, c->naux, n2, nb, 1.0, -1.0, c->stream));   // (I - P0)^-1 - I
   }
+  // all canonical (q, n) matrices in one launch each
+  GW_TRY(add_identity_fp64(c->Pw, c->naux, n2, c->nwlist, -1.0, 1.0, c->stream, c->wlist));   // I - P0
+  GW_TRY(batched_inverse_fp64(c->Pw, c->naux, n2, c->nwlist, c->status, c->stream, c->wlist));
+  GW_TRY(add_identity_fp64(c->Pw, c->naux, n2, c->nwlist, 1.0, -1.0, c->stream, c->wlist));    // (I - P0)^-1 - I
   GW_TRY(mirror_fill(c->Pw, c->nk, c->nwb, c->naux, c->mq_dev, c->stream));
   for (int q = 0; q < c->nk; ++q)
     GW_TRY(transform_q(c, 0, false, c->Pw, Pt, q, 0, canonical_end(c, q, c->ntau), n2));
@@ -446,6 +447,14 @@ int gw_create(gw_ctx** out, const gw_config* cfg, void* cuda_stream) {
     for (int q = 0; q < nk; ++q) c->mq[q] = kshift(cfg->nk, 0, q, -1);
     if ((rc = dev_alloc(c, &c->mq_dev, nk)) != GW_OK) break;
     cudaMemcpy(c->mq_dev, c->mq.data(), nk * sizeof(int), cudaMemcpyHostToDevice);
+    {
+      std::vector<int> wl;
+      for (int q = 0; q < nk; ++q)
+        for (int n = 0; n < canonical_end(c, q, c->nwb); ++n) wl.push_back(q * c->nwb + n);
+      c->nwlist = (int)wl.size();
+      if ((rc = dev_alloc(c, &c->wlist, wl.size())) != GW_OK) break;
+      cudaMemcpy(c->wlist, wl.data(), wl.size() * sizeof(int), cudaMemcpyHostToDevice);
+    }
     // tau chunk: intermediates of 2 * nk * pair complex per tau node, capped at 4 GiB
     const double per_t = 2.0 * nk * (double)c->pair * sizeof(double2);
     int nt = cfg->tau_chunk > 0 ? cfg->tau_chunk : (int)std::max(1.0, std::floor(4294967296.0 / per_t));

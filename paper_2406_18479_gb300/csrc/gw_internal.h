@@ -68,12 +68,13 @@ int zgemm_fp64(const ZGemm& g, void* stream);
 // In-place Gauss-Jordan inversion with partial pivoting of nbatch n x n matrices
 // (matrix b at base + b * stride). diag_shift: before inverting, M <- diag_sign*M + shift(b)*I
 // is applied by the callers' build kernels instead; here only the inversion.
+// list (optional, device): the matrix indices to process, nbatch of them.
 int batched_inverse_fp64(double2* base, int n, long long stride, int nbatch, int* status_dev,
-                         void* stream);
+                         void* stream, const int* list = nullptr);
 
 // Aux Dyson pieces: M <- I - M; and after inversion M <- M - I.
 int add_identity_fp64(double2* base, int n, long long stride, int nbatch, double scale_m,
-                      double shift, void* stream);
+                      double shift, void* stream, const int* list = nullptr);
 
 // G Dyson build: A[k][n] = (i w_n + mu) I - H[k] - Sw[k][n]   (in place over Sw)
 int build_g_dyson_fp64(double2* sw, const double2* H, const double* wn, double mu, int nk, int nw,

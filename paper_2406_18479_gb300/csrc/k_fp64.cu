@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(256) zgemm_fp64_kernel(const ZGemm g) {
 // One block per matrix; the matrix stays in global memory (L2), the pivot
 // column and the scaled pivot row in shared memory.
 __global__ void __launch_bounds__(256) gj_inverse_kernel(double2* base, int n, long long stride,
-                                                         int* status) {
+                                                         const int* list, int* status) {
   extern __shared__ double2 sm[];
   double2* f = sm;
   double2* row = sm + n;
@@ -135,7 +135,7 @@ __global__ void __launch_bounds__(256) gj_inverse_kernel(double2* base, int n, l
   __shared__ int red_i[8];
   __shared__ int s_p;
   __shared__ int s_bad;
-  double2* M = base + (long long)blockIdx.x * stride;
+  double2* M = base + (long long)(list ? list[blockIdx.x] : (int)blockIdx.x) * stride;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) s_bad = 0;
 
@@ -213,13 +213,14 @@ __global__ void __launch_bounds__(256) gj_inverse_kernel(double2* base, int n, l
   }
 }
 
-__global__ void add_identity_kernel(double2* base, int n, long long stride, int nbatch,
+__global__ void add_identity_kernel(double2* base, int n, long long stride, int nbatch, const int* list,
                                     double scale_m, double shift) {
   const long long nn = (long long)n * n;
   const long long total = nn * nbatch;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
-    const long long b = e / nn, r = e % nn;
+    const long long bl = e / nn, r = e % nn;
+    const long long b = list ? list[bl] : bl;
     double2* p = base + b * stride + r;
     double2 v = *p;
     v.x *= scale_m;
@@ -324,7 +325,7 @@ int zgemm_fp64(const ZGemm& g, void* stream) {
 }
 
 int batched_inverse_fp64(double2* base, int n, long long stride, int nbatch, int* status_dev,
-                         void* stream) {
+                         void* stream, const int* list) {
   if (nbatch <= 0) return GW_OK;
   const size_t smem = 2 * (size_t)n * sizeof(double2) + (size_t)n * sizeof(int);
   if (smem > 200 * 1024) return fail(GW_EINVAL, "batched_inverse_fp64: n=%d too large", n);
@@ -334,7 +335,7 @@ int batched_inverse_fp64(double2* base, int n, long long stride, int nbatch, int
     attr_set = true;
   }
   prof_begin(SLOT_INVERSE_FP64, (cudaStream_t)stream);
-  gj_inverse_kernel<<<nbatch, 256, smem, (cudaStream_t)stream>>>(base, n, stride, status_dev);
+  gj_inverse_kernel<<<nbatch, 256, smem, (cudaStream_t)stream>>>(base, n, stride, list, status_dev);
   prof_end(SLOT_INVERSE_FP64, (cudaStream_t)stream, 8.0 * (double)n * n * n * nbatch,
            32.0 * (double)n * n * nbatch);
   const cudaError_t e = cudaGetLastError();
@@ -342,10 +343,10 @@ int batched_inverse_fp64(double2* base, int n, long long stride, int nbatch, int
 }
 
 int add_identity_fp64(double2* base, int n, long long stride, int nbatch, double scale_m,
-                      double shift, void* stream) {
+                      double shift, void* stream, const int* list) {
   const long long total = (long long)n * n * nbatch;
   prof_begin(SLOT_ELEMENTWISE, (cudaStream_t)stream);
-  add_identity_kernel<<<grid_for(total, 256), 256, 0, (cudaStream_t)stream>>>(base, n, stride, nbatch,
+  add_identity_kernel<<<grid_for(total, 256), 256, 0, (cudaStream_t)stream>>>(base, n, stride, nbatch, list,
                                                                               scale_m, shift);
   prof_end(SLOT_ELEMENTWISE, (cudaStream_t)stream, 2.0 * total, 32.0 * total);
   const cudaError_t e = cudaGetLastError();

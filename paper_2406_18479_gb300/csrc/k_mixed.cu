@@ -220,6 +220,10 @@ struct OzParams {
   double alpha = 1.0;
   int accumulate = 0;
   int out_df = 0;                     // 1: write double-float complex (float4) instead of FP64 (alpha 1, no accumulate)
+  // block-diagonal batching: each GEMM "batch" is a group of dgroup problems of dblock x dblock
+  // outputs stacked along rows and columns (M = N = dgroup * dblock); only diagonal blocks are
+  // written, problem index b * dgroup + block, up to dtotal problems (0: off)
+  int dblock = 0, dgroup = 1, dtotal = 0;
   float4* ws = nullptr;               // per-CTA running sums across chunks, gridDim.x * 128 * BN
   int* status = nullptr;              // status[1] <- error code of a device-side wait that gave up
 };
@@ -508,11 +512,22 @@ __global__ void __launch_bounds__(320, 1)
     uint32_t chunk = 0;
     for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
       const int b = tile / tiles_per_batch, mt = (tile % tiles_per_batch) / p.ntiles, nt = tile % p.ntiles;
-      const int bo = b / p.bin, bi = b % p.bin;
-      double2* C = p.C + (p.bc.tab ? p.bc.tab[bi] : (long long)bi * p.bc.bs_in) + (long long)bo * p.bc.bs_out;
       const int lrow = quarter * 32 + lane;           // TMEM lane = row within the tile
-      const int row = mt * kBM + lrow;
-      const bool row_ok = row < p.M;
+      int row = mt * kBM + lrow;
+      bool row_ok = row < p.M;
+      // block-diagonal mode: the tile holds dgroup problems of dblock rows and columns; this
+      // row belongs to problem b * dgroup + row / dblock and only its own column block is kept
+      int dcol0 = 0;
+      int ob = b;
+      if (p.dblock) {
+        const int blk = row / p.dblock;
+        ob = b * p.dgroup + blk;
+        row_ok = row_ok && ob < p.dtotal;
+        dcol0 = blk * p.dblock;
+        row -= dcol0;
+      }
+      const int bo = ob / p.bin, bi = ob % p.bin;
+      double2* C = p.C + (p.bc.tab ? p.bc.tab[bi] : (long long)bi * p.bc.bs_in) + (long long)bo * p.bc.bs_out;
       const long long roff = row_ok ? s_view_row(p.vc, row) : 0;
       const int nchunks = (p.nsteps + p.steps_per_chunk - 1) / p.steps_per_chunk;
       // running sums, column-major per CTA so that a warp's 32 rows of one column are contiguous
@@ -549,7 +564,11 @@ __global__ void __launch_bounds__(320, 1)
           if (row_ok) {
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-              const int n = nt * BN + cb + u;
+              int n = nt * BN + cb + u;
+              if (p.dblock) {
+                n -= dcol0;
+                if (n < 0 || n >= p.dblock) continue;   // another problem's columns
+              }
               if (n < p.N) {
                 // the chunk value: orders 0 and 1 are exact, so their sum is exact as a pair
                 float rh, rl, ih, il;
@@ -908,14 +927,22 @@ int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double
     GW_TRY_INTERNAL(slice(s, s->y64, vz, s->pair, 0, 1 << 30, nt * nk, nao, naux * nao, ys, nao, 1));
   }
   OzParams p;                               // Sigma^k_ij(t) += -(1/N_k) sum_{Q,b} Z_{Q,i,b} R_{Q,b,j}
-  p.M = nao;
-  p.N = nao;
-  p.nbatch = nt * nk;
-  p.bin = nk;
-  p.a_bs_in = nao;
-  p.a_bs_out = (long long)nk * nao;
-  p.b_bs_in = nao;
-  p.b_bs_out = (long long)nk * nao;
+  // (t, k) problems of nao x nao are consecutive plane rows (t * nk + k) * nao; G of them share one
+  // block-diagonal tile, so one MMA of N = grp * nao does the work of grp narrow ones
+  const int grp = std::max(1, std::min(kBM, 80) / nao);
+  const int nprob = nt * nk;
+  p.M = grp * nao;
+  p.N = grp * nao;
+  p.nbatch = (nprob + grp - 1) / grp;
+  // group g = bo * nk + bi (bin = nk below) starts at plane row g * grp * nao
+  p.a_bs_in = (long long)grp * nao;
+  p.a_bs_out = (long long)nk * grp * nao;
+  p.b_bs_in = (long long)grp * nao;
+  p.b_bs_out = (long long)nk * grp * nao;
+  p.dblock = grp > 1 ? nao : 0;
+  p.dgroup = grp;
+  p.dtotal = nprob;
+  p.bin = nk;                               // output problem index -> (t, k) = (ob / nk, ob % nk)
   p.C = Sig + (long long)t0 * s->nao2;
   p.bc.bs_in = (long long)ntau * s->nao2;
   p.bc.bs_out = s->nao2;
@@ -925,7 +952,7 @@ int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double
   p.accumulate = 1;
   p.status = s->status;
   p.ws = s->ws;
-  return launch_oz<32>(xs, ys, p, SLOT_SIGMA_MIXED, s->stream);
+  return launch_oz<80>(xs, ys, p, SLOT_SIGMA_MIXED, s->stream);
 }
 
 }  // namespace
