@@ -9,6 +9,7 @@ beta=100), with V, G and all workspaces resident in HBM.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|fp16s|fp64]
     python bench.py --impl reference      # the FP64 CPU oracle on a bounded sample
+    python bench.py --serving [--serving-jobs N] [--precision P]   # scGW job stream alone
 
 Under torchrun (N > 1) every rank evaluates its own seeded system (weak
 scaling, no collective on the data path); the time is the maximum over ranks.
@@ -215,6 +216,75 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def job_flops(w):
+    """Algorithmic flops of one self-energy evaluation of a job (both contractions, symmetric count)."""
+    return 16.0 * w.nk ** 2 * w.ntau * (2.0 * w.naux * w.nao ** 3 + w.naux ** 2 * w.nao ** 2)
+
+
+def serving_measure(precision, n_jobs, slots=4, budget_gb=160.0, max_tflop=None, seed=5, alpha=0.5,
+                    tol=1e-6, itermax=10):
+    """scGW job stream through gw_submit / gw_poll.
+
+    Jobs are the first n_jobs of the seeded stream (70% molecules, 30% 2x2x2 / 3x3x3 solids,
+    naux = 4 nao, 80 tau nodes), optionally without those above max_tflop per evaluation. Two
+    passes over the same jobs: closed loop (all submitted at once) gives the capacity in jobs/s;
+    then an open loop with Poisson arrivals at 0.8 x that capacity gives the latency percentiles.
+    """
+    from paper_2406_18479_gb300 import gw, inputs as I
+    stream = I.serving_stream(n_jobs, seed)
+    if max_tflop is not None:
+        stream = [(gap, w) for gap, w in stream if job_flops(w) <= max_tflop * 1e12]
+    t_gen = time.perf_counter()
+    jobs = []
+    for gap, w in stream:
+        h, v, g = I.make_inputs(w)
+        cfg = gw.make_config(w.nk3, w.nao, w.naux, w.ntau, w.beta, mu=w.mu, precision=precision)
+        jobs.append((gap, w, cfg, h, v, g))
+    t_gen = time.perf_counter() - t_gen
+    srv = gw.gw_server(int(budget_gb * 2 ** 30), slots)
+
+    def run(gaps):
+        ids = []
+        t0 = time.perf_counter()
+        tnext = t0
+        for (gap, w, cfg, h, v, g), dt in zip(jobs, gaps):
+            tnext += dt
+            pause = tnext - time.perf_counter()
+            if pause > 0:
+                time.sleep(pause)
+            ids.append(srv.submit(cfg, h, v, g, alpha=alpha, tol=tol, itermax=itermax))
+        return [srv.poll(i, -1)[1] for i in ids]
+
+    try:
+        closed = run([0.0] * len(jobs))
+        span = max(r["t_end"] for r in closed) - min(r["t_submit"] for r in closed)
+        capacity = len(jobs) / span
+        rate = 0.8 * capacity
+        opened = run([gap / rate for gap, *_ in jobs])
+    finally:
+        srv.destroy()
+    lat = np.array([r["t_end"] - r["t_submit"] for r in opened])
+    wait = np.array([r["t_start"] - r["t_submit"] for r in opened])
+    ok = [r["status"] in (gw.GW_OK, gw.GW_ENOTCONV) for r in opened + closed]
+    span_o = max(r["t_end"] for r in opened) - min(r["t_submit"] for r in opened)
+    evals = sum(r["iterations"] for r in opened)
+    return {
+        "precision": precision, "jobs": len(jobs), "slots": slots, "hbm_budget_gb": budget_gb,
+        "sample": (f"first {n_jobs} jobs of the seeded stream (seed {seed})"
+                   + (f", jobs above {max_tflop} TFLOP per evaluation left out" if max_tflop else "")
+                   + f": {sum(1 for j in jobs if not j[1].solid)} molecules, "
+                   f"{sum(1 for j in jobs if j[1].solid)} solids"),
+        "alpha": alpha, "tol": tol, "itermax": itermax,
+        "capacity_jobs_per_s": capacity, "arrival_rate_jobs_per_s": rate,
+        "jobs_per_s": len(jobs) / span_o,
+        "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+        "p50_queue_s": float(np.percentile(wait, 50)),
+        "sigma_evals": evals, "converged": sum(1 for r in opened if r["status"] == gw.GW_OK),
+        "all_ok": all(ok), "tflop_per_eval_mean": float(np.mean([job_flops(j[1]) for j in jobs]) / 1e12),
+        "input_generation_s": t_gen,
+    }
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2406_18479_gb300 import gw, inputs as I
@@ -304,6 +374,10 @@ def run_ours(args, rank, world, local_rank):
             dist.destroy_process_group()
         return
 
+    serving = None
+    if world == 1 and args.serving_jobs > 0:
+        serving = serving_measure(args.precision, args.serving_jobs)
+
     nwb = gw.gw_sample_count(w.ntau, 0)
     flops = algorithmic_flops(w.nk, w.nao, w.naux, w.ntau, nwb)
     steps = args.steps
@@ -353,6 +427,8 @@ def run_ours(args, rank, world, local_rank):
     }
     if fp64 is not None:
         line["fp64"] = fp64
+    if serving is not None:
+        line["serving"] = serving
     if world == 1 and not args.no_cpu_baseline:
         val, sample, spent = oracle_sample(w, h, v, g, budget_s=args.ref_budget)
         line["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
@@ -361,6 +437,23 @@ def run_ours(args, rank, world, local_rank):
     ctx.destroy()
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_serving(args, rank, local_rank):
+    """One JSON line for the scGW job stream alone (rank 0; other ranks exit)."""
+    import torch
+    if rank != 0:
+        return
+    torch.cuda.set_device(local_rank)
+    n = args.serving_jobs if args.serving_jobs > 0 else 200
+    with ClockSampler(local_rank) as clk:
+        s = serving_measure(args.precision, n, slots=args.serving_slots, max_tflop=args.serving_max_tflop)
+    line = {"metric": "scGW jobs/s with p50/p99 latency (Poisson stream at 0.8 x capacity)",
+            "value": s["jobs_per_s"], "unit": "jobs/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": args.precision, "data": "synthetic (seeded molecules and solids)",
+            "config": {"workload": "scgw_job_stream", "jobs": s["jobs"], "precision": args.precision},
+            "serving": s, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
 
 
 def main():
@@ -376,6 +469,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--tau-chunk", type=int, default=0, help="tau nodes per contraction batch (0: automatic)")
+    ap.add_argument("--serving-jobs", type=int, default=12,
+                    help="jobs of the scGW stream measured beside the main line (0: none)")
+    ap.add_argument("--serving", action="store_true",
+                    help="measure only the scGW job stream and print its own line")
+    ap.add_argument("--serving-max-tflop", type=float, default=None,
+                    help="leave out stream jobs above this many TFLOP per evaluation")
+    ap.add_argument("--serving-slots", type=int, default=4)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -388,6 +488,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+    elif args.serving:
+        run_serving(args, rank, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -224,6 +224,62 @@ int gw_polarization_noalloc(const int nk3[3], int nao, int naux, int ntau, doubl
 /* Waits for all work queued on the context's stream. */
 int gw_synchronize(gw_ctx* ctx);
 
+/*
+ * Request loop for scGW jobs (self-consistency loop of Sec. 2.4 at fixed mu).
+ *
+ * A job runs, on its own CUDA stream and device buffers:
+ *   it = 1:  Sigma = Sigma[G0]                              (gw_sigma_eval)
+ *   it > 1:  Sigma <- alpha Sigma[G] + (1 - alpha) Sigma     (gw_mix, Sec. 5.3)
+ *   then     G = Dyson(H, Sigma)                            (gw_dyson_G, Eq. dyson)
+ * and stops when max |dSigma| < tol (it > 1) or after itermax evaluations.
+ *
+ * gw_server_create starts max_slots worker threads on the current device. A
+ * submitted job waits in arrival order until a slot is free and its device
+ * memory (gw_job_bytes) fits in what is left of hbm_budget; jobs are admitted
+ * while others run (continuous batching) and their kernels overlap on the GPU.
+ * A job computes exactly what it computes alone. The host buffers named in
+ * gw_job are borrowed until the job has finished (gw_poll returned GW_OK).
+ */
+typedef struct gw_server gw_server;
+
+typedef struct {
+  gw_config cfg;              /* sizes, beta, mu, spin factor, precision, tau chunk */
+  const gw_c128* H_host;      /* [nk][nao][nao] */
+  const gw_c128* V_host;      /* [nk][nk][naux][nao][nao] */
+  const gw_c128* G0_host;     /* [nk][ntau][nao][nao], the starting Green's function */
+  gw_c128* Sigma_out_host;    /* [nk][ntau][nao][nao] final Sigma, or NULL */
+  gw_c128* G_out_host;        /* [nk][ntau][nao][nao] final G, or NULL */
+  double alpha;               /* mixing weight in (0, 2) */
+  double tol;                 /* convergence threshold on max |dSigma| (Ha) */
+  int itermax;                /* self-energy evaluations at most, >= 1 */
+} gw_job;
+
+typedef struct {
+  int status;                 /* GW_OK, GW_ENOTCONV (itermax reached), or the failing call's status */
+  int iterations;             /* self-energy evaluations done */
+  double max_abs_dsigma;      /* last max |dSigma| (0 after a single evaluation) */
+  double t_submit, t_start, t_end;   /* seconds on the library's monotonic clock */
+} gw_job_result;
+
+/* Device bytes one job holds while it runs (0 for an invalid configuration). */
+size_t gw_job_bytes(const gw_config* cfg);
+
+/* GW_EINVAL for max_slots outside 1..64 or a zero budget. */
+int gw_server_create(gw_server** out, size_t hbm_budget, int max_slots);
+
+/* Finishes the running jobs, drops the waiting ones, joins the workers, frees everything. */
+int gw_server_destroy(gw_server* srv);
+
+/* Non-blocking. GW_ENOMEM if the job can never fit the budget. */
+int gw_submit(gw_server* srv, const gw_job* job, uint64_t* job_id);
+
+/*
+ * Result of a job. timeout_us = 0: does not wait (GW_EAGAIN while the job runs or
+ * waits); > 0: waits at most that long (GW_ETIMEOUT); < 0: waits until it finishes.
+ * GW_OK once the job has finished: *out then holds its status and timings.
+ */
+int gw_poll(gw_server* srv, uint64_t job_id, gw_job_result* out, int timeout_us);
+
 #ifdef __cplusplus
 }
 #endif

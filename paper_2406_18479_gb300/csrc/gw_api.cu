@@ -117,6 +117,7 @@ using namespace gwi;
 struct gw_ctx {
   gw_config cfg{};
   cudaStream_t stream = nullptr;
+  bool dry = false;                       // size-only build: count bytes, allocate and copy nothing
   int nk = 0, nao = 0, naux = 0, ntau = 0, nwb = 0, nwf = 0, nt = 1;
   long long nao2 = 0, naux2 = 0, pair = 0;
   double2 *Fb = nullptr, *Bb = nullptr, *Ff = nullptr, *Bf = nullptr;
@@ -154,6 +155,11 @@ int kshift(const int nk3[3], int k, int q, int sign) {
 template <class T>
 int dev_alloc(gw_ctx* c, T** p, size_t count) {
   if (count == 0) count = 1;
+  if (c->dry) {
+    *p = nullptr;
+    c->bytes += count * sizeof(T);
+    return GW_OK;
+  }
   const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -161,6 +167,11 @@ int dev_alloc(gw_ctx* c, T** p, size_t count) {
   }
   c->bytes += count * sizeof(T);
   return GW_OK;
+}
+
+// host -> device copy of a table; nothing in a size-only build
+void upload(const gw_ctx* c, void* dst, const void* src, size_t bytes) {
+  if (!c->dry) cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
 }
 
 int cuda_check(const char* what) {
@@ -191,16 +202,16 @@ int upload_grid(gw_ctx* c, int stat, double2** F, double2** B, int* nw_out) {
   GW_TRY(grid_build(c->ntau, c->cfg.beta, stat, nullptr, idx.data(), hF.data(), hB.data()));
   GW_TRY(dev_alloc(c, F, hF.size()));
   GW_TRY(dev_alloc(c, B, hB.size()));
-  cudaMemcpy(*F, hF.data(), hF.size() * sizeof(double2), cudaMemcpyHostToDevice);
-  cudaMemcpy(*B, hB.data(), hB.size() * sizeof(double2), cudaMemcpyHostToDevice);
+  upload(c, *F, hF.data(), hF.size() * sizeof(double2));
+  upload(c, *B, hB.data(), hB.size() * sizeof(double2));
   if (stat == 1) {
     std::vector<double> w(nw);
     for (int n = 0; n < nw; ++n) w[n] = (2.0 * (double)idx[n] + 1.0) * M_PI / c->cfg.beta;
     GW_TRY(dev_alloc(c, &c->wf, nw));
-    cudaMemcpy(c->wf, w.data(), nw * sizeof(double), cudaMemcpyHostToDevice);
+    upload(c, c->wf, w.data(), nw * sizeof(double));
   }
   *nw_out = nw;
-  return cuda_check("grid upload");
+  return c->dry ? GW_OK : cuda_check("grid upload");
 }
 
 // ---- FP64 stages ------------------------------------------------------------------------
@@ -398,17 +409,23 @@ int gw_grid_build(int ntau, double beta, int stat, double* tau_host, int64_t* id
   return grid_build(ntau, beta, stat, tau_host, idx_host, F_host, B_host);
 }
 
-int gw_create(gw_ctx** out, const gw_config* cfg, void* cuda_stream) {
-  if (!out || !cfg) return fail(GW_EINVAL, "gw_create: null argument");
-  *out = nullptr;
+}  // extern "C"
+
+namespace gwi {
+namespace {
+
+bool config_ok(const gw_config* cfg) {
+  const long long nk = (long long)cfg->nk[0] * cfg->nk[1] * cfg->nk[2];
+  return !(cfg->nk[0] < 1 || cfg->nk[1] < 1 || cfg->nk[2] < 1 || nk > 4096 || cfg->nao < 1 || cfg->nao > 512 ||
+           cfg->naux < 1 || cfg->naux > 4096 || cfg->ntau < 1 || cfg->ntau > 512 || !(cfg->beta > 0) ||
+           cfg->precision < GW_FP64 || cfg->precision > GW_MIXED_FP16S);
+}
+
+// Grids, gather tables and workspaces of a context; in a size-only build (c->dry)
+// the same sequence only sums the bytes it would allocate.
+int ctx_build(gw_ctx* c, const gw_config* cfg) {
   const int nk = cfg->nk[0] * cfg->nk[1] * cfg->nk[2];
-  if (cfg->nk[0] < 1 || cfg->nk[1] < 1 || cfg->nk[2] < 1 || nk > 4096 || cfg->nao < 1 || cfg->nao > 512 ||
-      cfg->naux < 1 || cfg->naux > 4096 || cfg->ntau < 1 || cfg->ntau > 512 || !(cfg->beta > 0) ||
-      cfg->precision < GW_FP64 || cfg->precision > GW_MIXED_FP16S)
-    return fail(GW_EINVAL, "gw_create: configuration out of range");
-  gw_ctx* c = new gw_ctx();
   c->cfg = *cfg;
-  c->stream = (cudaStream_t)cuda_stream;
   c->nk = nk;
   c->nao = cfg->nao;
   c->naux = cfg->naux;
@@ -435,7 +452,7 @@ int gw_create(gw_ctx** out, const gw_config* cfg, void* cuda_stream) {
         t[5 * s + i] = (long long)km * gk;
       }
     if ((rc = dev_alloc(c, &c->tabs, t.size())) != GW_OK) break;
-    cudaMemcpy(c->tabs, t.data(), t.size() * sizeof(long long), cudaMemcpyHostToDevice);
+    upload(c, c->tabs, t.data(), t.size() * sizeof(long long));
     const size_t s = (size_t)nk * nk;
     c->tab_kkpq = c->tabs;
     c->tab_kpqk = c->tabs + s;
@@ -446,14 +463,14 @@ int gw_create(gw_ctx** out, const gw_config* cfg, void* cuda_stream) {
     c->mq.resize(nk);
     for (int q = 0; q < nk; ++q) c->mq[q] = kshift(cfg->nk, 0, q, -1);
     if ((rc = dev_alloc(c, &c->mq_dev, nk)) != GW_OK) break;
-    cudaMemcpy(c->mq_dev, c->mq.data(), nk * sizeof(int), cudaMemcpyHostToDevice);
+    upload(c, c->mq_dev, c->mq.data(), nk * sizeof(int));
     {
       std::vector<int> wl;
       for (int q = 0; q < nk; ++q)
         for (int n = 0; n < canonical_end(c, q, c->nwb); ++n) wl.push_back(q * c->nwb + n);
       c->nwlist = (int)wl.size();
       if ((rc = dev_alloc(c, &c->wlist, wl.size())) != GW_OK) break;
-      cudaMemcpy(c->wlist, wl.data(), wl.size() * sizeof(int), cudaMemcpyHostToDevice);
+      upload(c, c->wlist, wl.data(), wl.size() * sizeof(int));
     }
     // tau chunk: intermediates of 2 * nk * pair complex per tau node, capped at 4 GiB
     const double per_t = 2.0 * nk * (double)c->pair * sizeof(double2);
@@ -469,17 +486,43 @@ int gw_create(gw_ctx** out, const gw_config* cfg, void* cuda_stream) {
     if ((rc = dev_alloc(c, &c->status, 4)) != GW_OK) break;
     if ((rc = dev_alloc(c, &c->maxdiff, 1)) != GW_OK) break;
     if ((rc = dev_alloc(c, &c->nonfinite, 1)) != GW_OK) break;
-    cudaMemset(c->status, 0, 4 * sizeof(int));
+    if (!c->dry) cudaMemset(c->status, 0, 4 * sizeof(int));
     if (cfg->precision != GW_FP64) {
       MixedDims d;
       d.nk3[0] = cfg->nk[0]; d.nk3[1] = cfg->nk[1]; d.nk3[2] = cfg->nk[2];
       d.nk = nk; d.nao = c->nao; d.naux = c->naux; d.ntau = c->ntau; d.precision = cfg->precision;
       d.tau_chunk = cfg->tau_chunk;
       d.mq = c->mq;
-      if ((rc = mixed_create(&c->mixed, d, c->stream, c->status, &c->bytes)) != GW_OK) break;
+      if ((rc = mixed_create(&c->mixed, d, c->stream, c->status, &c->bytes, c->dry)) != GW_OK) break;
     }
-    rc = cuda_check("gw_create");
+    if (!c->dry) rc = cuda_check("gw_create");
   } while (false);
+  return rc;
+}
+
+}  // namespace
+
+size_t job_device_bytes(const gw_config* cfg) {
+  if (!config_ok(cfg)) return 0;
+  gw_ctx c;
+  c.dry = true;
+  if (ctx_build(&c, cfg) != GW_OK) return 0;
+  const size_t nk = (size_t)cfg->nk[0] * cfg->nk[1] * cfg->nk[2], nao2 = (size_t)cfg->nao * cfg->nao;
+  // V, H, G, and two Sigma buffers of the job
+  return c.bytes + sizeof(gw_c128) * (nk * nk * cfg->naux * nao2 + nk * nao2 + 3 * nk * cfg->ntau * nao2);
+}
+
+}  // namespace gwi
+
+extern "C" {
+
+int gw_create(gw_ctx** out, const gw_config* cfg, void* cuda_stream) {
+  if (!out || !cfg) return fail(GW_EINVAL, "gw_create: null argument");
+  *out = nullptr;
+  if (!config_ok(cfg)) return fail(GW_EINVAL, "gw_create: configuration out of range");
+  gw_ctx* c = new gw_ctx();
+  c->stream = (cudaStream_t)cuda_stream;
+  const int rc = ctx_build(c, cfg);
   if (rc != GW_OK) {
     free_ctx(c);
     return rc;

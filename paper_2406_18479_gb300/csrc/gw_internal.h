@@ -17,6 +17,11 @@ std::vector<int64_t> matsubara_indices(int n, int stat);
 int grid_build(int ntau, double beta, int stat, double* tau, int64_t* idx, gw_c128* F, gw_c128* B);
 int fail(int code, const char* fmt, ...);
 
+// Device bytes of one scGW job: its context's workspaces (counted by running the
+// context build in size-only mode) plus V, H, G and two Sigma buffers. 0 for an
+// invalid configuration.
+size_t job_device_bytes(const gw_config* cfg);
+
 // ---- kernel timing and launch counting (gw_api.cu)
 //
 // Every kernel launch goes through prof_begin/prof_end with a slot naming the

@@ -16,7 +16,9 @@ struct MixedDims {
 struct MixedState;
 
 // status: the context's device status words (status[1] receives device-side wait failures).
-int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int* status, size_t* bytes);
+// dry: count the workspace bytes into *bytes only; *out stays null.
+int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int* status, size_t* bytes,
+                 bool dry = false);
 void mixed_destroy(MixedState* s);
 int mixed_set_coulomb(MixedState* s, const double2* V);
 int mixed_polarization(MixedState* s, const double2* G, double2* P0t, double spin_factor);

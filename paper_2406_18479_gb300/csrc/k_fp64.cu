@@ -329,11 +329,11 @@ int batched_inverse_fp64(double2* base, int n, long long stride, int nbatch, int
   if (nbatch <= 0) return GW_OK;
   const size_t smem = 2 * (size_t)n * sizeof(double2) + (size_t)n * sizeof(int);
   if (smem > 200 * 1024) return fail(GW_EINVAL, "batched_inverse_fp64: n=%d too large", n);
-  static bool attr_set = false;
-  if (!attr_set) {
+  static const bool attr_set = [] {   // once, also when several threads launch
     cudaFuncSetAttribute(gj_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
+    return true;
+  }();
+  (void)attr_set;
   prof_begin(SLOT_INVERSE_FP64, (cudaStream_t)stream);
   gj_inverse_kernel<<<nbatch, 256, smem, (cudaStream_t)stream>>>(base, n, stride, list, status_dev);
   prof_end(SLOT_INVERSE_FP64, (cudaStream_t)stream, 8.0 * (double)n * n * n * nbatch,

@@ -617,15 +617,16 @@ __global__ void __launch_bounds__(320, 1)
 // host side
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
     void* f = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
             cudaSuccess &&
         q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
-  }
+      return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    cudaGetLastError();
+    return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+  }();
   return fn;
 }
 
@@ -680,7 +681,6 @@ int launch_slice(const SliceJob& j, cudaStream_t st) {
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "slice launch: %s", cudaGetErrorString(e));
 }
 
-int g_num_sms = 0;
 
 template <int BN>
 int launch_oz(const Planes& A, const Planes& B, OzParams p, int slot, cudaStream_t st) {
@@ -696,17 +696,19 @@ int launch_oz(const Planes& A, const Planes& B, OzParams p, int slot, cudaStream
   CUtensorMap ma, mb;
   GW_TRY_INTERNAL(make_map(A, kBM, &ma));
   GW_TRY_INTERNAL(make_map(B, BN, &mb));
-  static bool attr = false;
-  if (!attr) {
+  // one-time setup; function-local statics initialise once even when contexts run on several threads
+  static const bool attr = [] {
     cudaFuncSetAttribute(oz_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
-    attr = true;
-  }
-  if (g_num_sms == 0) {
-    int dev = 0;
+    return true;
+  }();
+  (void)attr;
+  static const int num_sms = [] {
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-  }
-  const int grid = (int)std::min<long long>(total, g_num_sms);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return std::max(n, 1);
+  }();
+  const int grid = (int)std::min<long long>(total, num_sms);
   prof_begin(slot, st);
   oz_gemm_kernel<BN><<<grid, 320, S::kSmem, st>>>(ma, mb, p);
   // executed bf16 tensor flops: 10 slice products x 4 real products per complex multiply-add
@@ -740,6 +742,7 @@ struct MixedState {
   int* status = nullptr;
   int Kc_vg = 0, Kpad_vg = 0, Kc_p0 = 0, Kpad_p0 = 0, Kc_r = 0, Kpad_r = 0, Kc_s = 0, Kpad_s = 0;
   std::vector<void*> allocs;
+  bool dry = false;   // size-only: count bytes, allocate nothing
 };
 
 namespace {
@@ -747,6 +750,11 @@ namespace {
 template <class T>
 int m_alloc(MixedState* s, T** p, size_t count, size_t* bytes) {
   if (count == 0) count = 1;
+  if (s->dry) {
+    *p = nullptr;
+    *bytes += count * sizeof(T);
+    return GW_OK;
+  }
   if (cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T)) != cudaSuccess) {
     *p = nullptr;
     return fail(GW_ENOMEM, "mixed workspace: cudaMalloc of %zu bytes failed", count * sizeof(T));
@@ -957,11 +965,13 @@ int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double
 
 }  // namespace
 
-int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int* status, size_t* bytes) {
+int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int* status, size_t* bytes,
+                 bool dry) {
   *out = nullptr;
-  if (!encode_fn()) return fail(GW_ECUDA, "cuTensorMapEncodeTiled entry point not found");
+  if (!dry && !encode_fn()) return fail(GW_ECUDA, "cuTensorMapEncodeTiled entry point not found");
   if (d.nao > 512 || d.naux > 4096) return fail(GW_EINVAL, "mixed: nao <= 512 and naux <= 4096 required");
   MixedState* s = new MixedState();
+  s->dry = dry;
   s->d = d;
   s->stream = stream;
   s->status = status;
@@ -994,8 +1004,11 @@ int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int*
     if ((rc = m_alloc(s, &s->y64, (size_t)s->nt * nk * s->pair, bytes))) break;
     {
       int dev = 0, sms = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                    cudaSuccess) {
+        cudaGetLastError();
+        sms = 152;   // size-only build without a device: the GB300's SM count
+      }
       if ((rc = m_alloc(s, &s->ws, (size_t)std::max(sms, 1) * kBM * 80, bytes))) break;
     }
     std::vector<long long> t((size_t)kTabs * nk * nk);
@@ -1013,9 +1026,9 @@ int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int*
         at(T_VCOL_KMQK) = ((long long)km * nk + k) * s->nao2;
       }
     if ((rc = m_alloc(s, &s->rowtabs, t.size(), bytes))) break;
-    cudaMemcpy(s->rowtabs, t.data(), t.size() * sizeof(long long), cudaMemcpyHostToDevice);
+    if (!dry) cudaMemcpy(s->rowtabs, t.data(), t.size() * sizeof(long long), cudaMemcpyHostToDevice);
   } while (false);
-  if (rc != GW_OK) {
+  if (rc != GW_OK || dry) {
     mixed_destroy(s);
     return rc;
   }

@@ -27,7 +27,8 @@ ABI_SYMBOLS = [
     "gw_workspace_bytes", "gw_set_coulomb", "gw_polarization", "gw_to_matsubara", "gw_to_tau",
     "gw_aux_dyson", "gw_screened_interaction", "gw_self_energy", "gw_sigma_eval", "gw_dyson_G",
     "gw_mix", "gw_synchronize", "gw_profile_enable", "gw_launch_count", "gw_profile_slots",
-    "gw_profile_read", "gw_polarization_noalloc",
+    "gw_profile_read", "gw_polarization_noalloc", "gw_job_bytes", "gw_server_create",
+    "gw_server_destroy", "gw_submit", "gw_poll",
 ]
 
 
@@ -42,6 +43,21 @@ class gw_config(ctypes.Structure):
         ("nk", ctypes.c_int * 3), ("nao", ctypes.c_int), ("naux", ctypes.c_int), ("ntau", ctypes.c_int),
         ("beta", ctypes.c_double), ("mu", ctypes.c_double), ("spin_factor", ctypes.c_double),
         ("precision", ctypes.c_int), ("tau_chunk", ctypes.c_int),
+    ]
+
+
+class gw_job(ctypes.Structure):
+    _fields_ = [
+        ("cfg", gw_config), ("H_host", ctypes.c_void_p), ("V_host", ctypes.c_void_p),
+        ("G0_host", ctypes.c_void_p), ("Sigma_out_host", ctypes.c_void_p), ("G_out_host", ctypes.c_void_p),
+        ("alpha", ctypes.c_double), ("tol", ctypes.c_double), ("itermax", ctypes.c_int),
+    ]
+
+
+class gw_job_result(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int), ("iterations", ctypes.c_int), ("max_abs_dsigma", ctypes.c_double),
+        ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_end", ctypes.c_double),
     ]
 
 
@@ -83,6 +99,12 @@ def lib():
     L.gw_launch_count.restype = ctypes.c_longlong
     L.gw_profile_read.argtypes = [vp, i, ctypes.c_char_p, i, ctypes.POINTER(ll), ctypes.POINTER(d),
                                   ctypes.POINTER(d), ctypes.POINTER(d)]
+    L.gw_job_bytes.argtypes = [ctypes.POINTER(gw_config)]
+    L.gw_job_bytes.restype = ctypes.c_size_t
+    L.gw_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_size_t, i]
+    L.gw_server_destroy.argtypes = [vp]
+    L.gw_submit.argtypes = [vp, ctypes.POINTER(gw_job), ctypes.POINTER(ctypes.c_uint64)]
+    L.gw_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(gw_job_result), i]
     _lib = L
     return L
 
@@ -275,3 +297,84 @@ def gw_polarization_noalloc(nk3, nao, naux, ntau, spin_factor, V, G, P0t, stream
     _check(lib().gw_polarization_noalloc(arr, int(nao), int(naux), int(ntau), float(spin_factor),
                                          _ptr(V, (nk, nk, naux, nao, nao)), _ptr(G, (nk, ntau, nao, nao)),
                                          _ptr(P0t, (nk, ntau, naux, naux)), ctypes.c_void_p(s.cuda_stream)))
+
+
+# ---- request loop -------------------------------------------------------------------------
+
+
+def make_config(nk3, nao, naux, ntau, beta, mu=0.0, spin_factor=2.0, precision="fp64", tau_chunk=0):
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return gw_config((ctypes.c_int * 3)(*[int(x) for x in nk3]), int(nao), int(naux), int(ntau), float(beta),
+                     float(mu), float(spin_factor), prec, int(tau_chunk))
+
+
+def gw_job_bytes(cfg: gw_config) -> int:
+    """Device bytes one job with this configuration holds while it runs (0: invalid)."""
+    return int(lib().gw_job_bytes(ctypes.byref(cfg)))
+
+
+def _host(a, shape, name, writable=False):
+    """Address of a C-contiguous complex128 host array (numpy, or a CPU torch tensor)."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda or a.dtype != torch.complex128 or not a.is_contiguous() or tuple(a.shape) != tuple(shape):
+                raise GWError(GW_EINVAL, f"{name}: expected a contiguous complex128 CPU tensor of shape {shape}")
+            return ctypes.c_void_p(a.data_ptr())
+    except ImportError:
+        pass
+    if not isinstance(a, np.ndarray) or a.dtype != np.complex128 or not a.flags.c_contiguous \
+            or tuple(a.shape) != tuple(shape) or (writable and not a.flags.writeable):
+        raise GWError(GW_EINVAL, f"{name}: expected a C-contiguous complex128 array of shape {shape}")
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class gw_server:
+    """Owner of one gw_server* (gw_server_create ... gw_server_destroy).
+
+    submit() returns a job id; the host arrays of a job are kept alive here until
+    poll() has returned its finished result.
+    """
+
+    def __init__(self, hbm_budget: int, max_slots: int = 4):
+        h = ctypes.c_void_p()
+        _check(lib().gw_server_create(ctypes.byref(h), ctypes.c_size_t(int(hbm_budget)), int(max_slots)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, cfg: gw_config, H, V, G0, Sigma_out=None, G_out=None, alpha=0.7, tol=1e-8,
+               itermax=20) -> int:
+        nk = cfg.nk[0] * cfg.nk[1] * cfg.nk[2]
+        nao, naux, ntau = cfg.nao, cfg.naux, cfg.ntau
+        job = gw_job(cfg, _host(H, (nk, nao, nao), "H"), _host(V, (nk, nk, naux, nao, nao), "V"),
+                     _host(G0, (nk, ntau, nao, nao), "G0"),
+                     None if Sigma_out is None else _host(Sigma_out, (nk, ntau, nao, nao), "Sigma_out", True),
+                     None if G_out is None else _host(G_out, (nk, ntau, nao, nao), "G_out", True),
+                     float(alpha), float(tol), int(itermax))
+        jid = ctypes.c_uint64()
+        _check(lib().gw_submit(self._h, ctypes.byref(job), ctypes.byref(jid)))
+        self._keep[jid.value] = (H, V, G0, Sigma_out, G_out)
+        return jid.value
+
+    def poll(self, job_id: int, timeout_us: int = -1):
+        """(rc, result dict): rc is GW_OK once the job finished, else GW_EAGAIN / GW_ETIMEOUT."""
+        r = gw_job_result()
+        rc = lib().gw_poll(self._h, ctypes.c_uint64(job_id), ctypes.byref(r), int(timeout_us))
+        if rc not in (GW_OK, GW_EAGAIN, GW_ETIMEOUT):
+            _check(rc)
+        if rc == GW_OK:
+            self._keep.pop(job_id, None)
+        return rc, {"status": r.status, "iterations": r.iterations, "max_abs_dsigma": r.max_abs_dsigma,
+                    "t_submit": r.t_submit, "t_start": r.t_start, "t_end": r.t_end}
+
+    def destroy(self):
+        if self._h is not None:
+            lib().gw_server_destroy(self._h)
+            self._h = None
+            self._keep = {}
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass

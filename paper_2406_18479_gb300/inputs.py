@@ -22,7 +22,7 @@ import numpy as np
 
 __all__ = [
     "Workload", "WORKLOADS", "kmesh_points", "chebyshev_tau", "random_unitary",
-    "hamiltonian", "coulomb", "g0_tau", "make_inputs",
+    "hamiltonian", "coulomb", "g0_tau", "make_inputs", "batched_molecules", "serving_stream",
 ]
 
 
@@ -162,3 +162,37 @@ def make_inputs(w: Workload):
     tau = chebyshev_tau(w.ntau, w.beta)
     g = g0_tau(h, w.mu, w.beta, tau)
     return h, v, g
+
+
+def molecule(name: str, nao: int, ntau: int = 80, beta: float = 100.0, seed: int = 0) -> Workload:
+    """Gamma-only system with naux = 4 nao and V^Q decaying as exp(-4 Q / naux) (the nao=8 ratio)."""
+    naux = 4 * nao
+    return Workload(name, (1, 1, 1), nao, naux, ntau, ntau, beta, decay=naux / 4.0, seed=seed)
+
+
+def batched_molecules(n: int = 48, seed: int = 4):
+    """n Gamma-only systems with nao uniform on {10..120}, naux = 4 nao, 80 tau nodes, beta = 100."""
+    rng = np.random.default_rng(seed)
+    naos = rng.integers(10, 121, n)
+    return [molecule(f"mol{i}_nao{int(a)}", int(a), seed=seed * 1000 + i) for i, a in enumerate(naos)]
+
+
+def serving_stream(n: int = 200, seed: int = 5):
+    """Seeded scGW job stream: [(gap, Workload)], gaps exponential with unit mean (Poisson arrivals;
+    the caller divides by the rate). 70% molecules with nao on {10..120}; 30% solids on a 2x2x2 or
+    3x3x3 mesh with nao on {16..52}; naux = 4 nao, 80 tau nodes, beta = 100.
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        gap = float(rng.exponential(1.0))
+        if rng.random() < 0.7:
+            w = molecule(f"job{i}_mol_nao", int(rng.integers(10, 121)), seed=seed * 1000 + i)
+            w = dataclasses.replace(w, name=f"job{i}_mol_nao{w.nao}")
+        else:
+            m = (2, 2, 2) if rng.random() < 0.5 else (3, 3, 3)
+            nao = int(rng.integers(16, 53))
+            w = Workload(f"job{i}_solid{m[0]}_nao{nao}", m, nao, 4 * nao, 80, 80, 100.0, decay=40.0,
+                         seed=seed * 1000 + i, solid=True)
+        out.append((gap, w))
+    return out
