@@ -17,13 +17,14 @@
 // rounding into an FP32 pair and added to a double-float running sum (FP64 is
 // about 1/64 of the FP32 rate on this part, so no FP64 instruction runs per
 // chunk); the last chunk writes FP64, or double-float for intermediates that
-// are sliced again. Complex products use four real MMAs per slice pair (the
-// B-imaginary operand of the A_im B_im product negated by the instruction descriptor).
+// are sliced again. A complex slice product is two real MMAs of N = 160 with
+// the real and imaginary parts of B stacked along N (see OzShape).
 //
 // Kernels
-//   slice_kernel   FP64 or double-float complex view -> 8 bf16 planes [slice*2 + re/im][row][Kpad]
-//   oz_gemm_kernel persistent tcgen05 GEMM over plane tiles loaded by TMA
-//                  (SWIZZLE_32B K-major, one 16-wide k-step per pipeline stage)
+//   slice_kernel   FP64 or double-float complex view -> bf16 slice groups
+//                  [re | im | -im][k-step][row][4 slices x 16 k]
+//   oz_gemm_kernel persistent tcgen05 GEMM over group tiles loaded by TMA
+//                  (128-byte swizzle, K-major, one 16-wide k-step per pipeline stage)
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -49,7 +50,6 @@ namespace {
   } while (0)
 #endif
 
-constexpr int kPlanes = 8;     // 4 slices x (re, im)
 constexpr int kBM = 128;       // rows of an MMA tile (TMEM lanes)
 constexpr int kStepK = 16;     // k per MMA (kind::f16)
 constexpr int kMaxChunk = 256; // k per exact-accumulation chunk
@@ -70,7 +70,8 @@ struct SliceJob {
   int bin = 1 << 30;
   int rows = 0, K = 0, Kc = 0, Kpad = 0, nbatch = 1;
   __nv_bfloat16* dst = nullptr;
-  long long plane_stride = 0;   // elements between planes (= total rows * Kpad)
+  long long dst_rows = 0;       // rows of the destination planes buffer
+  int groups = 2;               // 3: also write the negated imaginary slices
   long long dst_row0 = 0;       // first destination row of batch 0
   long long dst_rows_per_batch = 0;
 };
@@ -169,7 +170,10 @@ __global__ void __launch_bounds__(256) slice_kernel(const SliceJob j) {
     E = eb - 1022;
   }
   const long long row = j.dst_row0 + (long long)b * j.dst_rows_per_batch + r;
-  __nv_bfloat16* out = j.dst + row * j.Kpad + (long long)c * j.Kc;
+  // element k: group g, k-step k / 16, this row, value (slice s, k % 16) at 16 s + k % 16
+  const long long kstride = j.dst_rows * 64;                      // between k-steps
+  const long long gstride = (long long)(j.Kpad / 16) * kstride;   // between groups
+  __nv_bfloat16* out = j.dst + row * 64;
   float scale[4];
 #pragma unroll
   for (int s = 0; s < 4; ++s) scale[s] = ldexpf(1.0f, E - 7 - 8 * s);
@@ -192,13 +196,16 @@ __global__ void __launch_bounds__(256) slice_kernel(const SliceJob j) {
         split_digits(fixed31_f64(xi[v], E), di[h]);
       }
     }
+    const int k = c * j.Kc + e;          // even: the pair (k, k + 1) shares its k-step
+    __nv_bfloat16* o = out + (long long)(k >> 4) * kstride + (k & 15);
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
       // digit * 2^(E - 7 - 8s) is exact in float and in bf16 (|digit| <= 128)
-      *reinterpret_cast<__nv_bfloat162*>(out + (long long)(2 * s) * j.plane_stride + e) =
+      *reinterpret_cast<__nv_bfloat162*>(o + 16 * s) =
           __floats2bfloat162_rn((float)dr[0][s] * scale[s], (float)dr[1][s] * scale[s]);
-      *reinterpret_cast<__nv_bfloat162*>(out + (long long)(2 * s + 1) * j.plane_stride + e) =
-          __floats2bfloat162_rn((float)di[0][s] * scale[s], (float)di[1][s] * scale[s]);
+      const __nv_bfloat162 im = __floats2bfloat162_rn((float)di[0][s] * scale[s], (float)di[1][s] * scale[s]);
+      *reinterpret_cast<__nv_bfloat162*>(o + gstride + 16 * s) = im;
+      if (j.groups == 3) *reinterpret_cast<__nv_bfloat162*>(o + 2 * gstride + 16 * s) = __hneg2(im);
     }
   }
 }
@@ -225,6 +232,7 @@ struct OzParams {
   // written, problem index b * dgroup + block, up to dtotal problems (0: off)
   int dblock = 0, dgroup = 1, dtotal = 0;
   float4* ws = nullptr;               // per-CTA running sums across chunks, gridDim.x * 128 * BN
+  float4* cw = nullptr;               // per-CTA newest chunk values, same shape
   int* status = nullptr;              // status[1] <- error code of a device-side wait that gave up
 };
 
@@ -302,18 +310,6 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
-// Shared-memory matrix descriptor, K-major, 32-byte swizzle: 8-row atoms of 32 bytes,
-// stride between 8-row groups 256 bytes; version 1 (bits 46-47); layout type 6.
-__device__ __forceinline__ uint64_t sw32_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(256 >> 4) << 32;        // stride byte offset
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)6 << 61;
-  return d;
-}
-
 // Instruction descriptor for kind::f16: D f32, A and B bf16, both K-major, M = 128; optionally B negated.
 __host__ __device__ constexpr uint32_t idesc_bf16(int n, bool neg_b) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((neg_b ? 1u : 0u) << 14) | ((uint32_t)(n >> 3) << 17) |
@@ -337,17 +333,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   uint32_t r[8];
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -359,26 +344,56 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-template <int BN>
+// Output tile 128 x 80. The planes of an operand are stored in groups of four
+// slices: group 0 holds the real parts, group 1 the imaginary parts and, for
+// operands used as B, group 2 the negated imaginary parts; within a group one
+// 128-byte row holds the four slices of 16 consecutive k (slice s at bytes
+// [32 s, 32 s + 32)). A stage is one such 128-byte row per operand row and
+// group, loaded by one TMA box per group with the 128-byte swizzle; slice s is
+// addressed by advancing the descriptor start by 32 s bytes inside the
+// swizzle atom. B's three groups sit as consecutive 80-row blocks [Bi; Br; -Bi]
+// so that one complex slice product is two MMAs of N = 160:
+//   A_r x [Bi; Br]  -> columns [0, 80) += A_r B_i,  [80, 160) += A_r B_r
+//   A_i x [Br; -Bi] -> columns [0, 80) += A_i B_r,  [80, 160) -= A_i B_i
+// (imaginary part first, real part second). Three orders take 480 TMEM
+// columns. After each chunk the epilogue moves the chunk value out of TMEM
+// (into the output when the contraction has one chunk, else into per-CTA
+// scratch), releases TMEM, and only then merges it into the running sum while
+// the next chunk's MMAs run.
 struct OzShape {
-  static constexpr int kStages = BN >= 64 ? 4 : 5;   // <= 213 KB of stages for BN <= 80
-  static constexpr int kATile = kBM * kStepK;     // bf16 elements per plane tile
-  static constexpr int kBTile = BN * kStepK;
-  static constexpr int kStageElems = kPlanes * (kATile + kBTile);
-  static constexpr uint32_t kStageBytes = kStageElems * 2;
-  static constexpr int kAccCols = 6 * BN;        // (order 0, order 1, orders 2-3) x (re, im)
-  static_assert(kAccCols <= 512, "six accumulators of BN columns must fit in TMEM");
-  static constexpr int kTmemCols = kAccCols <= 128 ? 128 : (kAccCols <= 256 ? 256 : 512);
+  static constexpr int kBN = 80;                       // output columns per tile
+  static constexpr int kStages = 3;
+  static constexpr int kRowBytes = 128;                // four slices x 16 k x bf16
+  static constexpr int kAGroup = kBM * kRowBytes;      // bytes of one A group tile
+  static constexpr int kBBlock = kBN * kRowBytes;      // bytes of one B group block
+  static constexpr uint32_t kStageBytes = 2 * kAGroup + 3 * kBBlock;
+  static constexpr int kOrderCols = 2 * kBN;           // [im | re] of one order
+  static constexpr int kTmemCols = 512;
   static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + 256;
+  static_assert(3 * kOrderCols <= kTmemCols, "three orders must fit in TMEM");
+  static_assert(kStageBytes % 1024 == 0, "stages must keep the 1024-byte swizzle alignment");
+  static_assert(kSmem <= 232448, "stages exceed shared memory");
 };
 
-template <int BN>
+// Shared-memory matrix descriptor, K-major, 128-byte swizzle: 8-row atoms of
+// 128 bytes, 1024 bytes between 8-row groups; version 1 (bits 46-47); layout
+// type 2 (bits 61-63).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
 __global__ void __launch_bounds__(320, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const OzParams p) {
-  using S = OzShape<BN>;
+  using S = OzShape;
+  constexpr int BN = S::kBN;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  __nv_bfloat16* tiles = reinterpret_cast<__nv_bfloat16*>(smem);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)S::kStages * S::kStageBytes);
   uint64_t* full = bars;
   uint64_t* empty = bars + S::kStages;
@@ -412,10 +427,11 @@ __global__ void __launch_bounds__(320, 1)
   const uint32_t tmem = *tmem_slot;
   const int tiles_per_batch = p.mtiles * p.ntiles;
   const int total_tiles = p.nbatch * tiles_per_batch;
+  const int nchunks = (p.nsteps + p.steps_per_chunk - 1) / p.steps_per_chunk;
 
   if (warp == 0) {
     if (lane == 0) {
-      // ---------------- TMA producer
+      // ---------------- TMA producer: per k-step A (re, im) and B (im, re, -im) group tiles
       uint32_t step = 0;
       for (int tile = blockIdx.x; tile < total_tiles && !*abort_flag; tile += gridDim.x) {
         const int b = tile / tiles_per_batch, mt = (tile % tiles_per_batch) / p.ntiles, nt = tile % p.ntiles;
@@ -427,12 +443,13 @@ __global__ void __launch_bounds__(320, 1)
           const uint32_t ph = (step / S::kStages) & 1;
           if (!mbar_wait(&empty[st], ph ^ 1, abort_flag, p.status, 11)) break;
           mbar_expect_tx(&full[st], S::kStageBytes);
-          __nv_bfloat16* sa = tiles + (size_t)st * S::kStageElems;
-          __nv_bfloat16* sb = sa + kPlanes * S::kATile;
-#pragma unroll
-          for (int pl = 0; pl < kPlanes; ++pl) tma_load_3d(sa + pl * S::kATile, &tmA, s * kStepK, arow, pl, &full[st]);
-#pragma unroll
-          for (int pl = 0; pl < kPlanes; ++pl) tma_load_3d(sb + pl * S::kBTile, &tmB, s * kStepK, brow, pl, &full[st]);
+          uint8_t* sa = smem + (size_t)st * S::kStageBytes;
+          uint8_t* sb = sa + 2 * S::kAGroup;
+          tma_load_3d(sa, &tmA, 0, arow, s, &full[st]);                                // A re
+          tma_load_3d(sa + S::kAGroup, &tmA, 0, arow, p.nsteps + s, &full[st]);        // A im
+          tma_load_3d(sb, &tmB, 0, brow, p.nsteps + s, &full[st]);                     // B im
+          tma_load_3d(sb + S::kBBlock, &tmB, 0, brow, s, &full[st]);                   // B re
+          tma_load_3d(sb + 2 * S::kBBlock, &tmB, 0, brow, 2 * p.nsteps + s, &full[st]); // -B im
         }
       }
       if (*abort_flag) {
@@ -451,9 +468,8 @@ __global__ void __launch_bounds__(320, 1)
     if (lane == 0) {
       // ---------------- MMA issuer
       uint32_t step = 0, chunk = 0;
-      const uint32_t id_pos = idesc_bf16(BN, false), id_neg = idesc_bf16(BN, true);
-      const uint64_t desc_a0 = sw32_desc(smem_u32(tiles));
-      const uint64_t desc_b0 = sw32_desc(smem_u32(tiles + kPlanes * S::kATile));
+      const uint32_t idesc = idesc_bf16(2 * BN, false);
+      const uint64_t desc0 = sw128_desc(smem_u32(smem));
       bool ok = true;
       for (int tile = blockIdx.x; tile < total_tiles && ok; tile += gridDim.x) {
         for (int s = 0; s < p.nsteps && ok; ++s, ++step) {
@@ -466,29 +482,24 @@ __global__ void __launch_bounds__(320, 1)
           const uint32_t ph = (step / S::kStages) & 1;
           if (!mbar_wait(&full[st], ph, abort_flag, p.status, 13)) { ok = false; break; }
           tc_fence_after();
-          // descriptors of this stage: the start-address field (bits 0-13, address >> 4) of the
-          // stage-0 descriptors advanced by the byte offset >> 4 (shared memory < 256 KB: no carry)
-          const uint64_t sa = desc_a0 + (uint64_t)((st * S::kStageBytes) >> 4);
-          const uint64_t sb = desc_b0 + (uint64_t)((st * S::kStageBytes) >> 4);
-          // products (i, j) with i + j <= 3, accumulated by order: 0, 1, and 2-3
+          // descriptor start fields (address >> 4) of this stage; shared memory < 256 KB: no carry
+          const uint64_t sa = desc0 + (uint64_t)((st * S::kStageBytes) >> 4);
+          const uint64_t sb = sa + (uint64_t)((2 * S::kAGroup) >> 4);
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
 #pragma unroll
             for (int jj = 0; jj < 4; ++jj) {
               if (i + jj > 3) continue;
               const int acc = (i + jj == 0) ? 0 : (i + jj == 1 ? 1 : 2);
-              const uint32_t d_re = tmem + (uint32_t)((2 * acc) * BN);
-              const uint32_t d_im = tmem + (uint32_t)((2 * acc + 1) * BN);
-              // first write of each accumulator pair in a chunk: (0,0), (0,1) and (0,2) in loop order
+              const uint32_t d = tmem + (uint32_t)(acc * S::kOrderCols);
+              // first write of each accumulator in a chunk: (0,0), (0,1) and (0,2) in loop order
               const bool first = chunk_start && i == 0 && jj == acc;
-              const uint64_t ar = sa + (uint64_t)(((2 * i) * S::kATile * 2) >> 4);
-              const uint64_t ai = sa + (uint64_t)(((2 * i + 1) * S::kATile * 2) >> 4);
-              const uint64_t br = sb + (uint64_t)(((2 * jj) * S::kBTile * 2) >> 4);
-              const uint64_t bim = sb + (uint64_t)(((2 * jj + 1) * S::kBTile * 2) >> 4);
-              mma_bf16(d_re, ar, br, id_pos, first ? 0u : 1u);
-              mma_bf16(d_re, ai, bim, id_neg, 1u);             // - A_im B_im (B negated)
-              mma_bf16(d_im, ar, bim, id_pos, first ? 0u : 1u);
-              mma_bf16(d_im, ai, br, id_pos, 1u);
+              const uint64_t ar = sa + (uint64_t)(2 * i);                          // +32 i bytes
+              const uint64_t ai = ar + (uint64_t)(S::kAGroup >> 4);
+              const uint64_t b01 = sb + (uint64_t)(2 * jj);                        // [Bi; Br]
+              const uint64_t b12 = b01 + (uint64_t)(S::kBBlock >> 4);              // [Br; -Bi]
+              mma_bf16(d, ar, b01, idesc, first ? 0u : 1u);
+              mma_bf16(d, ai, b12, idesc, 1u);
             }
           }
           mma_commit(&empty[st]);
@@ -505,99 +516,115 @@ __global__ void __launch_bounds__(320, 1)
       }
     }
   } else {
-    // ---------------- epilogue: warps 2..9; TMEM lane quarter = warp % 4, column half = (warp - 2) / 4
+    // ---------------- epilogue: warps 2..9; TMEM lane quarter = warp % 4, columns [40 half, 40 half + 40)
     const int quarter = warp & 3;
     const int half = (warp - 2) >> 2;
-    constexpr int kHalf = BN / 2;
+    constexpr int kCols = BN / 2;
+    const int lrow = quarter * 32 + lane;            // TMEM lane = row within the tile
+    // per-CTA scratch, column-major so that a warp's 32 rows of one column are contiguous:
+    // ws holds the running sum, cw the newest chunk value
+    float4* ws = p.ws + (size_t)blockIdx.x * BN * kBM + lrow;
+    float4* cw = p.cw + (size_t)blockIdx.x * BN * kBM + lrow;
     uint32_t chunk = 0;
     for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
       const int b = tile / tiles_per_batch, mt = (tile % tiles_per_batch) / p.ntiles, nt = tile % p.ntiles;
-      const int lrow = quarter * 32 + lane;           // TMEM lane = row within the tile
       int row = mt * kBM + lrow;
       bool row_ok = row < p.M;
       // block-diagonal mode: the tile holds dgroup problems of dblock rows and columns; this
       // row belongs to problem b * dgroup + row / dblock and only its own column block is kept
-      int dcol0 = 0;
+      int dcol0 = 0, ncols = 1 << 30;
       int ob = b;
       if (p.dblock) {
         const int blk = row / p.dblock;
         ob = b * p.dgroup + blk;
         row_ok = row_ok && ob < p.dtotal;
         dcol0 = blk * p.dblock;
+        ncols = p.dblock;
         row -= dcol0;
       }
       const int bo = ob / p.bin, bi = ob % p.bin;
       double2* C = p.C + (p.bc.tab ? p.bc.tab[bi] : (long long)bi * p.bc.bs_in) + (long long)bo * p.bc.bs_out;
       const long long roff = row_ok ? s_view_row(p.vc, row) : 0;
-      const int nchunks = (p.nsteps + p.steps_per_chunk - 1) / p.steps_per_chunk;
-      // running sums, column-major per CTA so that a warp's 32 rows of one column are contiguous
-      float4* wcol = p.ws + (size_t)blockIdx.x * BN * kBM + lrow;
+      // output column of tile column cl: nt * BN + cl - dcol0 (valid if in [0, min(N, ncols)))
+      auto col_ok = [&](int cl) {
+        const int n = nt * BN + cl - dcol0;
+        return row_ok && cl - dcol0 >= 0 && cl - dcol0 < ncols && n < p.N;
+      };
+      auto out_write = [&](int cl, float rh, float rl, float ih, float il) {
+        const int n = nt * BN + cl - dcol0;
+        double2* dst = C + roff + (long long)(n / p.vc.kin) * p.vc.ks_out + (long long)(n % p.vc.kin) * p.vc.ks_in;
+        if (p.out_df) {
+          *reinterpret_cast<float4*>(dst) = make_float4(rh, rl, ih, il);
+        } else {
+          double re = p.alpha * ((double)rh + (double)rl);
+          double im = p.alpha * ((double)ih + (double)il);
+          if (p.accumulate) {
+            const double2 o = *dst;
+            re += o.x;
+            im += o.y;
+          }
+          *dst = make_double2(re, im);
+        }
+      };
       bool ok = true;
       for (int c = 0; c < nchunks; ++c, ++chunk) {
         if (!mbar_wait(acc_full, chunk & 1, abort_flag, p.status, 14)) { ok = false; break; }
         tc_fence_after();
-        const bool last = c == nchunks - 1;
-        const bool need_prev = nchunks > 1 && c > 0 && row_ok;
+        const bool single = nchunks == 1;
+        // ---- drain: TMEM -> chunk value (an exact FP32 pair per part) -> output or scratch
 #pragma unroll 1
-        for (int cb = half * kHalf; cb < (half + 1) * kHalf; cb += 8) {
-          // running sums of the previous chunks, in flight while the accumulators are read
-          float4 prev[8];
-          if (need_prev) {
+        for (int g = 0; g < kCols / 8; ++g) {
+          const int cb = half * kCols + g * 8;
+          float v[3][2][8];                           // [order][im, re][column]
+          const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cb;
 #pragma unroll
-            for (int u = 0; u < 8; ++u) prev[u] = wcol[(size_t)(cb + u) * kBM];
+          for (int o = 0; o < 3; ++o) {
+            tmem_ld8(taddr + o * S::kOrderCols, v[o][0]);
+            tmem_ld8(taddr + o * S::kOrderCols + BN, v[o][1]);
           }
-          float mr[8], mi[8], ar[8], ai[8], br[8], bi[8];
-          const uint32_t lane_addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cb;
-          tmem_ld8(lane_addr + 0 * BN, mr);
-          tmem_ld8(lane_addr + 1 * BN, mi);
-          tmem_ld8(lane_addr + 2 * BN, ar);
-          tmem_ld8(lane_addr + 3 * BN, ai);
-          tmem_ld8(lane_addr + 4 * BN, br);
-          tmem_ld8(lane_addr + 5 * BN, bi);
           tmem_wait_ld();
-          if (cb + 8 >= (half + 1) * kHalf) {
-            // this warp's accumulator columns of the chunk are in registers: release TMEM
+          if (g == kCols / 8 - 1) {
+            // this warp's accumulator columns are in registers: release TMEM
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acc_empty);
           }
-          if (row_ok) {
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int cl = cb + u;
+            if (!col_ok(cl)) continue;
+            // orders 0 and 1 are exact, so their sum is exact as a pair
+            float rh, rl, ih, il;
+            two_sum(v[0][1][u], v[1][1][u], rh, rl);
+            rl = __fadd_rn(rl, v[2][1][u]);
+            two_sum(v[0][0][u], v[1][0][u], ih, il);
+            il = __fadd_rn(il, v[2][0][u]);
+            if (single) out_write(cl, rh, rl, ih, il);
+            else (c == 0 ? ws : cw)[(size_t)cl * kBM] = make_float4(rh, rl, ih, il);
+          }
+        }
+        // ---- merge into the running sum (overlaps the next chunk's MMAs)
+        if (!single && c > 0) {
+          const bool last = c == nchunks - 1;
+#pragma unroll 1
+          for (int g = 0; g < kCols / 8; ++g) {
+            const int cb = half * kCols + g * 8;
+            float4 a[8], x[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-              int n = nt * BN + cb + u;
-              if (p.dblock) {
-                n -= dcol0;
-                if (n < 0 || n >= p.dblock) continue;   // another problem's columns
+              if (col_ok(cb + u)) {
+                a[u] = ws[(size_t)(cb + u) * kBM];
+                x[u] = cw[(size_t)(cb + u) * kBM];
               }
-              if (n < p.N) {
-                // the chunk value: orders 0 and 1 are exact, so their sum is exact as a pair
-                float rh, rl, ih, il;
-                two_sum(mr[u], ar[u], rh, rl);
-                rl = __fadd_rn(rl, br[u]);
-                two_sum(mi[u], ai[u], ih, il);
-                il = __fadd_rn(il, bi[u]);
-                if (need_prev) {
-                  df_add(rh, rl, prev[u].x, prev[u].y);
-                  df_add(ih, il, prev[u].z, prev[u].w);
-                }
-                if (nchunks > 1 && !last) {
-                  wcol[(size_t)(cb + u) * kBM] = make_float4(rh, rl, ih, il);
-                  continue;
-                }
-                double2* dst = C + roff + (long long)(n / p.vc.kin) * p.vc.ks_out + (long long)(n % p.vc.kin) * p.vc.ks_in;
-                if (p.out_df) {
-                  *reinterpret_cast<float4*>(dst) = make_float4(rh, rl, ih, il);
-                } else {
-                  double re = p.alpha * ((double)rh + (double)rl);
-                  double im = p.alpha * ((double)ih + (double)il);
-                  if (p.accumulate) {
-                    const double2 o = *dst;
-                    re += o.x;
-                    im += o.y;
-                  }
-                  *dst = make_double2(re, im);
-                }
-              }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int cl = cb + u;
+              if (!col_ok(cl)) continue;
+              df_add(a[u].x, a[u].y, x[u].x, x[u].y);
+              df_add(a[u].z, a[u].w, x[u].z, x[u].w);
+              if (last) out_write(cl, a[u].x, a[u].y, a[u].z, a[u].w);
+              else ws[(size_t)cl * kBM] = a[u];
             }
           }
         }
@@ -631,22 +658,37 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // Planes buffer: [8][rows][Kpad] bf16.
+// Planes buffer: groups x (Kpad / 16) x rows x 64 bf16. Group 0 holds the real slices,
+// group 1 the imaginary ones and group 2 (operands used as B only) the negated imaginary
+// ones; the 64 values of (group, k-step, row) are the four slices of 16 consecutive k.
 struct Planes {
   __nv_bfloat16* ptr = nullptr;
   long long rows = 0;
   int Kpad = 0, Kc = 0;
-  long long plane_stride() const { return rows * Kpad; }
+  int groups = 2;
+  size_t elems() const { return (size_t)groups * 4 * rows * Kpad; }
 };
+
+int num_sms() {
+  static const int n = [] {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return std::max(v, 1);
+  }();
+  return n;
+}
 
 int make_map(const Planes& P, int box_rows, CUtensorMap* map) {
   auto enc = encode_fn();
   if (!enc) return fail(GW_ECUDA, "cuTensorMapEncodeTiled is not available");
-  cuuint64_t dims[3] = {(cuuint64_t)P.Kpad, (cuuint64_t)P.rows, (cuuint64_t)kPlanes};
-  cuuint64_t strides[2] = {(cuuint64_t)P.Kpad * 2, (cuuint64_t)P.rows * P.Kpad * 2};
-  cuuint32_t box[3] = {(cuuint32_t)kStepK, (cuuint32_t)box_rows, 1};
+  // (64 values of one row and k-step, rows, group * k-steps); one box: 64 x box_rows x 1
+  cuuint64_t dims[3] = {64, (cuuint64_t)P.rows, (cuuint64_t)P.groups * (P.Kpad / kStepK)};
+  cuuint64_t strides[2] = {128, (cuuint64_t)P.rows * 128};
+  cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
   const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)P.ptr, dims, strides, box, es,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(GW_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return GW_OK;
@@ -682,37 +724,33 @@ int launch_slice(const SliceJob& j, cudaStream_t st) {
 }
 
 
-template <int BN>
 int launch_oz(const Planes& A, const Planes& B, OzParams p, int slot, cudaStream_t st) {
-  using S = OzShape<BN>;
+  using S = OzShape;
   if (A.Kpad != B.Kpad || A.Kc != B.Kc) return fail(GW_EINVAL, "oz_gemm: operand chunking differs");
+  if (A.groups < 2 || B.groups < 3) return fail(GW_EINVAL, "oz_gemm: B needs its negated imaginary planes");
   p.nsteps = A.Kpad / kStepK;
   p.steps_per_chunk = A.Kc / kStepK;
   p.mtiles = (p.M + kBM - 1) / kBM;
-  p.ntiles = (p.N + BN - 1) / BN;
+  p.ntiles = (p.N + S::kBN - 1) / S::kBN;
   const long long total = (long long)p.nbatch * p.mtiles * p.ntiles;
   if (total == 0) return GW_OK;
   if (total > 2147483647LL) return fail(GW_EINVAL, "oz_gemm: too many tiles");
+  if (!p.ws) return fail(GW_EINVAL, "oz_gemm: no epilogue scratch");
+  p.cw = p.ws + (size_t)num_sms() * kBM * S::kBN;
   CUtensorMap ma, mb;
   GW_TRY_INTERNAL(make_map(A, kBM, &ma));
-  GW_TRY_INTERNAL(make_map(B, BN, &mb));
+  GW_TRY_INTERNAL(make_map(B, S::kBN, &mb));
   // one-time setup; function-local statics initialise once even when contexts run on several threads
   static const bool attr = [] {
-    cudaFuncSetAttribute(oz_gemm_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
+    cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
     return true;
   }();
   (void)attr;
-  static const int num_sms = [] {
-    int dev = 0, n = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    return std::max(n, 1);
-  }();
-  const int grid = (int)std::min<long long>(total, num_sms);
+  const int grid = (int)std::min<long long>(total, num_sms());
   prof_begin(slot, st);
-  oz_gemm_kernel<BN><<<grid, 320, S::kSmem, st>>>(ma, mb, p);
-  // executed bf16 tensor flops: 10 slice products x 4 real products per complex multiply-add
-  prof_end(slot, st, 2.0 * 40.0 * (double)total * kBM * BN * (double)p.nsteps * kStepK,
+  oz_gemm_kernel<<<grid, 320, S::kSmem, st>>>(ma, mb, p);
+  // executed bf16 tensor flops: 10 slice products x 2 real MMAs of 128 x 160 x 16 per k-step
+  prof_end(slot, st, 2.0 * 20.0 * (double)total * kBM * (2 * S::kBN) * (double)p.nsteps * kStepK,
            (double)total * p.nsteps * S::kStageBytes);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "oz_gemm launch: %s", cudaGetErrorString(e));
@@ -764,19 +802,21 @@ int m_alloc(MixedState* s, T** p, size_t count, size_t* bytes) {
   return GW_OK;
 }
 
-int alloc_planes(MixedState* s, Planes* P, long long rows, int Kc, int Kpad, size_t* bytes) {
+int alloc_planes(MixedState* s, Planes* P, long long rows, int Kc, int Kpad, int groups, size_t* bytes) {
   P->rows = rows;
   P->Kc = Kc;
   P->Kpad = Kpad;
-  return m_alloc(s, &P->ptr, (size_t)kPlanes * rows * Kpad, bytes);
+  P->groups = groups;
+  return m_alloc(s, &P->ptr, P->elems(), bytes);
 }
 
-Planes view(__nv_bfloat16* mem, long long rows, int Kc, int Kpad) {
+Planes view(__nv_bfloat16* mem, long long rows, int Kc, int Kpad, int groups) {
   Planes P;
   P.ptr = mem;
   P.rows = rows;
   P.Kc = Kc;
   P.Kpad = Kpad;
+  P.groups = groups;
   return P;
 }
 
@@ -810,7 +850,8 @@ int slice(MixedState* s, const double2* src, const ZView& v, long long b_in, lon
   j.Kpad = P.Kpad;
   j.nbatch = nbatch;
   j.dst = P.ptr;
-  j.plane_stride = P.plane_stride();
+  j.dst_rows = P.rows;
+  j.groups = P.groups;
   j.dst_rows_per_batch = dst_rows_per_batch;
   return launch_slice(j, s->stream);
 }
@@ -860,15 +901,15 @@ int vg_gemm(MixedState* s, int pair_tab, int g_tab, const Planes& Gp, int q, int
   p.status = s->status;
   p.ws = s->ws;
   p.out_df = 1;
-  return launch_oz<80>(s->vrow, Gp, p, SLOT_VG_MIXED, s->stream);
+  return launch_oz(s->vrow, Gp, p, SLOT_VG_MIXED, s->stream);
 }
 
 int polarization_chunk(MixedState* s, const double2* G, double2* P0t, double spin, int q, int t0, int nt) {
   const int nk = s->d.nk, nao = s->d.nao, naux = s->d.naux, ntau = s->d.ntau;
   GW_TRY_INTERNAL(vg_gemm(s, T_VKKPQ, T_GKPQ, s->gf, q, t0, nt, false, s->x64));
   GW_TRY_INTERNAL(vg_gemm(s, T_VKPQK, T_GK, s->gm, q, t0, nt, true, s->y64));
-  const Planes xs = view(s->xs_mem, (long long)nt * naux, s->Kc_p0, s->Kpad_p0);
-  const Planes ys = view(s->ys_mem, (long long)nt * naux, s->Kc_p0, s->Kpad_p0);
+  const Planes xs = view(s->xs_mem, (long long)nt * naux, s->Kc_p0, s->Kpad_p0, 2);
+  const Planes ys = view(s->ys_mem, (long long)nt * naux, s->Kc_p0, s->Kpad_p0, 3);
   ZView v;                                 // rows Q, k = (k, d, b)
   v.rs_in = s->nao2;
   v.kin = (int)s->nao2;
@@ -890,7 +931,7 @@ int polarization_chunk(MixedState* s, const double2* G, double2* P0t, double spi
   p.status = s->status;
   p.ws = s->ws;
   (void)nao;
-  return launch_oz<80>(xs, ys, p, SLOT_P0_TC, s->stream);
+  return launch_oz(xs, ys, p, SLOT_P0_TC, s->stream);
 }
 
 int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double2* Sig, int q, int t0, int nt) {
@@ -918,12 +959,12 @@ int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double
     p.status = s->status;
     p.ws = s->ws;
     p.out_df = 1;                           // double-float, sliced again for the Sigma contraction
-    GW_TRY_INTERNAL(launch_oz<80>(s->ps, s->vcol, p, SLOT_R_TC, s->stream));
+    GW_TRY_INTERNAL(launch_oz(s->ps, s->vcol, p, SLOT_R_TC, s->stream));
   }
   // Z^Q_{ib}(k,t) = sum_a V^{k,k-q}_ia(Q) G^{k-q}_ab(t) -> x64[t][k][Q][i][b]
   GW_TRY_INTERNAL(vg_gemm(s, T_VKKMQ, T_GKMQ, s->gf, q, t0, nt, false, s->x64));
-  const Planes xs = view(s->xs_mem, (long long)nt * nk * nao, s->Kc_s, s->Kpad_s);
-  const Planes ys = view(s->ys_mem, (long long)nt * nk * nao, s->Kc_s, s->Kpad_s);
+  const Planes xs = view(s->xs_mem, (long long)nt * nk * nao, s->Kc_s, s->Kpad_s, 2);
+  const Planes ys = view(s->ys_mem, (long long)nt * nk * nao, s->Kc_s, s->Kpad_s, 3);
   {
     ZView vz;                               // rows i, k = (Q, b)
     vz.rs_in = nao;
@@ -960,7 +1001,7 @@ int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double
   p.accumulate = 1;
   p.status = s->status;
   p.ws = s->ws;
-  return launch_oz<80>(xs, ys, p, SLOT_SIGMA_MIXED, s->stream);
+  return launch_oz(xs, ys, p, SLOT_SIGMA_MIXED, s->stream);
 }
 
 }  // namespace
@@ -985,21 +1026,21 @@ int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int*
   chunking(naux * nao, &s->Kc_s, &s->Kpad_s);
   // tau batch: FP64 intermediates plus operand planes per tau node, capped at 6 GiB
   const double per_t = 2.0 * nk * (double)s->pair * 16.0 +
-                       2.0 * std::max((double)naux * s->Kpad_p0, (double)nk * nao * s->Kpad_s) * kPlanes * 2.0 +
-                       (double)naux * s->Kpad_r * kPlanes * 2.0;
+                       (8.0 + 12.0) * std::max((double)naux * s->Kpad_p0, (double)nk * nao * s->Kpad_s) * 2.0 +
+                       (double)naux * s->Kpad_r * 8.0 * 2.0;
   int nt = d.tau_chunk > 0 ? d.tau_chunk : (int)std::max(1.0, std::floor(6442450944.0 / per_t));
   s->nt = std::min(nt, ntau);
   int rc = GW_OK;
   do {
-    if ((rc = alloc_planes(s, &s->vrow, (long long)nk * nk * naux * nao, s->Kc_vg, s->Kpad_vg, bytes))) break;
-    if ((rc = alloc_planes(s, &s->vcol, (long long)nk * nk * s->nao2, s->Kc_r, s->Kpad_r, bytes))) break;
-    if ((rc = alloc_planes(s, &s->gf, (long long)nk * ntau * nao, s->Kc_vg, s->Kpad_vg, bytes))) break;
-    if ((rc = alloc_planes(s, &s->gm, (long long)nk * ntau * nao, s->Kc_vg, s->Kpad_vg, bytes))) break;
-    if ((rc = alloc_planes(s, &s->ps, (long long)s->nt * naux, s->Kc_r, s->Kpad_r, bytes))) break;
-    const size_t xs_elems =
-        (size_t)kPlanes * std::max((size_t)s->nt * naux * s->Kpad_p0, (size_t)s->nt * nk * nao * s->Kpad_s);
-    if ((rc = m_alloc(s, &s->xs_mem, xs_elems, bytes))) break;
-    if ((rc = m_alloc(s, &s->ys_mem, xs_elems, bytes))) break;
+    if ((rc = alloc_planes(s, &s->vrow, (long long)nk * nk * naux * nao, s->Kc_vg, s->Kpad_vg, 2, bytes))) break;
+    if ((rc = alloc_planes(s, &s->vcol, (long long)nk * nk * s->nao2, s->Kc_r, s->Kpad_r, 3, bytes))) break;
+    if ((rc = alloc_planes(s, &s->gf, (long long)nk * ntau * nao, s->Kc_vg, s->Kpad_vg, 3, bytes))) break;
+    if ((rc = alloc_planes(s, &s->gm, (long long)nk * ntau * nao, s->Kc_vg, s->Kpad_vg, 3, bytes))) break;
+    if ((rc = alloc_planes(s, &s->ps, (long long)s->nt * naux, s->Kc_r, s->Kpad_r, 2, bytes))) break;
+    // A operands (re, im groups) and B operands (re, im, -im groups) of the P0 and Sigma contractions
+    const size_t op_elems = 4 * std::max((size_t)s->nt * naux * s->Kpad_p0, (size_t)s->nt * nk * nao * s->Kpad_s);
+    if ((rc = m_alloc(s, &s->xs_mem, 2 * op_elems, bytes))) break;
+    if ((rc = m_alloc(s, &s->ys_mem, 3 * op_elems, bytes))) break;
     if ((rc = m_alloc(s, &s->x64, (size_t)s->nt * nk * s->pair, bytes))) break;
     if ((rc = m_alloc(s, &s->y64, (size_t)s->nt * nk * s->pair, bytes))) break;
     {
@@ -1009,7 +1050,8 @@ int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int*
         cudaGetLastError();
         sms = 152;   // size-only build without a device: the GB300's SM count
       }
-      if ((rc = m_alloc(s, &s->ws, (size_t)std::max(sms, 1) * kBM * 80, bytes))) break;
+      // per-CTA running sums and chunk values of the GEMM epilogue
+      if ((rc = m_alloc(s, &s->ws, 2 * (size_t)std::max(sms, 1) * kBM * OzShape::kBN, bytes))) break;
     }
     std::vector<long long> t((size_t)kTabs * nk * nk);
     const long long vrows = (long long)naux * nao;
