@@ -59,9 +59,34 @@ constexpr int kMaxChunk = 256; // k per exact-accumulation chunk
 
 // Source elements are FP64 complex (double2) or, for intermediates written by
 // the GEMM epilogue, double-float complex: float4 (re_hi, re_lo, im_hi, im_lo)
-// in the same 16-byte slot. Slicing uses integer arithmetic only: the element
-// scaled to 2^31 / 2^E is rounded to an integer N (|N| <= 2^31) and split into
-// four signed base-256 digits, so no FP64 instruction runs per element.
+// in the same 16-byte slot. No FP64 instruction runs per element. An FP64
+// element scaled to 2^31 / 2^E is rounded to an integer N (|N| <= 2^31) and
+// split into four signed base-256 digits. A double-float element (h, l) is
+// rounded, level by level, to a multiple of the slice quantum q_i = 2^(E-7-8i)
+// by adding and subtracting 1.5 * 2^23 * q_i in FP32 (exact: |h| < 2^22 q_i);
+// the remainder h - s_i is exact and is renormalised with l before the next
+// level, so every digit stays within 128 and the four slices carry the value
+// to within 2^(E-32).
+
+// Division by a fixed divisor d < 2^31 for numerators x < 2^31: x / d = (x * m) >> sh
+// with m = ceil(2^sh / d), sh = 31 + ceil(log2 d) (the error of m times x stays below 2^sh).
+struct FastDiv {
+  unsigned long long m = 1ull << 31;
+  int sh = 31, d = 1;
+};
+__host__ FastDiv make_fastdiv(int d) {
+  FastDiv f;
+  int l = 0;
+  while ((1ll << l) < d) ++l;
+  f.d = d;
+  f.sh = 31 + l;
+  f.m = ((1ull << f.sh) + (unsigned long long)d - 1) / (unsigned long long)d;
+  return f;
+}
+__device__ __forceinline__ int fdiv(int x, const FastDiv& f) {
+  return (int)(((unsigned long long)(unsigned)x * f.m) >> f.sh);
+}
+
 struct SliceJob {
   const double2* src = nullptr;
   int src_df = 0;          // 1: src holds double-float complex values
@@ -74,13 +99,11 @@ struct SliceJob {
   int groups = 2;               // 3: also write the negated imaginary slices
   long long dst_row0 = 0;       // first destination row of batch 0
   long long dst_rows_per_batch = 0;
+  FastDiv kdiv;                 // division by v.kin
 };
 
 __device__ __forceinline__ long long s_view_row(const ZView& v, int r) {
   return (long long)(r / v.rin) * v.rs_out + (long long)(r % v.rin) * v.rs_in;
-}
-__device__ __forceinline__ long long s_view_k(const ZView& v, int k) {
-  return (long long)(k / v.kin) * v.ks_out + (long long)(k % v.kin) * v.ks_in;
 }
 
 // round(x * 2^(31 - E)) for an FP64 bit pattern x with |x| < 2^E (round half up on |x|).
@@ -93,16 +116,17 @@ __device__ __forceinline__ long long fixed31_f64(unsigned long long bits, int E)
   return (bits >> 63) ? -n : n;
 }
 
-// round(x * 2^(31 - E)) for an FP32 bit pattern x with |x| < 2^E (shift may be to the left).
-__device__ __forceinline__ long long fixed31_f32(uint32_t bits, int E) {
-  const int eb = (int)((bits >> 23) & 0xFF);
-  if (eb == 0) return 0;
-  const long long m = (long long)((bits & 0x7FFFFFu) | (1u << 23));
-  const int sh = 119 + E - eb;           // x = m 2^(eb - 150); sh >= -7 because |x| < 2^E
-  long long n;
-  if (sh <= 0) n = m << (-sh);
-  else n = sh >= 62 ? 0 : ((m + (1ll << (sh - 1))) >> sh);
-  return (bits >> 31) ? -n : n;
+// Slices of the double-float value h + l (|h + l| < 2^E): s_i, a multiple of q_i with
+// |s_i| <= 128 q_i, for i = 0..3 (magic[i] = 1.5 * 2^23 * q_i).
+__device__ __forceinline__ void df_slices(float h, float l, const float magic[4], float s[4]) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    s[i] = __fsub_rn(__fadd_rn(h, magic[i]), magic[i]);   // h rounded to a multiple of q_i
+    h = __fsub_rn(h, s[i]);                               // exact
+    const float t = __fadd_rn(h, l);                      // renormalise (|h| >= |l| or h = 0)
+    l = __fsub_rn(l, __fsub_rn(t, h));
+    h = t;
+  }
 }
 
 // N (|N| <= 2^31 + 1) -> signed base-256 digits d0..d3, N = d0 2^24 + d1 2^16 + d2 2^8 + d3, |d| <= 128.
@@ -141,7 +165,8 @@ __global__ void __launch_bounds__(256) slice_kernel(const SliceJob j) {
     const int k = c * j.Kc + e;
     xr[v] = xi[v] = 0;
     if (e < j.Kc && k < j.K) {
-      const long long off = s_view_k(j.v, k);
+      const int kq = fdiv(k, j.kdiv);
+      const long long off = (long long)kq * j.v.ks_out + (long long)(k - kq * j.v.kin) * j.v.ks_in;
       if (DF) {
         const float4 f = reinterpret_cast<const float4*>(src)[off];
         xr[v] = ((unsigned long long)__float_as_uint(f.y) << 32) | __float_as_uint(f.x);
@@ -174,26 +199,37 @@ __global__ void __launch_bounds__(256) slice_kernel(const SliceJob j) {
   const long long kstride = j.dst_rows * 64;                      // between k-steps
   const long long gstride = (long long)(j.Kpad / 16) * kstride;   // between groups
   __nv_bfloat16* out = j.dst + row * 64;
-  float scale[4];
+  // chunks whose largest value is below 2^-90 are taken as zero (their slices would be subnormal)
+  if (E < -90) zero = true;
+  float scale[4], magic[4];
 #pragma unroll
-  for (int s = 0; s < 4; ++s) scale[s] = ldexpf(1.0f, E - 7 - 8 * s);
+  for (int s = 0; s < 4; ++s) {
+    scale[s] = ldexpf(1.0f, E - 7 - 8 * s);
+    magic[s] = ldexpf(3.0f, E + 15 - 8 * s);      // 1.5 * 2^23 * q_s
+  }
 #pragma unroll
   for (int u = 0; u < kPairs; ++u) {
     const int e = 2 * lane + 64 * u;
     if (e >= j.Kc) break;                // Kc is a multiple of 16, so e + 1 < Kc as well
-    int dr[2][4], di[2][4];
+    float fr[2][4], fi[2][4];            // slice values, digit * q_s (exact in bf16)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int v = 2 * u + h;
       if (zero) {
 #pragma unroll
-        for (int s = 0; s < 4; ++s) dr[h][s] = di[h][s] = 0;
+        for (int s = 0; s < 4; ++s) fr[h][s] = fi[h][s] = 0.0f;
       } else if (DF) {
-        split_digits(fixed31_f32((uint32_t)xr[v], E) + fixed31_f32((uint32_t)(xr[v] >> 32), E), dr[h]);
-        split_digits(fixed31_f32((uint32_t)xi[v], E) + fixed31_f32((uint32_t)(xi[v] >> 32), E), di[h]);
+        df_slices(__uint_as_float((uint32_t)xr[v]), __uint_as_float((uint32_t)(xr[v] >> 32)), magic, fr[h]);
+        df_slices(__uint_as_float((uint32_t)xi[v]), __uint_as_float((uint32_t)(xi[v] >> 32)), magic, fi[h]);
       } else {
-        split_digits(fixed31_f64(xr[v], E), dr[h]);
-        split_digits(fixed31_f64(xi[v], E), di[h]);
+        int dr[4], di[4];
+        split_digits(fixed31_f64(xr[v], E), dr);
+        split_digits(fixed31_f64(xi[v], E), di);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          fr[h][s] = (float)dr[s] * scale[s];
+          fi[h][s] = (float)di[s] * scale[s];
+        }
       }
     }
     const int k = c * j.Kc + e;          // even: the pair (k, k + 1) shares its k-step
@@ -201,9 +237,8 @@ __global__ void __launch_bounds__(256) slice_kernel(const SliceJob j) {
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
       // digit * 2^(E - 7 - 8s) is exact in float and in bf16 (|digit| <= 128)
-      *reinterpret_cast<__nv_bfloat162*>(o + 16 * s) =
-          __floats2bfloat162_rn((float)dr[0][s] * scale[s], (float)dr[1][s] * scale[s]);
-      const __nv_bfloat162 im = __floats2bfloat162_rn((float)di[0][s] * scale[s], (float)di[1][s] * scale[s]);
+      *reinterpret_cast<__nv_bfloat162*>(o + 16 * s) = __floats2bfloat162_rn(fr[0][s], fr[1][s]);
+      const __nv_bfloat162 im = __floats2bfloat162_rn(fi[0][s], fi[1][s]);
       *reinterpret_cast<__nv_bfloat162*>(o + gstride + 16 * s) = im;
       if (j.groups == 3) *reinterpret_cast<__nv_bfloat162*>(o + 2 * gstride + 16 * s) = __hneg2(im);
     }
@@ -233,6 +268,7 @@ struct OzParams {
   int dblock = 0, dgroup = 1, dtotal = 0;
   float4* ws = nullptr;               // per-CTA running sums across chunks, gridDim.x * 128 * BN
   float4* cw = nullptr;               // per-CTA newest chunk values, same shape
+  FastDiv cdiv;                       // division by vc.kin
   int* status = nullptr;              // status[1] <- error code of a device-side wait that gave up
 };
 
@@ -552,7 +588,8 @@ __global__ void __launch_bounds__(320, 1)
       };
       auto out_write = [&](int cl, float rh, float rl, float ih, float il) {
         const int n = nt * BN + cl - dcol0;
-        double2* dst = C + roff + (long long)(n / p.vc.kin) * p.vc.ks_out + (long long)(n % p.vc.kin) * p.vc.ks_in;
+        const int nq = fdiv(n, p.cdiv);
+        double2* dst = C + roff + (long long)nq * p.vc.ks_out + (long long)(n - nq * p.vc.kin) * p.vc.ks_in;
         if (p.out_df) {
           *reinterpret_cast<float4*>(dst) = make_float4(rh, rl, ih, il);
         } else {
@@ -736,6 +773,7 @@ int launch_oz(const Planes& A, const Planes& B, OzParams p, int slot, cudaStream
   if (total == 0) return GW_OK;
   if (total > 2147483647LL) return fail(GW_EINVAL, "oz_gemm: too many tiles");
   if (!p.ws) return fail(GW_EINVAL, "oz_gemm: no epilogue scratch");
+  p.cdiv = make_fastdiv(p.vc.kin);
   p.cw = p.ws + (size_t)num_sms() * kBM * S::kBN;
   CUtensorMap ma, mb;
   GW_TRY_INTERNAL(make_map(A, kBM, &ma));
@@ -849,6 +887,7 @@ int slice(MixedState* s, const double2* src, const ZView& v, long long b_in, lon
   j.Kc = P.Kc;
   j.Kpad = P.Kpad;
   j.nbatch = nbatch;
+  j.kdiv = make_fastdiv(v.kin);
   j.dst = P.ptr;
   j.dst_rows = P.rows;
   j.groups = P.groups;
@@ -873,34 +912,42 @@ int slice_g(MixedState* s, const double2* G) {
 
 // out[t][k][Q][i][b] = sum_a V^{pair(k)}_ia(Q) G^{kg(k)}_ab(t) for t in [t0, t0+nt) (A and Z), or, with
 // transposed, out[t][k][Q'][d][b] = sum_c V^{pair(k)}_bc(Q') G^{kg(k)}_cd(beta - t) (the B operand of P0).
+// Both put the innermost output index b on the TMEM lanes, so a warp's stores are contiguous: the first
+// as the GEMM rows (t, b) of G^T times columns (Q, i) of V, the second as rows (Q', b) of V times
+// columns (t, d) of G.
 int vg_gemm(MixedState* s, int pair_tab, int g_tab, const Planes& Gp, int q, int t0, int nt, bool transposed,
             double2* out) {
   const int nk = s->d.nk, nao = s->d.nao, naux = s->d.naux;
   OzParams p;
-  p.M = naux * nao;
-  p.N = nt * nao;
   p.nbatch = nk;
-  p.a_tab = tab(s, pair_tab, q);
-  p.b_tab = tab(s, g_tab, q);
-  p.b_row0 = (long long)t0 * nao;
   p.C = out;
   p.bc.bs_in = s->pair;
-  if (!transposed) {
-    p.vc.rs_in = nao;
-    p.vc.kin = nao;
-    p.vc.ks_in = 1;
-    p.vc.ks_out = (long long)nk * s->pair;
-  } else {
-    p.vc.rin = nao;
-    p.vc.rs_in = 1;
-    p.vc.rs_out = s->nao2;
-    p.vc.kin = nao;
-    p.vc.ks_in = nao;
-    p.vc.ks_out = (long long)nk * s->pair;
-  }
   p.status = s->status;
   p.ws = s->ws;
   p.out_df = 1;
+  if (!transposed) {
+    p.M = nt * nao;                       // (t, b)
+    p.N = naux * nao;                     // (Q, i)
+    p.a_tab = tab(s, g_tab, q);
+    p.a_row0 = (long long)t0 * nao;
+    p.b_tab = tab(s, pair_tab, q);
+    p.vc.rin = nao;
+    p.vc.rs_in = 1;
+    p.vc.rs_out = (long long)nk * s->pair;
+    p.vc.ks_in = nao;
+    return launch_oz(Gp, s->vrow, p, SLOT_VG_MIXED, s->stream);
+  }
+  p.M = naux * nao;                       // (Q', b)
+  p.N = nt * nao;                         // (t, d)
+  p.a_tab = tab(s, pair_tab, q);
+  p.b_tab = tab(s, g_tab, q);
+  p.b_row0 = (long long)t0 * nao;
+  p.vc.rin = nao;
+  p.vc.rs_in = 1;
+  p.vc.rs_out = s->nao2;
+  p.vc.kin = nao;
+  p.vc.ks_in = nao;
+  p.vc.ks_out = (long long)nk * s->pair;
   return launch_oz(s->vrow, Gp, p, SLOT_VG_MIXED, s->stream);
 }
 
@@ -943,23 +990,24 @@ int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double
     GW_TRY_INTERNAL(slice(s, Pt + ((long long)q * ntau + t0) * s->naux2, v, s->naux2, 0, 1 << 30, nt, naux, naux,
                           s->ps, naux));
   }
-  {  // R^Q_{bj}(k,t) = sum_Q' P~_QQ'(t) V^{k-q,k}_bj(Q')  -> y64[t][k][Q][j][b]
+  {  // R^Q_{bj}(k,t) = sum_Q' P~_QQ'(t) V^{k-q,k}_bj(Q')  -> y64[t][k][Q][j][b], computed as
+     // rows (j, b) of V times columns Q of P~ so that the stores of a warp are contiguous
     OzParams p;
-    p.M = naux;
-    p.N = (int)s->nao2;
+    p.M = (int)s->nao2;
+    p.N = naux;
     p.nbatch = nt * nk;
     p.bin = nk;
-    p.a_bs_out = naux;                      // rows t * naux
-    p.b_tab = tab(s, T_VCOL_KMQK, q);
+    p.a_tab = tab(s, T_VCOL_KMQK, q);       // per k
+    p.b_bs_out = naux;                      // rows t * naux
     p.C = s->y64;
     p.bc.bs_in = s->pair;
     p.bc.bs_out = (long long)nk * s->pair;
-    p.vc.rs_in = s->nao2;
-    p.vc.ks_in = 1;
+    p.vc.rs_in = 1;
+    p.vc.ks_in = s->nao2;
     p.status = s->status;
     p.ws = s->ws;
     p.out_df = 1;                           // double-float, sliced again for the Sigma contraction
-    GW_TRY_INTERNAL(launch_oz(s->ps, s->vcol, p, SLOT_R_TC, s->stream));
+    GW_TRY_INTERNAL(launch_oz(s->vcol, s->ps, p, SLOT_R_TC, s->stream));
   }
   // Z^Q_{ib}(k,t) = sum_a V^{k,k-q}_ia(Q) G^{k-q}_ab(t) -> x64[t][k][Q][i][b]
   GW_TRY_INTERNAL(vg_gemm(s, T_VKKMQ, T_GKMQ, s->gf, q, t0, nt, false, s->x64));
@@ -1032,11 +1080,11 @@ int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int*
   s->nt = std::min(nt, ntau);
   int rc = GW_OK;
   do {
-    if ((rc = alloc_planes(s, &s->vrow, (long long)nk * nk * naux * nao, s->Kc_vg, s->Kpad_vg, 2, bytes))) break;
-    if ((rc = alloc_planes(s, &s->vcol, (long long)nk * nk * s->nao2, s->Kc_r, s->Kpad_r, 3, bytes))) break;
-    if ((rc = alloc_planes(s, &s->gf, (long long)nk * ntau * nao, s->Kc_vg, s->Kpad_vg, 3, bytes))) break;
+    if ((rc = alloc_planes(s, &s->vrow, (long long)nk * nk * naux * nao, s->Kc_vg, s->Kpad_vg, 3, bytes))) break;
+    if ((rc = alloc_planes(s, &s->vcol, (long long)nk * nk * s->nao2, s->Kc_r, s->Kpad_r, 2, bytes))) break;
+    if ((rc = alloc_planes(s, &s->gf, (long long)nk * ntau * nao, s->Kc_vg, s->Kpad_vg, 2, bytes))) break;
     if ((rc = alloc_planes(s, &s->gm, (long long)nk * ntau * nao, s->Kc_vg, s->Kpad_vg, 3, bytes))) break;
-    if ((rc = alloc_planes(s, &s->ps, (long long)s->nt * naux, s->Kc_r, s->Kpad_r, 2, bytes))) break;
+    if ((rc = alloc_planes(s, &s->ps, (long long)s->nt * naux, s->Kc_r, s->Kpad_r, 3, bytes))) break;
     // A operands (re, im groups) and B operands (re, im, -im groups) of the P0 and Sigma contractions
     const size_t op_elems = 4 * std::max((size_t)s->nt * naux * s->Kpad_p0, (size_t)s->nt * nk * nao * s->Kpad_s);
     if ((rc = m_alloc(s, &s->xs_mem, 2 * op_elems, bytes))) break;
