@@ -22,7 +22,7 @@
 //
 // Kernels
 //   slice_kernel   FP64 or double-float complex view -> bf16 slice groups
-//                  [re | im | -im][k-step][row][4 slices x 16 k]
+//                  [re | im][k-step][row][4 slices x 16 k]
 //   oz_gemm_kernel persistent tcgen05 GEMM over group tiles loaded by TMA
 //                  (128-byte swizzle, K-major, one 16-wide k-step per pipeline stage)
 #include <cuda.h>
@@ -96,7 +96,6 @@ struct SliceJob {
   int rows = 0, K = 0, Kc = 0, Kpad = 0, nbatch = 1;
   __nv_bfloat16* dst = nullptr;
   long long dst_rows = 0;       // rows of the destination planes buffer
-  int groups = 2;               // 3: also write the negated imaginary slices
   long long dst_row0 = 0;       // first destination row of batch 0
   long long dst_rows_per_batch = 0;
   FastDiv kdiv;                 // division by v.kin
@@ -147,10 +146,11 @@ __global__ void __launch_bounds__(256) slice_kernel(const SliceJob j) {
   const int nchunk = j.Kpad / j.Kc;
   const long long total = (long long)j.nbatch * j.rows * nchunk;
   if (warp_global >= total) return;
-  const int c = (int)(warp_global % nchunk);
-  const long long br = warp_global / nchunk;
-  const int r = (int)(br % j.rows);
-  const int b = (int)(br / j.rows);
+  // consecutive warps take consecutive rows of one chunk: their 128-byte output lines are adjacent
+  const int r = (int)(warp_global % j.rows);
+  const long long bc = warp_global / j.rows;
+  const int c = (int)(bc % nchunk);
+  const int b = (int)(bc / nchunk);
   const int bo = b / j.bin, bi = b % j.bin;
   const double2* src = j.src + (j.b.tab ? j.b.tab[bi] : (long long)bi * j.b.bs_in) + (long long)bo * j.b.bs_out +
                        s_view_row(j.v, r);
@@ -238,9 +238,7 @@ __global__ void __launch_bounds__(256) slice_kernel(const SliceJob j) {
     for (int s = 0; s < 4; ++s) {
       // digit * 2^(E - 7 - 8s) is exact in float and in bf16 (|digit| <= 128)
       *reinterpret_cast<__nv_bfloat162*>(o + 16 * s) = __floats2bfloat162_rn(fr[0][s], fr[1][s]);
-      const __nv_bfloat162 im = __floats2bfloat162_rn(fi[0][s], fi[1][s]);
-      *reinterpret_cast<__nv_bfloat162*>(o + gstride + 16 * s) = im;
-      if (j.groups == 3) *reinterpret_cast<__nv_bfloat162*>(o + 2 * gstride + 16 * s) = __hneg2(im);
+      *reinterpret_cast<__nv_bfloat162*>(o + gstride + 16 * s) = __floats2bfloat162_rn(fi[0][s], fi[1][s]);
     }
   }
 }
@@ -381,14 +379,14 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Output tile 128 x 80. The planes of an operand are stored in groups of four
-// slices: group 0 holds the real parts, group 1 the imaginary parts and, for
-// operands used as B, group 2 the negated imaginary parts; within a group one
+// slices: group 0 holds the real parts, group 1 the imaginary parts; within a group one
 // 128-byte row holds the four slices of 16 consecutive k (slice s at bytes
 // [32 s, 32 s + 32)). A stage is one such 128-byte row per operand row and
 // group, loaded by one TMA box per group with the 128-byte swizzle; slice s is
 // addressed by advancing the descriptor start by 32 s bytes inside the
-// swizzle atom. B's three groups sit as consecutive 80-row blocks [Bi; Br; -Bi]
-// so that one complex slice product is two MMAs of N = 160:
+// swizzle atom. B sits as three consecutive 80-row blocks [Bi; Br; -Bi] (the
+// third made from the first by a sign flip in shared memory, by warp 10) so
+// that one complex slice product is two MMAs of N = 160:
 //   A_r x [Bi; Br]  -> columns [0, 80) += A_r B_i,  [80, 160) += A_r B_r
 //   A_i x [Br; -Bi] -> columns [0, 80) += A_i B_r,  [80, 160) -= A_i B_i
 // (imaginary part first, real part second). Three orders take 480 TMEM
@@ -403,6 +401,8 @@ struct OzShape {
   static constexpr int kAGroup = kBM * kRowBytes;      // bytes of one A group tile
   static constexpr int kBBlock = kBN * kRowBytes;      // bytes of one B group block
   static constexpr uint32_t kStageBytes = 2 * kAGroup + 3 * kBBlock;
+  static constexpr uint32_t kTxBytes = 2 * kAGroup + 2 * kBBlock;   // what TMA brings per stage
+  static constexpr int kThreads = 352;                 // producer, MMA, 8 epilogue warps, negation warp
   static constexpr int kOrderCols = 2 * kBN;           // [im | re] of one order
   static constexpr int kTmemCols = 512;
   static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + 256;
@@ -424,16 +424,17 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-__global__ void __launch_bounds__(320, 1)
+__global__ void __launch_bounds__(352, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const OzParams p) {
   using S = OzShape;
   constexpr int BN = S::kBN;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + (size_t)S::kStages * S::kStageBytes);
-  uint64_t* full = bars;
-  uint64_t* empty = bars + S::kStages;
-  uint64_t* acc_full = bars + 2 * S::kStages;
+  uint64_t* full = bars;                           // TMA landed
+  uint64_t* empty = bars + S::kStages;             // MMAs done with the stage
+  uint64_t* ready = bars + 2 * S::kStages;         // -Bi block written
+  uint64_t* acc_full = bars + 3 * S::kStages;
   uint64_t* acc_empty = acc_full + 1;
   uint64_t* drain_bar = acc_full + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 3);
@@ -444,6 +445,7 @@ __global__ void __launch_bounds__(320, 1)
     for (int s = 0; s < S::kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
+      mbar_init(&ready[s], 1);
     }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, 8);                 // one arrival per epilogue warp
@@ -467,7 +469,7 @@ __global__ void __launch_bounds__(320, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      // ---------------- TMA producer: per k-step A (re, im) and B (im, re, -im) group tiles
+      // ---------------- TMA producer: per k-step A (re, im) and B (im, re) group tiles
       uint32_t step = 0;
       for (int tile = blockIdx.x; tile < total_tiles && !*abort_flag; tile += gridDim.x) {
         const int b = tile / tiles_per_batch, mt = (tile % tiles_per_batch) / p.ntiles, nt = tile % p.ntiles;
@@ -478,14 +480,13 @@ __global__ void __launch_bounds__(320, 1)
           const int st = step % S::kStages;
           const uint32_t ph = (step / S::kStages) & 1;
           if (!mbar_wait(&empty[st], ph ^ 1, abort_flag, p.status, 11)) break;
-          mbar_expect_tx(&full[st], S::kStageBytes);
+          mbar_expect_tx(&full[st], S::kTxBytes);
           uint8_t* sa = smem + (size_t)st * S::kStageBytes;
           uint8_t* sb = sa + 2 * S::kAGroup;
           tma_load_3d(sa, &tmA, 0, arow, s, &full[st]);                                // A re
           tma_load_3d(sa + S::kAGroup, &tmA, 0, arow, p.nsteps + s, &full[st]);        // A im
           tma_load_3d(sb, &tmB, 0, brow, p.nsteps + s, &full[st]);                     // B im
           tma_load_3d(sb + S::kBBlock, &tmB, 0, brow, s, &full[st]);                   // B re
-          tma_load_3d(sb + 2 * S::kBBlock, &tmB, 0, brow, 2 * p.nsteps + s, &full[st]); // -B im
         }
       }
       if (*abort_flag) {
@@ -516,7 +517,7 @@ __global__ void __launch_bounds__(320, 1)
           }
           const int st = step % S::kStages;
           const uint32_t ph = (step / S::kStages) & 1;
-          if (!mbar_wait(&full[st], ph, abort_flag, p.status, 13)) { ok = false; break; }
+          if (!mbar_wait(&ready[st], ph, abort_flag, p.status, 13)) { ok = false; break; }
           tc_fence_after();
           // descriptor start fields (address >> 4) of this stage; shared memory < 256 KB: no carry
           const uint64_t sa = desc0 + (uint64_t)((st * S::kStageBytes) >> 4);
@@ -549,6 +550,34 @@ __global__ void __launch_bounds__(320, 1)
       mma_commit(drain_bar);
       const uint64_t t0 = globaltimer();
       while (!mbar_try(drain_bar, 0) && globaltimer() - t0 < kWaitLimitNs) {
+      }
+    }
+  } else if (warp == 10) {
+    // ---------------- -Bi block of each stage: sign flip of the Bi block (same swizzle phase)
+    uint32_t step = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < total_tiles && ok; tile += gridDim.x) {
+      for (int s = 0; s < p.nsteps; ++s, ++step) {
+        const int st = step % S::kStages;
+        const uint32_t ph = (step / S::kStages) & 1;
+        int w = 1;
+        if (lane == 0) w = mbar_wait(&full[st], ph, abort_flag, p.status, 15);
+        if (!__shfl_sync(0xffffffffu, w, 0)) { ok = false; break; }
+        const uint4* src = reinterpret_cast<const uint4*>(smem + (size_t)st * S::kStageBytes + 2 * S::kAGroup);
+        uint4* dst = const_cast<uint4*>(src) + 2 * S::kBBlock / 16;
+        constexpr int kVec = S::kBBlock / 16;          // 640 per block
+#pragma unroll 4
+        for (int v = lane; v < kVec; v += 32) {
+          uint4 x = src[v];
+          x.x ^= 0x80008000u;
+          x.y ^= 0x80008000u;
+          x.z ^= 0x80008000u;
+          x.w ^= 0x80008000u;
+          dst[v] = x;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ready[st]);
       }
     }
   } else {
@@ -694,10 +723,9 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// Planes buffer: [8][rows][Kpad] bf16.
-// Planes buffer: groups x (Kpad / 16) x rows x 64 bf16. Group 0 holds the real slices,
-// group 1 the imaginary ones and group 2 (operands used as B only) the negated imaginary
-// ones; the 64 values of (group, k-step, row) are the four slices of 16 consecutive k.
+// Planes buffer: 2 groups x (Kpad / 16) x rows x 64 bf16. Group 0 holds the real slices,
+// group 1 the imaginary ones; the 64 values of (group, k-step, row) are the four slices
+// of 16 consecutive k.
 struct Planes {
   __nv_bfloat16* ptr = nullptr;
   long long rows = 0;
@@ -764,7 +792,7 @@ int launch_slice(const SliceJob& j, cudaStream_t st) {
 int launch_oz(const Planes& A, const Planes& B, OzParams p, int slot, cudaStream_t st) {
   using S = OzShape;
   if (A.Kpad != B.Kpad || A.Kc != B.Kc) return fail(GW_EINVAL, "oz_gemm: operand chunking differs");
-  if (A.groups < 2 || B.groups < 3) return fail(GW_EINVAL, "oz_gemm: B needs its negated imaginary planes");
+  if (A.groups != 2 || B.groups != 2) return fail(GW_EINVAL, "oz_gemm: operands need two slice groups");
   p.nsteps = A.Kpad / kStepK;
   p.steps_per_chunk = A.Kc / kStepK;
   p.mtiles = (p.M + kBM - 1) / kBM;
@@ -786,10 +814,10 @@ int launch_oz(const Planes& A, const Planes& B, OzParams p, int slot, cudaStream
   (void)attr;
   const int grid = (int)std::min<long long>(total, num_sms());
   prof_begin(slot, st);
-  oz_gemm_kernel<<<grid, 320, S::kSmem, st>>>(ma, mb, p);
+  oz_gemm_kernel<<<grid, S::kThreads, S::kSmem, st>>>(ma, mb, p);
   // executed bf16 tensor flops: 10 slice products x 2 real MMAs of 128 x 160 x 16 per k-step
   prof_end(slot, st, 2.0 * 20.0 * (double)total * kBM * (2 * S::kBN) * (double)p.nsteps * kStepK,
-           (double)total * p.nsteps * S::kStageBytes);
+           (double)total * p.nsteps * S::kTxBytes);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "oz_gemm launch: %s", cudaGetErrorString(e));
 }
@@ -890,7 +918,6 @@ int slice(MixedState* s, const double2* src, const ZView& v, long long b_in, lon
   j.kdiv = make_fastdiv(v.kin);
   j.dst = P.ptr;
   j.dst_rows = P.rows;
-  j.groups = P.groups;
   j.dst_rows_per_batch = dst_rows_per_batch;
   return launch_slice(j, s->stream);
 }
@@ -956,7 +983,7 @@ int polarization_chunk(MixedState* s, const double2* G, double2* P0t, double spi
   GW_TRY_INTERNAL(vg_gemm(s, T_VKKPQ, T_GKPQ, s->gf, q, t0, nt, false, s->x64));
   GW_TRY_INTERNAL(vg_gemm(s, T_VKPQK, T_GK, s->gm, q, t0, nt, true, s->y64));
   const Planes xs = view(s->xs_mem, (long long)nt * naux, s->Kc_p0, s->Kpad_p0, 2);
-  const Planes ys = view(s->ys_mem, (long long)nt * naux, s->Kc_p0, s->Kpad_p0, 3);
+  const Planes ys = view(s->ys_mem, (long long)nt * naux, s->Kc_p0, s->Kpad_p0, 2);
   ZView v;                                 // rows Q, k = (k, d, b)
   v.rs_in = s->nao2;
   v.kin = (int)s->nao2;
@@ -1012,7 +1039,7 @@ int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double
   // Z^Q_{ib}(k,t) = sum_a V^{k,k-q}_ia(Q) G^{k-q}_ab(t) -> x64[t][k][Q][i][b]
   GW_TRY_INTERNAL(vg_gemm(s, T_VKKMQ, T_GKMQ, s->gf, q, t0, nt, false, s->x64));
   const Planes xs = view(s->xs_mem, (long long)nt * nk * nao, s->Kc_s, s->Kpad_s, 2);
-  const Planes ys = view(s->ys_mem, (long long)nt * nk * nao, s->Kc_s, s->Kpad_s, 3);
+  const Planes ys = view(s->ys_mem, (long long)nt * nk * nao, s->Kc_s, s->Kpad_s, 2);
   {
     ZView vz;                               // rows i, k = (Q, b)
     vz.rs_in = nao;
@@ -1072,23 +1099,23 @@ int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int*
   chunking(nk * (int)s->nao2, &s->Kc_p0, &s->Kpad_p0);
   chunking(naux, &s->Kc_r, &s->Kpad_r);
   chunking(naux * nao, &s->Kc_s, &s->Kpad_s);
-  // tau batch: FP64 intermediates plus operand planes per tau node, capped at 6 GiB
+  // tau batch: FP64 intermediates plus operand planes per tau node, capped at 12 GiB
   const double per_t = 2.0 * nk * (double)s->pair * 16.0 +
-                       (8.0 + 12.0) * std::max((double)naux * s->Kpad_p0, (double)nk * nao * s->Kpad_s) * 2.0 +
+                       (8.0 + 8.0) * std::max((double)naux * s->Kpad_p0, (double)nk * nao * s->Kpad_s) * 2.0 +
                        (double)naux * s->Kpad_r * 8.0 * 2.0;
-  int nt = d.tau_chunk > 0 ? d.tau_chunk : (int)std::max(1.0, std::floor(6442450944.0 / per_t));
+  int nt = d.tau_chunk > 0 ? d.tau_chunk : (int)std::max(1.0, std::floor(12884901888.0 / per_t));
   s->nt = std::min(nt, ntau);
   int rc = GW_OK;
   do {
-    if ((rc = alloc_planes(s, &s->vrow, (long long)nk * nk * naux * nao, s->Kc_vg, s->Kpad_vg, 3, bytes))) break;
+    if ((rc = alloc_planes(s, &s->vrow, (long long)nk * nk * naux * nao, s->Kc_vg, s->Kpad_vg, 2, bytes))) break;
     if ((rc = alloc_planes(s, &s->vcol, (long long)nk * nk * s->nao2, s->Kc_r, s->Kpad_r, 2, bytes))) break;
     if ((rc = alloc_planes(s, &s->gf, (long long)nk * ntau * nao, s->Kc_vg, s->Kpad_vg, 2, bytes))) break;
-    if ((rc = alloc_planes(s, &s->gm, (long long)nk * ntau * nao, s->Kc_vg, s->Kpad_vg, 3, bytes))) break;
-    if ((rc = alloc_planes(s, &s->ps, (long long)s->nt * naux, s->Kc_r, s->Kpad_r, 3, bytes))) break;
-    // A operands (re, im groups) and B operands (re, im, -im groups) of the P0 and Sigma contractions
+    if ((rc = alloc_planes(s, &s->gm, (long long)nk * ntau * nao, s->Kc_vg, s->Kpad_vg, 2, bytes))) break;
+    if ((rc = alloc_planes(s, &s->ps, (long long)s->nt * naux, s->Kc_r, s->Kpad_r, 2, bytes))) break;
+    // A and B operands (re and im slice groups) of the P0 and Sigma contractions
     const size_t op_elems = 4 * std::max((size_t)s->nt * naux * s->Kpad_p0, (size_t)s->nt * nk * nao * s->Kpad_s);
     if ((rc = m_alloc(s, &s->xs_mem, 2 * op_elems, bytes))) break;
-    if ((rc = m_alloc(s, &s->ys_mem, 3 * op_elems, bytes))) break;
+    if ((rc = m_alloc(s, &s->ys_mem, 2 * op_elems, bytes))) break;
     if ((rc = m_alloc(s, &s->x64, (size_t)s->nt * nk * s->pair, bytes))) break;
     if ((rc = m_alloc(s, &s->y64, (size_t)s->nt * nk * s->pair, bytes))) break;
     {
@@ -1154,8 +1181,12 @@ int mixed_polarization(MixedState* s, const double2* G, double2* P0t, double spi
     // canonical tau nodes only (the caller fills P0^q(beta - tau) = P0^{-q}(tau)^T)
     const int mq = s->d.mq[q];
     const int tend = mq < q ? 0 : (mq == q ? (s->d.ntau + 1) / 2 : s->d.ntau);
-    for (int t0 = 0; t0 < tend; t0 += s->nt)
-      GW_TRY_INTERNAL(polarization_chunk(s, G, P0t, spin_factor, q, t0, std::min(s->nt, tend - t0)));
+    // equal batches of at most nt nodes (no short last batch that would leave the GPU half idle)
+    const int nb = (tend + s->nt - 1) / s->nt;
+    for (int i = 0; i < nb; ++i) {
+      const int t0 = (int)((long long)tend * i / nb), t1 = (int)((long long)tend * (i + 1) / nb);
+      GW_TRY_INTERNAL(polarization_chunk(s, G, P0t, spin_factor, q, t0, t1 - t0));
+    }
   }
   return GW_OK;
 }
@@ -1164,9 +1195,12 @@ int mixed_self_energy(MixedState* s, const double2* G, const double2* Pt, double
   if (cudaMemsetAsync(Sig, 0, (size_t)s->d.nk * s->d.ntau * s->nao2 * sizeof(double2), s->stream) != cudaSuccess)
     return fail(GW_ECUDA, "memset Sigma");
   GW_TRY_INTERNAL(slice_g(s, G));
+  const int nb = (s->d.ntau + s->nt - 1) / s->nt;      // equal batches of at most nt nodes
   for (int q = 0; q < s->d.nk; ++q)
-    for (int t0 = 0; t0 < s->d.ntau; t0 += s->nt)
-      GW_TRY_INTERNAL(self_energy_chunk(s, G, Pt, Sig, q, t0, std::min(s->nt, s->d.ntau - t0)));
+    for (int i = 0; i < nb; ++i) {
+      const int t0 = (int)((long long)s->d.ntau * i / nb), t1 = (int)((long long)s->d.ntau * (i + 1) / nb);
+      GW_TRY_INTERNAL(self_energy_chunk(s, G, Pt, Sig, q, t0, t1 - t0));
+    }
   return GW_OK;
 }
 
