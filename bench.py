@@ -38,12 +38,24 @@ WORKLOAD = "solid_3x3x3_nao26"
 FP64_PEAK_TFLOPS = 1.25      # GB300 nominal FP64 (no FP64 tensor path is faster on this part)
 
 
-def algorithmic_flops(nk, nao, naux, ntau, nwb):
-    """Real flops of one evaluation, 8 per complex multiply-add (Eqs. tilde_P0_tau ... sigma_gw)."""
+def canonical_fraction(nk3, n):
+    """Share of (q, index) pairs computed when X^q(n-1-i) = X^{-q}(i)^T is used: the q with
+    -q = q (mod the Gamma-centred mesh) keep (n+1)/2 of n indices, the other q half of theirs."""
+    sc = 1
+    for m in nk3:
+        sc *= 2 if m % 2 == 0 else 1
+    nk = int(np.prod(nk3))
+    return (sc * ((n + 1) // 2) + (nk - sc) * n / 2.0) / (nk * n)
+
+
+def algorithmic_flops(nk3, nao, naux, ntau, nwb):
+    """Real flops of one evaluation as computed, 8 per complex multiply-add (Eqs. tilde_P0_tau ...
+    sigma_gw): P0 and the aux Dyson solves only at canonical (q, tau) and (q, n); Sigma in full."""
+    nk = int(np.prod(nk3))
     contraction = 8.0 * nk * nk * ntau * (2.0 * naux * nao ** 3 + naux ** 2 * nao ** 2)   # each of P0, Sigma
     transforms = 2 * 8.0 * nk * nwb * ntau * naux ** 2
-    dyson = 8.0 * nk * nwb * naux ** 3 + 2.0 * nk * nwb * naux ** 2
-    return 2 * contraction + transforms + dyson
+    dyson = (8.0 * nk * nwb * naux ** 3 + 2.0 * nk * nwb * naux ** 2) * canonical_fraction(nk3, nwb)
+    return contraction * canonical_fraction(nk3, ntau) + contraction + transforms + dyson
 
 
 def measured_peaks():
@@ -379,7 +391,7 @@ def run_ours(args, rank, world, local_rank):
         serving = serving_measure(args.precision, args.serving_jobs)
 
     nwb = gw.gw_sample_count(w.ntau, 0)
-    flops = algorithmic_flops(w.nk, w.nao, w.naux, w.ntau, nwb)
+    flops = algorithmic_flops(w.nk3, w.nao, w.naux, w.ntau, nwb)
     steps = args.steps
     value = world * steps / (t_max / 1e3)
     peaks, peak_src = measured_peaks()
