@@ -138,34 +138,3 @@ def test_invalid_arguments_rejected(G):
     with pytest.raises(G.GWError):
         G.gw_set_coulomb(ctx, torch.zeros((1, 1, 4, 3, 2), dtype=torch.complex128, device="cuda"))
     ctx.destroy()
-
-
-def test_fp64_solid_3x3x3_nao26_sampled(G):
-    """Full-size Si-like solid (nk=27, nao=26, naux=200, ntau=100) through gw_sigma_eval;
-    the oracle recomputes sampled P0(q,tau) entries, P~ for one q, and Sigma at sampled (k,tau)."""
-    w = I.WORKLOADS["solid_3x3x3_nao26"]
-    h, v, g = I.make_inputs(w)
-    ctx = G.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision="fp64")
-    s = ctx.shapes()
-    V, Gd = dev(v), dev(g)
-    G.gw_set_coulomb(ctx, V)
-    P0t = torch.empty(s["Pt"], dtype=torch.complex128, device="cuda")
-    G.gw_polarization(ctx, Gd, P0t)
-    Pt = torch.empty_like(P0t)
-    G.gw_screened_interaction(ctx, P0t, Pt)
-    Sig = torch.empty(s["Sig"], dtype=torch.complex128, device="cuda")
-    G.gw_self_energy(ctx, Gd, Pt, Sig)
-    p0_gpu, pt_gpu, sig_gpu = host(P0t), host(Pt), host(Sig)
-    ctx.destroy()
-    rng = np.random.default_rng(12)
-    q_s = sorted(rng.choice(w.nk, 2, replace=False).tolist())
-    t_s = sorted(rng.choice(w.ntau, 3, replace=False).tolist()) + [0, w.ntau - 1]
-    p0_ref = O.polarization(v, g, w.nk3, 2.0, q_list=q_s, t_list=t_s)
-    assert rel(p0_gpu[q_s][:, t_s], p0_ref) < TOL
-    # P~ for one q needs P0 of that q at every tau
-    q1 = q_s[:1]
-    p0_q = O.polarization(v, g, w.nk3, 2.0, q_list=q1)
-    _, F, B = grids.transform_matrices(w.ntau, w.beta, 0)
-    _, _, pt_q = O.screened_interaction(p0_q, F, B)
-    assert rel(pt_gpu[q1], pt_q) < TOL
-    assert rel(sig_gpu, sig_gpu.conj().swapaxes(-1, -2)) < 1e-11
