@@ -56,10 +56,13 @@ typedef enum {
 
 typedef enum {
   GW_FP64 = 0,          /* every contraction in FP64 */
-  GW_MIXED_BF16X3 = 1,  /* V.G.V contractions on tcgen05 tensor cores with 3 bf16 limbs
-                           per FP32-rounded operand and FP32 accumulation; transforms,
-                           Dyson solves and the Sigma accumulation stay FP64 */
-  GW_MIXED_FP16S = 2    /* as above with one fp16 limb and a power-of-two scale per tile */
+  GW_MIXED_BF16X3 = 1,  /* V.G.V contractions on tcgen05 tensor cores: each operand row is cut,
+                           per chunk of at most 256 k, into four bf16 slices on one power-of-two
+                           alignment; slice products of order 0 and 1 sum exactly in their own
+                           FP32 accumulators, orders 2-3 share a third, higher orders are dropped
+                           (2^-32 relative); transforms, Dyson solves and the Sigma accumulation
+                           stay FP64 */
+  GW_MIXED_FP16S = 2    /* reserved: gw_create returns GW_ENOTIMPL */
 } gw_precision;
 
 typedef struct {
@@ -223,6 +226,45 @@ int gw_polarization_noalloc(const int nk3[3], int nao, int naux, int ntau, doubl
 
 /* Waits for all work queued on the context's stream. */
 int gw_synchronize(gw_ctx* ctx);
+
+/*
+ * Batched self-energy evaluation of many independent systems (molecules or k-meshes of
+ * uneven size). One context per system on one of max_streams CUDA streams (chosen by
+ * predicted cost, longest first onto the least-loaded stream). Modes of gw_batch_sigma_eval:
+ *   GW_BATCH_SERIAL   one system after another (the per-system launch loop),
+ *   GW_BATCH_STREAMS  all systems enqueued at once on their streams,
+ *   GW_BATCH_GRAPH    the same work captured once into a CUDA graph and replayed as one
+ *                     graph launch; recaptured when the G or Sigma pointers change (the
+ *                     first call after creation or gw_batch_set_coulomb runs uncaptured).
+ * Every mode computes, per system, exactly what gw_sigma_eval computes alone. Calls are
+ * asynchronous: the batch starts after the work queued on cuda_stream and cuda_stream waits
+ * for the batch. V, G and Sigma are caller-owned device arrays per system, laid out as for
+ * gw_sigma_eval; the pointer arrays themselves are host arrays of n entries, read during
+ * the call.
+ */
+typedef struct gw_batch gw_batch;
+enum { GW_BATCH_SERIAL = 0, GW_BATCH_STREAMS = 1, GW_BATCH_GRAPH = 2 };
+
+/*
+ * GW_EINVAL for n outside 1..4096 or max_streams outside 1..64. Systems whose tau_chunk is 0
+ * get the largest equal tau batch whose device bytes fit their share of hbm_budget: each
+ * system's need with all tau nodes in one batch, scaled by one common factor so that the
+ * needs add up to the budget, and at least 256 MiB (hbm_budget 0 = 128 GiB).
+ */
+int gw_batch_create(gw_batch** out, const gw_config* cfgs, int n, int max_streams, size_t hbm_budget,
+                    void* cuda_stream);
+int gw_batch_destroy(gw_batch* batch);
+int gw_batch_set_coulomb(gw_batch* batch, const gw_c128* const* V_dev);
+int gw_batch_sigma_eval(gw_batch* batch, const gw_c128* const* G_dev, gw_c128* const* Sig_dev, int mode);
+/*
+ * Per-system tuner: times one evaluation of each system for equal tau batches of
+ * ntau / {1, 2, 3, 4, 6, 8} nodes (the grid of the GEMM launches) that fit the system's
+ * budget share, keeps the fastest, and rebuilds the contexts. chosen (optional, n ints)
+ * receives the batch sizes. Blocks until done; Sigma_dev is used as scratch.
+ */
+int gw_batch_autotune(gw_batch* batch, const gw_c128* const* G_dev, gw_c128* const* Sig_dev, int* chosen);
+/* Waits for the batch and reports any device-side failure of its contexts. */
+int gw_batch_synchronize(gw_batch* batch);
 
 /*
  * Request loop for scGW jobs (self-consistency loop of Sec. 2.4 at fixed mu).

@@ -520,6 +520,7 @@ int gw_create(gw_ctx** out, const gw_config* cfg, void* cuda_stream) {
   if (!out || !cfg) return fail(GW_EINVAL, "gw_create: null argument");
   *out = nullptr;
   if (!config_ok(cfg)) return fail(GW_EINVAL, "gw_create: configuration out of range");
+  if (cfg->precision == GW_MIXED_FP16S) return fail(GW_ENOTIMPL, "gw_create: GW_MIXED_FP16S is not implemented");
   gw_ctx* c = new gw_ctx();
   c->stream = (cudaStream_t)cuda_stream;
   const int rc = ctx_build(c, cfg);

@@ -28,8 +28,11 @@ ABI_SYMBOLS = [
     "gw_aux_dyson", "gw_screened_interaction", "gw_self_energy", "gw_sigma_eval", "gw_dyson_G",
     "gw_mix", "gw_synchronize", "gw_profile_enable", "gw_launch_count", "gw_profile_slots",
     "gw_profile_read", "gw_polarization_noalloc", "gw_job_bytes", "gw_server_create",
-    "gw_server_destroy", "gw_submit", "gw_poll",
+    "gw_server_destroy", "gw_submit", "gw_poll", "gw_batch_create", "gw_batch_destroy",
+    "gw_batch_set_coulomb", "gw_batch_sigma_eval", "gw_batch_autotune", "gw_batch_synchronize",
 ]
+GW_BATCH_SERIAL, GW_BATCH_STREAMS, GW_BATCH_GRAPH = 0, 1, 2
+BATCH_MODES = {"serial": GW_BATCH_SERIAL, "streams": GW_BATCH_STREAMS, "graph": GW_BATCH_GRAPH}
 
 
 class GWError(RuntimeError):
@@ -105,6 +108,12 @@ def lib():
     L.gw_server_destroy.argtypes = [vp]
     L.gw_submit.argtypes = [vp, ctypes.POINTER(gw_job), ctypes.POINTER(ctypes.c_uint64)]
     L.gw_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(gw_job_result), i]
+    L.gw_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(gw_config), i, i, ctypes.c_size_t, vp]
+    L.gw_batch_destroy.argtypes = [vp]
+    L.gw_batch_set_coulomb.argtypes = [vp, ctypes.POINTER(vp)]
+    L.gw_batch_sigma_eval.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i]
+    L.gw_batch_autotune.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i)]
+    L.gw_batch_synchronize.argtypes = [vp]
     _lib = L
     return L
 
@@ -370,6 +379,66 @@ class gw_server:
     def destroy(self):
         if self._h is not None:
             lib().gw_server_destroy(self._h)
+            self._h = None
+            self._keep = {}
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+# ---- batched evaluation of independent systems ------------------------------------------------
+
+
+class gw_batch:
+    """Owner of one gw_batch* (gw_batch_create ... gw_batch_destroy); cfgs are gw_config
+    structures (see make_config). The torch tensors handed in are kept alive here."""
+
+    def __init__(self, cfgs, max_streams=8, hbm_budget=0, stream=None):
+        import torch
+        self.n = len(cfgs)
+        self.cfgs = (gw_config * self.n)(*cfgs)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check(lib().gw_batch_create(ctypes.byref(h), self.cfgs, self.n, int(max_streams),
+                                     ctypes.c_size_t(int(hbm_budget)), ctypes.c_void_p(self.stream.cuda_stream)))
+        self._h = h
+        self._keep = {}
+
+    def _shape(self, i, what):
+        c = self.cfgs[i]
+        nk = c.nk[0] * c.nk[1] * c.nk[2]
+        if what == "V":
+            return (nk, nk, c.naux, c.nao, c.nao)
+        return (nk, c.ntau, c.nao, c.nao)
+
+    def _ptrs(self, tensors, what):
+        if len(tensors) != self.n:
+            raise GWError(GW_EINVAL, f"expected {self.n} {what} tensors")
+        return (ctypes.c_void_p * self.n)(*[_ptr(t, self._shape(i, what)) for i, t in enumerate(tensors)])
+
+    def set_coulomb(self, V):
+        _check(lib().gw_batch_set_coulomb(self._h, self._ptrs(V, "V")))
+        self._keep["V"] = list(V)
+
+    def sigma_eval(self, G, Sig, mode="graph"):
+        m = BATCH_MODES[mode] if isinstance(mode, str) else int(mode)
+        _check(lib().gw_batch_sigma_eval(self._h, self._ptrs(G, "G"), self._ptrs(Sig, "Sig"), m))
+        self._keep["G"], self._keep["Sig"] = list(G), list(Sig)
+
+    def autotune(self, G, Sig):
+        chosen = (ctypes.c_int * self.n)()
+        _check(lib().gw_batch_autotune(self._h, self._ptrs(G, "G"), self._ptrs(Sig, "Sig"), chosen))
+        return list(chosen)
+
+    def synchronize(self):
+        _check(lib().gw_batch_synchronize(self._h))
+
+    def destroy(self):
+        if self._h is not None:
+            lib().gw_batch_destroy(self._h)
             self._h = None
             self._keep = {}
 
