@@ -65,6 +65,14 @@ typedef enum {
   GW_MIXED_FP16S = 2    /* reserved: gw_create returns GW_ENOTIMPL */
 } gw_precision;
 
+/*
+ * Where the mixed precisions keep the bf16 slices of V: for all nk^2 (k1, k2) pairs, made
+ * once by gw_set_coulomb (GW_V_ALL_PAIRS), or for the 4 nk pairs of one q at a time, made
+ * before each q from V (GW_V_PER_Q: about nk times less memory, V read again per q).
+ * GW_V_AUTO takes all pairs when they need at most 24 GiB. Results are the same either way.
+ */
+enum { GW_V_AUTO = 0, GW_V_ALL_PAIRS = 1, GW_V_PER_Q = 2 };
+
 typedef struct {
   int nk[3];            /* k-mesh N1, N2, N3 (1,1,1 for a molecule) */
   int nao;              /* orbitals, 1..512 */
@@ -75,6 +83,7 @@ typedef struct {
   double spin_factor;   /* spin sum of Eq. tilde_P0_tau: 2 for spin-restricted G */
   int precision;        /* gw_precision */
   int tau_chunk;        /* tau nodes per batch in the contractions; 0 = automatic */
+  int v_slices;         /* mixed precisions: GW_V_AUTO, GW_V_ALL_PAIRS or GW_V_PER_Q */
 } gw_config;
 
 /* Library version string. */

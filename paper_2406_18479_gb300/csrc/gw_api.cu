@@ -418,7 +418,8 @@ bool config_ok(const gw_config* cfg) {
   const long long nk = (long long)cfg->nk[0] * cfg->nk[1] * cfg->nk[2];
   return !(cfg->nk[0] < 1 || cfg->nk[1] < 1 || cfg->nk[2] < 1 || nk > 4096 || cfg->nao < 1 || cfg->nao > 512 ||
            cfg->naux < 1 || cfg->naux > 4096 || cfg->ntau < 1 || cfg->ntau > 512 || !(cfg->beta > 0) ||
-           cfg->precision < GW_FP64 || cfg->precision > GW_MIXED_FP16S);
+           cfg->precision < GW_FP64 || cfg->precision > GW_MIXED_FP16S || cfg->v_slices < GW_V_AUTO ||
+           cfg->v_slices > GW_V_PER_Q);
 }
 
 // Grids, gather tables and workspaces of a context; in a size-only build (c->dry)
@@ -492,6 +493,7 @@ int ctx_build(gw_ctx* c, const gw_config* cfg) {
       d.nk3[0] = cfg->nk[0]; d.nk3[1] = cfg->nk[1]; d.nk3[2] = cfg->nk[2];
       d.nk = nk; d.nao = c->nao; d.naux = c->naux; d.ntau = c->ntau; d.precision = cfg->precision;
       d.tau_chunk = cfg->tau_chunk;
+      d.v_slices = cfg->v_slices;
       d.mq = c->mq;
       if ((rc = mixed_create(&c->mixed, d, c->stream, c->status, &c->bytes, c->dry)) != GW_OK) break;
     }

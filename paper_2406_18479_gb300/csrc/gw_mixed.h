@@ -9,7 +9,7 @@ namespace gwi {
 
 struct MixedDims {
   int nk3[3] = {1, 1, 1};
-  int nk = 1, nao = 0, naux = 0, ntau = 0, precision = 0, tau_chunk = 0;
+  int nk = 1, nao = 0, naux = 0, ntau = 0, precision = 0, tau_chunk = 0, v_slices = 0;
   std::vector<int> mq;    // index of -q for every q
 };
 

@@ -762,14 +762,11 @@ int make_map(const Planes& P, int box_rows, CUtensorMap* map) {
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 // chunk length and padded K for a contraction of length K
+// (equal chunks of at most 256, each a multiple of 16: the padding stays below 16 per chunk)
 inline void chunking(int K, int* Kc, int* Kpad) {
-  if (K <= kMaxChunk) {
-    *Kc = round_up(std::max(K, 1), kStepK);
-    *Kpad = *Kc;
-  } else {
-    *Kc = kMaxChunk;
-    *Kpad = round_up(K, kMaxChunk);
-  }
+  const int nc = (std::max(K, 1) + kMaxChunk - 1) / kMaxChunk;
+  *Kc = round_up((std::max(K, 1) + nc - 1) / nc, kStepK);
+  *Kpad = nc * *Kc;
 }
 
 int launch_slice(const SliceJob& j, cudaStream_t st) {
@@ -828,7 +825,13 @@ int launch_oz(const Planes& A, const Planes& B, OzParams p, int slot, cudaStream
 // the mixed stages
 
 // Plane-row tables, [kTabs][nq][nk]: first plane row of each operand block.
-enum { T_VKKPQ = 0, T_VKPQK, T_GKPQ, T_GK, T_VKKMQ, T_GKMQ, T_VCOL_KMQK, kTabs };
+// Plane-row tables T_* index the per-context V slices (all nk^2 pairs) and G slices; in per-q
+// mode the V operands come from per-q slices with rows k * naux * nao (T_LOC_V) or k * nao^2
+// (T_LOC_VC), staged from V through the element-offset tables E_* before each q.
+enum {
+  T_VKKPQ = 0, T_VKPQK, T_GKPQ, T_GK, T_VKKMQ, T_GKMQ, T_VCOL_KMQK, T_LOC_V, T_LOC_VC,
+  E_KKPQ, E_KPQK, E_KKMQ, E_KMQK, kTabs
+};
 
 struct MixedState {
   MixedDims d;
@@ -837,6 +840,8 @@ struct MixedState {
   long long nao2 = 0, naux2 = 0, pair = 0;
   const double2* V = nullptr;
   Planes vrow, vcol, gf, gm;    // V rows (Q,i) over orbitals; V rows (j,b) over Q'; G^T forward / mirrored tau
+  bool per_q = false;           // V slices staged per q (vq, vcq) instead of held for all pairs
+  Planes vq[2], vcq;
   __nv_bfloat16* xs_mem = nullptr;   // operand planes for the batched GEMMs (two buffers)
   __nv_bfloat16* ys_mem = nullptr;
   Planes ps;                    // P~ planes
@@ -902,8 +907,10 @@ const long long* tab(const MixedState* s, int which, int q) {
 // Slice a batch of FP64 (or, with src_df, double-float) matrices into planes
 // (rows x K, per-row chunk alignment).
 int slice(MixedState* s, const double2* src, const ZView& v, long long b_in, long long b_out, int bin, int nbatch,
-          int rows, int K, const Planes& P, long long dst_rows_per_batch, int src_df = 0) {
+          int rows, int K, const Planes& P, long long dst_rows_per_batch, int src_df = 0,
+          const long long* b_tab = nullptr) {
   SliceJob j;
+  j.b.tab = b_tab;
   j.src = src;
   j.src_df = src_df;
   j.v = v;
@@ -937,6 +944,38 @@ int slice_g(MixedState* s, const double2* G) {
   return GW_OK;
 }
 
+// V slices with rows (Q, i) over the orbital a, for nb pairs (pair b at element offset tab[b],
+// or b * pair without a table)
+int stage_vrow(MixedState* s, const double2* V, int nb, const long long* tab, const Planes& P) {
+  const int nao = s->d.nao, naux = s->d.naux;
+  ZView vr;
+  vr.rs_in = nao;
+  vr.ks_in = 1;
+  return slice(s, V, vr, s->pair, 0, 1 << 30, nb, naux * nao, nao, P, (long long)naux * nao, 0, tab);
+}
+
+// V slices with rows (j, b) over Q': row j * nao + b reads V[Q'][b][j]
+int stage_vcol(MixedState* s, const double2* V, int nb, const long long* tab, const Planes& P) {
+  const int nao = s->d.nao, naux = s->d.naux;
+  ZView vc;
+  vc.rin = nao;
+  vc.rs_in = nao;
+  vc.rs_out = 1;
+  vc.ks_in = s->nao2;
+  return slice(s, V, vc, s->pair, 0, 1 << 30, nb, (int)s->nao2, naux, P, s->nao2, 0, tab);
+}
+
+// The V operand for a pair table: the per-context slices, or in per-q mode the staged slices
+struct VOp {
+  const Planes* P;
+  int tab;
+};
+VOp v_op(const MixedState* s, int which) {
+  if (!s->per_q) return {which == T_VCOL_KMQK ? &s->vcol : &s->vrow, which};
+  if (which == T_VCOL_KMQK) return {&s->vcq, T_LOC_VC};
+  return {which == T_VKPQK ? &s->vq[1] : &s->vq[0], T_LOC_V};
+}
+
 // out[t][k][Q][i][b] = sum_a V^{pair(k)}_ia(Q) G^{kg(k)}_ab(t) for t in [t0, t0+nt) (A and Z), or, with
 // transposed, out[t][k][Q'][d][b] = sum_c V^{pair(k)}_bc(Q') G^{kg(k)}_cd(beta - t) (the B operand of P0).
 // Both put the innermost output index b on the TMEM lanes, so a warp's stores are contiguous: the first
@@ -945,6 +984,7 @@ int slice_g(MixedState* s, const double2* G) {
 int vg_gemm(MixedState* s, int pair_tab, int g_tab, const Planes& Gp, int q, int t0, int nt, bool transposed,
             double2* out) {
   const int nk = s->d.nk, nao = s->d.nao, naux = s->d.naux;
+  const VOp vo = v_op(s, pair_tab);
   OzParams p;
   p.nbatch = nk;
   p.C = out;
@@ -957,16 +997,16 @@ int vg_gemm(MixedState* s, int pair_tab, int g_tab, const Planes& Gp, int q, int
     p.N = naux * nao;                     // (Q, i)
     p.a_tab = tab(s, g_tab, q);
     p.a_row0 = (long long)t0 * nao;
-    p.b_tab = tab(s, pair_tab, q);
+    p.b_tab = tab(s, vo.tab, q);
     p.vc.rin = nao;
     p.vc.rs_in = 1;
     p.vc.rs_out = (long long)nk * s->pair;
     p.vc.ks_in = nao;
-    return launch_oz(Gp, s->vrow, p, SLOT_VG_MIXED, s->stream);
+    return launch_oz(Gp, *vo.P, p, SLOT_VG_MIXED, s->stream);
   }
   p.M = naux * nao;                       // (Q', b)
   p.N = nt * nao;                         // (t, d)
-  p.a_tab = tab(s, pair_tab, q);
+  p.a_tab = tab(s, vo.tab, q);
   p.b_tab = tab(s, g_tab, q);
   p.b_row0 = (long long)t0 * nao;
   p.vc.rin = nao;
@@ -975,7 +1015,7 @@ int vg_gemm(MixedState* s, int pair_tab, int g_tab, const Planes& Gp, int q, int
   p.vc.kin = nao;
   p.vc.ks_in = nao;
   p.vc.ks_out = (long long)nk * s->pair;
-  return launch_oz(s->vrow, Gp, p, SLOT_VG_MIXED, s->stream);
+  return launch_oz(*vo.P, Gp, p, SLOT_VG_MIXED, s->stream);
 }
 
 int polarization_chunk(MixedState* s, const double2* G, double2* P0t, double spin, int q, int t0, int nt) {
@@ -1024,7 +1064,8 @@ int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double
     p.N = naux;
     p.nbatch = nt * nk;
     p.bin = nk;
-    p.a_tab = tab(s, T_VCOL_KMQK, q);       // per k
+    const VOp vo = v_op(s, T_VCOL_KMQK);
+    p.a_tab = tab(s, vo.tab, q);            // per k
     p.b_bs_out = naux;                      // rows t * naux
     p.C = s->y64;
     p.bc.bs_in = s->pair;
@@ -1034,7 +1075,7 @@ int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double
     p.status = s->status;
     p.ws = s->ws;
     p.out_df = 1;                           // double-float, sliced again for the Sigma contraction
-    GW_TRY_INTERNAL(launch_oz(s->vcol, s->ps, p, SLOT_R_TC, s->stream));
+    GW_TRY_INTERNAL(launch_oz(*vo.P, s->ps, p, SLOT_R_TC, s->stream));
   }
   // Z^Q_{ib}(k,t) = sum_a V^{k,k-q}_ia(Q) G^{k-q}_ab(t) -> x64[t][k][Q][i][b]
   GW_TRY_INTERNAL(vg_gemm(s, T_VKKMQ, T_GKMQ, s->gf, q, t0, nt, false, s->x64));
@@ -1107,8 +1148,19 @@ int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int*
   s->nt = std::min(nt, ntau);
   int rc = GW_OK;
   do {
-    if ((rc = alloc_planes(s, &s->vrow, (long long)nk * nk * naux * nao, s->Kc_vg, s->Kpad_vg, 2, bytes))) break;
-    if ((rc = alloc_planes(s, &s->vcol, (long long)nk * nk * s->nao2, s->Kc_r, s->Kpad_r, 2, bytes))) break;
+    // V slices for every pair when they take at most 24 GiB; else per q (4 nk pairs at a time)
+    const double full_v = 16.0 * nk * nk * ((double)naux * nao * s->Kpad_vg + (double)s->nao2 * s->Kpad_r);
+    s->per_q = d.v_slices == GW_V_PER_Q || (d.v_slices == GW_V_AUTO && full_v > 25769803776.0);
+    const long long vpairs = s->per_q ? nk : (long long)nk * nk;
+    if (s->per_q) {
+      for (int i = 0; i < 2; ++i)
+        if ((rc = alloc_planes(s, &s->vq[i], (long long)nk * naux * nao, s->Kc_vg, s->Kpad_vg, 2, bytes))) break;
+      if (rc) break;
+      if ((rc = alloc_planes(s, &s->vcq, (long long)nk * s->nao2, s->Kc_r, s->Kpad_r, 2, bytes))) break;
+    } else {
+      if ((rc = alloc_planes(s, &s->vrow, vpairs * naux * nao, s->Kc_vg, s->Kpad_vg, 2, bytes))) break;
+      if ((rc = alloc_planes(s, &s->vcol, vpairs * s->nao2, s->Kc_r, s->Kpad_r, 2, bytes))) break;
+    }
     if ((rc = alloc_planes(s, &s->gf, (long long)nk * ntau * nao, s->Kc_vg, s->Kpad_vg, 2, bytes))) break;
     if ((rc = alloc_planes(s, &s->gm, (long long)nk * ntau * nao, s->Kc_vg, s->Kpad_vg, 2, bytes))) break;
     if ((rc = alloc_planes(s, &s->ps, (long long)s->nt * naux, s->Kc_r, s->Kpad_r, 2, bytes))) break;
@@ -1141,6 +1193,12 @@ int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int*
         at(T_VKKMQ) = ((long long)k * nk + km) * vrows;
         at(T_GKMQ) = (long long)km * ntau * nao;
         at(T_VCOL_KMQK) = ((long long)km * nk + k) * s->nao2;
+        at(T_LOC_V) = (long long)k * vrows;
+        at(T_LOC_VC) = (long long)k * s->nao2;
+        at(E_KKPQ) = ((long long)k * nk + kp) * s->pair;
+        at(E_KPQK) = ((long long)kp * nk + k) * s->pair;
+        at(E_KKMQ) = ((long long)k * nk + km) * s->pair;
+        at(E_KMQK) = ((long long)km * nk + k) * s->pair;
       }
     if ((rc = m_alloc(s, &s->rowtabs, t.size(), bytes))) break;
     if (!dry) cudaMemcpy(s->rowtabs, t.data(), t.size() * sizeof(long long), cudaMemcpyHostToDevice);
@@ -1161,18 +1219,10 @@ void mixed_destroy(MixedState* s) {
 
 int mixed_set_coulomb(MixedState* s, const double2* V) {
   s->V = V;
-  const int nk = s->d.nk, nao = s->d.nao, naux = s->d.naux;
-  ZView vr;                                 // rows (Q, i) over orbital a
-  vr.rs_in = nao;
-  vr.ks_in = 1;
-  GW_TRY_INTERNAL(slice(s, V, vr, s->pair, 0, 1 << 30, nk * nk, naux * nao, nao, s->vrow, (long long)naux * nao));
-  ZView vc;                                 // rows (j, b) over Q': row j*nao + b reads V[Q'][b][j]
-  vc.rin = nao;
-  vc.rs_in = nao;
-  vc.rs_out = 1;
-  vc.ks_in = s->nao2;
-  GW_TRY_INTERNAL(slice(s, V, vc, s->pair, 0, 1 << 30, nk * nk, (int)s->nao2, naux, s->vcol, s->nao2));
-  return GW_OK;
+  if (s->per_q) return GW_OK;               // sliced per q, when used
+  const int nk = s->d.nk;
+  GW_TRY_INTERNAL(stage_vrow(s, V, nk * nk, nullptr, s->vrow));
+  return stage_vcol(s, V, nk * nk, nullptr, s->vcol);
 }
 
 int mixed_polarization(MixedState* s, const double2* G, double2* P0t, double spin_factor) {
@@ -1181,6 +1231,10 @@ int mixed_polarization(MixedState* s, const double2* G, double2* P0t, double spi
     // canonical tau nodes only (the caller fills P0^q(beta - tau) = P0^{-q}(tau)^T)
     const int mq = s->d.mq[q];
     const int tend = mq < q ? 0 : (mq == q ? (s->d.ntau + 1) / 2 : s->d.ntau);
+    if (tend > 0 && s->per_q) {
+      GW_TRY_INTERNAL(stage_vrow(s, s->V, s->d.nk, tab(s, E_KKPQ, q), s->vq[0]));
+      GW_TRY_INTERNAL(stage_vrow(s, s->V, s->d.nk, tab(s, E_KPQK, q), s->vq[1]));
+    }
     // equal batches of at most nt nodes (no short last batch that would leave the GPU half idle)
     const int nb = (tend + s->nt - 1) / s->nt;
     for (int i = 0; i < nb; ++i) {
@@ -1196,11 +1250,16 @@ int mixed_self_energy(MixedState* s, const double2* G, const double2* Pt, double
     return fail(GW_ECUDA, "memset Sigma");
   GW_TRY_INTERNAL(slice_g(s, G));
   const int nb = (s->d.ntau + s->nt - 1) / s->nt;      // equal batches of at most nt nodes
-  for (int q = 0; q < s->d.nk; ++q)
+  for (int q = 0; q < s->d.nk; ++q) {
+    if (s->per_q) {
+      GW_TRY_INTERNAL(stage_vrow(s, s->V, s->d.nk, tab(s, E_KKMQ, q), s->vq[0]));
+      GW_TRY_INTERNAL(stage_vcol(s, s->V, s->d.nk, tab(s, E_KMQK, q), s->vcq));
+    }
     for (int i = 0; i < nb; ++i) {
       const int t0 = (int)((long long)s->d.ntau * i / nb), t1 = (int)((long long)s->d.ntau * (i + 1) / nb);
       GW_TRY_INTERNAL(self_energy_chunk(s, G, Pt, Sig, q, t0, t1 - t0));
     }
+  }
   return GW_OK;
 }
 

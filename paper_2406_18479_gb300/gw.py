@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libgw_gb300.so")
 GW_OK, GW_EINVAL, GW_ENOMEM, GW_ECUDA, GW_ETIMEOUT, GW_EDEVTIMEOUT = 0, 1, 2, 3, 4, 5
 GW_ENOTFINITE, GW_ENOTCONV, GW_EAGAIN, GW_ENOTIMPL = 6, 7, 8, 9
 GW_FP64, GW_MIXED_BF16X3, GW_MIXED_FP16S = 0, 1, 2
+GW_V_AUTO, GW_V_ALL_PAIRS, GW_V_PER_Q = 0, 1, 2
 PRECISIONS = {"fp64": GW_FP64, "bf16x3": GW_MIXED_BF16X3, "fp16s": GW_MIXED_FP16S}
 
 # Every symbol declared in include/gw.h.
@@ -45,7 +46,7 @@ class gw_config(ctypes.Structure):
     _fields_ = [
         ("nk", ctypes.c_int * 3), ("nao", ctypes.c_int), ("naux", ctypes.c_int), ("ntau", ctypes.c_int),
         ("beta", ctypes.c_double), ("mu", ctypes.c_double), ("spin_factor", ctypes.c_double),
-        ("precision", ctypes.c_int), ("tau_chunk", ctypes.c_int),
+        ("precision", ctypes.c_int), ("tau_chunk", ctypes.c_int), ("v_slices", ctypes.c_int),
     ]
 
 
@@ -160,7 +161,7 @@ class gw_ctx:
     """Owner of one gw_ctx* (gw_create ... gw_destroy)."""
 
     def __init__(self, nk3, nao, naux, ntau, beta, mu=0.0, spin_factor=2.0, precision="fp64",
-                 tau_chunk=0, stream=None):
+                 tau_chunk=0, v_slices=0, stream=None):
         import torch
         self.nk3 = tuple(int(x) for x in nk3)
         self.nk = int(np.prod(self.nk3))
@@ -170,7 +171,7 @@ class gw_ctx:
         self.nwf = gw_sample_count(ntau, 1)
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         cfg = gw_config((ctypes.c_int * 3)(*self.nk3), self.nao, self.naux, self.ntau, self.beta,
-                        self.mu, float(spin_factor), prec, int(tau_chunk))
+                        self.mu, float(spin_factor), prec, int(tau_chunk), int(v_slices))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = ctypes.c_void_p()
         _check(lib().gw_create(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(self.stream.cuda_stream)))
@@ -311,10 +312,11 @@ def gw_polarization_noalloc(nk3, nao, naux, ntau, spin_factor, V, G, P0t, stream
 # ---- request loop -------------------------------------------------------------------------
 
 
-def make_config(nk3, nao, naux, ntau, beta, mu=0.0, spin_factor=2.0, precision="fp64", tau_chunk=0):
+def make_config(nk3, nao, naux, ntau, beta, mu=0.0, spin_factor=2.0, precision="fp64", tau_chunk=0,
+                v_slices=0):
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     return gw_config((ctypes.c_int * 3)(*[int(x) for x in nk3]), int(nao), int(naux), int(ntau), float(beta),
-                     float(mu), float(spin_factor), prec, int(tau_chunk))
+                     float(mu), float(spin_factor), prec, int(tau_chunk), int(v_slices))
 
 
 def gw_job_bytes(cfg: gw_config) -> int:

@@ -1,0 +1,75 @@
+"""Parity at the size of the 4x4x4 solid (nk=64, nao=52, naux=400, ntau=120, beta=200) in the
+mixed precision. V alone is 71 GB, so the bf16 slices of V are made per q (automatic at this
+size) and the tau batch is set to 15 nodes (300 P0 tiles per launch).
+
+The oracle recomputes samples from the same inputs: P0 at 2 q x 3 tau; P~ of one q from the
+GPU's own P0 of that q (steps a2-a4 at full size); Sigma at 4 k x 8 tau from the GPU's P~
+(step a5 at full size). Tolerance 1e-7 relative per sampled array. The FP64 path is not run
+here: one evaluation at this size takes about an hour of FP64 work.
+"""
+import numpy as np
+import pytest
+
+from oracle import grids, gw as O
+from paper_2406_18479_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+W = I.WORKLOADS["solid_4x4x4_nao52"]
+TOL = 1e-7
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def run():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_18479_gb300 import gw
+    h, v, g = I.make_inputs(W)
+    ctx = gw.gw_create(W.nk3, W.nao, W.naux, W.ntau, W.beta, precision="bf16x3", tau_chunk=15)
+    s = ctx.shapes()
+    Gd = torch.from_numpy(g).cuda()
+    V = torch.from_numpy(v).cuda()
+    gw.gw_set_coulomb(ctx, V)
+    P0t = torch.empty(s["Pt"], dtype=torch.complex128, device="cuda")
+    gw.gw_polarization(ctx, Gd, P0t)
+    Pt = torch.empty_like(P0t)
+    gw.gw_screened_interaction(ctx, P0t, Pt)
+    Sig = torch.empty(s["Sig"], dtype=torch.complex128, device="cuda")
+    gw.gw_self_energy(ctx, Gd, Pt, Sig)
+    gw.gw_synchronize(ctx)
+    rng = np.random.default_rng(3)
+    q_s = sorted(rng.choice(W.nk, 2, replace=False).tolist())
+    t_s = sorted(rng.choice(W.ntau, 3, replace=False).tolist())
+    k_s = sorted(rng.choice(W.nk, 4, replace=False).tolist())
+    kt_t = sorted(rng.choice(W.ntau, 8, replace=False).tolist())
+    out = {"P0_s": P0t[q_s][:, t_s].cpu().numpy(), "P0_q": P0t[q_s[:1]].cpu().numpy(),
+           "Pt_q": Pt[q_s[:1]].cpu().numpy(), "Pt": Pt.cpu().numpy(),
+           "Sig_s": Sig[k_s][:, kt_t].cpu().numpy(), "q_s": q_s, "t_s": t_s, "k_s": k_s, "kt_t": kt_t}
+    ctx.destroy()
+    del V, Gd, P0t, Pt, Sig
+    torch.cuda.empty_cache()
+    return h, v, g, out
+
+
+def test_c3_polarization_sampled(run):
+    h, v, g, out = run
+    ref = O.polarization(v, g, W.nk3, 2.0, q_list=out["q_s"], t_list=out["t_s"])
+    assert rel(out["P0_s"], ref) < TOL
+
+
+def test_c3_screened_interaction_from_gpu_p0(run):
+    h, v, g, out = run
+    _, F, B = grids.transform_matrices(W.ntau, W.beta, 0)
+    _, _, pt = O.screened_interaction(out["P0_q"], F, B)
+    assert rel(out["Pt_q"], pt) < 1e-10
+
+
+def test_c3_self_energy_sampled_from_gpu_pt(run):
+    h, v, g, out = run
+    ref = O.self_energy(v, g, out["Pt"], W.nk3, k_list=out["k_s"], t_list=out["kt_t"])
+    assert rel(out["Sig_s"], ref) < TOL

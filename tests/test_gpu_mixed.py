@@ -92,3 +92,22 @@ def test_mixed_molecule_nao8_target(G):
     print(f"molecule nao=8: max|dSigma| = {err:.3e} Ha, max|Sigma| = {np.abs(ref['Sig']).max():.3f} Ha")
     assert err <= 1e-6
     ctx.destroy()
+
+
+@pytest.mark.parametrize("nk3,nao,naux,ntau,beta,chunk", [CASES[2], CASES[4], ((3, 2, 1), 4, 18, 5, 7.0, 2)])
+def test_mixed_v_per_q_equals_all_pairs(G, nk3, nao, naux, ntau, beta, chunk):
+    """V sliced per q, just before use, gives bit for bit what slices of all pairs give."""
+    w = I.Workload("case", nk3, nao, naux, ntau, ntau, beta, 0.0, 4.0, nao + naux, solid=int(np.prod(nk3)) > 1)
+    h, v, g = I.make_inputs(w)
+    ref = O.sigma_eval(v, g, nk3, beta, spin_factor=2.0)
+    out = {}
+    for mode in (G.GW_V_ALL_PAIRS, G.GW_V_PER_Q):
+        ctx = G.gw_create(nk3, nao, naux, ntau, beta, precision="bf16x3", tau_chunk=chunk, v_slices=mode)
+        G.gw_set_coulomb(ctx, dev(v))
+        S = torch.empty(ctx.shapes()["Sig"], dtype=torch.complex128, device="cuda")
+        G.gw_sigma_eval(ctx, dev(g), S)
+        G.gw_synchronize(ctx)
+        out[mode] = host(S)
+        ctx.destroy()
+    assert np.array_equal(out[G.GW_V_ALL_PAIRS], out[G.GW_V_PER_Q])
+    assert rel(out[G.GW_V_PER_Q], ref["Sig"]) < TOL
