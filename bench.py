@@ -170,8 +170,10 @@ def blas_threads():
     return os.cpu_count()
 
 
-def ncu_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if its source is unchanged."""
+def ncu_traffic(kernel, algorithmic_bytes_per_launch):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if its source is unchanged:
+    the capture's DRAM bytes per algorithmic byte (a smaller case of the same kernel) times the
+    bench launches' algorithmic bytes."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
@@ -185,7 +187,9 @@ def ncu_traffic(kernel):
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     except OSError:
         return None
-    return rec["dram_bytes_per_launch"] if sha == rec["source_sha256"] else None
+    if sha != rec["source_sha256"]:
+        return None
+    return rec["dram_per_algorithmic_byte"] * algorithmic_bytes_per_launch
 
 
 def max_over_ranks(value, dist=None):
@@ -415,7 +419,7 @@ def run_ours(args, rank, world, local_rank):
         achieved = d["flops"] / d["launches"] / (per_launch_ms * 1e-3) / 1e12
         peak = FP64_PEAK_TFLOPS
         peak_note = "FP64 pipe, GB300 nominal 1.25 TFLOP/s (cuBLAS ZGEMM measured 1.10)"
-    traffic = ncu_traffic(dname)
+    traffic = ncu_traffic(dname, d["bytes"] / d["launches"])
     clocks = clk.summary()
     kernels = {k: {"launches": x["launches"], "ms": round(x["ms"], 3),
                    "share": round(x["ms"] / sum(y["ms"] for y in prof.values()), 4)} for k, x in prof.items()}
