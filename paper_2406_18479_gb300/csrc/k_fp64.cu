@@ -213,6 +213,180 @@ __global__ void __launch_bounds__(256) gj_inverse_kernel(double2* base, int n, l
   }
 }
 
+// Blocked form of the same inversion (same pivots, same result up to rounding order), for
+// n <= kGjBlockedMaxN. Columns are taken in panels of kGjPanel: the panel (n x kGjPanel) is
+// eliminated in shared memory with partial pivoting (explicit row swaps), written back, the
+// panel's row swaps are applied to the other columns, and those columns receive the panel's
+// effect as one rank-kGjPanel update,
+//   A[i][c] <- (i in the panel's pivot rows ? 0 : A[i][c]) + sum_t P[i][t] A_old[k0 + t][c],
+// so the matrix is read and written once per panel instead of once per column. The column
+// swaps that undo the row interchanges are applied at the end through one permutation.
+constexpr int kGjPanel = 16;
+constexpr int kGjBlockedMaxN = 430;   // dynamic shared memory n * (2 * 16 * 16 + 16 + 8) bytes, plus the
+                                      // kernel's static shared memory, within 227 KB
+
+size_t gj_blocked_smem(int n) {
+  return (size_t)n * (2 * kGjPanel * sizeof(double2) + sizeof(double2) + 2 * sizeof(int));
+}
+
+__global__ void __launch_bounds__(256) gj_inverse_blocked_kernel(double2* base, int n, long long stride,
+                                                                 const int* list, int* status) {
+  constexpr int B = kGjPanel;
+  extern __shared__ double2 sm[];
+  double2* P = sm;                         // [n][B]  panel
+  double2* AK = P + (size_t)n * B;         // [B][n]  pivot rows at the panel start; staging at the end
+  double2* fcol = AK + (size_t)n * B;      // [n]     pivot column of one step
+  int* swp = reinterpret_cast<int*>(fcol + n);   // [n] row swapped with row c at step c
+  int* pi = swp + n;                       // [n]     final column permutation
+  __shared__ double red_v[8];
+  __shared__ int red_i[8];
+  __shared__ int s_p, s_bad;
+  __shared__ double2 rowc[B];
+  double2* M = base + (long long)(list ? list[blockIdx.x] : (int)blockIdx.x) * stride;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+
+  for (int k0 = 0; k0 < n; k0 += B) {
+    const int kb = min(B, n - k0);
+    for (int e = tid; e < n * B; e += blockDim.x) {
+      const int i = e / B, j = e % B;
+      P[e] = j < kb ? M[(long long)i * n + k0 + j] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    // ---- elimination of the panel, column by column
+    for (int j = 0; j < kb; ++j) {
+      const int c = k0 + j;
+      double best = -1.0;
+      int bi = c;
+      for (int i = c + tid; i < n; i += blockDim.x) {
+        const double2 v = P[i * B + j];
+        const double a = v.x * v.x + v.y * v.y;
+        if (a > best) { best = a; bi = i; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) { red_v[warp] = best; red_i[warp] = bi; }
+      __syncthreads();
+      if (tid == 0) {
+        double bb = red_v[0];
+        int ii = red_i[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+          if (red_v[w] > bb || (red_v[w] == bb && red_i[w] < ii)) { bb = red_v[w]; ii = red_i[w]; }
+        s_p = ii;
+        swp[c] = ii;
+        if (!(bb > 0.0)) s_bad = 1;
+      }
+      __syncthreads();
+      if (s_bad) break;
+      const int p = s_p;
+      if (p != c && tid < B) {
+        const double2 t = P[c * B + tid];
+        P[c * B + tid] = P[p * B + tid];
+        P[p * B + tid] = t;
+      }
+      __syncthreads();
+      const double2 pv = P[c * B + j];
+      const double den = pv.x * pv.x + pv.y * pv.y;
+      const double2 inv = make_double2(pv.x / den, -pv.y / den);
+      for (int i = tid; i < n; i += blockDim.x) fcol[i] = P[i * B + j];
+      if (tid < B) rowc[tid] = (tid == j) ? inv : cmul(P[c * B + tid], inv);
+      __syncthreads();
+      for (int e = tid; e < n * B; e += blockDim.x) {
+        const int i = e / B, jj = e % B;
+        if (jj >= kb) continue;
+        if (i == c) {
+          P[e] = rowc[jj];
+        } else {
+          const double2 f = fcol[i];
+          if (jj == j) {
+            const double2 t = cmul(f, inv);
+            P[e] = make_double2(-t.x, -t.y);
+          } else {
+            const double2 t = cmul(f, rowc[jj]);
+            P[e] = make_double2(P[e].x - t.x, P[e].y - t.y);
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (s_bad) break;
+    // ---- panel back; its row swaps on the other columns (each thread keeps its columns)
+    for (int e = tid; e < n * B; e += blockDim.x) {
+      const int i = e / B, j = e % B;
+      if (j < kb) M[(long long)i * n + k0 + j] = P[e];
+    }
+    for (int j = 0; j < kb; ++j) {
+      const int c = k0 + j, p = swp[c];
+      if (p == c) continue;
+      for (int col = tid; col < n; col += blockDim.x) {
+        if (col >= k0 && col < k0 + kb) continue;
+        const double2 t = M[(long long)c * n + col];
+        M[(long long)c * n + col] = M[(long long)p * n + col];
+        M[(long long)p * n + col] = t;
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < B * n; e += blockDim.x) {
+      const int t = e / n, col = e % n;
+      AK[e] = t < kb ? M[(long long)(k0 + t) * n + col] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    // ---- rank-kb update of the other columns: one warp per row, lanes along the columns
+    for (int i = warp; i < n; i += (int)(blockDim.x >> 5)) {
+      const bool pivot_row = i >= k0 && i < k0 + kb;
+      double2 pr[B];
+#pragma unroll
+      for (int t = 0; t < B; ++t) pr[t] = P[i * B + t];
+      for (int col = lane; col < n; col += 32) {
+        if (col >= k0 && col < k0 + kb) continue;
+        double2 v = pivot_row ? make_double2(0.0, 0.0) : M[(long long)i * n + col];
+#pragma unroll
+        for (int t = 0; t < B; ++t) {
+          const double2 a = AK[t * n + col];
+          v.x = fma(pr[t].x, a.x, v.x);
+          v.x = fma(-pr[t].y, a.y, v.x);
+          v.y = fma(pr[t].x, a.y, v.y);
+          v.y = fma(pr[t].y, a.x, v.y);
+        }
+        M[(long long)i * n + col] = v;
+      }
+    }
+    __syncthreads();
+  }
+  if (s_bad) {
+    if (tid == 0) atomicExch(status, 1);
+    return;
+  }
+  // ---- undo the row interchanges as column swaps in reverse order, composed into one permutation
+  if (tid == 0) {
+    for (int i = 0; i < n; ++i) pi[i] = i;
+    for (int c = n - 1; c >= 0; --c) {
+      const int r = swp[c];
+      if (r != c) {
+        const int t = pi[c];
+        pi[c] = pi[r];
+        pi[r] = t;
+      }
+    }
+  }
+  __syncthreads();
+  for (int r0 = 0; r0 < n; r0 += B) {
+    const int rb = min(B, n - r0);
+    for (int e = tid; e < rb * n; e += blockDim.x) AK[e] = M[(long long)r0 * n + e];
+    __syncthreads();
+    for (int e = tid; e < rb * n; e += blockDim.x) {
+      const int t = e / n, y = e % n;
+      M[(long long)(r0 + t) * n + y] = AK[t * n + pi[y]];
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void add_identity_kernel(double2* base, int n, long long stride, int nbatch, const int* list,
                                     double scale_m, double shift) {
   const long long nn = (long long)n * n;
@@ -327,6 +501,22 @@ int zgemm_fp64(const ZGemm& g, void* stream) {
 int batched_inverse_fp64(double2* base, int n, long long stride, int nbatch, int* status_dev,
                          void* stream, const int* list) {
   if (nbatch <= 0) return GW_OK;
+  if (n <= kGjBlockedMaxN) {
+    static const bool blocked_attr = [] {
+      const bool ok = cudaFuncSetAttribute(gj_inverse_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)gj_blocked_smem(kGjBlockedMaxN)) == cudaSuccess;
+      cudaGetLastError();
+      return ok;
+    }();
+    if (!blocked_attr) return fail(GW_ECUDA, "gj_inverse_blocked: shared memory attribute refused");
+    prof_begin(SLOT_INVERSE_FP64, (cudaStream_t)stream);
+    gj_inverse_blocked_kernel<<<nbatch, 256, gj_blocked_smem(n), (cudaStream_t)stream>>>(base, n, stride, list,
+                                                                                         status_dev);
+    prof_end(SLOT_INVERSE_FP64, (cudaStream_t)stream, 8.0 * (double)n * n * n * nbatch,
+             32.0 * (double)n * n * nbatch);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "gj_inverse_blocked launch: %s", cudaGetErrorString(e));
+  }
   const size_t smem = 2 * (size_t)n * sizeof(double2) + (size_t)n * sizeof(int);
   if (smem > 200 * 1024) return fail(GW_EINVAL, "batched_inverse_fp64: n=%d too large", n);
   static const bool attr_set = [] {   // once, also when several threads launch

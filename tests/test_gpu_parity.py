@@ -138,3 +138,24 @@ def test_invalid_arguments_rejected(G):
     with pytest.raises(G.GWError):
         G.gw_set_coulomb(ctx, torch.zeros((1, 1, 4, 3, 2), dtype=torch.complex128, device="cuda"))
     ctx.destroy()
+
+
+@pytest.mark.parametrize("n", [1, 15, 16, 17, 33, 200, 430, 431])
+def test_aux_dyson_inverse_with_pivoting(G, n):
+    """gw_aux_dyson = (I - P0)^{-1} - I per (q, n) (Eq. tilde_P_omega) against numpy, with unit
+    diagonals in P0 so that I - P0 has a zero diagonal and every step must pivot; sizes around
+    the 16-column panels of the blocked inversion and beyond its 430 limit."""
+    ntau = 4
+    ctx = G.gw_create((1, 1, 1), 1, n, ntau, 10.0, precision="fp64")
+    nw = ctx.nwb
+    rng = np.random.default_rng(n)
+    p0 = (rng.standard_normal((1, nw, n, n)) + 1j * rng.standard_normal((1, nw, n, n))) / np.sqrt(n)
+    if n > 1:                           # (for n = 1 that would make I - P0 singular)
+        idx = np.arange(n)
+        p0[..., idx, idx] = 1.0
+    out = torch.empty((1, nw, n, n), dtype=torch.complex128, device="cuda")
+    G.gw_aux_dyson(ctx, dev(p0), out)
+    G.gw_synchronize(ctx)
+    ref = np.linalg.inv(np.eye(n) - p0) - np.eye(n)
+    assert rel(host(out), ref) < 1e-10
+    ctx.destroy()
