@@ -376,6 +376,15 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Output tile 128 x 80. The planes of an operand are stored in groups of four
@@ -394,8 +403,9 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 // (into the output when the contraction has one chunk, else into per-CTA
 // scratch), releases TMEM, and only then merges it into the running sum while
 // the next chunk's MMAs run.
+template <int BN_>
 struct OzShape {
-  static constexpr int kBN = 80;                       // output columns per tile
+  static constexpr int kBN = BN_;                      // output columns per tile (72 or 80)
   static constexpr int kStages = 3;
   static constexpr int kRowBytes = 128;                // four slices x 16 k x bf16
   static constexpr int kAGroup = kBM * kRowBytes;      // bytes of one A group tile
@@ -409,7 +419,10 @@ struct OzShape {
   static_assert(3 * kOrderCols <= kTmemCols, "three orders must fit in TMEM");
   static_assert(kStageBytes % 1024 == 0, "stages must keep the 1024-byte swizzle alignment");
   static_assert(kSmem <= 232448, "stages exceed shared memory");
+  static_assert((2 * kBN) % 16 == 0, "M = 128 MMAs need N a multiple of 16");
+  static constexpr int kG = (kBN / 2) % 8 == 0 ? 8 : 4;   // epilogue column group
 };
+constexpr int kMaxBN = 80;
 
 // Shared-memory matrix descriptor, K-major, 128-byte swizzle: 8-row atoms of
 // 128 bytes, 1024 bytes between 8-row groups; version 1 (bits 46-47); layout
@@ -424,9 +437,17 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
+template <int G>
+__device__ __forceinline__ void tmem_ldg(uint32_t taddr, float* v) {
+  if constexpr (G == 8) tmem_ld8(taddr, v);
+  else tmem_ld4(taddr, v);
+}
+
+template <int BN_>
 __global__ void __launch_bounds__(352, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const OzParams p) {
-  using S = OzShape;
+  using S = OzShape<BN_>;
+  constexpr int G = S::kG;
   constexpr int BN = S::kBN;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -639,24 +660,24 @@ __global__ void __launch_bounds__(352, 1)
         const bool single = nchunks == 1;
         // ---- drain: TMEM -> chunk value (an exact FP32 pair per part) -> output or scratch
 #pragma unroll 1
-        for (int g = 0; g < kCols / 8; ++g) {
-          const int cb = half * kCols + g * 8;
-          float v[3][2][8];                           // [order][im, re][column]
+        for (int g = 0; g < kCols / G; ++g) {
+          const int cb = half * kCols + g * G;
+          float v[3][2][G];                           // [order][im, re][column]
           const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cb;
 #pragma unroll
           for (int o = 0; o < 3; ++o) {
-            tmem_ld8(taddr + o * S::kOrderCols, v[o][0]);
-            tmem_ld8(taddr + o * S::kOrderCols + BN, v[o][1]);
+            tmem_ldg<G>(taddr + o * S::kOrderCols, v[o][0]);
+            tmem_ldg<G>(taddr + o * S::kOrderCols + BN, v[o][1]);
           }
           tmem_wait_ld();
-          if (g == kCols / 8 - 1) {
+          if (g == kCols / G - 1) {
             // this warp's accumulator columns are in registers: release TMEM
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(acc_empty);
           }
 #pragma unroll
-          for (int u = 0; u < 8; ++u) {
+          for (int u = 0; u < G; ++u) {
             const int cl = cb + u;
             if (!col_ok(cl)) continue;
             // orders 0 and 1 are exact, so their sum is exact as a pair
@@ -673,18 +694,18 @@ __global__ void __launch_bounds__(352, 1)
         if (!single && c > 0) {
           const bool last = c == nchunks - 1;
 #pragma unroll 1
-          for (int g = 0; g < kCols / 8; ++g) {
-            const int cb = half * kCols + g * 8;
-            float4 a[8], x[8];
+          for (int g = 0; g < kCols / G; ++g) {
+            const int cb = half * kCols + g * G;
+            float4 a[G], x[G];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < G; ++u) {
               if (col_ok(cb + u)) {
                 a[u] = ws[(size_t)(cb + u) * kBM];
                 x[u] = cw[(size_t)(cb + u) * kBM];
               }
             }
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < G; ++u) {
               const int cl = cb + u;
               if (!col_ok(cl)) continue;
               df_add(a[u].x, a[u].y, x[u].x, x[u].y);
@@ -786,8 +807,9 @@ int launch_slice(const SliceJob& j, cudaStream_t st) {
 }
 
 
-int launch_oz(const Planes& A, const Planes& B, OzParams p, int slot, cudaStream_t st) {
-  using S = OzShape;
+template <int BN_>
+int launch_oz_bn(const Planes& A, const Planes& B, OzParams p, int slot, cudaStream_t st) {
+  using S = OzShape<BN_>;
   if (A.Kpad != B.Kpad || A.Kc != B.Kc) return fail(GW_EINVAL, "oz_gemm: operand chunking differs");
   if (A.groups != 2 || B.groups != 2) return fail(GW_EINVAL, "oz_gemm: operands need two slice groups");
   p.nsteps = A.Kpad / kStepK;
@@ -805,18 +827,27 @@ int launch_oz(const Planes& A, const Planes& B, OzParams p, int slot, cudaStream
   GW_TRY_INTERNAL(make_map(B, S::kBN, &mb));
   // one-time setup; function-local statics initialise once even when contexts run on several threads
   static const bool attr = [] {
-    cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
+    cudaFuncSetAttribute(oz_gemm_kernel<BN_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
     return true;
   }();
   (void)attr;
   const int grid = (int)std::min<long long>(total, num_sms());
   prof_begin(slot, st);
-  oz_gemm_kernel<<<grid, S::kThreads, S::kSmem, st>>>(ma, mb, p);
-  // executed bf16 tensor flops: 10 slice products x 2 real MMAs of 128 x 160 x 16 per k-step
+  oz_gemm_kernel<BN_><<<grid, S::kThreads, S::kSmem, st>>>(ma, mb, p);
+  // executed bf16 tensor flops: 10 slice products x 2 real MMAs of 128 x (2 BN) x 16 per k-step
   prof_end(slot, st, 2.0 * 20.0 * (double)total * kBM * (2 * S::kBN) * (double)p.nsteps * kStepK,
            (double)total * p.nsteps * S::kTxBytes);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "oz_gemm launch: %s", cudaGetErrorString(e));
+}
+
+// Tile width by the padding of N: 72 columns (MMA N = 144) when that covers N with fewer padded
+// columns than 80 (for example N = 200: 216 instead of 240), else 80. Block-diagonal launches
+// keep 80, the width their problem grouping was chosen for.
+int launch_oz(const Planes& A, const Planes& B, OzParams p, int slot, cudaStream_t st) {
+  const long long pad72 = (p.N + 71) / 72 * 72LL, pad80 = (p.N + 79) / 80 * 80LL;
+  if (!p.dblock && pad72 < pad80) return launch_oz_bn<72>(A, B, p, slot, st);
+  return launch_oz_bn<80>(A, B, p, slot, st);
 }
 
 }  // namespace
@@ -1178,7 +1209,7 @@ int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int*
         sms = 152;   // size-only build without a device: the GB300's SM count
       }
       // per-CTA running sums and chunk values of the GEMM epilogue
-      if ((rc = m_alloc(s, &s->ws, 2 * (size_t)std::max(sms, 1) * kBM * OzShape::kBN, bytes))) break;
+      if ((rc = m_alloc(s, &s->ws, 2 * (size_t)std::max(sms, 1) * kBM * kMaxBN, bytes))) break;
     }
     std::vector<long long> t((size_t)kTabs * nk * nk);
     const long long vrows = (long long)naux * nao;
