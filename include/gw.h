@@ -129,10 +129,26 @@ int gw_destroy(gw_ctx* ctx);
 size_t gw_workspace_bytes(const gw_ctx* ctx);
 
 /*
+ * Replaces the context's grids (built by gw_create from the Chebyshev interpolant, see
+ * gw_grid_build) with the caller's, for example transforms of another basis (the paper's
+ * grid files, Sec. 2.3 and Eq. P0t_to_P0w). Host arrays, copied; sizes as gw_create made
+ * them: T = ntau nodes, nb = gw_sample_count(ntau, 0), nf = gw_sample_count(ntau, 1):
+ *   tau_host[T], Fb_host[nb][T], Bb_host[T][nb] (bosonic), Ff_host[nf][T], Bf_host[T][nf]
+ *   and omega_f_host[nf] (fermionic, used by gw_dyson_G), omega_b_host[nb] (optional, checked only).
+ * G(beta - tau) is read at the mirrored node and only canonical (q, tau), (q, n) are computed,
+ * so the grids must be symmetric: tau ascending in (0, beta) with tau[T-1-t] = beta - tau[t],
+ * omega_b[nb-1-n] = -omega_b[n], and Fb[nb-1-n][T-1-t] = Fb[n][t], Bb[T-1-t][nb-1-n] = Bb[t][n]
+ * (relative 1e-10); GW_EINVAL otherwise. Synchronizes the context's stream first.
+ */
+int gw_set_grids(gw_ctx* ctx, const double* tau_host, const gw_c128* Fb_host, const gw_c128* Bb_host,
+                 const gw_c128* Ff_host, const gw_c128* Bf_host, const double* omega_b_host,
+                 const double* omega_f_host);
+
+/*
  * Borrows the Coulomb factor V (layout above, Eq. CoulombDF). The caller keeps
  * V_dev alive and unchanged until gw_destroy or the next gw_set_coulomb. In the
- * mixed precisions this call also converts V into its limb planes (a device
- * workspace).
+ * mixed precisions this call also cuts V into its bf16 slices (a device workspace), or,
+ * with per-q slices, only records V.
  */
 int gw_set_coulomb(gw_ctx* ctx, const gw_c128* V_dev);
 

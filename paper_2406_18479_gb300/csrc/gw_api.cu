@@ -2,6 +2,8 @@
 // and the FP64 stages (arXiv 2406.18479, Sec. 2.3 and Eq. dyson).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -542,6 +544,51 @@ int gw_destroy(gw_ctx* ctx) {
 }
 
 size_t gw_workspace_bytes(const gw_ctx* ctx) { return ctx ? ctx->bytes : 0; }
+
+int gw_set_grids(gw_ctx* ctx, const double* tau_host, const gw_c128* Fb_host, const gw_c128* Bb_host,
+                 const gw_c128* Ff_host, const gw_c128* Bf_host, const double* omega_b_host,
+                 const double* omega_f_host) {
+  if (!ctx || !tau_host || !Fb_host || !Bb_host || !Ff_host || !Bf_host || !omega_f_host)
+    return fail(GW_EINVAL, "gw_set_grids: null argument");
+  const int T = ctx->ntau, nb = ctx->nwb, nf = ctx->nwf;
+  const double beta = ctx->cfg.beta;
+  for (int t = 0; t < T; ++t) {
+    if (!(tau_host[t] > 0.0 && tau_host[t] < beta) || (t > 0 && !(tau_host[t] > tau_host[t - 1])))
+      return fail(GW_EINVAL, "gw_set_grids: tau must ascend inside (0, beta)");
+    if (std::fabs(tau_host[t] + tau_host[T - 1 - t] - beta) > 1e-12 * beta)
+      return fail(GW_EINVAL, "gw_set_grids: tau must be symmetric (tau[T-1-t] = beta - tau[t])");
+  }
+  if (omega_b_host) {
+    double wmax = 0.0;
+    for (int n = 0; n < nb; ++n) wmax = std::max(wmax, std::fabs(omega_b_host[n]));
+    for (int n = 0; n < nb; ++n)
+      if (std::fabs(omega_b_host[n] + omega_b_host[nb - 1 - n]) > 1e-12 * wmax)
+        return fail(GW_EINVAL, "gw_set_grids: bosonic frequencies must be symmetric");
+  }
+  // the bosonic transforms must map the mirrored node to the mirrored frequency (what the
+  // canonical-index shortcut of P0, P~ relies on): F[nb-1-n][T-1-t] = F[n][t], likewise B
+  double fmax = 0.0, bmax = 0.0, fd = 0.0, bd = 0.0;
+  for (int n = 0; n < nb; ++n)
+    for (int t = 0; t < T; ++t) {
+      const gw_c128 f = Fb_host[(size_t)n * T + t], fm = Fb_host[(size_t)(nb - 1 - n) * T + (T - 1 - t)];
+      const gw_c128 b = Bb_host[(size_t)t * nb + n], bm = Bb_host[(size_t)(T - 1 - t) * nb + (nb - 1 - n)];
+      fmax = std::max(fmax, std::hypot(f.re, f.im));
+      bmax = std::max(bmax, std::hypot(b.re, b.im));
+      fd = std::max(fd, std::hypot(f.re - fm.re, f.im - fm.im));
+      bd = std::max(bd, std::hypot(b.re - bm.re, b.im - bm.im));
+    }
+  if (!(fd <= 1e-10 * fmax) || !(bd <= 1e-10 * bmax))
+    return fail(GW_EINVAL, "gw_set_grids: bosonic F and B must map mirrored nodes to mirrored frequencies");
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) return cuda_check("gw_set_grids");
+  const size_t sb = (size_t)nb * T * sizeof(double2), sf = (size_t)nf * T * sizeof(double2);
+  if (cudaMemcpy(ctx->Fb, Fb_host, sb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(ctx->Bb, Bb_host, sb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(ctx->Ff, Ff_host, sf, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(ctx->Bf, Bf_host, sf, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(ctx->wf, omega_f_host, (size_t)nf * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return cuda_check("gw_set_grids copy");
+  return GW_OK;
+}
 
 int gw_set_coulomb(gw_ctx* ctx, const gw_c128* V_dev) {
   ProfScope _ps(ctx ? &ctx->prof : nullptr);

@@ -25,7 +25,7 @@ PRECISIONS = {"fp64": GW_FP64, "bf16x3": GW_MIXED_BF16X3, "fp16s": GW_MIXED_FP16
 # Every symbol declared in include/gw.h.
 ABI_SYMBOLS = [
     "gw_version", "gw_last_error", "gw_sample_count", "gw_grid_build", "gw_create", "gw_destroy",
-    "gw_workspace_bytes", "gw_set_coulomb", "gw_polarization", "gw_to_matsubara", "gw_to_tau",
+    "gw_workspace_bytes", "gw_set_grids", "gw_set_coulomb", "gw_polarization", "gw_to_matsubara", "gw_to_tau",
     "gw_aux_dyson", "gw_screened_interaction", "gw_self_energy", "gw_sigma_eval", "gw_dyson_G",
     "gw_mix", "gw_synchronize", "gw_profile_enable", "gw_launch_count", "gw_profile_slots",
     "gw_profile_read", "gw_polarization_noalloc", "gw_job_bytes", "gw_server_create",
@@ -87,6 +87,7 @@ def lib():
     L.gw_workspace_bytes.argtypes = [vp]
     L.gw_workspace_bytes.restype = ctypes.c_size_t
     L.gw_set_coulomb.argtypes = [vp, vp]
+    L.gw_set_grids.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
     L.gw_polarization.argtypes = [vp, vp, vp]
     L.gw_to_matsubara.argtypes = [vp, i, vp, vp, i, ll]
     L.gw_to_tau.argtypes = [vp, i, vp, vp, i, ll]
@@ -212,6 +213,26 @@ def gw_create(nk3, nao, naux, ntau, beta, **kw) -> gw_ctx:
 
 def gw_destroy(ctx: gw_ctx):
     ctx.destroy()
+
+
+def _host_arr(a, shape, dtype, name):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=dtype)
+    if tuple(a.shape) != tuple(shape):
+        raise GWError(GW_EINVAL, f"{name}: expected shape {tuple(shape)}, got {a.shape}")
+    return a
+
+
+def gw_set_grids(ctx: gw_ctx, tau, Fb, Bb, Ff, Bf, omega_f, omega_b=None):
+    """Replaces the context's grids (host arrays, copied); see include/gw.h for the symmetry rules."""
+    T, nb, nf = ctx.ntau, ctx.nwb, ctx.nwf
+    arrs = [_host_arr(tau, (T,), np.float64, "tau"), _host_arr(Fb, (nb, T), np.complex128, "Fb"),
+            _host_arr(Bb, (T, nb), np.complex128, "Bb"), _host_arr(Ff, (nf, T), np.complex128, "Ff"),
+            _host_arr(Bf, (T, nf), np.complex128, "Bf"), _host_arr(omega_b, (nb,), np.float64, "omega_b"),
+            _host_arr(omega_f, (nf,), np.float64, "omega_f")]
+    ptr = [None if a is None else ctypes.c_void_p(a.ctypes.data) for a in arrs]
+    _check(lib().gw_set_grids(ctx.handle, *ptr))
 
 
 def gw_set_coulomb(ctx: gw_ctx, V):

@@ -159,3 +159,57 @@ def test_aux_dyson_inverse_with_pivoting(G, n):
     ref = np.linalg.inv(np.eye(n) - p0) - np.eye(n)
     assert rel(host(out), ref) < 1e-10
     ctx.destroy()
+
+
+def _library_grids(ntau, beta):
+    tau, mb, Fb, Bb = G_grids(ntau, beta, 0)
+    _, mf, Ff, Bf = G_grids(ntau, beta, 1)
+    return tau, Fb, Bb, Ff, Bf, 2 * np.pi * mb / beta, (2 * mf + 1) * np.pi / beta
+
+
+def G_grids(ntau, beta, stat):
+    from paper_2406_18479_gb300 import gw
+    return gw.gw_grid_build(ntau, beta, stat)
+
+
+def test_set_grids_uses_the_given_transforms(G):
+    """gw_set_grids: the library's own grids give bit-identical results; a different left
+    inverse B' = B + N (N F = 0, mirror-symmetric; possible since nb = ntau + 1) gives the
+    oracle's chain computed with B'; grids without the mirror symmetry are rejected."""
+    nk3, nao, naux, ntau, beta = (2, 1, 1), 4, 9, 6, 8.0
+    w, (h, v, g) = random_case(nk3, nao, naux, ntau, beta, 5)
+    tau, Fb, Bb, Ff, Bf, wb, wf = _library_grids(ntau, beta)
+    ctx = G.gw_create(nk3, nao, naux, ntau, beta, precision="fp64")
+    G.gw_set_coulomb(ctx, dev(v))
+    S0 = torch.empty(ctx.shapes()["Sig"], dtype=torch.complex128, device="cuda")
+    G.gw_sigma_eval(ctx, dev(g), S0)
+    G.gw_set_grids(ctx, tau, Fb, Bb, Ff, Bf, wf, wb)
+    S1 = torch.empty_like(S0)
+    G.gw_sigma_eval(ctx, dev(g), S1)
+    assert torch.equal(S0, S1)
+    # another left inverse of F with the same mirror symmetry
+    rng = np.random.default_rng(1)
+    Z = rng.standard_normal(Bb.shape) + 1j * rng.standard_normal(Bb.shape)
+    N = Z @ (np.eye(Fb.shape[0]) - Fb @ np.linalg.pinv(Fb))
+    N = 0.5 * (N + N[::-1, ::-1])
+    N *= 0.1 * np.abs(Bb).max() / np.abs(N).max()
+    B2 = Bb + N
+    assert np.abs(B2 @ Fb - np.eye(ntau)).max() < 1e-12
+    G.gw_set_grids(ctx, tau, Fb, B2, Ff, Bf, wf, wb)
+    S2 = torch.empty_like(S0)
+    G.gw_sigma_eval(ctx, dev(g), S2)
+    G.gw_synchronize(ctx)
+    p0 = O.polarization(v, g, nk3, 2.0)
+    _, _, pt = O.screened_interaction(p0, Fb, B2)
+    ref = O.self_energy(v, g, pt, nk3)
+    assert rel(host(S2), ref) < TOL
+    assert rel(host(S2), host(S0)) > 1e-6            # the second left inverse changed the result
+    with pytest.raises(G.GWError) as e:
+        G.gw_set_grids(ctx, tau * 0.9, Fb, Bb, Ff, Bf, wf, wb)
+    assert e.value.code == G.GW_EINVAL
+    Fbad = Fb.copy()
+    Fbad[0, 0] += 0.1
+    with pytest.raises(G.GWError) as e:
+        G.gw_set_grids(ctx, tau, Fbad, Bb, Ff, Bf, wf, wb)
+    assert e.value.code == G.GW_EINVAL
+    ctx.destroy()
