@@ -170,6 +170,22 @@ def blas_threads():
     return os.cpu_count()
 
 
+def source_hash(rec):
+    """sha256 of the kernel's source: the lines from rec["region"][0] up to rec["region"][1] of
+    rec["source"] (the whole file without a region); None if the file or a marker is missing."""
+    try:
+        text = open(os.path.join(ROOT, rec["source"]), encoding="utf-8").read()
+    except OSError:
+        return None
+    if rec.get("region"):
+        a = text.find(rec["region"][0])
+        b = text.find(rec["region"][1], a + 1) if a >= 0 else -1
+        if a < 0 or b < 0:
+            return None
+        text = text[a:b]
+    return hashlib.sha256(text.encode()).hexdigest()
+
+
 def ncu_traffic(kernel, algorithmic_bytes_per_launch):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if its source is unchanged:
     the capture's DRAM bytes per algorithmic byte (a smaller case of the same kernel) times the
@@ -182,12 +198,7 @@ def ncu_traffic(kernel, algorithmic_bytes_per_launch):
         return None
     if not rec:
         return None
-    src = os.path.join(ROOT, rec["source"])
-    try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    except OSError:
-        return None
-    if sha != rec["source_sha256"]:
+    if source_hash(rec) != rec["source_sha256"]:
         return None
     return rec["dram_per_algorithmic_byte"] * algorithmic_bytes_per_launch
 

@@ -122,7 +122,9 @@ __device__ __forceinline__ void df_slices(float h, float l, const float magic[4]
   for (int i = 0; i < 4; ++i) {
     s[i] = __fsub_rn(__fadd_rn(h, magic[i]), magic[i]);   // h rounded to a multiple of q_i
     h = __fsub_rn(h, s[i]);                               // exact
-    const float t = __fadd_rn(h, l);                      // renormalise (|h| >= |l| or h = 0)
+    // renormalise; the epilogue's pairs are not normalised (l holds the order 2-3 sum, up to
+    // 2^-16 of the chunk maximum), so t may round, by at most 2^(E-39), far below q_3 = 2^(E-31)
+    const float t = __fadd_rn(h, l);
     l = __fsub_rn(l, __fsub_rn(t, h));
     h = t;
   }
