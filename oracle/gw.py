@@ -172,3 +172,98 @@ def scgw(H, V, G0, nk3, beta, mu, spin_factor=2.0, alpha=0.5, tol=1e-6, itermax=
         if hist and hist[-1] < tol:
             break
     return sig_old, G, hist
+
+
+# ---- the static part and the rest of the loop (Sec. 2.2 Eq. sigma_inf, Sec. 2.4, Sec. 5.3) ------
+
+
+def density_matrix(G, beta):
+    """gamma^k = G^k(0^-) = -G^k(beta^-) (antiperiodicity), the density matrix of Eq. (sigma_inf).
+
+    The nodes exclude tau = beta, so G(beta^-) is the Chebyshev interpolant of the node values
+    evaluated there: with x = 2 tau / beta - 1, x = 1 where every T_l(1) = 1, so
+    G(beta^-) = sum_l c_l with c_l = (2 - delta_l0)/n sum_j G(tau_j) T_l(x_j).
+    """
+    nk, ntau = G.shape[:2]
+    x = 2.0 * grids.chebyshev_nodes(ntau, beta) / beta - 1.0
+    l = np.arange(ntau)
+    T = np.cos(np.outer(l, np.arccos(np.clip(x, -1.0, 1.0))))    # T_l(x_j)
+    coef = ((2.0 - (l == 0)) / ntau)[:, None] * T                  # c_l = sum_j coef[l, j] G_j
+    g_beta = np.einsum("lj,kjab->kab", coef, G)                    # sum over l of c_l
+    return -g_beta
+
+
+def sigma_inf(V, gamma, nk3, spin_factor=2.0):
+    """Static (Hartree-Fock) self-energy, Eq. (sigma_inf), with G(0^-) = gamma:
+
+      Sigma^inf,k_ij = (s/N_k) sum_{k'Q ab} V_{ik,jk}(Q) gamma^{k'}_ab V_{bk',ak'}(Q)
+                     - (1/N_k) sum_{k'Q ab} V_{ik,ak'}(Q) gamma^{k'}_ab V_{bk',jk}(Q),
+
+    s the spin sum of the first (Hartree) term; the exchange term keeps one spin.
+    """
+    nk = V.shape[0]
+    rho = sum(np.einsum("ab,Qba->Q", gamma[kp], V[kp, kp]) for kp in range(nk))
+    out = np.empty((nk,) + gamma.shape[1:], complex)
+    for k in range(nk):
+        hartree = np.einsum("Qij,Q->ij", V[k, k], rho)
+        exchange = sum(np.einsum("Qia,ab,Qbj->ij", V[k, kp], gamma[kp], V[kp, k], optimize=True)
+                       for kp in range(nk))
+        out[k] = (spin_factor * hartree - exchange) / nk
+    return out
+
+
+def particle_number(gamma, spin_factor=2.0):
+    """Electrons per cell, (s/N_k) sum_k Tr gamma^k."""
+    nk = gamma.shape[0]
+    return float(np.real(spin_factor * np.einsum("kii->", gamma) / nk))
+
+
+def dyson_G_static(H, sig_inf, Sig, mu, beta):
+    """Eq. (dyson) with the static part: [(i w_n + mu) I - H^k - Sigma^inf,k - Sigma~^k(i w_n)]^{-1};
+    the static part enters exactly like H, so this is dyson_G with H + Sigma^inf."""
+    return dyson_G(H if sig_inf is None else H + sig_inf, Sig, mu, beta)
+
+
+def find_mu(H, sig_inf, Sig, beta, n_target, spin_factor=2.0, lo=-5.0, hi=5.0, tol=1e-10, maxit=200):
+    """Chemical potential with (s/N_k) sum_k Tr gamma^k = n_target (Sec. 2.4, step 3), by bisection
+    on the particle number of the Dyson solution, which grows with mu. Returns (mu, G)."""
+    def number(mu):
+        G = dyson_G_static(H, sig_inf, Sig, mu, beta)
+        return particle_number(density_matrix(G, beta), spin_factor), G
+    n_lo, _ = number(lo)
+    n_hi, _ = number(hi)
+    if not (n_lo <= n_target <= n_hi):
+        raise ValueError("target particle number outside [N(lo), N(hi)]")
+    for _ in range(maxit):
+        mid = 0.5 * (lo + hi)
+        n_mid, G = number(mid)
+        if n_mid < n_target:
+            lo = mid
+        else:
+            hi = mid
+        if hi - lo < tol:
+            break
+    mu = 0.5 * (lo + hi)
+    return mu, number(mu)[1]
+
+
+def diis_coefficients(residuals):
+    """Pulay's extrapolation coefficients (Sec. 5.3): c minimising |sum_i c_i r_i|^2 with
+    sum_i c_i = 1, from B_ij = Re <r_i, r_j> and one Lagrange multiplier."""
+    m = len(residuals)
+    Bm = np.empty((m + 1, m + 1))
+    for i in range(m):
+        for j in range(m):
+            Bm[i, j] = np.real(np.vdot(residuals[i], residuals[j]))
+    Bm[m, :m] = Bm[:m, m] = -1.0
+    Bm[m, m] = 0.0
+    rhs = np.zeros(m + 1)
+    rhs[m] = -1.0
+    return np.linalg.solve(Bm, rhs)[:m]
+
+
+def diis_extrapolate(outputs, inputs):
+    """Next self-energy sum_i c_i Sigma[G_i] from the outputs Sigma[G_i] of the last iterations and
+    the self-energies Sigma_i they were computed from (residual r_i = Sigma[G_i] - Sigma_i)."""
+    c = diis_coefficients([o - x for o, x in zip(outputs, inputs)])
+    return sum(ci * o for ci, o in zip(c, outputs)), c

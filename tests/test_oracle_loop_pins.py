@@ -1,0 +1,98 @@
+"""Pins of the oracle's loop pieces (Eq. sigma_inf, Sec. 2.4 steps 2-3, Sec. 5.3), each against
+something other than the formula it implements: closed forms of the non-interacting system, the
+explicit 4-index interaction, a scalar root finder, and the exact behaviour of Pulay's
+extrapolation on linear maps."""
+import numpy as np
+import pytest
+from scipy.optimize import brentq
+
+from oracle import gw as O
+from paper_2406_18479_gb300 import inputs as I
+
+
+def fermi(e, beta):
+    return 0.5 * (1.0 - np.tanh(0.5 * beta * e))
+
+
+@pytest.mark.parametrize("nk3,beta,mu", [((1, 1, 1), 2.0, 0.3), ((2, 1, 1), 1.5, -0.2), ((2, 2, 1), 2.5, 0.0)])
+def test_density_matrix_of_g0_is_fermi(nk3, beta, mu):
+    """G0(0^-) = U diag(f(eps - mu)) U^dagger; the interpolant is exact to 1e-12 at this beta."""
+    w = I.Workload("m", nk3, 5, 10, 40, 40, beta, mu, 4.0, 3, solid=int(np.prod(nk3)) > 1)
+    h, v, g = I.make_inputs(w)
+    gam = O.density_matrix(g, beta)
+    for k in range(w.nk):
+        e, u = np.linalg.eigh(h[k])
+        assert np.abs(gam[k] - (u * fermi(e - mu, beta)) @ u.conj().T).max() < 1e-12
+
+
+def test_particle_number_of_g0():
+    w = I.Workload("m", (2, 1, 1), 6, 12, 40, 40, 2.0, 0.1, 4.0, 5, solid=True)
+    h, v, g = I.make_inputs(w)
+    n = O.particle_number(O.density_matrix(g, w.beta), 2.0)
+    ref = 2.0 / w.nk * sum(fermi(np.linalg.eigvalsh(h[k]) - w.mu, w.beta).sum() for k in range(w.nk))
+    assert abs(n - ref) < 1e-11
+
+
+def brute_sigma_inf(V, gamma, spin):
+    """Eq. (sigma_inf) through the explicit 4-index interaction
+    U^{k1 k2, k3 k4}_{ij,kl} = sum_Q V^{k1 k2}_ij(Q) V^{k3 k4}_kl(Q) (no conjugation)."""
+    nk, _, naux, nao, _ = V.shape
+    out = np.zeros((nk, nao, nao), complex)
+    for k in range(nk):
+        for kp in range(nk):
+            UH = np.tensordot(V[k, k], V[kp, kp], axes=([0], [0]))        # [i j b a]
+            UX = np.tensordot(V[k, kp], V[kp, k], axes=([0], [0]))        # [i a b j]
+            for i in range(nao):
+                for j in range(nao):
+                    hart = sum(UH[i, j, b, a] * gamma[kp, a, b] for a in range(nao) for b in range(nao))
+                    exch = sum(UX[i, a, b, j] * gamma[kp, a, b] for a in range(nao) for b in range(nao))
+                    out[k, i, j] += (spin * hart - exch) / nk
+    return out
+
+
+@pytest.mark.parametrize("nk3", [(1, 1, 1), (3, 1, 1)])
+def test_sigma_inf_against_four_index(nk3):
+    w = I.Workload("m", nk3, 3, 5, 8, 8, 3.0, 0.0, 3.0, 7, solid=int(np.prod(nk3)) > 1)
+    h, v, g = I.make_inputs(w)
+    gam = O.density_matrix(g, w.beta)
+    s = O.sigma_inf(v, gam, nk3, 2.0)
+    assert np.abs(s - brute_sigma_inf(v, gam, 2.0)).max() < 1e-12 * max(1.0, np.abs(s).max())
+    # Hermitian for a Hermitian density matrix and V(k2,k1)^Q_ji = conj V(k1,k2)^Q_ij
+    assert np.abs(s - s.conj().transpose(0, 2, 1)).max() < 1e-12 * np.abs(s).max()
+
+
+def test_find_mu_matches_scalar_root_of_fermi_count():
+    w = I.Workload("m", (2, 1, 1), 6, 12, 40, 40, 2.0, 0.0, 4.0, 9, solid=True)
+    h, v, g = I.make_inputs(w)
+    eps = [np.linalg.eigvalsh(h[k]) for k in range(w.nk)]
+    target = 5.0
+
+    def count(mu):
+        return 2.0 / w.nk * sum(fermi(e - mu, w.beta).sum() for e in eps) - target
+    mu_ref = brentq(count, -10, 10, xtol=1e-14)
+    Sig = np.zeros_like(g)
+    mu, G = O.find_mu(h, None, Sig, w.beta, target, 2.0, lo=-5.0, hi=5.0, tol=1e-12)
+    assert abs(mu - mu_ref) < 1e-8
+    assert abs(O.particle_number(O.density_matrix(G, w.beta), 2.0) - target) < 1e-8
+
+
+def test_diis_solves_linear_fixed_points_exactly():
+    """On x = A x + b (|A| < 1) Pulay's extrapolation over all past iterates reaches the fixed
+    point once the real span of the residuals (real coefficients on C^n: dimension 2n) is
+    exhausted, after 2n + 1 iterations; with one vector it returns the newest output unchanged;
+    the coefficients sum to 1."""
+    rng = np.random.default_rng(0)
+    n = 7
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    A *= 0.4 / np.abs(np.linalg.eigvals(A)).max()
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    xstar = np.linalg.solve(np.eye(n) - A, b)
+    xs, fs = [np.zeros(n, complex)], []
+    for it in range(2 * n + 1):
+        fs.append(A @ xs[-1] + b)
+        nxt, c = O.diis_extrapolate(fs, xs)
+        assert abs(c.sum() - 1.0) < 1e-12
+        if it == 0:
+            assert np.array_equal(nxt, fs[0])
+        xs.append(nxt)
+    assert np.abs(xs[-1] - xstar).max() < 1e-10 * np.abs(xstar).max()

@@ -83,3 +83,37 @@ def test_unmutated_pins_hold():
 def test_planted_mistake_is_caught(monkeypatch, name, target, variant):
     monkeypatch.setattr(gw, target, variant)
     assert not all(_pins_hold()), name
+
+
+# ---- the loop pieces: planted mistakes in Sigma^inf and the density matrix --------------------
+
+def _sigma_inf_variant(hartree_spin=True, exchange_pair_swapped=False, exchange_sign=-1.0):
+    def sinf(V, gamma, nk3, spin_factor=2.0):
+        nk = V.shape[0]
+        rho = sum(np.einsum("ab,Qba->Q", gamma[kp], V[kp, kp]) for kp in range(nk))
+        out = np.empty((nk,) + gamma.shape[1:], complex)
+        for k in range(nk):
+            h = np.einsum("Qij,Q->ij", V[k, k], rho) * (spin_factor if hartree_spin else 1.0)
+            x = sum(np.einsum("Qia,ab,Qbj->ij", V[k, kp], gamma[kp], V[k, kp] if exchange_pair_swapped else V[kp, k])
+                    for kp in range(nk))
+            out[k] = (h + exchange_sign * x) / nk
+        return out
+    return sinf
+
+
+@pytest.mark.parametrize("variant", [_sigma_inf_variant(hartree_spin=False),
+                                     _sigma_inf_variant(exchange_pair_swapped=True),
+                                     _sigma_inf_variant(exchange_sign=+1.0)])
+def test_planted_sigma_inf_mistake_is_caught(monkeypatch, variant):
+    import test_oracle_loop_pins as LP
+    monkeypatch.setattr(gw, "sigma_inf", variant)
+    with pytest.raises(AssertionError):
+        LP.test_sigma_inf_against_four_index((3, 1, 1))
+
+
+def test_planted_density_sign_is_caught(monkeypatch):
+    import test_oracle_loop_pins as LP
+    real = gw.density_matrix
+    monkeypatch.setattr(gw, "density_matrix", lambda G, beta: -real(G, beta))
+    with pytest.raises(AssertionError):
+        LP.test_density_matrix_of_g0_is_fermi((1, 1, 1), 2.0, 0.3)
