@@ -267,3 +267,53 @@ def diis_extrapolate(outputs, inputs):
     the self-energies Sigma_i they were computed from (residual r_i = Sigma[G_i] - Sigma_i)."""
     c = diis_coefficients([o - x for o, x in zip(outputs, inputs)])
     return sum(ci * o for ci, o in zip(c, outputs)), c
+
+
+def scgw_full(H, V, G0, nk3, beta, mu, spin_factor=2.0, alpha=0.5, tol=1e-6, itermax=10, static=True,
+              n_electrons=None, mu_lo=-5.0, mu_hi=5.0, mu_tol=1e-10, diis_size=0, diis_start=2):
+    """The self-consistency loop of Sec. 2.4 with its four steps per iteration n:
+
+      (1) the static part Sigma^inf[G_{n-1}] (Eq. sigma_inf; left out when static is False) and
+          the dynamic part Sigma~[G_{n-1}] (Eq. sigma_gw) -- together the output F_n;
+      (2) acceleration (Sec. 5.3): Sigma_1 = F_1; afterwards iteration mixing
+          Sigma_n = alpha F_n + (1 - alpha) Sigma_{n-1}, or, with diis_size > 0, Pulay's
+          extrapolation over the newest diis_size pairs (Sigma_{i-1}, F_i) from iteration
+          diis_start on (the iterations before it mix and fill the subspace);
+      (3) with n_electrons given, mu such that the Dyson solution holds n_electrons per cell;
+      (4) G_n = Dyson(H + Sigma^inf_n, Sigma~_n, mu).
+
+    The pair (Sigma^inf, Sigma~) is one vector for mixing, DIIS and the stopping test
+    max |Sigma_n - Sigma_{n-1}| < tol. Returns a dict with Sig (dynamic), SigInf, G, mu,
+    iterations and hist (the max |dSigma| of iterations 2, 3, ...)."""
+    nk, ntau, nao, _ = G0.shape
+    G = G0
+    prev = None                         # (SigInf, Sig) of the previous iteration
+    ins, outs = [], []
+    hist = []
+    it = 0
+    for it in range(1, itermax + 1):
+        sinf = sigma_inf(V, density_matrix(G, beta), nk3, spin_factor) if static else np.zeros((nk, nao, nao), complex)
+        sdyn = sigma_eval(V, G, nk3, beta, spin_factor)["Sig"]
+        out = np.concatenate([sinf.ravel(), sdyn.ravel()])
+        if prev is None:
+            cur = out
+        else:
+            if diis_size > 0:
+                ins.append(prev)
+                outs.append(out)
+                ins, outs = ins[-diis_size:], outs[-diis_size:]
+            if diis_size > 0 and it >= diis_start:
+                cur, _ = diis_extrapolate(outs, ins)
+            else:
+                cur = mix(out, prev, alpha)
+            hist.append(float(np.max(np.abs(cur - prev))))
+        prev = cur
+        sinf = cur[:nk * nao * nao].reshape(nk, nao, nao)
+        sdyn = cur[nk * nao * nao:].reshape(G0.shape)
+        if n_electrons is not None:
+            mu, G = find_mu(H, sinf, sdyn, beta, n_electrons, spin_factor, lo=mu_lo, hi=mu_hi, tol=mu_tol)
+        else:
+            G = dyson_G_static(H, sinf, sdyn, mu, beta)
+        if hist and hist[-1] < tol:
+            break
+    return {"Sig": sdyn, "SigInf": sinf, "G": G, "mu": mu, "iterations": it, "hist": hist}

@@ -96,3 +96,46 @@ def test_diis_solves_linear_fixed_points_exactly():
             assert np.array_equal(nxt, fs[0])
         xs.append(nxt)
     assert np.abs(xs[-1] - xstar).max() < 1e-10 * np.abs(xstar).max()
+
+
+def loop_case():
+    w = I.Workload("m", (2, 1, 1), 4, 8, 16, 16, 5.0, 0.0, 4.0, 21, solid=True)
+    h, v, g = I.make_inputs(w)
+    return w, h, 0.3 * v, g
+
+
+def test_full_loop_reduces_to_the_fixed_mu_loop():
+    """Without the static part, the mu search and DIIS the full loop is the fixed-mu loop."""
+    w, h, v, g = loop_case()
+    a = O.scgw_full(h, v, g, w.nk3, w.beta, 0.1, alpha=0.6, tol=1e-9, itermax=4, static=False)
+    sig, G, hist = O.scgw(h, v, g, w.nk3, w.beta, 0.1, alpha=0.6, tol=1e-9, itermax=4)
+    assert np.array_equal(a["Sig"], sig) and np.array_equal(a["G"], G)
+    assert a["hist"] == hist
+
+
+@pytest.mark.parametrize("diis", [0, 4])
+def test_full_loop_reaches_its_fixed_point(diis):
+    """At convergence every step of Sec. 2.4 holds at once: Sigma^inf and Sigma~ are those of G,
+    G holds n_electrons, and G solves the Dyson equation with them."""
+    w, h, v, g = loop_case()
+    n_e = 3.0
+    r = O.scgw_full(h, v, g, w.nk3, w.beta, 0.0, alpha=0.7, tol=1e-10, itermax=60, n_electrons=n_e,
+                    mu_tol=1e-13, diis_size=diis, diis_start=3)
+    assert r["hist"][-1] < 1e-10
+    gam = O.density_matrix(r["G"], w.beta)
+    assert abs(O.particle_number(gam, 2.0) - n_e) < 1e-9
+    assert np.abs(O.sigma_inf(v, gam, w.nk3, 2.0) - r["SigInf"]).max() < 1e-8
+    assert np.abs(O.sigma_eval(v, r["G"], w.nk3, w.beta)["Sig"] - r["Sig"]).max() < 1e-8
+    assert np.abs(O.dyson_G(h + r["SigInf"], r["Sig"], r["mu"], w.beta) - r["G"]).max() < 1e-12
+
+
+def test_full_loop_fixed_point_does_not_depend_on_the_acceleration():
+    """Mixing and DIIS reach the same (Sigma, G, mu); DIIS in fewer iterations here."""
+    w, h, v, g = loop_case()
+    kw = dict(tol=1e-10, itermax=80, n_electrons=3.0, mu_tol=1e-13)
+    a = O.scgw_full(h, v, g, w.nk3, w.beta, 0.0, alpha=0.5, **kw)
+    b = O.scgw_full(h, v, g, w.nk3, w.beta, 0.0, alpha=0.5, diis_size=5, diis_start=2, **kw)
+    assert abs(a["mu"] - b["mu"]) < 1e-8
+    for key in ("Sig", "SigInf", "G"):
+        assert np.abs(a[key] - b[key]).max() < 1e-8
+    assert b["iterations"] < a["iterations"]
