@@ -253,6 +253,92 @@ int gw_polarization_noalloc(const int nk3[3], int nao, int naux, int ntau, doubl
 int gw_synchronize(gw_ctx* ctx);
 
 /*
+ * Density matrix gamma^k = G^k(0^-) = -G^k(beta^-), the G(0^-) of Eq. sigma_inf (Sec. 2.2).
+ * The tau nodes exclude beta, so G(beta^-) is the polynomial through the ntau node values
+ * evaluated at tau = beta: the Chebyshev series on the default grid, the interpolant of the
+ * nodes given to gw_set_grids otherwise. Writes gamma_dev [nk][nao][nao].
+ */
+int gw_density(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* gamma_dev);
+
+/*
+ * Static self-energy, Eq. sigma_inf (Sec. 2.2), with gamma from G as in gw_density:
+ *   Sigma^inf,k_ij = (s/N_k) sum_{k'Q ab} V^{kk}_ij(Q) gamma^{k'}_ab V^{k'k'}_ba(Q)
+ *                  - (1/N_k) sum_{k'Q ab} V^{kk'}_ia(Q) gamma^{k'}_ab V^{k'k}_bj(Q),
+ * s = spin_factor on the Hartree term only. FP64 in every precision. Writes SigInf_dev
+ * [nk][nao][nao]. In the Dyson equation it enters like H: pass H + Sigma^inf to gw_dyson_G.
+ */
+int gw_sigma_inf(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* SigInf_dev);
+
+/* Sets the chemical potential used by gw_dyson_G. */
+int gw_set_mu(gw_ctx* ctx, double mu);
+
+/* Electrons per cell (s/N_k) sum_k Tr gamma^k of G (synchronous). */
+int gw_particle_number(gw_ctx* ctx, const gw_c128* G_dev, double* n_host);
+
+/*
+ * Sec. 2.4 step 3: the chemical potential in [mu_lo, mu_hi] whose Dyson solution
+ * G = Dyson(Heff, Sigma, mu) (Heff = H + Sigma^inf) holds n_target electrons per cell,
+ * by bisection to tol (the particle number grows with mu). Writes G_dev, *mu_host, and sets
+ * the context's mu. GW_EINVAL if n_target lies outside [N(mu_lo), N(mu_hi)]. Synchronous.
+ */
+int gw_find_mu(gw_ctx* ctx, const gw_c128* Heff_dev, const gw_c128* Sig_dev, double n_target, double mu_lo,
+               double mu_hi, double tol, gw_c128* G_dev, double* mu_host);
+
+/*
+ * Convergence acceleration by direct inversion in the iterative subspace (Sec. 5.3), the
+ * Pulay form: push the self-energy Sigma_i an iteration's G was built from and the one
+ * computed from that G, Sigma[G_i]; extrapolate gives sum_i c_i Sigma[G_i] with c minimising
+ * |sum_i c_i (Sigma[G_i] - Sigma_i)|^2 subject to sum_i c_i = 1 (real c, inner products
+ * Re <r_i, r_j> over all n_elem complex entries). At most max_vectors (1..16) are kept, the
+ * oldest leaves first. Vectors are copied; work runs on cuda_stream (push synchronizes it).
+ */
+typedef struct gw_diis gw_diis;
+int gw_diis_create(gw_diis** out, long long n_elem, int max_vectors, void* cuda_stream);
+int gw_diis_destroy(gw_diis* diis);
+int gw_diis_push(gw_diis* diis, const gw_c128* sigma_in_dev, const gw_c128* sigma_out_dev);
+/* coeffs_host (optional, max_vectors doubles) and *nvec_host (optional) receive c, oldest first. */
+int gw_diis_extrapolate(gw_diis* diis, gw_c128* out_dev, double* coeffs_host, int* nvec_host);
+
+/*
+ * The self-consistency loop of Sec. 2.4 on one context. Iteration n takes G_{n-1} and
+ *   (1) evaluates the output F_n = (Sigma^inf[G], Sigma~[G]) (gw_sigma_inf, gw_sigma_eval;
+ *       Sigma^inf = 0 with static_part = 0);
+ *   (2) accelerates (Sec. 5.3): Sigma_1 = F_1; then Sigma_n = alpha F_n + (1 - alpha) Sigma_{n-1},
+ *       or with diis_size > 0 Pulay's extrapolation over the newest diis_size pairs
+ *       (Sigma_{i-1}, F_i) from iteration diis_start on (earlier iterations mix and fill the
+ *       subspace; gw_diis_*);
+ *   (3) with n_electrons > 0, finds mu in [mu_lo, mu_hi] (to mu_tol) whose Dyson solution holds
+ *       n_electrons per cell (gw_find_mu); otherwise keeps the context's mu;
+ *   (4) G_n = Dyson(H + Sigma^inf_n, Sigma~_n, mu) (gw_dyson_G).
+ * (Sigma^inf, Sigma~) is one vector for mixing, DIIS and the stop test max |Sigma_n - Sigma_{n-1}|
+ * < tol. G_dev holds G_0 on entry and the last G on return; Sigma_dev [nk][ntau][nao][nao] and
+ * SigInf_dev [nk][nao][nao] receive the last Sigma_n (either may be NULL). The loop allocates
+ * gw_scgw_bytes() of device memory for its duration and synchronizes the context's stream.
+ * GW_ENOTCONV after itermax evaluations without convergence (outputs and *res still written).
+ */
+typedef struct {
+  double alpha;               /* mixing weight in (0, 2) */
+  double tol;                 /* stop threshold on max |dSigma| (Ha), >= 0 */
+  int itermax;                /* self-energy evaluations at most, >= 1 */
+  int static_part;            /* 1: include Sigma^inf (Eq. sigma_inf) */
+  int diis_size;              /* 0: mixing only; 1..16: DIIS subspace size */
+  int diis_start;             /* first extrapolating iteration, >= 2 */
+  double n_electrons;         /* > 0: search mu each iteration for this many electrons per cell */
+  double mu_lo, mu_hi, mu_tol;   /* bracket and tolerance of that search */
+} gw_scgw_options;
+
+typedef struct {
+  int iterations;             /* self-energy evaluations done */
+  double max_abs_dsigma;      /* last max |dSigma| (0 after a single evaluation) */
+  double mu;                  /* chemical potential of the last G */
+  double n_electrons;         /* electrons per cell of the last G */
+} gw_scgw_result;
+
+size_t gw_scgw_bytes(const gw_config* cfg, const gw_scgw_options* opt);
+int gw_scgw(gw_ctx* ctx, const gw_c128* H_dev, gw_c128* G_dev, gw_c128* Sigma_dev, gw_c128* SigInf_dev,
+            const gw_scgw_options* opt, gw_scgw_result* res);
+
+/*
  * Batched self-energy evaluation of many independent systems (molecules or k-meshes of
  * uneven size). One context per system on one of max_streams CUDA streams (chosen by
  * predicted cost, longest first onto the least-loaded stream). Modes of gw_batch_sigma_eval:
@@ -319,6 +405,12 @@ typedef struct {
   double alpha;               /* mixing weight in (0, 2) */
   double tol;                 /* convergence threshold on max |dSigma| (Ha) */
   int itermax;                /* self-energy evaluations at most, >= 1 */
+  /* the rest of the loop of gw_scgw; all zero: fixed mu, no static part, mixing only */
+  int static_part;
+  int diis_size;
+  int diis_start;
+  double n_electrons;
+  double mu_lo, mu_hi, mu_tol;
 } gw_job;
 
 typedef struct {
@@ -326,9 +418,11 @@ typedef struct {
   int iterations;             /* self-energy evaluations done */
   double max_abs_dsigma;      /* last max |dSigma| (0 after a single evaluation) */
   double t_submit, t_start, t_end;   /* seconds on the library's monotonic clock */
+  double mu;                  /* chemical potential of the final G */
 } gw_job_result;
 
-/* Device bytes one job holds while it runs (0 for an invalid configuration). */
+/* Device bytes a job holds while it runs with the loop options all zero (0 for an invalid
+ * configuration); gw_submit also counts the DIIS subspace a job's options ask for. */
 size_t gw_job_bytes(const gw_config* cfg);
 
 /* GW_EINVAL for max_slots outside 1..64 or a zero budget. */

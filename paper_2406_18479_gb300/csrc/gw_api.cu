@@ -78,7 +78,8 @@ static thread_local Prof* t_prof = nullptr;
 const char* prof_slot_name(int slot) {
   static const char* names[SLOT_COUNT] = {
       "vg_fp64", "p0_gemm_fp64", "r_gemm_fp64", "sigma_gemm_fp64", "transform_fp64", "inverse_fp64",
-      "elementwise", "slice_planes", "vg_gemm_tc", "p0_gemm_tc", "r_gemm_tc", "sigma_gemm_tc", "reduce"};
+      "elementwise", "slice_planes", "vg_gemm_tc", "p0_gemm_tc", "r_gemm_tc", "sigma_gemm_tc", "reduce",
+      "static_fp64"};
   return (slot >= 0 && slot < SLOT_COUNT) ? names[slot] : "";
 }
 
@@ -140,6 +141,12 @@ struct gw_ctx {
   const double2* V = nullptr;
   size_t bytes = 0;
   MixedState* mixed = nullptr;
+  // static part and loop helpers
+  double* wbeta = nullptr;                // weights of the interpolant at tau = beta, [ntau]
+  double2* gamma = nullptr;               // density matrix, [nk][nao][nao]
+  double2* rho = nullptr;                 // Hartree density in the auxiliary basis, [naux]
+  double2* xinf = nullptr;                // exchange intermediate of one k, [nk][naux][nao][nao]
+  double* scal = nullptr;                 // reduction partials and results
   Prof prof;
 };
 
@@ -191,7 +198,8 @@ void free_ctx(gw_ctx* c) {
   if (!c) return;
   mixed_destroy(c->mixed);
   void* ptrs[] = {c->Fb, c->Bb, c->Ff, c->Bf, c->wf, c->tabs, c->mq_dev, c->wlist, c->work, c->P0t, c->Pw,
-                  c->Pt, c->dyson_ws, c->status, c->maxdiff, c->nonfinite};
+                  c->Pt, c->dyson_ws, c->status, c->maxdiff, c->nonfinite, c->wbeta, c->gamma, c->rho,
+                  c->xinf, c->scal};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -424,6 +432,33 @@ bool config_ok(const gw_config* cfg) {
            cfg->v_slices > GW_V_PER_Q);
 }
 
+// Weights w_j with p(beta) = sum_j w_j f(tau_j) for the polynomial p of degree n - 1 through the
+// n nodes (all inside (0, beta)): the barycentric form w_j = (lambda_j / (beta - tau_j)) /
+// sum_i lambda_i / (beta - tau_i), lambda_j = 1 / prod_{i != j} (tau_j - tau_i), taken in
+// logarithms of x = 2 tau / beta - 1 so that no product over- or underflows. For the
+// first-kind Chebyshev nodes p is the Chebyshev series of the nodes evaluated at tau = beta.
+static void weights_at_beta(const double* tau, int n, double beta, std::vector<double>& w) {
+  std::vector<double> lg(n), sg(n);
+  double top = -INFINITY;
+  for (int j = 0; j < n; ++j) {
+    const double xj = 2.0 * tau[j] / beta - 1.0;
+    double l = -std::log(1.0 - xj), sgn = 1.0;
+    for (int i = 0; i < n; ++i) {
+      if (i == j) continue;
+      const double d = xj - (2.0 * tau[i] / beta - 1.0);
+      l -= std::log(std::fabs(d));
+      if (d < 0) sgn = -sgn;
+    }
+    lg[j] = l;
+    sg[j] = sgn;
+    top = std::max(top, l);
+  }
+  w.assign(n, 0.0);
+  double norm = 0.0;
+  for (int j = 0; j < n; ++j) norm += (w[j] = sg[j] * std::exp(lg[j] - top));
+  for (double& x : w) x /= norm;
+}
+
 // Grids, gather tables and workspaces of a context; in a size-only build (c->dry)
 // the same sequence only sums the bytes it would allocate.
 int ctx_build(gw_ctx* c, const gw_config* cfg) {
@@ -489,6 +524,20 @@ int ctx_build(gw_ctx* c, const gw_config* cfg) {
     if ((rc = dev_alloc(c, &c->status, 4)) != GW_OK) break;
     if ((rc = dev_alloc(c, &c->maxdiff, 1)) != GW_OK) break;
     if ((rc = dev_alloc(c, &c->nonfinite, 1)) != GW_OK) break;
+    if ((rc = dev_alloc(c, &c->gamma, (size_t)nk * c->nao2)) != GW_OK) break;
+    if ((rc = dev_alloc(c, &c->rho, (size_t)c->naux)) != GW_OK) break;
+    if ((rc = dev_alloc(c, &c->xinf, (size_t)nk * c->pair)) != GW_OK) break;
+    if ((rc = dev_alloc(c, &c->scal, (size_t)kDotBlocks + 8)) != GW_OK) break;
+    {
+      std::vector<double> w, tau(c->ntau);
+      for (int j = 0; j < c->ntau; ++j) {
+        const double th = M_PI * (c->ntau - j - 0.5) / c->ntau;   // ascending first-kind Chebyshev nodes
+        tau[j] = 0.5 * cfg->beta * (1.0 + std::cos(th));
+      }
+      weights_at_beta(tau.data(), c->ntau, cfg->beta, w);
+      if ((rc = dev_alloc(c, &c->wbeta, (size_t)c->ntau)) != GW_OK) break;
+      upload(c, c->wbeta, w.data(), w.size() * sizeof(double));
+    }
     if (!c->dry) cudaMemset(c->status, 0, 4 * sizeof(int));
     if (cfg->precision != GW_FP64) {
       MixedDims d;
@@ -506,14 +555,18 @@ int ctx_build(gw_ctx* c, const gw_config* cfg) {
 
 }  // namespace
 
+CtxInfo ctx_info(const gw_ctx* c) { return CtxInfo{c->stream, c->nk, c->ntau, c->nao, c->cfg.mu}; }
+
 size_t job_device_bytes(const gw_config* cfg) {
   if (!config_ok(cfg)) return 0;
   gw_ctx c;
   c.dry = true;
   if (ctx_build(&c, cfg) != GW_OK) return 0;
   const size_t nk = (size_t)cfg->nk[0] * cfg->nk[1] * cfg->nk[2], nao2 = (size_t)cfg->nao * cfg->nao;
-  // V, H, G, and two Sigma buffers of the job
-  return c.bytes + sizeof(gw_c128) * (nk * nk * cfg->naux * nao2 + nk * nao2 + 3 * nk * cfg->ntau * nao2);
+  // V, H, G and the Sigma output of the job, and the loop's buffers with its default options
+  gw_scgw_options o{};
+  return c.bytes + sizeof(gw_c128) * (nk * nk * cfg->naux * nao2 + nk * nao2 + 2 * nk * cfg->ntau * nao2) +
+         scgw_device_bytes(cfg, &o);
 }
 
 }  // namespace gwi
@@ -586,6 +639,10 @@ int gw_set_grids(gw_ctx* ctx, const double* tau_host, const gw_c128* Fb_host, co
       cudaMemcpy(ctx->Ff, Ff_host, sf, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(ctx->Bf, Bf_host, sf, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(ctx->wf, omega_f_host, (size_t)nf * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+    return cuda_check("gw_set_grids copy");
+  std::vector<double> w;
+  weights_at_beta(tau_host, T, beta, w);
+  if (cudaMemcpy(ctx->wbeta, w.data(), (size_t)T * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
     return cuda_check("gw_set_grids copy");
   return GW_OK;
 }
@@ -670,6 +727,119 @@ int gw_dyson_G(gw_ctx* ctx, const gw_c128* H_dev, const gw_c128* Sig_dev, gw_c12
   GW_TRY(build_g_dyson_fp64(ctx->dyson_ws, H, ctx->wf, ctx->cfg.mu, ctx->nk, ctx->nwf, ctx->nao, ctx->stream));
   GW_TRY(batched_inverse_fp64(ctx->dyson_ws, ctx->nao, ctx->nao2, ctx->nk * ctx->nwf, ctx->status, ctx->stream));
   GW_TRY(transform(ctx, 1, false, ctx->dyson_ws, G, ctx->nk, ctx->nao2));
+  return GW_OK;
+}
+
+int gw_density(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* gamma_dev) {
+  ProfScope _ps(ctx ? &ctx->prof : nullptr);
+  if (!ctx || !G_dev || !gamma_dev) return fail(GW_EINVAL, "gw_density: null argument");
+  return density_fp64(reinterpret_cast<const double2*>(G_dev), ctx->wbeta, reinterpret_cast<double2*>(gamma_dev),
+                      ctx->nk, ctx->ntau, ctx->nao, ctx->stream);
+}
+
+int gw_sigma_inf(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* SigInf_dev) {
+  ProfScope _ps(ctx ? &ctx->prof : nullptr);
+  if (!ctx || !G_dev || !SigInf_dev) return fail(GW_EINVAL, "gw_sigma_inf: null argument");
+  if (!ctx->V) return fail(GW_EINVAL, "gw_sigma_inf: call gw_set_coulomb first");
+  const int nk = ctx->nk, nao = ctx->nao, naux = ctx->naux;
+  double2* S = reinterpret_cast<double2*>(SigInf_dev);
+  GW_TRY(density_fp64(reinterpret_cast<const double2*>(G_dev), ctx->wbeta, ctx->gamma, nk, ctx->ntau, nao, ctx->stream));
+  // Hartree: (s / N_k) sum_Q V^{kk}_ij(Q) rho_Q
+  GW_TRY(hartree_fp64(ctx->V, ctx->gamma, ctx->rho, S, nk, naux, nao, ctx->cfg.spin_factor / nk, ctx->stream));
+  // exchange: -(1 / N_k) sum_{k'} sum_{Q b} X^{k'}_{Q i b} V^{k'k}_bj(Q), X^{k'}_{Q i b} = sum_a V^{kk'}_ia(Q) gamma^{k'}_ab
+  for (int k = 0; k < nk; ++k) {
+    ZGemm a;
+    a.M = naux * nao;
+    a.N = nao;
+    a.K = nao;
+    a.nbatch = nk;
+    a.A = ctx->V + (long long)k * nk * ctx->pair;
+    a.ba.bs_in = ctx->pair;
+    a.va.rs_in = nao;
+    a.va.ks_in = 1;
+    a.B = ctx->gamma;
+    a.bb.bs_in = ctx->nao2;
+    a.vb.rs_in = 1;
+    a.vb.ks_in = nao;
+    a.C = ctx->xinf;
+    a.bc.bs_in = ctx->pair;
+    a.vc.rs_in = nao;
+    a.vc.ks_in = 1;
+    a.slot = SLOT_STATIC_FP64;
+    GW_TRY(zgemm_fp64(a, ctx->stream));
+    for (int kp = 0; kp < nk; ++kp) {
+      ZGemm b;
+      b.M = nao;
+      b.N = nao;
+      b.K = naux * nao;
+      b.A = ctx->xinf + (long long)kp * ctx->pair;
+      b.va.rs_in = nao;
+      b.va.kin = nao;
+      b.va.ks_in = 1;
+      b.va.ks_out = ctx->nao2;
+      b.B = ctx->V + ((long long)kp * nk + k) * ctx->pair;
+      b.vb.rs_in = 1;
+      b.vb.kin = nao;
+      b.vb.ks_in = nao;
+      b.vb.ks_out = ctx->nao2;
+      b.C = S + (long long)k * ctx->nao2;
+      b.vc.rs_in = nao;
+      b.vc.ks_in = 1;
+      b.alpha = -1.0 / nk;
+      b.accumulate = 1;
+      b.slot = SLOT_STATIC_FP64;
+      GW_TRY(zgemm_fp64(b, ctx->stream));
+    }
+  }
+  return GW_OK;
+}
+
+int gw_set_mu(gw_ctx* ctx, double mu) {
+  if (!ctx || !std::isfinite(mu)) return fail(GW_EINVAL, "gw_set_mu: bad argument");
+  ctx->cfg.mu = mu;
+  return GW_OK;
+}
+
+int gw_particle_number(gw_ctx* ctx, const gw_c128* G_dev, double* n_host) {
+  ProfScope _ps(ctx ? &ctx->prof : nullptr);
+  if (!ctx || !G_dev || !n_host) return fail(GW_EINVAL, "gw_particle_number: null argument");
+  GW_TRY(density_fp64(reinterpret_cast<const double2*>(G_dev), ctx->wbeta, ctx->gamma, ctx->nk, ctx->ntau, ctx->nao,
+                      ctx->stream));
+  GW_TRY(trace_fp64(ctx->gamma, ctx->nk, ctx->nao, ctx->scal, ctx->stream));
+  double tr = 0.0;
+  if (cudaMemcpyAsync(&tr, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+      cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+    return cuda_check("gw_particle_number");
+  *n_host = ctx->cfg.spin_factor * tr / ctx->nk;
+  return GW_OK;
+}
+
+int gw_find_mu(gw_ctx* ctx, const gw_c128* Heff_dev, const gw_c128* Sig_dev, double n_target, double mu_lo,
+               double mu_hi, double tol, gw_c128* G_dev, double* mu_host) {
+  if (!ctx || !Heff_dev || !Sig_dev || !G_dev || !mu_host || !(mu_lo < mu_hi) || !(tol > 0))
+    return fail(GW_EINVAL, "gw_find_mu: bad argument");
+  auto number = [&](double mu, double* n) {
+    ctx->cfg.mu = mu;
+    GW_TRY(gw_dyson_G(ctx, Heff_dev, Sig_dev, G_dev));
+    return gw_particle_number(ctx, G_dev, n);
+  };
+  double n_lo = 0.0, n_hi = 0.0;
+  GW_TRY(number(mu_lo, &n_lo));
+  GW_TRY(number(mu_hi, &n_hi));
+  if (!(n_lo <= n_target && n_target <= n_hi))
+    return fail(GW_EINVAL, "gw_find_mu: target %.6g outside [N(mu_lo), N(mu_hi)] = [%.6g, %.6g]", n_target, n_lo,
+                n_hi);
+  for (int it = 0; it < 200 && mu_hi - mu_lo >= tol; ++it) {
+    const double mid = 0.5 * (mu_lo + mu_hi);
+    double n = 0.0;
+    GW_TRY(number(mid, &n));
+    if (n < n_target) mu_lo = mid;
+    else mu_hi = mid;
+  }
+  const double mu = 0.5 * (mu_lo + mu_hi);
+  double n = 0.0;
+  GW_TRY(number(mu, &n));
+  *mu_host = mu;
   return GW_OK;
 }
 

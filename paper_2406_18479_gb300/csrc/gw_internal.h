@@ -31,7 +31,7 @@ size_t job_device_bytes(const gw_config* cfg);
 enum ProfSlot {
   SLOT_VG_FP64 = 0, SLOT_P0_FP64, SLOT_R_FP64, SLOT_SIGMA_FP64, SLOT_TRANSFORM_FP64, SLOT_INVERSE_FP64,
   SLOT_ELEMENTWISE, SLOT_LIMBS, SLOT_VG_MIXED, SLOT_P0_TC, SLOT_R_TC, SLOT_SIGMA_MIXED, SLOT_REDUCE,
-  SLOT_COUNT
+  SLOT_STATIC_FP64, SLOT_COUNT
 };
 const char* prof_slot_name(int slot);
 void prof_begin(int slot, cudaStream_t s);
@@ -89,6 +89,31 @@ int build_g_dyson_fp64(double2* sw, const double2* H, const double* wn, double m
 // samples, which are symmetric): X[q][t] <- X[mq[q]][T-1-t]^T for every (q, t) that is not
 // canonical; canonical (q, t): q < mq[q], or q == mq[q] and t <= T-1-t. X is [nk][T][n][n].
 int mirror_fill(double2* X, int nk, int T, int n, const int* mq_dev, void* stream);
+
+// Static part and loop helpers (Eq. sigma_inf, Sec. 2.4, Sec. 5.3), all FP64:
+//   density:  gamma^k = -sum_t w_t G^k(tau_t)          (w: weights of the interpolant at tau = beta)
+//   hartree:  out^k = scale sum_Q V^{kk}(Q) rho_Q, rho_Q = sum_{k'ab} gamma^{k'}_ab V^{k'k'}_ba(Q)
+//   trace:    *out = sum_k Re Tr gamma^k;  add: c = a + b
+//   dot_re:   *out = Re <x, y> (kDotBlocks partial sums, in a fixed order);  lincomb: out = sum_i c_i v_i
+constexpr int kDotBlocks = 512;
+int density_fp64(const double2* G, const double* w, double2* gamma, int nk, int ntau, int nao, void* stream);
+int hartree_fp64(const double2* V, const double2* gamma, double2* rho, double2* out, int nk, int naux, int nao,
+                 double scale, void* stream);
+int trace_fp64(const double2* gamma, int nk, int nao, double* out_dev, void* stream);
+int add_fp64(const double2* a, const double2* b, double2* c, long long n, void* stream);
+int dot_re_fp64(const double2* x, const double2* y, long long n, double* partial_dev, double* out_dev, void* stream);
+int lincomb_fp64(const double2* const* v, const double* c, int m, double2* out, long long n, void* stream);
+
+// sizes, stream and mu of a context (for host code outside the file that defines gw_ctx)
+struct CtxInfo {
+  void* stream;
+  int nk, ntau, nao;
+  double mu;
+};
+CtxInfo ctx_info(const gw_ctx* ctx);
+
+// device bytes of the scGW loop's own buffers; job_device_bytes plus these for a serving job
+size_t scgw_device_bytes(const gw_config* cfg, const gw_scgw_options* opt);
 
 // Sig_inout = alpha*new + (1-alpha)*old; *maxdiff (device double) = max |change|; nonfinite flag
 int mix_fp64(const double2* s_new, double2* s_inout, double alpha, long long n, double* maxdiff_dev,

@@ -1,9 +1,9 @@
 // Request loop for scGW jobs: admission by device-memory budget, one worker
 // thread and one CUDA stream per slot, continuous batching.
 //
-// A job is the self-consistency loop of Sec. 2.4 at fixed mu: Sigma = Sigma[G]
-// (gw_sigma_eval), iteration mixing (Sec. 5.3, gw_mix), and the Dyson update of
-// G (Eq. dyson, gw_dyson_G), until max |dSigma| < tol or itermax evaluations.
+// A job is the self-consistency loop of Sec. 2.4 (gw_scgw): self-energy, iteration
+// mixing or DIIS (Sec. 5.3), optionally the static part and the chemical-potential search,
+// and the Dyson update of G, until max |dSigma| < tol or itermax evaluations.
 // Jobs that arrive while others run are admitted as soon as a slot and enough
 // of the budget are free; admitted jobs run on their own streams, so their
 // kernels overlap on the device. Every job computes exactly what it computes
@@ -60,6 +60,21 @@ struct gw_server {
 
 namespace {
 
+gw_scgw_options job_options(const gw_job& s) {
+  gw_scgw_options o{};
+  o.alpha = s.alpha;
+  o.tol = s.tol;
+  o.itermax = s.itermax;
+  o.static_part = s.static_part;
+  o.diis_size = s.diis_size;
+  o.diis_start = s.diis_start;
+  o.n_electrons = s.n_electrons;
+  o.mu_lo = s.mu_lo;
+  o.mu_hi = s.mu_hi;
+  o.mu_tol = s.mu_tol;
+  return o;
+}
+
 int run_job(Job* j) {
   const gw_job& s = j->spec;
   const gw_config& c = s.cfg;
@@ -69,13 +84,13 @@ int run_job(Job* j) {
   const size_t bH = sizeof(gw_c128) * nk * nao2;
   const size_t bG = sizeof(gw_c128) * nk * c.ntau * nao2;
   cudaStream_t st = nullptr;
-  gw_c128 *V = nullptr, *H = nullptr, *G = nullptr, *S = nullptr, *Snew = nullptr;
+  gw_c128 *V = nullptr, *H = nullptr, *G = nullptr, *S = nullptr;
   gw_ctx* ctx = nullptr;
   int rc = GW_OK;
   auto cleanup = [&]() {
     if (ctx) gw_destroy(ctx);
     if (st) cudaStreamSynchronize(st);
-    for (void* p : {(void*)V, (void*)H, (void*)G, (void*)S, (void*)Snew})
+    for (void* p : {(void*)V, (void*)H, (void*)G, (void*)S})
       if (p) cudaFree(p);
     if (st) cudaStreamDestroy(st);
   };
@@ -85,8 +100,7 @@ int run_job(Job* j) {
       break;
     }
     if (cudaMalloc((void**)&V, bV) != cudaSuccess || cudaMalloc((void**)&H, bH) != cudaSuccess ||
-        cudaMalloc((void**)&G, bG) != cudaSuccess || cudaMalloc((void**)&S, bG) != cudaSuccess ||
-        cudaMalloc((void**)&Snew, bG) != cudaSuccess) {
+        cudaMalloc((void**)&G, bG) != cudaSuccess || cudaMalloc((void**)&S, bG) != cudaSuccess) {
       rc = fail(GW_ENOMEM, "job %llu: device allocation failed", (unsigned long long)j->id);
       break;
     }
@@ -95,31 +109,19 @@ int run_job(Job* j) {
     cudaMemcpyAsync(G, s.G0_host, bG, cudaMemcpyHostToDevice, st);
     if ((rc = gw_create(&ctx, &c, st)) != GW_OK) break;
     if ((rc = gw_set_coulomb(ctx, V)) != GW_OK) break;
-    double d = 0.0;
-    int it = 0;
-    bool converged = false;
-    for (it = 1; it <= s.itermax; ++it) {
-      if ((rc = gw_sigma_eval(ctx, G, it == 1 ? S : Snew)) != GW_OK) break;
-      if (it > 1) {
-        if ((rc = gw_mix(ctx, Snew, S, s.alpha, &d)) != GW_OK) break;
-      }
-      if ((rc = gw_dyson_G(ctx, H, S, G)) != GW_OK) break;
-      if (it > 1 && d < s.tol) {
-        converged = true;
-        break;
-      }
-    }
-    if (rc != GW_OK) break;
-    if ((rc = gw_synchronize(ctx)) != GW_OK) break;
-    j->result.iterations = converged ? it : s.itermax;
-    j->result.max_abs_dsigma = d;
+    const gw_scgw_options o = job_options(s);
+    gw_scgw_result r{};
+    rc = gw_scgw(ctx, H, G, S, nullptr, &o, &r);
+    if (rc != GW_OK && rc != GW_ENOTCONV) break;
+    j->result.iterations = r.iterations;
+    j->result.max_abs_dsigma = r.max_abs_dsigma;
+    j->result.mu = r.mu;
     if (s.Sigma_out_host) cudaMemcpyAsync(s.Sigma_out_host, S, bG, cudaMemcpyDeviceToHost, st);
     if (s.G_out_host) cudaMemcpyAsync(s.G_out_host, G, bG, cudaMemcpyDeviceToHost, st);
     if (cudaStreamSynchronize(st) != cudaSuccess) {
       rc = fail(GW_ECUDA, "job %llu: result copy failed", (unsigned long long)j->id);
       break;
     }
-    if (!converged) rc = GW_ENOTCONV;
   } while (false);
   cleanup();
   return rc;
@@ -197,8 +199,10 @@ int gw_server_destroy(gw_server* s) {
 int gw_submit(gw_server* s, const gw_job* job, uint64_t* job_id) {
   if (!s || !job || !job_id || !job->H_host || !job->V_host || !job->G0_host || job->itermax < 1)
     return fail(GW_EINVAL, "gw_submit: bad arguments");
-  const size_t bytes = job_device_bytes(&job->cfg);
+  size_t bytes = job_device_bytes(&job->cfg);
   if (bytes == 0) return fail(GW_EINVAL, "gw_submit: configuration out of range");
+  const gw_scgw_options o = job_options(*job), o0{};
+  bytes += scgw_device_bytes(&job->cfg, &o) - scgw_device_bytes(&job->cfg, &o0);
   if (bytes > s->budget)
     return fail(GW_ENOMEM, "gw_submit: job needs %zu bytes, budget is %zu", bytes, s->budget);
   Job* j = new Job();

@@ -476,6 +476,135 @@ __global__ void __launch_bounds__(256) mirror_fill_kernel(double2* X, int nk, in
   }
 }
 
+// ---- static part and loop helpers (Eq. sigma_inf, Sec. 2.4, Sec. 5.3)
+
+// gamma^k = -sum_t w_t G^k(tau_t): minus the interpolant of G at tau = beta (w: extrapolation weights)
+__global__ void density_kernel(const double2* G, const double* w, double2* gamma, int nk, int ntau, long long nao2) {
+  const long long total = (long long)nk * nao2;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long k = e / nao2, r = e % nao2;
+    const double2* g = G + k * ntau * nao2 + r;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int t = 0; t < ntau; ++t) {
+      const double2 v = g[(long long)t * nao2];
+      acc.x = fma(w[t], v.x, acc.x);
+      acc.y = fma(w[t], v.y, acc.y);
+    }
+    gamma[e] = make_double2(-acc.x, -acc.y);
+  }
+}
+
+// rho_Q = sum_{k'} sum_ab gamma^{k'}_ab V^{k'k'}_ba(Q); one block per Q
+__global__ void __launch_bounds__(256) hartree_rho_kernel(const double2* V, const double2* gamma, double2* rho, int nk,
+                                                          int naux, int nao) {
+  const int Q = blockIdx.x;
+  const long long nao2 = (long long)nao * nao, pair = (long long)naux * nao2;
+  double2 acc = make_double2(0.0, 0.0);
+  for (long long e = threadIdx.x; e < (long long)nk * nao2; e += blockDim.x) {
+    const int kp = (int)(e / nao2);
+    const int a = (int)((e % nao2) / nao), b = (int)(e % nao);
+    const double2 g = gamma[(long long)kp * nao2 + (long long)a * nao + b];
+    const double2 v = V[((long long)kp * nk + kp) * pair + (long long)Q * nao2 + (long long)b * nao + a];
+    cmac(acc, g, v);
+  }
+  __shared__ double sx[256], sy[256];
+  sx[threadIdx.x] = acc.x;
+  sy[threadIdx.x] = acc.y;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      sx[threadIdx.x] += sx[threadIdx.x + o];
+      sy[threadIdx.x] += sy[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) rho[Q] = make_double2(sx[0], sy[0]);
+}
+
+// out^k_ij = scale sum_Q V^{kk}_ij(Q) rho_Q
+__global__ void hartree_j_kernel(const double2* V, const double2* rho, double2* out, int nk, int naux, int nao,
+                                 double scale) {
+  const long long nao2 = (long long)nao * nao, pair = (long long)naux * nao2;
+  const long long total = (long long)nk * nao2;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long k = e / nao2, r = e % nao2;
+    const double2* v = V + (k * nk + k) * pair + r;
+    double2 acc = make_double2(0.0, 0.0);
+    for (int Q = 0; Q < naux; ++Q) cmac(acc, v[(long long)Q * nao2], rho[Q]);
+    out[e] = make_double2(scale * acc.x, scale * acc.y);
+  }
+}
+
+// *out = sum_k sum_i Re gamma^k_ii (one block)
+__global__ void __launch_bounds__(256) trace_kernel(const double2* gamma, int nk, int nao, double* out) {
+  double acc = 0.0;
+  for (long long e = threadIdx.x; e < (long long)nk * nao; e += blockDim.x) {
+    const long long k = e / nao, i = e % nao;
+    acc += gamma[(k * nao + i) * nao + i].x;
+  }
+  __shared__ double sh[256];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+// c = a + b elementwise
+__global__ void add_kernel(const double2* a, const double2* b, double2* c, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    c[e] = make_double2(a[e].x + b[e].x, a[e].y + b[e].y);
+}
+
+// partial[block] = sum over the block's share of Re(conj(x_e) y_e), in a fixed order
+__global__ void __launch_bounds__(256) dot_re_kernel(const double2* x, const double2* y, long long n, double* partial) {
+  double acc = 0.0;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    acc = fma(x[e].x, y[e].x, fma(x[e].y, y[e].y, acc));
+  __shared__ double sh[256];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+}
+
+// one block sums the partials
+__global__ void __launch_bounds__(256) sum_kernel(const double* partial, int m, double* out) {
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < m; e += blockDim.x) acc += partial[e];
+  __shared__ double sh[256];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+// out = sum_i c_i v_i (m <= 16 vectors, coefficients in constant-size parameter)
+struct LinComb {
+  const double2* v[16];
+  double c[16];
+  int m;
+};
+__global__ void lincomb_kernel(const LinComb lc, double2* out, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int i = 0; i < lc.m; ++i) {
+      const double2 x = lc.v[i][e];
+      acc.x = fma(lc.c[i], x.x, acc.x);
+      acc.y = fma(lc.c[i], x.y, acc.y);
+    }
+    out[e] = acc;
+  }
+}
+
 inline int grid_for(long long total, int block) {
   long long g = (total + block - 1) / block;
   if (g > 152LL * 32) g = 152LL * 32;
@@ -574,6 +703,66 @@ int mix_fp64(const double2* s_new, double2* s_inout, double alpha, long long n, 
   prof_end(SLOT_ELEMENTWISE, (cudaStream_t)stream, 8.0 * n, 48.0 * n);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "mix launch: %s", cudaGetErrorString(e));
+}
+
+int density_fp64(const double2* G, const double* w, double2* gamma, int nk, int ntau, int nao, void* stream) {
+  const long long n = (long long)nk * nao * nao;
+  prof_begin(SLOT_ELEMENTWISE, (cudaStream_t)stream);
+  density_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(G, w, gamma, nk, ntau, (long long)nao * nao);
+  prof_end(SLOT_ELEMENTWISE, (cudaStream_t)stream, 4.0 * n * ntau, 16.0 * n * (ntau + 1));
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "density launch: %s", cudaGetErrorString(e));
+}
+
+int hartree_fp64(const double2* V, const double2* gamma, double2* rho, double2* out, int nk, int naux, int nao,
+                 double scale, void* stream) {
+  const long long n = (long long)nk * nao * nao;
+  prof_begin(SLOT_STATIC_FP64, (cudaStream_t)stream);
+  hartree_rho_kernel<<<naux, 256, 0, (cudaStream_t)stream>>>(V, gamma, rho, nk, naux, nao);
+  hartree_j_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(V, rho, out, nk, naux, nao, scale);
+  prof_end(SLOT_STATIC_FP64, (cudaStream_t)stream, 16.0 * n * naux, 32.0 * n * naux);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "hartree launch: %s", cudaGetErrorString(e));
+}
+
+int trace_fp64(const double2* gamma, int nk, int nao, double* out_dev, void* stream) {
+  prof_begin(SLOT_ELEMENTWISE, (cudaStream_t)stream);
+  trace_kernel<<<1, 256, 0, (cudaStream_t)stream>>>(gamma, nk, nao, out_dev);
+  prof_end(SLOT_ELEMENTWISE, (cudaStream_t)stream, (double)nk * nao, 16.0 * nk * nao);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "trace launch: %s", cudaGetErrorString(e));
+}
+
+int add_fp64(const double2* a, const double2* b, double2* c, long long n, void* stream) {
+  prof_begin(SLOT_ELEMENTWISE, (cudaStream_t)stream);
+  add_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(a, b, c, n);
+  prof_end(SLOT_ELEMENTWISE, (cudaStream_t)stream, 2.0 * n, 48.0 * n);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "add launch: %s", cudaGetErrorString(e));
+}
+
+int dot_re_fp64(const double2* x, const double2* y, long long n, double* partial_dev, double* out_dev, void* stream) {
+  prof_begin(SLOT_REDUCE, (cudaStream_t)stream);
+  dot_re_kernel<<<kDotBlocks, 256, 0, (cudaStream_t)stream>>>(x, y, n, partial_dev);
+  sum_kernel<<<1, 256, 0, (cudaStream_t)stream>>>(partial_dev, kDotBlocks, out_dev);
+  prof_end(SLOT_REDUCE, (cudaStream_t)stream, 4.0 * n, 32.0 * n);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "dot launch: %s", cudaGetErrorString(e));
+}
+
+int lincomb_fp64(const double2* const* v, const double* c, int m, double2* out, long long n, void* stream) {
+  if (m < 1 || m > 16) return fail(GW_EINVAL, "lincomb: 1..16 vectors");
+  LinComb lc{};
+  for (int i = 0; i < m; ++i) {
+    lc.v[i] = v[i];
+    lc.c[i] = c[i];
+  }
+  lc.m = m;
+  prof_begin(SLOT_ELEMENTWISE, (cudaStream_t)stream);
+  lincomb_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(lc, out, n);
+  prof_end(SLOT_ELEMENTWISE, (cudaStream_t)stream, 4.0 * n * m, 16.0 * n * (m + 1));
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "lincomb launch: %s", cudaGetErrorString(e));
 }
 
 }  // namespace gwi

@@ -31,6 +31,8 @@ ABI_SYMBOLS = [
     "gw_profile_read", "gw_polarization_noalloc", "gw_job_bytes", "gw_server_create",
     "gw_server_destroy", "gw_submit", "gw_poll", "gw_batch_create", "gw_batch_destroy",
     "gw_batch_set_coulomb", "gw_batch_sigma_eval", "gw_batch_autotune", "gw_batch_synchronize",
+    "gw_density", "gw_sigma_inf", "gw_set_mu", "gw_particle_number", "gw_find_mu", "gw_diis_create",
+    "gw_diis_destroy", "gw_diis_push", "gw_diis_extrapolate", "gw_scgw_bytes", "gw_scgw",
 ]
 GW_BATCH_SERIAL, GW_BATCH_STREAMS, GW_BATCH_GRAPH = 0, 1, 2
 BATCH_MODES = {"serial": GW_BATCH_SERIAL, "streams": GW_BATCH_STREAMS, "graph": GW_BATCH_GRAPH}
@@ -55,6 +57,25 @@ class gw_job(ctypes.Structure):
         ("cfg", gw_config), ("H_host", ctypes.c_void_p), ("V_host", ctypes.c_void_p),
         ("G0_host", ctypes.c_void_p), ("Sigma_out_host", ctypes.c_void_p), ("G_out_host", ctypes.c_void_p),
         ("alpha", ctypes.c_double), ("tol", ctypes.c_double), ("itermax", ctypes.c_int),
+        ("static_part", ctypes.c_int), ("diis_size", ctypes.c_int), ("diis_start", ctypes.c_int),
+        ("n_electrons", ctypes.c_double), ("mu_lo", ctypes.c_double), ("mu_hi", ctypes.c_double),
+        ("mu_tol", ctypes.c_double),
+    ]
+
+
+class gw_scgw_options(ctypes.Structure):
+    _fields_ = [
+        ("alpha", ctypes.c_double), ("tol", ctypes.c_double), ("itermax", ctypes.c_int),
+        ("static_part", ctypes.c_int), ("diis_size", ctypes.c_int), ("diis_start", ctypes.c_int),
+        ("n_electrons", ctypes.c_double), ("mu_lo", ctypes.c_double), ("mu_hi", ctypes.c_double),
+        ("mu_tol", ctypes.c_double),
+    ]
+
+
+class gw_scgw_result(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int), ("max_abs_dsigma", ctypes.c_double), ("mu", ctypes.c_double),
+        ("n_electrons", ctypes.c_double),
     ]
 
 
@@ -62,6 +83,7 @@ class gw_job_result(ctypes.Structure):
     _fields_ = [
         ("status", ctypes.c_int), ("iterations", ctypes.c_int), ("max_abs_dsigma", ctypes.c_double),
         ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_end", ctypes.c_double),
+        ("mu", ctypes.c_double),
     ]
 
 
@@ -116,6 +138,18 @@ def lib():
     L.gw_batch_sigma_eval.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i]
     L.gw_batch_autotune.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i)]
     L.gw_batch_synchronize.argtypes = [vp]
+    L.gw_density.argtypes = [vp, vp, vp]
+    L.gw_sigma_inf.argtypes = [vp, vp, vp]
+    L.gw_set_mu.argtypes = [vp, d]
+    L.gw_particle_number.argtypes = [vp, vp, ctypes.POINTER(d)]
+    L.gw_find_mu.argtypes = [vp, vp, vp, d, d, d, d, vp, ctypes.POINTER(d)]
+    L.gw_diis_create.argtypes = [ctypes.POINTER(vp), ctypes.c_longlong, i, vp]
+    L.gw_diis_destroy.argtypes = [vp]
+    L.gw_diis_push.argtypes = [vp, vp, vp]
+    L.gw_diis_extrapolate.argtypes = [vp, vp, ctypes.POINTER(d), ctypes.POINTER(i)]
+    L.gw_scgw_bytes.argtypes = [ctypes.POINTER(gw_config), ctypes.POINTER(gw_scgw_options)]
+    L.gw_scgw_bytes.restype = ctypes.c_size_t
+    L.gw_scgw.argtypes = [vp, vp, vp, vp, vp, ctypes.POINTER(gw_scgw_options), ctypes.POINTER(gw_scgw_result)]
     _lib = L
     return L
 
@@ -375,14 +409,16 @@ class gw_server:
         self._keep = {}
 
     def submit(self, cfg: gw_config, H, V, G0, Sigma_out=None, G_out=None, alpha=0.7, tol=1e-8,
-               itermax=20) -> int:
+               itermax=20, static_part=False, diis_size=0, diis_start=2, n_electrons=0.0, mu_lo=-5.0,
+               mu_hi=5.0, mu_tol=1e-10) -> int:
         nk = cfg.nk[0] * cfg.nk[1] * cfg.nk[2]
         nao, naux, ntau = cfg.nao, cfg.naux, cfg.ntau
         job = gw_job(cfg, _host(H, (nk, nao, nao), "H"), _host(V, (nk, nk, naux, nao, nao), "V"),
                      _host(G0, (nk, ntau, nao, nao), "G0"),
                      None if Sigma_out is None else _host(Sigma_out, (nk, ntau, nao, nao), "Sigma_out", True),
                      None if G_out is None else _host(G_out, (nk, ntau, nao, nao), "G_out", True),
-                     float(alpha), float(tol), int(itermax))
+                     float(alpha), float(tol), int(itermax), int(bool(static_part)), int(diis_size),
+                     int(diis_start), float(n_electrons), float(mu_lo), float(mu_hi), float(mu_tol))
         jid = ctypes.c_uint64()
         _check(lib().gw_submit(self._h, ctypes.byref(job), ctypes.byref(jid)))
         self._keep[jid.value] = (H, V, G0, Sigma_out, G_out)
@@ -397,7 +433,7 @@ class gw_server:
         if rc == GW_OK:
             self._keep.pop(job_id, None)
         return rc, {"status": r.status, "iterations": r.iterations, "max_abs_dsigma": r.max_abs_dsigma,
-                    "t_submit": r.t_submit, "t_start": r.t_start, "t_end": r.t_end}
+                    "t_submit": r.t_submit, "t_start": r.t_start, "t_end": r.t_end, "mu": r.mu}
 
     def destroy(self):
         if self._h is not None:
@@ -470,3 +506,99 @@ class gw_batch:
             self.destroy()
         except Exception:
             pass
+
+
+# ---- static part, chemical potential, DIIS (Eq. sigma_inf, Sec. 2.4, Sec. 5.3) -------------
+
+
+def gw_density(ctx: gw_ctx, G, gamma):
+    nk, nao = ctx.nk, ctx.nao
+    _check(lib().gw_density(ctx.handle, _ptr(G, (nk, ctx.ntau, nao, nao)), _ptr(gamma, (nk, nao, nao))))
+
+
+def gw_sigma_inf(ctx: gw_ctx, G, SigInf):
+    nk, nao = ctx.nk, ctx.nao
+    _check(lib().gw_sigma_inf(ctx.handle, _ptr(G, (nk, ctx.ntau, nao, nao)), _ptr(SigInf, (nk, nao, nao))))
+
+
+def gw_set_mu(ctx: gw_ctx, mu: float):
+    _check(lib().gw_set_mu(ctx.handle, float(mu)))
+    ctx.mu = float(mu)
+
+
+def gw_particle_number(ctx: gw_ctx, G) -> float:
+    n = ctypes.c_double()
+    _check(lib().gw_particle_number(ctx.handle, _ptr(G, (ctx.nk, ctx.ntau, ctx.nao, ctx.nao)), ctypes.byref(n)))
+    return n.value
+
+
+def gw_find_mu(ctx: gw_ctx, Heff, Sig, n_target, mu_lo, mu_hi, tol, G) -> float:
+    nk, nao = ctx.nk, ctx.nao
+    mu = ctypes.c_double()
+    _check(lib().gw_find_mu(ctx.handle, _ptr(Heff, (nk, nao, nao)), _ptr(Sig, (nk, ctx.ntau, nao, nao)),
+                            float(n_target), float(mu_lo), float(mu_hi), float(tol),
+                            _ptr(G, (nk, ctx.ntau, nao, nao)), ctypes.byref(mu)))
+    ctx.mu = mu.value
+    return mu.value
+
+
+class gw_diis:
+    """Owner of one gw_diis* (Pulay extrapolation of the self-energy)."""
+
+    def __init__(self, n_elem, max_vectors=5, stream=None):
+        import torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.max_vectors = int(max_vectors)
+        h = ctypes.c_void_p()
+        _check(lib().gw_diis_create(ctypes.byref(h), ctypes.c_longlong(int(n_elem)), self.max_vectors,
+                                    ctypes.c_void_p(self.stream.cuda_stream)))
+        self._h = h
+        self.n = int(n_elem)
+
+    def push(self, sigma_in, sigma_out):
+        _check(lib().gw_diis_push(self._h, _ptr(sigma_in), _ptr(sigma_out)))
+
+    def extrapolate(self, out):
+        c = (ctypes.c_double * self.max_vectors)()
+        m = ctypes.c_int()
+        _check(lib().gw_diis_extrapolate(self._h, _ptr(out), c, ctypes.byref(m)))
+        return list(c)[:m.value]
+
+    def destroy(self):
+        if self._h is not None:
+            lib().gw_diis_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def scgw_options(alpha=0.5, tol=1e-8, itermax=20, static_part=True, diis_size=0, diis_start=2, n_electrons=0.0,
+                 mu_lo=-5.0, mu_hi=5.0, mu_tol=1e-10) -> gw_scgw_options:
+    return gw_scgw_options(float(alpha), float(tol), int(itermax), int(bool(static_part)), int(diis_size),
+                           int(diis_start), float(n_electrons), float(mu_lo), float(mu_hi), float(mu_tol))
+
+
+def gw_scgw_bytes(cfg: gw_config, opt: gw_scgw_options) -> int:
+    return int(lib().gw_scgw_bytes(ctypes.byref(cfg), ctypes.byref(opt)))
+
+
+def gw_scgw(ctx: gw_ctx, H, G, Sigma=None, SigInf=None, opt: gw_scgw_options = None):
+    """Runs the loop (G in: G0, out: the last G). Returns (status, result dict); status is GW_OK or
+    GW_ENOTCONV, any other failure raises."""
+    s = ctx.shapes()
+    opt = opt if opt is not None else scgw_options()
+    r = gw_scgw_result()
+    rc = lib().gw_scgw(ctx.handle, _ptr(H, s["H"]), _ptr(G, s["G"]),
+                       None if Sigma is None else _ptr(Sigma, s["Sig"]),
+                       None if SigInf is None else _ptr(SigInf, (ctx.nk, ctx.nao, ctx.nao)),
+                       ctypes.byref(opt), ctypes.byref(r))
+    if rc != GW_ENOTCONV:
+        _check(rc)
+    if opt.n_electrons > 0:
+        ctx.mu = r.mu
+    return rc, {"iterations": r.iterations, "max_abs_dsigma": r.max_abs_dsigma, "mu": r.mu,
+                "n_electrons": r.n_electrons}
