@@ -278,8 +278,10 @@ int gw_particle_number(gw_ctx* ctx, const gw_c128* G_dev, double* n_host);
 /*
  * Sec. 2.4 step 3: the chemical potential in [mu_lo, mu_hi] whose Dyson solution
  * G = Dyson(Heff, Sigma, mu) (Heff = H + Sigma^inf) holds n_target electrons per cell,
- * by bisection to tol (the particle number grows with mu). Writes G_dev, *mu_host, and sets
- * the context's mu. GW_EINVAL if n_target lies outside [N(mu_lo), N(mu_hi)]. Synchronous.
+ * to tol (the particle number grows with mu): a bracketing search, regula falsi with the Illinois
+ * modification and a bisection step whenever two steps have not halved the bracket. Writes
+ * G_dev (the solution at the returned mu), *mu_host, and sets the context's mu. GW_EINVAL if
+ * n_target lies outside [N(mu_lo), N(mu_hi)]. Synchronous; every step is one gw_dyson_G.
  */
 int gw_find_mu(gw_ctx* ctx, const gw_c128* Heff_dev, const gw_c128* Sig_dev, double n_target, double mu_lo,
                double mu_hi, double tol, gw_c128* G_dev, double* mu_host);

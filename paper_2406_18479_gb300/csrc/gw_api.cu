@@ -526,7 +526,10 @@ int ctx_build(gw_ctx* c, const gw_config* cfg) {
     if ((rc = dev_alloc(c, &c->nonfinite, 1)) != GW_OK) break;
     if ((rc = dev_alloc(c, &c->gamma, (size_t)nk * c->nao2)) != GW_OK) break;
     if ((rc = dev_alloc(c, &c->rho, (size_t)c->naux)) != GW_OK) break;
-    if ((rc = dev_alloc(c, &c->xinf, (size_t)nk * c->pair)) != GW_OK) break;
+    // exchange partials of the fused kernel, or the per-k intermediate of the GEMM path (nao above its limit)
+    const size_t nxinf = c->nao <= kExchangeMaxNao ? (size_t)nk * nk * exchange_chunks(nk, c->naux) * c->nao2
+                                                   : (size_t)nk * c->pair;
+    if ((rc = dev_alloc(c, &c->xinf, nxinf)) != GW_OK) break;
     if ((rc = dev_alloc(c, &c->scal, (size_t)kDotBlocks + 8)) != GW_OK) break;
     {
       std::vector<double> w, tau(c->ntau);
@@ -747,6 +750,7 @@ int gw_sigma_inf(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* SigInf_dev) {
   // Hartree: (s / N_k) sum_Q V^{kk}_ij(Q) rho_Q
   GW_TRY(hartree_fp64(ctx->V, ctx->gamma, ctx->rho, S, nk, naux, nao, ctx->cfg.spin_factor / nk, ctx->stream));
   // exchange: -(1 / N_k) sum_{k'} sum_{Q b} X^{k'}_{Q i b} V^{k'k}_bj(Q), X^{k'}_{Q i b} = sum_a V^{kk'}_ia(Q) gamma^{k'}_ab
+  if (nao <= kExchangeMaxNao) return exchange_fp64(ctx->V, ctx->gamma, ctx->xinf, S, nk, naux, nao, -1.0 / nk, ctx->stream);
   for (int k = 0; k < nk; ++k) {
     ZGemm a;
     a.M = naux * nao;
@@ -823,22 +827,51 @@ int gw_find_mu(gw_ctx* ctx, const gw_c128* Heff_dev, const gw_c128* Sig_dev, dou
     GW_TRY(gw_dyson_G(ctx, Heff_dev, Sig_dev, G_dev));
     return gw_particle_number(ctx, G_dev, n);
   };
-  double n_lo = 0.0, n_hi = 0.0;
-  GW_TRY(number(mu_lo, &n_lo));
-  GW_TRY(number(mu_hi, &n_hi));
-  if (!(n_lo <= n_target && n_target <= n_hi))
-    return fail(GW_EINVAL, "gw_find_mu: target %.6g outside [N(mu_lo), N(mu_hi)] = [%.6g, %.6g]", n_target, n_lo,
-                n_hi);
-  for (int it = 0; it < 200 && mu_hi - mu_lo >= tol; ++it) {
-    const double mid = 0.5 * (mu_lo + mu_hi);
-    double n = 0.0;
-    GW_TRY(number(mid, &n));
-    if (n < n_target) mu_lo = mid;
-    else mu_hi = mid;
+  // f(mu) = N(mu) - n_target grows with mu. Regula falsi with the Illinois modification (the
+  // retained end's value is halved when the same end is kept twice), and a bisection step
+  // whenever two steps have not halved the bracket; stops once the bracket is below tol or f
+  // vanishes. G_dev holds the solution at the returned mu, the last point evaluated.
+  double f_lo = 0.0, f_hi = 0.0;
+  GW_TRY(number(mu_lo, &f_lo));
+  GW_TRY(number(mu_hi, &f_hi));
+  f_lo -= n_target;
+  f_hi -= n_target;
+  if (!(f_lo <= 0.0 && f_hi >= 0.0))
+    return fail(GW_EINVAL, "gw_find_mu: target %.6g outside [N(mu_lo), N(mu_hi)] = [%.6g, %.6g]", n_target,
+                f_lo + n_target, f_hi + n_target);
+  double mu = mu_hi;                   // G_dev holds the solution at mu_hi now
+  if (f_lo == 0.0) {
+    mu = mu_lo;
+    GW_TRY(number(mu, &f_lo));
+  } else if (f_hi != 0.0) {
+    int kept = 0;                        // -1: the low end was kept last, +1: the high end
+    double width_ref = mu_hi - mu_lo;
+    for (int it = 0; it < 200; ++it) {
+      double m = (mu_lo * f_hi - mu_hi * f_lo) / (f_hi - f_lo);
+      if (it % 2 == 1) {
+        if (mu_hi - mu_lo > 0.5 * width_ref) m = 0.5 * (mu_lo + mu_hi);
+        width_ref = mu_hi - mu_lo;
+      }
+      if (!(m > mu_lo && m < mu_hi)) m = 0.5 * (mu_lo + mu_hi);
+      double f = 0.0;
+      GW_TRY(number(m, &f));
+      f -= n_target;
+      mu = m;
+      if (f == 0.0) break;
+      if (f < 0.0) {
+        mu_lo = m;
+        f_lo = f;
+        if (kept == +1) f_hi *= 0.5;
+        kept = +1;
+      } else {
+        mu_hi = m;
+        f_hi = f;
+        if (kept == -1) f_lo *= 0.5;
+        kept = -1;
+      }
+      if (mu_hi - mu_lo < tol) break;
+    }
   }
-  const double mu = 0.5 * (mu_lo + mu_hi);
-  double n = 0.0;
-  GW_TRY(number(mu, &n));
   *mu_host = mu;
   return GW_OK;
 }

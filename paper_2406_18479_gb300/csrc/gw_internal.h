@@ -99,6 +99,12 @@ constexpr int kDotBlocks = 512;
 int density_fp64(const double2* G, const double* w, double2* gamma, int nk, int ntau, int nao, void* stream);
 int hartree_fp64(const double2* V, const double2* gamma, double2* rho, double2* out, int nk, int naux, int nao,
                  double scale, void* stream);
+//   exchange: out^k += scale sum_{k'Q b} (V^{kk'}(Q) gamma^{k'})_ib V^{k'k}_bj(Q), for nao <= kExchangeMaxNao,
+//             through part [nk][nk][exchange_chunks][nao][nao]
+constexpr int kExchangeMaxNao = 52;
+int exchange_chunks(int nk, int naux);
+int exchange_fp64(const double2* V, const double2* gamma, double2* part, double2* out, int nk, int naux, int nao,
+                  double scale, void* stream);
 int trace_fp64(const double2* gamma, int nk, int nao, double* out_dev, void* stream);
 int add_fp64(const double2* a, const double2* b, double2* c, long long n, void* stream);
 int dot_re_fp64(const double2* x, const double2* y, long long n, double* partial_dev, double* out_dev, void* stream);

@@ -6,6 +6,7 @@
 // shared memory, keeps that pipe busy without deeper register blocking.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <climits>
 
 #include "gw_internal.h"
@@ -535,6 +536,81 @@ __global__ void hartree_j_kernel(const double2* V, const double2* rho, double2* 
   }
 }
 
+// Exchange term of Eq. sigma_inf, fused per (k, k', chunk c of the auxiliary index):
+//   part[(k nk + k') qc + c]_ij = sum_{Q in c} sum_b X_ib(Q) V^{k'k}_bj(Q),
+//   X(Q) = V^{kk'}(Q) gamma^{k'},
+// with gamma^{k'}, V^{kk'}(Q), X(Q) and V^{k'k}(Q) staged in shared memory one Q at a time and
+// each thread holding up to kExMaxPerThread entries of the 'ij' block in registers.
+constexpr int kExThreads = 256;
+constexpr int kExMaxPerThread = 11;    // nao^2 <= 256 * 11: nao <= kExchangeMaxNao
+__global__ void __launch_bounds__(kExThreads) exchange_partial_kernel(const double2* __restrict__ V,
+                                                                      const double2* __restrict__ gamma,
+                                                                      double2* __restrict__ part, int nk, int naux,
+                                                                      int nao, int qc) {
+  extern __shared__ double2 ex_sm[];
+  const int n2 = nao * nao;
+  double2* g = ex_sm;
+  double2* v1 = g + n2;
+  double2* x = v1 + n2;
+  double2* v2 = x + n2;
+  const int c = blockIdx.x % qc, kp = (blockIdx.x / qc) % nk, k = blockIdx.x / (qc * nk);
+  const int q0 = (int)((long long)naux * c / qc), q1 = (int)((long long)naux * (c + 1) / qc);
+  const long long pair = (long long)naux * n2;
+  const double2* Va = V + ((long long)k * nk + kp) * pair;
+  const double2* Vb = V + ((long long)kp * nk + k) * pair;
+  for (int e = threadIdx.x; e < n2; e += kExThreads) g[e] = gamma[(long long)kp * n2 + e];
+  double2 acc[kExMaxPerThread];
+#pragma unroll
+  for (int t = 0; t < kExMaxPerThread; ++t) acc[t] = make_double2(0.0, 0.0);
+  for (int Q = q0; Q < q1; ++Q) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < n2; e += kExThreads) {
+      v1[e] = Va[(long long)Q * n2 + e];
+      v2[e] = Vb[(long long)Q * n2 + e];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n2; e += kExThreads) {
+      const int i = e / nao, b = e - i * nao;
+      double2 s = make_double2(0.0, 0.0);
+      for (int a = 0; a < nao; ++a) cmac(s, v1[i * nao + a], g[a * nao + b]);
+      x[e] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < kExMaxPerThread; ++t) {
+      const int e = threadIdx.x + t * kExThreads;
+      if (e < n2) {
+        const int i = e / nao, j = e - i * nao;
+        for (int b = 0; b < nao; ++b) cmac(acc[t], x[i * nao + b], v2[b * nao + j]);
+      }
+    }
+  }
+  double2* out = part + (long long)blockIdx.x * n2;
+#pragma unroll
+  for (int t = 0; t < kExMaxPerThread; ++t) {
+    const int e = threadIdx.x + t * kExThreads;
+    if (e < n2) out[e] = acc[t];
+  }
+}
+
+// out^k_ij += scale sum_{k', c} part[(k nk + k') qc + c]_ij, summed in that fixed order
+__global__ void exchange_reduce_kernel(const double2* __restrict__ part, double2* __restrict__ out, int nk, int n2,
+                                       int qc, double scale) {
+  const long long total = (long long)nk * n2;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long k = e / n2, r = e % n2;
+    const double2* p = part + k * nk * qc * n2 + r;
+    double2 s = make_double2(0.0, 0.0);
+    for (int u = 0; u < nk * qc; ++u) {
+      const double2 v = p[(long long)u * n2];
+      s.x += v.x;
+      s.y += v.y;
+    }
+    out[e].x += scale * s.x;
+    out[e].y += scale * s.y;
+  }
+}
+
 // *out = sum_k sum_i Re gamma^k_ii (one block)
 __global__ void __launch_bounds__(256) trace_kernel(const double2* gamma, int nk, int nao, double* out) {
   double acc = 0.0;
@@ -723,6 +799,35 @@ int hartree_fp64(const double2* V, const double2* gamma, double2* rho, double2* 
   prof_end(SLOT_STATIC_FP64, (cudaStream_t)stream, 16.0 * n * naux, 32.0 * n * naux);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "hartree launch: %s", cudaGetErrorString(e));
+}
+
+int exchange_chunks(int nk, int naux) {
+  // enough blocks for every SM several times over: 4 x 152 at least, when naux allows
+  const int want = (608 + nk * nk - 1) / (nk * nk);
+  return std::max(1, std::min(want, naux));
+}
+
+int exchange_fp64(const double2* V, const double2* gamma, double2* part, double2* out, int nk, int naux, int nao,
+                  double scale, void* stream) {
+  if (nao > kExchangeMaxNao) return fail(GW_EINVAL, "exchange_fp64: nao=%d above %d", nao, kExchangeMaxNao);
+  static const bool attr = [] {
+    const bool ok = cudaFuncSetAttribute(exchange_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         4 * kExchangeMaxNao * kExchangeMaxNao * (int)sizeof(double2)) == cudaSuccess;
+    cudaGetLastError();
+    return ok;
+  }();
+  if (!attr) return fail(GW_ECUDA, "exchange_fp64: shared memory attribute refused");
+  const int qc = exchange_chunks(nk, naux), n2 = nao * nao;
+  const size_t smem = 4 * (size_t)n2 * sizeof(double2);
+  prof_begin(SLOT_STATIC_FP64, (cudaStream_t)stream);
+  exchange_partial_kernel<<<nk * nk * qc, kExThreads, smem, (cudaStream_t)stream>>>(V, gamma, part, nk, naux, nao,
+                                                                                     qc);
+  exchange_reduce_kernel<<<grid_for((long long)nk * n2, 256), 256, 0, (cudaStream_t)stream>>>(part, out, nk, n2, qc,
+                                                                                             scale);
+  prof_end(SLOT_STATIC_FP64, (cudaStream_t)stream, 16.0 * (double)nk * nk * naux * n2 * nao,
+           32.0 * (double)nk * nk * naux * n2);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "exchange launch: %s", cudaGetErrorString(e));
 }
 
 int trace_fp64(const double2* gamma, int nk, int nao, double* out_dev, void* stream) {

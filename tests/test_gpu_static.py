@@ -52,6 +52,7 @@ CASES = [
     ((2, 1, 3), 2, 5, 4, 6.0, "fp64"),
     ((1, 1, 1), 33, 65, 8, 30.0, "fp64"),
     ((3, 3, 1), 7, 20, 12, 20.0, "bf16x3"),
+    ((2, 1, 1), 53, 3, 2, 5.0, "fp64"),          # above the fused exchange kernel's limit: GEMM path
 ]
 
 
