@@ -269,8 +269,20 @@ def diis_extrapolate(outputs, inputs):
     return sum(ci * o for ci, o in zip(c, outputs)), c
 
 
+def commutator_residual(H, sig_inf, Sig, G, beta):
+    """Error vector of the commutator variant of DIIS (Sec. 5.3, after Pulay's SCF commutator
+    F D S - S D F with S = I): e^k(i w_n) = [G^k(i w_n), H^k + Sigma^inf,k + Sigma~^k(i w_n)],
+    with G(i w) = F^f G(tau) and Sigma~(i w) = F^f Sigma~(tau). A G that solves the Dyson
+    equation with this very (Sigma^inf, Sigma~) commutes with it, so e vanishes at self-consistency."""
+    nk, ntau, nao, _ = G.shape
+    _, Ff, _ = grids.transform_matrices(ntau, beta, 1)
+    Gw = to_matsubara(G, Ff)
+    Fw = to_matsubara(Sig, Ff) + (H + (0 if sig_inf is None else sig_inf))[:, None]
+    return Gw @ Fw - Fw @ Gw
+
+
 def scgw_full(H, V, G0, nk3, beta, mu, spin_factor=2.0, alpha=0.5, tol=1e-6, itermax=10, static=True,
-              n_electrons=None, mu_lo=-5.0, mu_hi=5.0, mu_tol=1e-10, diis_size=0, diis_start=2):
+              n_electrons=None, mu_lo=-5.0, mu_hi=5.0, mu_tol=1e-10, diis_size=0, diis_start=2, diis_kind="diis"):
     """The self-consistency loop of Sec. 2.4 with its four steps per iteration n:
 
       (1) the static part Sigma^inf[G_{n-1}] (Eq. sigma_inf; left out when static is False) and
@@ -278,7 +290,9 @@ def scgw_full(H, V, G0, nk3, beta, mu, spin_factor=2.0, alpha=0.5, tol=1e-6, ite
       (2) acceleration (Sec. 5.3): Sigma_1 = F_1; afterwards iteration mixing
           Sigma_n = alpha F_n + (1 - alpha) Sigma_{n-1}, or, with diis_size > 0, Pulay's
           extrapolation over the newest diis_size pairs (Sigma_{i-1}, F_i) from iteration
-          diis_start on (the iterations before it mix and fill the subspace);
+          diis_start on (the iterations before it mix and fill the subspace); the residual of
+          a pair is F_i - Sigma_{i-1}, or with diis_kind "cdiis" the commutator
+          [G_{i-1}(i w), H + F_i(i w)] (commutator_residual);
       (3) with n_electrons given, mu such that the Dyson solution holds n_electrons per cell;
       (4) G_n = Dyson(H + Sigma^inf_n, Sigma~_n, mu).
 
@@ -288,7 +302,7 @@ def scgw_full(H, V, G0, nk3, beta, mu, spin_factor=2.0, alpha=0.5, tol=1e-6, ite
     nk, ntau, nao, _ = G0.shape
     G = G0
     prev = None                         # (SigInf, Sig) of the previous iteration
-    ins, outs = [], []
+    ins, outs = [], []                  # residuals and outputs of the DIIS subspace
     hist = []
     it = 0
     for it in range(1, itermax + 1):
@@ -299,11 +313,16 @@ def scgw_full(H, V, G0, nk3, beta, mu, spin_factor=2.0, alpha=0.5, tol=1e-6, ite
             cur = out
         else:
             if diis_size > 0:
-                ins.append(prev)
+                if diis_kind == "cdiis":
+                    ins.append(commutator_residual(H, out[:nk * nao * nao].reshape(nk, nao, nao),
+                                                   out[nk * nao * nao:].reshape(G0.shape), G, beta).ravel())
+                else:
+                    ins.append(out - prev)
                 outs.append(out)
                 ins, outs = ins[-diis_size:], outs[-diis_size:]
             if diis_size > 0 and it >= diis_start:
-                cur, _ = diis_extrapolate(outs, ins)
+                c = diis_coefficients(ins)
+                cur = sum(ci * o for ci, o in zip(c, outs))
             else:
                 cur = mix(out, prev, alpha)
             hist.append(float(np.max(np.abs(cur - prev))))

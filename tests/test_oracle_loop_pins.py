@@ -139,3 +139,39 @@ def test_full_loop_fixed_point_does_not_depend_on_the_acceleration():
     for key in ("Sig", "SigInf", "G"):
         assert np.abs(a[key] - b[key]).max() < 1e-8
     assert b["iterations"] < a["iterations"]
+
+
+def test_commutator_residual_vanishes_for_a_dyson_solution():
+    """G = Dyson(H + Sigma^inf, Sigma~) commutes with H + Sigma^inf + Sigma~(i w) on every sample
+    (ntau even: the fermionic sample set is square, F^f B^f = I); a G from another self-energy
+    does not, and the residual is linear in the static shift's commutator."""
+    w = I.Workload("m", (2, 1, 1), 4, 6, 16, 16, 5.0, 0.0, 4.0, 13, solid=True)
+    h, v, g = I.make_inputs(w)
+    rng = np.random.default_rng(1)
+    sig = 0.05 * (rng.standard_normal(g.shape) + 1j * rng.standard_normal(g.shape))
+    sig = 0.5 * (sig + sig.conj().swapaxes(-1, -2))
+    sinf = O.sigma_inf(v, O.density_matrix(g, w.beta), w.nk3, 2.0)
+    G = O.dyson_G(h + sinf, sig, 0.2, w.beta)
+    e = O.commutator_residual(h, sinf, sig, G, w.beta)
+    assert np.abs(e).max() < 1e-12
+    e_other = O.commutator_residual(h, None, sig, G, w.beta)      # drop the static part
+    assert np.abs(e_other).max() > 1e-3
+    # [G, X + D] - [G, X] = [G, D] for a static D: here D = -Sigma^inf
+    _, Ff, _ = O.grids.transform_matrices(w.ntau, w.beta, 1)
+    Gw = np.einsum("nt,ktij->knij", Ff, G)
+    D = -sinf[:, None]
+    assert np.abs((e_other - e) - (Gw @ D - D @ Gw)).max() < 1e-12
+
+
+def test_cdiis_loop_reaches_the_same_fixed_point():
+    w, h, v, g = loop_case()
+    kw = dict(tol=1e-10, itermax=80, n_electrons=3.0, mu_tol=1e-13)
+    a = O.scgw_full(h, v, g, w.nk3, w.beta, 0.0, alpha=0.5, **kw)
+    b = O.scgw_full(h, v, g, w.nk3, w.beta, 0.0, alpha=0.5, diis_size=5, diis_start=2, diis_kind="cdiis", **kw)
+    assert b["hist"][-1] < 1e-10
+    assert abs(a["mu"] - b["mu"]) < 1e-8
+    for key in ("Sig", "SigInf", "G"):
+        assert np.abs(a[key] - b[key]).max() < 1e-8
+    assert b["iterations"] < a["iterations"]
+    e = O.commutator_residual(h, b["SigInf"], b["Sig"], b["G"], w.beta)
+    assert np.abs(e).max() < 1e-8
