@@ -269,6 +269,16 @@ int gw_density(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* gamma_dev);
  */
 int gw_sigma_inf(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* SigInf_dev);
 
+/*
+ * Error vector of the commutator variant of DIIS (Sec. 5.3; Pulay's SCF commutator with an
+ * orthonormal basis): e^k(i w_n) = [G^k(i w_n), H^k + Sigma^inf,k + Sigma~^k(i w_n)] on the
+ * fermionic samples, G(i w) = F^f G(tau), Sigma~(i w) = F^f Sigma~(tau). It vanishes when G
+ * solves the Dyson equation with this (Sigma^inf, Sigma~). SigInf_dev may be NULL (zero).
+ * Writes e_dev [nk][nw_f][nao][nao] (nw_f from gw_grid_build, statistics 1).
+ */
+int gw_commutator_residual(gw_ctx* ctx, const gw_c128* H_dev, const gw_c128* SigInf_dev, const gw_c128* Sig_dev,
+                           const gw_c128* G_dev, gw_c128* e_dev);
+
 /* Sets the chemical potential used by gw_dyson_G. */
 int gw_set_mu(gw_ctx* ctx, double mu);
 
@@ -290,14 +300,18 @@ int gw_find_mu(gw_ctx* ctx, const gw_c128* Heff_dev, const gw_c128* Sig_dev, dou
  * Convergence acceleration by direct inversion in the iterative subspace (Sec. 5.3), the
  * Pulay form: push the self-energy Sigma_i an iteration's G was built from and the one
  * computed from that G, Sigma[G_i]; extrapolate gives sum_i c_i Sigma[G_i] with c minimising
- * |sum_i c_i (Sigma[G_i] - Sigma_i)|^2 subject to sum_i c_i = 1 (real c, inner products
- * Re <r_i, r_j> over all n_elem complex entries). At most max_vectors (1..16) are kept, the
- * oldest leaves first. Vectors are copied; work runs on cuda_stream (push synchronizes it).
+ * |sum_i c_i r_i|^2 subject to sum_i c_i = 1, r_i = Sigma[G_i] - Sigma_i (real c, inner
+ * products Re <r_i, r_j> over all complex entries). With n_residual > 0 the residuals are the
+ * caller's, n_residual entries each, given to gw_diis_push_residual (the commutator variant
+ * passes gw_commutator_residual); n_residual = 0 takes r_i = Sigma[G_i] - Sigma_i through
+ * gw_diis_push. At most max_vectors (1..16) are kept, the oldest leaves first. Vectors are
+ * copied; work runs on cuda_stream (a push synchronizes it).
  */
 typedef struct gw_diis gw_diis;
-int gw_diis_create(gw_diis** out, long long n_elem, int max_vectors, void* cuda_stream);
+int gw_diis_create(gw_diis** out, long long n_elem, long long n_residual, int max_vectors, void* cuda_stream);
 int gw_diis_destroy(gw_diis* diis);
 int gw_diis_push(gw_diis* diis, const gw_c128* sigma_in_dev, const gw_c128* sigma_out_dev);
+int gw_diis_push_residual(gw_diis* diis, const gw_c128* sigma_out_dev, const gw_c128* residual_dev);
 /* coeffs_host (optional, max_vectors doubles) and *nvec_host (optional) receive c, oldest first. */
 int gw_diis_extrapolate(gw_diis* diis, gw_c128* out_dev, double* coeffs_host, int* nvec_host);
 
@@ -308,7 +322,8 @@ int gw_diis_extrapolate(gw_diis* diis, gw_c128* out_dev, double* coeffs_host, in
  *   (2) accelerates (Sec. 5.3): Sigma_1 = F_1; then Sigma_n = alpha F_n + (1 - alpha) Sigma_{n-1},
  *       or with diis_size > 0 Pulay's extrapolation over the newest diis_size pairs
  *       (Sigma_{i-1}, F_i) from iteration diis_start on (earlier iterations mix and fill the
- *       subspace; gw_diis_*);
+ *       subspace; gw_diis_*), with the residual F_i - Sigma_{i-1} or the commutator of G_{i-1}
+ *       and F_i (diis_kind);
  *   (3) with n_electrons > 0, finds mu in [mu_lo, mu_hi] (to mu_tol) whose Dyson solution holds
  *       n_electrons per cell (gw_find_mu); otherwise keeps the context's mu;
  *   (4) G_n = Dyson(H + Sigma^inf_n, Sigma~_n, mu) (gw_dyson_G).
@@ -327,6 +342,8 @@ typedef struct {
   int diis_start;             /* first extrapolating iteration, >= 2 */
   double n_electrons;         /* > 0: search mu each iteration for this many electrons per cell */
   double mu_lo, mu_hi, mu_tol;   /* bracket and tolerance of that search */
+  int diis_kind;              /* 0: residual F_i - Sigma_{i-1}; 1: commutator (gw_commutator_residual
+                                 of G_{i-1} and F_i) */
 } gw_scgw_options;
 
 typedef struct {
@@ -413,6 +430,7 @@ typedef struct {
   int diis_start;
   double n_electrons;
   double mu_lo, mu_hi, mu_tol;
+  int diis_kind;
 } gw_job;
 
 typedef struct {

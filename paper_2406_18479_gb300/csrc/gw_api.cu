@@ -146,6 +146,8 @@ struct gw_ctx {
   double2* gamma = nullptr;               // density matrix, [nk][nao][nao]
   double2* rho = nullptr;                 // Hartree density in the auxiliary basis, [naux]
   double2* xinf = nullptr;                // exchange intermediate of one k, [nk][naux][nao][nao]
+  double2* gw_w = nullptr;                // G on the fermionic samples, [nk][nwf][nao][nao]
+  double2* heff = nullptr;                // H + Sigma^inf, [nk][nao][nao]
   double* scal = nullptr;                 // reduction partials and results
   Prof prof;
 };
@@ -199,7 +201,7 @@ void free_ctx(gw_ctx* c) {
   mixed_destroy(c->mixed);
   void* ptrs[] = {c->Fb, c->Bb, c->Ff, c->Bf, c->wf, c->tabs, c->mq_dev, c->wlist, c->work, c->P0t, c->Pw,
                   c->Pt, c->dyson_ws, c->status, c->maxdiff, c->nonfinite, c->wbeta, c->gamma, c->rho,
-                  c->xinf, c->scal};
+                  c->xinf, c->scal, c->gw_w, c->heff};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -531,6 +533,8 @@ int ctx_build(gw_ctx* c, const gw_config* cfg) {
                                                    : (size_t)nk * c->pair;
     if ((rc = dev_alloc(c, &c->xinf, nxinf)) != GW_OK) break;
     if ((rc = dev_alloc(c, &c->scal, (size_t)kDotBlocks + 8)) != GW_OK) break;
+    if ((rc = dev_alloc(c, &c->gw_w, (size_t)nk * c->nwf * c->nao2)) != GW_OK) break;
+    if ((rc = dev_alloc(c, &c->heff, (size_t)nk * c->nao2)) != GW_OK) break;
     {
       std::vector<double> w, tau(c->ntau);
       for (int j = 0; j < c->ntau; ++j) {
@@ -558,7 +562,7 @@ int ctx_build(gw_ctx* c, const gw_config* cfg) {
 
 }  // namespace
 
-CtxInfo ctx_info(const gw_ctx* c) { return CtxInfo{c->stream, c->nk, c->ntau, c->nao, c->cfg.mu}; }
+CtxInfo ctx_info(const gw_ctx* c) { return CtxInfo{c->stream, c->nk, c->ntau, c->nao, c->nwf, c->cfg.mu}; }
 
 size_t job_device_bytes(const gw_config* cfg) {
   if (!config_ok(cfg)) return 0;
@@ -794,6 +798,45 @@ int gw_sigma_inf(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* SigInf_dev) {
       b.slot = SLOT_STATIC_FP64;
       GW_TRY(zgemm_fp64(b, ctx->stream));
     }
+  }
+  return GW_OK;
+}
+
+int gw_commutator_residual(gw_ctx* ctx, const gw_c128* H_dev, const gw_c128* SigInf_dev, const gw_c128* Sig_dev,
+                           const gw_c128* G_dev, gw_c128* e_dev) {
+  ProfScope _ps(ctx ? &ctx->prof : nullptr);
+  if (!ctx || !H_dev || !Sig_dev || !G_dev || !e_dev) return fail(GW_EINVAL, "gw_commutator_residual: null argument");
+  const int nk = ctx->nk, nao = ctx->nao, nw = ctx->nwf;
+  const double2* H = reinterpret_cast<const double2*>(H_dev);
+  if (SigInf_dev) {
+    GW_TRY(add_fp64(H, reinterpret_cast<const double2*>(SigInf_dev), ctx->heff, (long long)nk * ctx->nao2,
+                    ctx->stream));
+    H = ctx->heff;
+  }
+  double2* Fw = ctx->dyson_ws;
+  GW_TRY(transform(ctx, 1, true, reinterpret_cast<const double2*>(G_dev), ctx->gw_w, nk, ctx->nao2));
+  GW_TRY(transform(ctx, 1, true, reinterpret_cast<const double2*>(Sig_dev), Fw, nk, ctx->nao2));
+  // Fw <- (i w_n + mu) I - H - Sigma~(i w_n); the multiple of I commutes exactly, so
+  // e = Fw G - G Fw = [G, H + Sigma~]
+  GW_TRY(build_g_dyson_fp64(Fw, H, ctx->wf, ctx->cfg.mu, nk, nw, nao, ctx->stream));
+  for (int pass = 0; pass < 2; ++pass) {
+    ZGemm g;
+    g.M = g.N = g.K = nao;
+    g.nbatch = nk * nw;
+    g.A = pass == 0 ? Fw : ctx->gw_w;
+    g.B = pass == 0 ? ctx->gw_w : Fw;
+    g.C = reinterpret_cast<double2*>(e_dev);
+    g.ba.bs_in = g.bb.bs_in = g.bc.bs_in = ctx->nao2;
+    g.va.rs_in = nao;                  // A(m, k) = X[m][k]
+    g.va.ks_in = 1;
+    g.vb.rs_in = 1;                    // B(n, k) = Y[k][n]
+    g.vb.ks_in = nao;
+    g.vc.rs_in = nao;
+    g.vc.ks_in = 1;
+    g.alpha = pass == 0 ? 1.0 : -1.0;
+    g.accumulate = pass;
+    g.slot = SLOT_STATIC_FP64;
+    GW_TRY(zgemm_fp64(g, ctx->stream));
   }
   return GW_OK;
 }

@@ -1,7 +1,8 @@
 // Pulay's direct inversion in the iterative subspace for the self-energy (Sec. 5.3).
 //
-// Each push stores the output Sigma[G_i] of an iteration and its residual
-// r_i = Sigma[G_i] - Sigma_i (Sigma_i: the self-energy G_i was built from), and
+// Each push stores the output Sigma[G_i] of an iteration and its residual, either
+// r_i = Sigma[G_i] - Sigma_i (Sigma_i: the self-energy G_i was built from) or one the caller
+// computed (the commutator variant passes [G_i(i w), H + Sigma[G_i](i w)]), and
 // extends the matrix B_ij = Re <r_i, r_j> by one row from device reductions in a
 // fixed order. Extrapolation solves the bordered system for the coefficients c
 // minimising |sum_i c_i r_i|^2 with sum_i c_i = 1 (partial pivoting, on the host)
@@ -18,7 +19,7 @@ using namespace gwi;
 
 struct gw_diis {
   cudaStream_t stream = nullptr;
-  long long n = 0;
+  long long n = 0, nres = 0;     // elements of a self-energy vector and of a residual
   int max_vec = 0;
   std::vector<double2*> f, r;     // slots; order[] lists the live ones, oldest first
   std::vector<int> order;
@@ -60,14 +61,52 @@ int solve_bordered(const std::vector<double>& Bsub, int m, std::vector<double>& 
 
 }  // namespace
 
+namespace {
+
+// Takes the next slot (the oldest leaves when the subspace is full), stores the output there
+// and has fill(r) write the residual; then adds its row of B.
+template <class Fill>
+int push_common(gw_diis* d, const gw_c128* sigma_out_dev, Fill fill) {
+  int slot;
+  if ((int)d->order.size() < d->max_vec) {
+    std::vector<bool> used(d->max_vec, false);
+    for (int s : d->order) used[s] = true;
+    slot = 0;
+    while (used[slot]) ++slot;
+  } else {
+    slot = d->order.front();
+    d->order.erase(d->order.begin());
+  }
+  const double2* fo = reinterpret_cast<const double2*>(sigma_out_dev);
+  if (cudaMemcpyAsync(d->f[slot], fo, d->n * sizeof(double2), cudaMemcpyDeviceToDevice, d->stream) != cudaSuccess)
+    return fail(GW_ECUDA, "gw_diis_push: copy");
+  const int rc = fill(d->r[slot]);
+  if (rc != GW_OK) return rc;
+  d->order.push_back(slot);
+  for (int j : d->order) {
+    const int r2 = dot_re_fp64(d->r[slot], d->r[j], d->nres, d->scal, d->scal + kDotBlocks, d->stream);
+    if (r2 != GW_OK) return r2;
+    double v = 0.0;
+    if (cudaMemcpyAsync(&v, d->scal + kDotBlocks, sizeof(double), cudaMemcpyDeviceToHost, d->stream) != cudaSuccess ||
+        cudaStreamSynchronize(d->stream) != cudaSuccess)
+      return fail(GW_ECUDA, "gw_diis_push: reduction");
+    d->B[(size_t)slot * d->max_vec + j] = d->B[(size_t)j * d->max_vec + slot] = v;
+  }
+  return GW_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
-int gw_diis_create(gw_diis** out, long long n_elem, int max_vectors, void* cuda_stream) {
-  if (!out || n_elem < 1 || max_vectors < 1 || max_vectors > 16) return fail(GW_EINVAL, "gw_diis_create: bad arguments");
+int gw_diis_create(gw_diis** out, long long n_elem, long long n_residual, int max_vectors, void* cuda_stream) {
+  if (!out || n_elem < 1 || n_residual < 0 || max_vectors < 1 || max_vectors > 16)
+    return fail(GW_EINVAL, "gw_diis_create: bad arguments");
   *out = nullptr;
   gw_diis* d = new gw_diis();
   d->stream = (cudaStream_t)cuda_stream;
   d->n = n_elem;
+  d->nres = n_residual > 0 ? n_residual : n_elem;
   d->max_vec = max_vectors;
   d->f.assign(max_vectors, nullptr);
   d->r.assign(max_vectors, nullptr);
@@ -75,7 +114,7 @@ int gw_diis_create(gw_diis** out, long long n_elem, int max_vectors, void* cuda_
   bool ok = cudaMalloc(reinterpret_cast<void**>(&d->scal), (kDotBlocks + 1) * sizeof(double)) == cudaSuccess;
   for (int i = 0; i < max_vectors && ok; ++i)
     ok = cudaMalloc(reinterpret_cast<void**>(&d->f[i]), n_elem * sizeof(double2)) == cudaSuccess &&
-         cudaMalloc(reinterpret_cast<void**>(&d->r[i]), n_elem * sizeof(double2)) == cudaSuccess;
+         cudaMalloc(reinterpret_cast<void**>(&d->r[i]), d->nres * sizeof(double2)) == cudaSuccess;
   if (!ok) {
     gw_diis_destroy(d);
     return fail(GW_ENOMEM, "gw_diis_create: device allocation failed");
@@ -96,37 +135,26 @@ int gw_diis_destroy(gw_diis* d) {
   return GW_OK;
 }
 
+
 int gw_diis_push(gw_diis* d, const gw_c128* sigma_in_dev, const gw_c128* sigma_out_dev) {
   if (!d || !sigma_in_dev || !sigma_out_dev) return fail(GW_EINVAL, "gw_diis_push: null argument");
-  int slot;
-  if ((int)d->order.size() < d->max_vec) {
-    std::vector<bool> used(d->max_vec, false);
-    for (int s : d->order) used[s] = true;
-    slot = 0;
-    while (used[slot]) ++slot;
-  } else {
-    slot = d->order.front();
-    d->order.erase(d->order.begin());
-  }
-  const double2* x = reinterpret_cast<const double2*>(sigma_in_dev);
-  const double2* fo = reinterpret_cast<const double2*>(sigma_out_dev);
-  if (cudaMemcpyAsync(d->f[slot], fo, d->n * sizeof(double2), cudaMemcpyDeviceToDevice, d->stream) != cudaSuccess)
-    return fail(GW_ECUDA, "gw_diis_push: copy");
-  const double2* vv[2] = {fo, x};
-  const double cc[2] = {1.0, -1.0};
-  const int rc = lincomb_fp64(vv, cc, 2, d->r[slot], d->n, d->stream);
-  if (rc != GW_OK) return rc;
-  d->order.push_back(slot);
-  for (int j : d->order) {
-    const int r2 = dot_re_fp64(d->r[slot], d->r[j], d->n, d->scal, d->scal + kDotBlocks, d->stream);
-    if (r2 != GW_OK) return r2;
-    double v = 0.0;
-    if (cudaMemcpyAsync(&v, d->scal + kDotBlocks, sizeof(double), cudaMemcpyDeviceToHost, d->stream) != cudaSuccess ||
-        cudaStreamSynchronize(d->stream) != cudaSuccess)
-      return fail(GW_ECUDA, "gw_diis_push: reduction");
-    d->B[(size_t)slot * d->max_vec + j] = d->B[(size_t)j * d->max_vec + slot] = v;
-  }
-  return GW_OK;
+  if (d->nres != d->n) return fail(GW_EINVAL, "gw_diis_push: this subspace takes explicit residuals");
+  const double2* vv[2] = {reinterpret_cast<const double2*>(sigma_out_dev),
+                          reinterpret_cast<const double2*>(sigma_in_dev)};
+  return push_common(d, sigma_out_dev, [&](double2* r) {
+    const double cc[2] = {1.0, -1.0};
+    return lincomb_fp64(vv, cc, 2, r, d->n, d->stream);
+  });
+}
+
+int gw_diis_push_residual(gw_diis* d, const gw_c128* sigma_out_dev, const gw_c128* residual_dev) {
+  if (!d || !sigma_out_dev || !residual_dev) return fail(GW_EINVAL, "gw_diis_push_residual: null argument");
+  return push_common(d, sigma_out_dev, [&](double2* r) {
+    return cudaMemcpyAsync(r, residual_dev, d->nres * sizeof(double2), cudaMemcpyDeviceToDevice, d->stream) ==
+                   cudaSuccess
+               ? GW_OK
+               : fail(GW_ECUDA, "gw_diis_push_residual: copy");
+  });
 }
 
 int gw_diis_extrapolate(gw_diis* d, gw_c128* out_dev, double* coeffs_host, int* nvec_host) {

@@ -113,7 +113,7 @@ int lincomb_fp64(const double2* const* v, const double* c, int m, double2* out, 
 // sizes, stream and mu of a context (for host code outside the file that defines gw_ctx)
 struct CtxInfo {
   void* stream;
-  int nk, ntau, nao;
+  int nk, ntau, nao, nwf;
   double mu;
 };
 CtxInfo ctx_info(const gw_ctx* ctx);

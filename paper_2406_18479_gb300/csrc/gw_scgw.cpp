@@ -1,5 +1,6 @@
 // The self-consistency loop of Sec. 2.4 on one context: static and dynamic self-energy,
-// acceleration (iteration mixing or Pulay's DIIS, Sec. 5.3), the chemical-potential search and
+// acceleration (iteration mixing, or DIIS with the difference or the commutator residual,
+// Sec. 5.3), the chemical-potential search and
 // the Dyson update, until max |Sigma_n - Sigma_{n-1}| < tol.
 //
 // The pair (Sigma^inf, Sigma~) lives in one buffer [nk][nao][nao] + [nk][ntau][nao][nao], so
@@ -20,7 +21,14 @@ size_t scgw_device_bytes(const gw_config* cfg, const gw_scgw_options* opt) {
   const size_t nall = nk * nao2 * (1 + (size_t)cfg->ntau);
   // Sigma_{n-1}, F_n, H + Sigma^inf, two flags
   size_t b = sizeof(gw_c128) * (2 * nall + nk * nao2) + 256;
-  if (opt && opt->diis_size > 0) b += sizeof(gw_c128) * 2 * (size_t)opt->diis_size * nall + (kDotBlocks + 1) * sizeof(double);
+  if (opt && opt->diis_size > 0) {
+    // the subspace: outputs and residuals; the commutator variant's residuals live on the
+    // fermionic samples, plus one buffer to compute them in
+    const bool comm = opt->diis_kind == 1;
+    const size_t nres = comm ? nk * (size_t)sample_count(cfg->ntau, 1) * nao2 : nall;
+    b += sizeof(gw_c128) * ((size_t)opt->diis_size * (nall + nres) + (comm ? nres : 0)) +
+         (kDotBlocks + 1) * sizeof(double);
+  }
   return b;
 }
 
@@ -36,7 +44,7 @@ int gw_scgw(gw_ctx* ctx, const gw_c128* H_dev, gw_c128* G_dev, gw_c128* Sigma_de
             const gw_scgw_options* o, gw_scgw_result* res) {
   if (!ctx || !H_dev || !G_dev || !o || !res) return fail(GW_EINVAL, "gw_scgw: null argument");
   if (!(o->alpha > 0.0 && o->alpha < 2.0) || !(o->tol >= 0.0) || o->itermax < 1 || o->diis_size < 0 ||
-      o->diis_size > 16 || (o->diis_size > 0 && o->diis_start < 2) ||
+      o->diis_size > 16 || (o->diis_size > 0 && o->diis_start < 2) || o->diis_kind < 0 || o->diis_kind > 1 ||
       (o->n_electrons > 0.0 && !(o->mu_lo < o->mu_hi && o->mu_tol > 0.0)))
     return fail(GW_EINVAL, "gw_scgw: options out of range");
   const CtxInfo ci = ctx_info(ctx);
@@ -45,17 +53,20 @@ int gw_scgw(gw_ctx* ctx, const gw_c128* H_dev, gw_c128* G_dev, gw_c128* Sigma_de
   const long long off = o->static_part ? 0 : nst;   // the vector starts at Sigma^inf only when it is used
   const long long nvec = nall - off;
   const size_t cb = sizeof(double2);
-  double2 *S = nullptr, *F = nullptr, *Heff = nullptr;
+  const bool comm = o->diis_size > 0 && o->diis_kind == 1;
+  const long long nres = comm ? (long long)ci.nk * ci.nwf * ci.nao * ci.nao : 0;
+  double2 *S = nullptr, *F = nullptr, *Heff = nullptr, *E = nullptr;
   void* flags = nullptr;
   gw_diis* diis = nullptr;
   auto cleanup = [&]() {
     if (diis) gw_diis_destroy(diis);
     cudaStreamSynchronize(st);
-    for (void* p : {(void*)S, (void*)F, (void*)Heff, flags})
+    for (void* p : {(void*)S, (void*)F, (void*)Heff, (void*)E, flags})
       if (p) cudaFree(p);
   };
   if (cudaMalloc((void**)&S, nall * cb) != cudaSuccess || cudaMalloc((void**)&F, nall * cb) != cudaSuccess ||
-      cudaMalloc((void**)&Heff, nst * cb) != cudaSuccess || cudaMalloc(&flags, 16) != cudaSuccess) {
+      cudaMalloc((void**)&Heff, nst * cb) != cudaSuccess || cudaMalloc(&flags, 16) != cudaSuccess ||
+      (comm && cudaMalloc((void**)&E, nres * cb) != cudaSuccess)) {
     cleanup();
     return fail(GW_ENOMEM, "gw_scgw: device allocation failed");
   }
@@ -66,7 +77,7 @@ int gw_scgw(gw_ctx* ctx, const gw_c128* H_dev, gw_c128* G_dev, gw_c128* Sigma_de
   int it = 1;
   bool converged = false;
   do {
-    if (o->diis_size > 0 && (rc = gw_diis_create(&diis, nvec, o->diis_size, st)) != GW_OK) break;
+    if (o->diis_size > 0 && (rc = gw_diis_create(&diis, nvec, nres, o->diis_size, st)) != GW_OK) break;
     if (!o->static_part) {
       cudaMemsetAsync(S, 0, nst * cb, st);
       cudaMemsetAsync(F, 0, nst * cb, st);
@@ -83,15 +94,23 @@ int gw_scgw(gw_ctx* ctx, const gw_c128* H_dev, gw_c128* G_dev, gw_c128* Sigma_de
         }
       } else {
         double alpha = o->alpha;
-        if (diis) {
+        if (comm) {
+          // residual of G_{n-1} (still in G_dev) against its own output F_n
+          if ((rc = gw_commutator_residual(ctx, H_dev, o->static_part ? reinterpret_cast<gw_c128*>(F) : nullptr,
+                                           reinterpret_cast<gw_c128*>(F + nst), G_dev,
+                                           reinterpret_cast<gw_c128*>(E))) != GW_OK ||
+              (rc = gw_diis_push_residual(diis, reinterpret_cast<gw_c128*>(F + off), reinterpret_cast<gw_c128*>(E))) !=
+                  GW_OK)
+            break;
+        } else if (diis) {
           if ((rc = gw_diis_push(diis, reinterpret_cast<gw_c128*>(S + off), reinterpret_cast<gw_c128*>(F + off))) !=
               GW_OK)
             break;
-          if (it >= o->diis_start) {
-            // the extrapolation replaces F_n and is taken whole (alpha = 1)
-            if ((rc = gw_diis_extrapolate(diis, reinterpret_cast<gw_c128*>(F + off), nullptr, nullptr)) != GW_OK) break;
-            alpha = 1.0;
-          }
+        }
+        if (diis && it >= o->diis_start) {
+          // the extrapolation replaces F_n and is taken whole (alpha = 1)
+          if ((rc = gw_diis_extrapolate(diis, reinterpret_cast<gw_c128*>(F + off), nullptr, nullptr)) != GW_OK) break;
+          alpha = 1.0;
         }
         cudaMemsetAsync(flags, 0, 16, st);
         if ((rc = mix_fp64(F + off, S + off, alpha, nvec, maxdiff, nonfinite, st)) != GW_OK) break;

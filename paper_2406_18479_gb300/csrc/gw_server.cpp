@@ -72,6 +72,7 @@ gw_scgw_options job_options(const gw_job& s) {
   o.mu_lo = s.mu_lo;
   o.mu_hi = s.mu_hi;
   o.mu_tol = s.mu_tol;
+  o.diis_kind = s.diis_kind;
   return o;
 }
 

@@ -32,7 +32,8 @@ ABI_SYMBOLS = [
     "gw_server_destroy", "gw_submit", "gw_poll", "gw_batch_create", "gw_batch_destroy",
     "gw_batch_set_coulomb", "gw_batch_sigma_eval", "gw_batch_autotune", "gw_batch_synchronize",
     "gw_density", "gw_sigma_inf", "gw_set_mu", "gw_particle_number", "gw_find_mu", "gw_diis_create",
-    "gw_diis_destroy", "gw_diis_push", "gw_diis_extrapolate", "gw_scgw_bytes", "gw_scgw",
+    "gw_diis_destroy", "gw_diis_push", "gw_diis_extrapolate", "gw_scgw_bytes", "gw_scgw", "gw_diis_push_residual",
+    "gw_commutator_residual",
 ]
 GW_BATCH_SERIAL, GW_BATCH_STREAMS, GW_BATCH_GRAPH = 0, 1, 2
 BATCH_MODES = {"serial": GW_BATCH_SERIAL, "streams": GW_BATCH_STREAMS, "graph": GW_BATCH_GRAPH}
@@ -59,7 +60,7 @@ class gw_job(ctypes.Structure):
         ("alpha", ctypes.c_double), ("tol", ctypes.c_double), ("itermax", ctypes.c_int),
         ("static_part", ctypes.c_int), ("diis_size", ctypes.c_int), ("diis_start", ctypes.c_int),
         ("n_electrons", ctypes.c_double), ("mu_lo", ctypes.c_double), ("mu_hi", ctypes.c_double),
-        ("mu_tol", ctypes.c_double),
+        ("mu_tol", ctypes.c_double), ("diis_kind", ctypes.c_int),
     ]
 
 
@@ -68,7 +69,7 @@ class gw_scgw_options(ctypes.Structure):
         ("alpha", ctypes.c_double), ("tol", ctypes.c_double), ("itermax", ctypes.c_int),
         ("static_part", ctypes.c_int), ("diis_size", ctypes.c_int), ("diis_start", ctypes.c_int),
         ("n_electrons", ctypes.c_double), ("mu_lo", ctypes.c_double), ("mu_hi", ctypes.c_double),
-        ("mu_tol", ctypes.c_double),
+        ("mu_tol", ctypes.c_double), ("diis_kind", ctypes.c_int),
     ]
 
 
@@ -143,7 +144,9 @@ def lib():
     L.gw_set_mu.argtypes = [vp, d]
     L.gw_particle_number.argtypes = [vp, vp, ctypes.POINTER(d)]
     L.gw_find_mu.argtypes = [vp, vp, vp, d, d, d, d, vp, ctypes.POINTER(d)]
-    L.gw_diis_create.argtypes = [ctypes.POINTER(vp), ctypes.c_longlong, i, vp]
+    L.gw_diis_create.argtypes = [ctypes.POINTER(vp), ctypes.c_longlong, ctypes.c_longlong, i, vp]
+    L.gw_diis_push_residual.argtypes = [vp, vp, vp]
+    L.gw_commutator_residual.argtypes = [vp, vp, vp, vp, vp, vp]
     L.gw_diis_destroy.argtypes = [vp]
     L.gw_diis_push.argtypes = [vp, vp, vp]
     L.gw_diis_extrapolate.argtypes = [vp, vp, ctypes.POINTER(d), ctypes.POINTER(i)]
@@ -410,7 +413,7 @@ class gw_server:
 
     def submit(self, cfg: gw_config, H, V, G0, Sigma_out=None, G_out=None, alpha=0.7, tol=1e-8,
                itermax=20, static_part=False, diis_size=0, diis_start=2, n_electrons=0.0, mu_lo=-5.0,
-               mu_hi=5.0, mu_tol=1e-10) -> int:
+               mu_hi=5.0, mu_tol=1e-10, diis_kind="diis") -> int:
         nk = cfg.nk[0] * cfg.nk[1] * cfg.nk[2]
         nao, naux, ntau = cfg.nao, cfg.naux, cfg.ntau
         job = gw_job(cfg, _host(H, (nk, nao, nao), "H"), _host(V, (nk, nk, naux, nao, nao), "V"),
@@ -418,7 +421,8 @@ class gw_server:
                      None if Sigma_out is None else _host(Sigma_out, (nk, ntau, nao, nao), "Sigma_out", True),
                      None if G_out is None else _host(G_out, (nk, ntau, nao, nao), "G_out", True),
                      float(alpha), float(tol), int(itermax), int(bool(static_part)), int(diis_size),
-                     int(diis_start), float(n_electrons), float(mu_lo), float(mu_hi), float(mu_tol))
+                     int(diis_start), float(n_electrons), float(mu_lo), float(mu_hi), float(mu_tol),
+                     DIIS_KINDS[diis_kind] if isinstance(diis_kind, str) else int(diis_kind))
         jid = ctypes.c_uint64()
         _check(lib().gw_submit(self._h, ctypes.byref(job), ctypes.byref(jid)))
         self._keep[jid.value] = (H, V, G0, Sigma_out, G_out)
@@ -545,18 +549,22 @@ def gw_find_mu(ctx: gw_ctx, Heff, Sig, n_target, mu_lo, mu_hi, tol, G) -> float:
 class gw_diis:
     """Owner of one gw_diis* (Pulay extrapolation of the self-energy)."""
 
-    def __init__(self, n_elem, max_vectors=5, stream=None):
+    def __init__(self, n_elem, max_vectors=5, stream=None, n_residual=0):
         import torch
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.max_vectors = int(max_vectors)
         h = ctypes.c_void_p()
-        _check(lib().gw_diis_create(ctypes.byref(h), ctypes.c_longlong(int(n_elem)), self.max_vectors,
+        _check(lib().gw_diis_create(ctypes.byref(h), ctypes.c_longlong(int(n_elem)),
+                                    ctypes.c_longlong(int(n_residual)), self.max_vectors,
                                     ctypes.c_void_p(self.stream.cuda_stream)))
         self._h = h
         self.n = int(n_elem)
 
     def push(self, sigma_in, sigma_out):
         _check(lib().gw_diis_push(self._h, _ptr(sigma_in), _ptr(sigma_out)))
+
+    def push_residual(self, sigma_out, residual):
+        _check(lib().gw_diis_push_residual(self._h, _ptr(sigma_out), _ptr(residual)))
 
     def extrapolate(self, out):
         c = (ctypes.c_double * self.max_vectors)()
@@ -576,10 +584,22 @@ class gw_diis:
             pass
 
 
+DIIS_KINDS = {"diis": 0, "cdiis": 1}
+
+
 def scgw_options(alpha=0.5, tol=1e-8, itermax=20, static_part=True, diis_size=0, diis_start=2, n_electrons=0.0,
-                 mu_lo=-5.0, mu_hi=5.0, mu_tol=1e-10) -> gw_scgw_options:
+                 mu_lo=-5.0, mu_hi=5.0, mu_tol=1e-10, diis_kind="diis") -> gw_scgw_options:
     return gw_scgw_options(float(alpha), float(tol), int(itermax), int(bool(static_part)), int(diis_size),
-                           int(diis_start), float(n_electrons), float(mu_lo), float(mu_hi), float(mu_tol))
+                           int(diis_start), float(n_electrons), float(mu_lo), float(mu_hi), float(mu_tol),
+                           DIIS_KINDS[diis_kind] if isinstance(diis_kind, str) else int(diis_kind))
+
+
+def gw_commutator_residual(ctx: gw_ctx, H, SigInf, Sig, G, e):
+    s = ctx.shapes()
+    nk, nao = ctx.nk, ctx.nao
+    _check(lib().gw_commutator_residual(ctx.handle, _ptr(H, s["H"]),
+                                        None if SigInf is None else _ptr(SigInf, (nk, nao, nao)),
+                                        _ptr(Sig, s["Sig"]), _ptr(G, s["G"]), _ptr(e, (nk, ctx.nwf, nao, nao))))
 
 
 def gw_scgw_bytes(cfg: gw_config, opt: gw_scgw_options) -> int:

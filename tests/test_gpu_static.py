@@ -199,22 +199,25 @@ def loop_case():
 
 
 LOOPS = [
-    # static part, electrons per cell (None: fixed mu), DIIS size, DIIS start
-    (False, None, 0, 2),
-    (True, None, 0, 2),
-    (True, 3.0, 0, 2),
-    (True, 3.0, 5, 2),
-    (True, None, 3, 3),
+    # static part, electrons per cell (None: fixed mu), DIIS size, DIIS start, residual
+    (False, None, 0, 2, "diis"),
+    (True, None, 0, 2, "diis"),
+    (True, 3.0, 0, 2, "diis"),
+    (True, 3.0, 5, 2, "diis"),
+    (True, None, 3, 3, "diis"),
+    (True, 3.0, 5, 2, "cdiis"),
+    (False, None, 4, 3, "cdiis"),
 ]
 
 
-@pytest.mark.parametrize("static,n_e,diis,start", LOOPS)
-def test_scgw_loop_matches_oracle(G, static, n_e, diis, start):
+@pytest.mark.parametrize("static,n_e,diis,start,kind", LOOPS)
+def test_scgw_loop_matches_oracle(G, static, n_e, diis, start, kind):
     """gw_scgw against the oracle's loop: the same number of iterations (to one, at the stop
     threshold) and the same fixed point."""
     w, h, v, g = loop_case()
     ref = O.scgw_full(h, v, g, w.nk3, w.beta, 0.1, alpha=0.6, tol=1e-10, itermax=60, static=static,
-                      n_electrons=n_e, mu_lo=-4.0, mu_hi=4.0, mu_tol=1e-12, diis_size=diis, diis_start=start)
+                      n_electrons=n_e, mu_lo=-4.0, mu_hi=4.0, mu_tol=1e-12, diis_size=diis, diis_start=start,
+                      diis_kind=kind)
     ctx = G.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, mu=0.1, precision="fp64")
     vd = dev(v)
     G.gw_set_coulomb(ctx, vd)
@@ -222,7 +225,7 @@ def test_scgw_loop_matches_oracle(G, static, n_e, diis, start):
     S = torch.empty(ctx.shapes()["Sig"], dtype=torch.complex128, device="cuda")
     Sinf = torch.empty((w.nk, w.nao, w.nao), dtype=torch.complex128, device="cuda")
     opt = G.scgw_options(alpha=0.6, tol=1e-10, itermax=60, static_part=static, diis_size=diis, diis_start=start,
-                         n_electrons=n_e or 0.0, mu_lo=-4.0, mu_hi=4.0, mu_tol=1e-12)
+                         n_electrons=n_e or 0.0, mu_lo=-4.0, mu_hi=4.0, mu_tol=1e-12, diis_kind=kind)
     rc, r = G.gw_scgw(ctx, dev(h), Gd, S, Sinf, opt)
     assert rc == G.GW_OK
     assert abs(r["iterations"] - ref["iterations"]) <= 1
@@ -256,16 +259,16 @@ def test_scgw_loop_mixed_precision(G):
 
 
 def test_scgw_serving_job_with_the_full_loop(G):
-    """A serving job with the static part, the mu search and DIIS returns the oracle's loop."""
+    """A serving job with the static part, the mu search and CDIIS returns the oracle's loop."""
     w, h, v, g = loop_case()
     ref = O.scgw_full(h, v, g, w.nk3, w.beta, 0.0, alpha=0.6, tol=1e-10, itermax=60, n_electrons=3.0,
-                      mu_lo=-4.0, mu_hi=4.0, mu_tol=1e-12, diis_size=4, diis_start=2)
+                      mu_lo=-4.0, mu_hi=4.0, mu_tol=1e-12, diis_size=4, diis_start=2, diis_kind="cdiis")
     cfg = G.make_config(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision="fp64")
     srv = G.gw_server(8 << 30, 2)
     S = np.empty(g.shape, complex)
     Gout = np.empty(g.shape, complex)
     jid = srv.submit(cfg, h, v, g, S, Gout, alpha=0.6, tol=1e-10, itermax=60, static_part=True, diis_size=4,
-                     diis_start=2, n_electrons=3.0, mu_lo=-4.0, mu_hi=4.0, mu_tol=1e-12)
+                     diis_start=2, n_electrons=3.0, mu_lo=-4.0, mu_hi=4.0, mu_tol=1e-12, diis_kind="cdiis")
     rc, res = srv.poll(jid, -1)
     assert rc == G.GW_OK and res["status"] == G.GW_OK
     assert abs(res["mu"] - ref["mu"]) < 1e-9
@@ -279,8 +282,50 @@ def test_scgw_rejects_bad_options(G):
     ctx = G.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision="fp64")
     G.gw_set_coulomb(ctx, dev(v))
     for bad in (dict(alpha=2.0), dict(itermax=0), dict(diis_size=17), dict(diis_size=2, diis_start=1),
-                dict(n_electrons=3.0, mu_lo=1.0, mu_hi=0.0)):
+                dict(n_electrons=3.0, mu_lo=1.0, mu_hi=0.0), dict(diis_size=2, diis_kind=2)):
         with pytest.raises(G.GWError) as e:
             G.gw_scgw(ctx, dev(h), dev(g), None, None, G.scgw_options(**bad))
         assert e.value.code == G.GW_EINVAL
     ctx.destroy()
+
+
+@pytest.mark.parametrize("static", [True, False])
+def test_commutator_residual_against_oracle(G, static):
+    w, h, v, g = loop_case()
+    sig = hermitian_noise(g.shape, 0.05, 2)
+    sinf = hermitian_noise((w.nk, w.nao, w.nao), 0.1, 3) if static else None
+    ctx = G.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, mu=0.3, precision="fp64")
+    e = torch.empty((w.nk, ctx.nwf, w.nao, w.nao), dtype=torch.complex128, device="cuda")
+    G.gw_commutator_residual(ctx, dev(h), None if sinf is None else dev(sinf), dev(sig), dev(g), e)
+    ref = O.commutator_residual(h, sinf, sig, g, w.beta)
+    assert rel(host(e), ref) < 1e-12
+    # a Dyson solution commutes with its own self-energy
+    Gd = torch.empty(ctx.shapes()["G"], dtype=torch.complex128, device="cuda")
+    heff = h if sinf is None else h + sinf
+    G.gw_dyson_G(ctx, dev(heff), dev(sig), Gd)
+    G.gw_commutator_residual(ctx, dev(h), None if sinf is None else dev(sinf), dev(sig), Gd, e)
+    assert np.abs(host(e)).max() < 1e-12 * np.abs(ref).max() * 1e3
+    ctx.destroy()
+
+
+def test_diis_with_explicit_residuals(G):
+    """Residuals of another length than the vectors (the commutator variant's case)."""
+    rng = np.random.default_rng(7)
+    n, nr, m = 500, 333, 4
+    d = G.gw_diis(n, m, n_residual=nr)
+    outs, res = [], []
+    out = torch.empty(n, dtype=torch.complex128, device="cuda")
+    for i in range(6):
+        f = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        r = (0.5 ** i) * (rng.standard_normal(nr) + 1j * rng.standard_normal(nr))
+        outs.append(f)
+        res.append(r)
+        d.push_residual(dev(f), dev(r))
+        c = d.extrapolate(out)
+        c_ref = O.diis_coefficients(res[-m:])
+        assert np.abs(np.array(c) - c_ref).max() < 1e-9 * max(1.0, np.abs(c_ref).max())
+        assert rel(host(out), sum(ci * o for ci, o in zip(c_ref, outs[-m:]))) < 1e-10
+    with pytest.raises(G.GWError) as e:
+        d.push(dev(outs[0]), dev(outs[1]))            # difference residuals need n_residual = 0
+    assert e.value.code == G.GW_EINVAL
+    d.destroy()
