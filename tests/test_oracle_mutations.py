@@ -117,3 +117,31 @@ def test_planted_density_sign_is_caught(monkeypatch):
     monkeypatch.setattr(gw, "density_matrix", lambda G, beta: -real(G, beta))
     with pytest.raises(AssertionError):
         LP.test_density_matrix_of_g0_is_fermi((1, 1, 1), 2.0, 0.3)
+
+
+def test_planted_diis_constraint_sign_is_caught(monkeypatch):
+    """Lagrange row with the wrong sign: the coefficients sum to -1."""
+    import test_oracle_loop_pins as LP
+
+    def wrong(residuals):
+        m = len(residuals)
+        Bm = np.empty((m + 1, m + 1))
+        for i in range(m):
+            for j in range(m):
+                Bm[i, j] = np.real(np.vdot(residuals[i], residuals[j]))
+        Bm[m, :m] = Bm[:m, m] = -1.0
+        Bm[m, m] = 0.0
+        rhs = np.zeros(m + 1)
+        rhs[m] = 1.0
+        return np.linalg.solve(Bm, rhs)[:m]
+    monkeypatch.setattr(gw, "diis_coefficients", wrong)
+    with pytest.raises(AssertionError):
+        LP.test_diis_solves_linear_fixed_points_exactly()
+
+
+def test_planted_commutator_without_static_part_is_caught(monkeypatch):
+    import test_oracle_loop_pins as LP
+    real = gw.commutator_residual
+    monkeypatch.setattr(gw, "commutator_residual", lambda H, sinf, Sig, G, beta: real(H, None, Sig, G, beta))
+    with pytest.raises(AssertionError):
+        LP.test_commutator_residual_vanishes_for_a_dyson_solution()
