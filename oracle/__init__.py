@@ -9,9 +9,12 @@ can be checked against the paper by eye:
 
   grids.py  Chebyshev tau grid and the tau <-> i Omega transform matrices (Eq. P0t_to_P0w)
   gw.py     P0(tau) (Eq. tilde_P0_tau), P(i Omega) (Eq. tilde_P_omega), Sigma(tau)
-            (Eqs. sigma_gw, tilde_W_DF2), the G Dyson equation (Eq. dyson) and mixing
+            (Eqs. sigma_gw, tilde_W_DF2), the G Dyson equation (Eq. dyson) and mixing,
+            the static part (Eq. sigma_inf), the mu search, DIIS/CDIIS and the full loop
+  gf2.py    the second-order self-energy (Eq. sigma2)
 
-Parity status: every function is pinned by tests/test_oracle_pins.py against
+Parity status: every function is pinned (tests/test_oracle_pins.py,
+tests/test_oracle_loop_pins.py, tests/test_oracle_gf2_pins.py) against
 closed forms, brute force with 4-index integrals, the pole-pair sum and
 invariants. No function is "parity unpinned".
 """

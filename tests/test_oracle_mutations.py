@@ -145,3 +145,47 @@ def test_planted_commutator_without_static_part_is_caught(monkeypatch):
     monkeypatch.setattr(gw, "commutator_residual", lambda H, sinf, Sig, G, beta: real(H, None, Sig, G, beta))
     with pytest.raises(AssertionError):
         LP.test_commutator_residual_vanishes_for_a_dyson_solution()
+
+
+# ---- the second-order self-energy (Eq. sigma2) -----------------------------------------------
+
+def _gf2_variant(mirror=True, exchange_spin=False, exchange_pair_swapped=False):
+    from oracle import gf2
+
+    def terms(V, G, nk3, spin_factor=2.0, k_list=None, t_list=None):
+        nk, ntau, nao = G.shape[0], G.shape[1], G.shape[2]
+        k_list = range(nk) if k_list is None else k_list
+        t_list = range(ntau) if t_list is None else t_list
+        d = np.zeros((len(k_list), len(t_list), nao, nao), complex)
+        x = np.zeros_like(d)
+        for ik, k in enumerate(k_list):
+            for k1 in range(nk):
+                for k2 in range(nk):
+                    k3 = gw.k_shift(nk3, gw.k_shift(nk3, k1, k2, +1), k, -1)
+                    for it, t in enumerate(t_list):
+                        gm = G[k3, ntau - 1 - t] if mirror else G[k3, t]
+                        d[ik, it] += np.einsum("Qip,pq,Rqj,Rln,nm,Qmk,kl->ij", V[k, k1], G[k1, t], V[k1, k],
+                                               V[k2, k3], gm, V[k3, k2], G[k2, t], optimize=True)
+                        vx = V[k, k2] if exchange_pair_swapped else V[k2, k]
+                        x[ik, it] += np.einsum("Qip,pq,Rqn,nm,Qmk,kl,Rlj->ij", V[k, k1], G[k1, t], V[k1, k3],
+                                               gm, V[k3, k2], G[k2, t], vx, optimize=True)
+        return spin_factor * d / nk ** 2, (spin_factor if exchange_spin else 1.0) * x / nk ** 2
+    return gf2, terms
+
+
+@pytest.mark.parametrize("kw,pin", [
+    (dict(mirror=False), "direct"),
+    (dict(exchange_spin=True), "pauli"),
+    (dict(exchange_pair_swapped=True), "brute"),
+])
+def test_planted_gf2_mistake_is_caught(monkeypatch, kw, pin):
+    import test_oracle_gf2_pins as GP
+    mod, variant = _gf2_variant(**kw)
+    monkeypatch.setattr(mod, "gf2_terms", variant)
+    with pytest.raises(AssertionError):
+        if pin == "direct":
+            GP.test_direct_term_is_the_second_order_gw_term((2, 1, 1))
+        elif pin == "pauli":
+            GP.test_one_spin_orbital_has_no_second_order_term(3)
+        else:
+            GP.test_against_four_index_brute_force((2, 1, 1))
