@@ -253,6 +253,23 @@ int gw_polarization_noalloc(const int nk3[3], int nao, int naux, int ntau, doubl
 int gw_synchronize(gw_ctx* ctx);
 
 /*
+ * Second-order (GF2) self-energy, Eq. sigma2 (Sec. 2.2), with G^{k3}(-tau) = -G^{k3}(beta - tau)
+ * (the mirrored node) and the momentum delta normalised to N_k:
+ *   Sigma^k_ij(tau) = (1/N_k^2) sum_{k1 k2} sum_{QQ' klmnpq}
+ *       [ s V^{k1 k}_qj(Q') V^{k2 k3}_ln(Q') - V^{k2 k}_lj(Q') V^{k1 k3}_qn(Q') ]
+ *       V^{k k1}_ip(Q) V^{k3 k2}_mk(Q) G^{k1}_pq(tau) G^{k2}_kl(tau) G^{k3}_nm(beta - tau),
+ * k3 = k1 + k2 - k, s = spin_factor. The direct (first) term is the GW self-energy contraction
+ * with P0 in place of P~ (gw_polarization then gw_self_energy, in the context's precision); the
+ * exchange term runs in FP64 (naux^2 nao^3 complex MACs twice per (k, k1, k2, tau)) through a
+ * device workspace of at most about 2 GiB (fewer tau nodes per batch with cfg.tau_chunk),
+ * allocated on first use. Writes Sig_dev [nk][ntau][nao][nao];
+ * uses the context's P0 buffer. gw_gf2_exchange writes the exchange term alone,
+ * (1/N_k^2) sum ... V^{k2 k}_lj(Q') V^{k1 k3}_qn(Q') ..., so that Sigma = direct - exchange.
+ */
+int gw_gf2_self_energy(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* Sig_dev);
+int gw_gf2_exchange(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* SigX_dev);
+
+/*
  * Density matrix gamma^k = G^k(0^-) = -G^k(beta^-), the G(0^-) of Eq. sigma_inf (Sec. 2.2).
  * The tau nodes exclude beta, so G(beta^-) is the polynomial through the ntau node values
  * evaluated at tau = beta: the Chebyshev series on the default grid, the interpolant of the
@@ -317,8 +334,8 @@ int gw_diis_extrapolate(gw_diis* diis, gw_c128* out_dev, double* coeffs_host, in
 
 /*
  * The self-consistency loop of Sec. 2.4 on one context. Iteration n takes G_{n-1} and
- *   (1) evaluates the output F_n = (Sigma^inf[G], Sigma~[G]) (gw_sigma_inf, gw_sigma_eval;
- *       Sigma^inf = 0 with static_part = 0);
+ *   (1) evaluates the output F_n = (Sigma^inf[G], Sigma~[G]) (gw_sigma_inf, and gw_sigma_eval or
+ *       gw_gf2_self_energy by method; Sigma^inf = 0 with static_part = 0);
  *   (2) accelerates (Sec. 5.3): Sigma_1 = F_1; then Sigma_n = alpha F_n + (1 - alpha) Sigma_{n-1},
  *       or with diis_size > 0 Pulay's extrapolation over the newest diis_size pairs
  *       (Sigma_{i-1}, F_i) from iteration diis_start on (earlier iterations mix and fill the
@@ -344,6 +361,7 @@ typedef struct {
   double mu_lo, mu_hi, mu_tol;   /* bracket and tolerance of that search */
   int diis_kind;              /* 0: residual F_i - Sigma_{i-1}; 1: commutator (gw_commutator_residual
                                  of G_{i-1} and F_i) */
+  int method;                 /* dynamic self-energy: 0 GW (gw_sigma_eval), 1 GF2 (gw_gf2_self_energy) */
 } gw_scgw_options;
 
 typedef struct {
@@ -431,6 +449,7 @@ typedef struct {
   double n_electrons;
   double mu_lo, mu_hi, mu_tol;
   int diis_kind;
+  int method;
 } gw_job;
 
 typedef struct {

@@ -37,10 +37,16 @@ def gf2_terms(V, G, nk3, spin_factor=2.0, k_list=None, t_list=None):
                 k3 = k_shift(nk3, k_shift(nk3, k1, k2, +1), k, -1)
                 for it, t in enumerate(t_list):
                     gm = G[k3, ntau - 1 - t]                      # G^{k3}(beta - tau)
-                    d[ik, it] += np.einsum("Qip,pq,Rqj,Rln,nm,Qmk,kl->ij", V[k, k1], G[k1, t], V[k1, k],
-                                           V[k2, k3], gm, V[k3, k2], G[k2, t], optimize=True)
-                    x[ik, it] += np.einsum("Qip,pq,Rqn,nm,Qmk,kl,Rlj->ij", V[k, k1], G[k1, t], V[k1, k3],
-                                           gm, V[k3, k2], G[k2, t], V[k2, k], optimize=True)
+                    # the Q-side factors V^{k k1}(Q) G^{k1} and V^{k3 k2}(Q) G^{k2}
+                    vg1 = np.einsum("Qip,pq->Qiq", V[k, k1], G[k1, t])
+                    vg2 = np.einsum("Qmk,kl->Qml", V[k3, k2], G[k2, t])
+                    # direct: sum_{QR} [V G V](Q, R)_ij * Tr[V^{k3k2}(Q) G^{k2} V^{k2k3}(R) G^{k3}(beta - tau)]
+                    m = np.einsum("Qiq,Rqj->QRij", vg1, V[k1, k])
+                    bub = np.einsum("Qml,Rlm->QR", vg2, np.einsum("Rln,nm->Rlm", V[k2, k3], gm))
+                    d[ik, it] += np.einsum("QRij,QR->ij", m, bub)
+                    # exchange: sum_{QR} [V G](Q)_iq [V^{k1k3} G^{k3}(beta - tau)](R)_qm [V G](Q)_ml V^{k2k}_lj(R)
+                    e = np.einsum("Qiq,Rqm->QiRm", vg1, np.einsum("Rqn,nm->Rqm", V[k1, k3], gm))
+                    x[ik, it] += np.einsum("Ril,Rlj->ij", np.einsum("QiRm,Qml->Ril", e, vg2), V[k2, k])
     return spin_factor * d / nk ** 2, x / nk ** 2
 
 

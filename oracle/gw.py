@@ -282,11 +282,13 @@ def commutator_residual(H, sig_inf, Sig, G, beta):
 
 
 def scgw_full(H, V, G0, nk3, beta, mu, spin_factor=2.0, alpha=0.5, tol=1e-6, itermax=10, static=True,
-              n_electrons=None, mu_lo=-5.0, mu_hi=5.0, mu_tol=1e-10, diis_size=0, diis_start=2, diis_kind="diis"):
+              n_electrons=None, mu_lo=-5.0, mu_hi=5.0, mu_tol=1e-10, diis_size=0, diis_start=2, diis_kind="diis",
+              method="gw"):
     """The self-consistency loop of Sec. 2.4 with its four steps per iteration n:
 
       (1) the static part Sigma^inf[G_{n-1}] (Eq. sigma_inf; left out when static is False) and
-          the dynamic part Sigma~[G_{n-1}] (Eq. sigma_gw) -- together the output F_n;
+          the dynamic part Sigma~[G_{n-1}] (Eq. sigma_gw, or Eq. sigma2 with method "gf2") --
+          together the output F_n;
       (2) acceleration (Sec. 5.3): Sigma_1 = F_1; afterwards iteration mixing
           Sigma_n = alpha F_n + (1 - alpha) Sigma_{n-1}, or, with diis_size > 0, Pulay's
           extrapolation over the newest diis_size pairs (Sigma_{i-1}, F_i) from iteration
@@ -307,7 +309,11 @@ def scgw_full(H, V, G0, nk3, beta, mu, spin_factor=2.0, alpha=0.5, tol=1e-6, ite
     it = 0
     for it in range(1, itermax + 1):
         sinf = sigma_inf(V, density_matrix(G, beta), nk3, spin_factor) if static else np.zeros((nk, nao, nao), complex)
-        sdyn = sigma_eval(V, G, nk3, beta, spin_factor)["Sig"]
+        if method == "gf2":
+            from .gf2 import gf2_self_energy
+            sdyn = gf2_self_energy(V, G, nk3, spin_factor)
+        else:
+            sdyn = sigma_eval(V, G, nk3, beta, spin_factor)["Sig"]
         out = np.concatenate([sinf.ravel(), sdyn.ravel()])
         if prev is None:
             cur = out

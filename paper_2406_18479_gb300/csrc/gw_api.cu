@@ -79,7 +79,7 @@ const char* prof_slot_name(int slot) {
   static const char* names[SLOT_COUNT] = {
       "vg_fp64", "p0_gemm_fp64", "r_gemm_fp64", "sigma_gemm_fp64", "transform_fp64", "inverse_fp64",
       "elementwise", "slice_planes", "vg_gemm_tc", "p0_gemm_tc", "r_gemm_tc", "sigma_gemm_tc", "reduce",
-      "static_fp64"};
+      "static_fp64", "gf2_exchange_fp64"};
   return (slot >= 0 && slot < SLOT_COUNT) ? names[slot] : "";
 }
 
@@ -148,6 +148,8 @@ struct gw_ctx {
   double2* xinf = nullptr;                // exchange intermediate of one k, [nk][naux][nao][nao]
   double2* gw_w = nullptr;                // G on the fermionic samples, [nk][nwf][nao][nao]
   double2* heff = nullptr;                // H + Sigma^inf, [nk][nao][nao]
+  double2* gf2_ws = nullptr;              // GF2 exchange intermediates (allocated on first use)
+  size_t gf2_n = 0;
   double* scal = nullptr;                 // reduction partials and results
   Prof prof;
 };
@@ -201,7 +203,7 @@ void free_ctx(gw_ctx* c) {
   mixed_destroy(c->mixed);
   void* ptrs[] = {c->Fb, c->Bb, c->Ff, c->Bf, c->wf, c->tabs, c->mq_dev, c->wlist, c->work, c->P0t, c->Pw,
                   c->Pt, c->dyson_ws, c->status, c->maxdiff, c->nonfinite, c->wbeta, c->gamma, c->rho,
-                  c->xinf, c->scal, c->gw_w, c->heff};
+                  c->xinf, c->scal, c->gw_w, c->heff, c->gf2_ws};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -839,6 +841,173 @@ int gw_commutator_residual(gw_ctx* ctx, const gw_c128* H_dev, const gw_c128* Sig
     GW_TRY(zgemm_fp64(g, ctx->stream));
   }
   return GW_OK;
+}
+
+// Exchange term of Eq. sigma2 for every k and tau node, added to S with weight alpha:
+//   S^k(t) += alpha sum_{k1 k2} X, X_ij = sum_{Q R q m l} A_iq(Q) D_qm(R) B_ml(Q) V^{k2 k}_lj(R),
+//   A(Q) = V^{k k1}(Q) G^{k1}(t), D(R) = V^{k1 k3}(R) G^{k3}(beta - t), B(Q) = V^{k3 k2}(Q) G^{k2}(t),
+//   k3 = k1 + k2 - k. Per batch of tau nodes: A, D, B (one V.G product each), then
+//   E[t][Q][i][R][m] = sum_q A D (batched over Q), H[t][R][i][l] = sum_{Q m} E B, and
+//   X = sum_{R l} H V^{k2 k}; naux^2 nao^3 complex MACs twice per (k, k1, k2, t).
+static int gf2_exchange(gw_ctx* c, const double2* G, double2* S, double alpha) {
+  const int nk = c->nk, nao = c->nao, naux = c->naux, T = c->ntau;
+  const long long n2 = c->nao2, pair = c->pair;
+  const double per_t = (double)pair * (4.0 + naux) * sizeof(double2);   // A, D, B, H and E per node
+  int nt = (int)std::min<double>(T, std::max(1.0, std::floor(2147483648.0 / per_t)));
+  nt = std::max(1, std::min(nt, 65535 / naux));              // batch count of the E product
+  if (c->cfg.tau_chunk > 0) nt = std::min(nt, c->cfg.tau_chunk);
+  const size_t need = (size_t)nt * pair * (4 + naux);
+  if (c->gf2_n < need) {
+    if (c->gf2_ws) {
+      cudaStreamSynchronize(c->stream);
+      cudaFree(c->gf2_ws);
+    }
+    c->gf2_ws = nullptr;
+    c->gf2_n = 0;
+    if (cudaMalloc(reinterpret_cast<void**>(&c->gf2_ws), need * sizeof(double2)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(GW_ENOMEM, "gf2 exchange: cannot allocate %zu bytes", need * sizeof(double2));
+    }
+    c->gf2_n = need;
+  }
+  double2* A = c->gf2_ws;
+  double2* D = A + (size_t)nt * pair;
+  double2* B = D + (size_t)nt * pair;
+  double2* H = B + (size_t)nt * pair;
+  double2* E = H + (size_t)nt * pair;
+  // out[t][Q][i][b] = sum_a V[Q][i][a] Gt[a][b], Gt = g0 + t * gstep
+  auto vg = [&](const double2* Vb, const double2* g0, long long gstep, int m, double2* out) {
+    ZGemm g;
+    g.M = naux * nao;
+    g.N = nao;
+    g.K = nao;
+    g.nbatch = m;
+    g.A = Vb;
+    g.va.rs_in = nao;
+    g.va.ks_in = 1;
+    g.B = g0;
+    g.vb.rs_in = 1;
+    g.vb.ks_in = nao;
+    g.bb.bs_in = gstep;
+    g.C = out;
+    g.vc.rs_in = nao;
+    g.vc.ks_in = 1;
+    g.bc.bs_in = pair;
+    g.slot = SLOT_GF2_FP64;
+    return zgemm_fp64(g, c->stream);
+  };
+  for (int k = 0; k < nk; ++k)
+    for (int k1 = 0; k1 < nk; ++k1)
+      for (int k2 = 0; k2 < nk; ++k2) {
+        const int k3 = kshift(c->cfg.nk, kshift(c->cfg.nk, k1, k2, +1), k, -1);
+        for (int t0 = 0; t0 < T; t0 += nt) {
+          const int m = std::min(nt, T - t0);
+          GW_TRY(vg(c->V + ((long long)k * nk + k1) * pair, G + ((long long)k1 * T + t0) * n2, n2, m, A));
+          GW_TRY(vg(c->V + ((long long)k1 * nk + k3) * pair, G + ((long long)k3 * T + (T - 1 - t0)) * n2, -n2, m, D));
+          GW_TRY(vg(c->V + ((long long)k3 * nk + k2) * pair, G + ((long long)k2 * T + t0) * n2, n2, m, B));
+          {  // E[t][Q][i][(R, m)] = sum_q A[t][Q][i][q] D[t][R][q][m]
+            ZGemm g;
+            g.M = nao;
+            g.N = naux * nao;
+            g.K = nao;
+            g.nbatch = m * naux;
+            g.bin = naux;
+            g.A = A;
+            g.va.rs_in = nao;
+            g.va.ks_in = 1;
+            g.ba.bs_in = n2;
+            g.ba.bs_out = pair;
+            g.B = D;
+            g.vb.rin = nao;
+            g.vb.rs_in = 1;
+            g.vb.rs_out = n2;
+            g.vb.ks_in = nao;
+            g.bb.bs_out = pair;
+            g.C = E;
+            g.vc.rs_in = (long long)naux * nao;
+            g.vc.ks_in = 1;
+            g.bc.bs_in = pair;
+            g.bc.bs_out = (long long)naux * pair;
+            g.slot = SLOT_GF2_FP64;
+            GW_TRY(zgemm_fp64(g, c->stream));
+          }
+          {  // H[t][R][i][l] = sum_{Q, m} E[t][Q][i][R][m] B[t][Q][m][l]; row (R, i), k (Q, m)
+            ZGemm g;
+            g.M = naux * nao;
+            g.N = nao;
+            g.K = naux * nao;
+            g.nbatch = m;
+            g.A = E;
+            g.va.rin = nao;
+            g.va.rs_out = nao;
+            g.va.rs_in = (long long)naux * nao;
+            g.va.kin = nao;
+            g.va.ks_out = pair;
+            g.va.ks_in = 1;
+            g.ba.bs_in = (long long)naux * pair;
+            g.B = B;
+            g.vb.rs_in = 1;
+            g.vb.kin = nao;
+            g.vb.ks_out = n2;
+            g.vb.ks_in = nao;
+            g.bb.bs_in = pair;
+            g.C = H;
+            g.vc.rs_in = nao;
+            g.vc.ks_in = 1;
+            g.bc.bs_in = pair;
+            g.slot = SLOT_GF2_FP64;
+            GW_TRY(zgemm_fp64(g, c->stream));
+          }
+          {  // S^k(t) += alpha sum_{R, l} H[t][R][i][l] V^{k2 k}[R][l][j]
+            ZGemm g;
+            g.M = nao;
+            g.N = nao;
+            g.K = naux * nao;
+            g.nbatch = m;
+            g.A = H;
+            g.va.rs_in = nao;
+            g.va.kin = nao;
+            g.va.ks_out = n2;
+            g.va.ks_in = 1;
+            g.ba.bs_in = pair;
+            g.B = c->V + ((long long)k2 * nk + k) * pair;
+            g.vb.rs_in = 1;
+            g.vb.kin = nao;
+            g.vb.ks_out = n2;
+            g.vb.ks_in = nao;
+            g.C = S + ((long long)k * T + t0) * n2;
+            g.vc.rs_in = nao;
+            g.vc.ks_in = 1;
+            g.bc.bs_in = n2;
+            g.alpha = alpha;
+            g.accumulate = 1;
+            g.slot = SLOT_GF2_FP64;
+            GW_TRY(zgemm_fp64(g, c->stream));
+          }
+        }
+      }
+  return GW_OK;
+}
+
+int gw_gf2_exchange(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* SigX_dev) {
+  ProfScope _ps(ctx ? &ctx->prof : nullptr);
+  if (!ctx || !G_dev || !SigX_dev) return fail(GW_EINVAL, "gw_gf2_exchange: null argument");
+  if (!ctx->V) return fail(GW_EINVAL, "gw_gf2_exchange: call gw_set_coulomb first");
+  double2* S = reinterpret_cast<double2*>(SigX_dev);
+  if (cudaMemsetAsync(S, 0, (size_t)ctx->nk * ctx->ntau * ctx->nao2 * sizeof(double2), ctx->stream) != cudaSuccess)
+    return cuda_check("gw_gf2_exchange memset");
+  return gf2_exchange(ctx, reinterpret_cast<const double2*>(G_dev), S, 1.0 / ((double)ctx->nk * ctx->nk));
+}
+
+int gw_gf2_self_energy(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* Sig_dev) {
+  ProfScope _ps(ctx ? &ctx->prof : nullptr);
+  if (!ctx || !G_dev || !Sig_dev) return fail(GW_EINVAL, "gw_gf2_self_energy: null argument");
+  if (!ctx->V) return fail(GW_EINVAL, "gw_gf2_self_energy: call gw_set_coulomb first");
+  // direct term: the GW self-energy contraction with P0 in place of P~
+  GW_TRY(gw_polarization(ctx, G_dev, reinterpret_cast<gw_c128*>(ctx->P0t)));
+  GW_TRY(gw_self_energy(ctx, G_dev, reinterpret_cast<const gw_c128*>(ctx->P0t), Sig_dev));
+  return gf2_exchange(ctx, reinterpret_cast<const double2*>(G_dev), reinterpret_cast<double2*>(Sig_dev),
+                      -1.0 / ((double)ctx->nk * ctx->nk));
 }
 
 int gw_set_mu(gw_ctx* ctx, double mu) {

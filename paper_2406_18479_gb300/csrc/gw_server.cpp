@@ -73,6 +73,7 @@ gw_scgw_options job_options(const gw_job& s) {
   o.mu_hi = s.mu_hi;
   o.mu_tol = s.mu_tol;
   o.diis_kind = s.diis_kind;
+  o.method = s.method;
   return o;
 }
 

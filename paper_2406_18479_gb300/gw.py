@@ -33,7 +33,7 @@ ABI_SYMBOLS = [
     "gw_batch_set_coulomb", "gw_batch_sigma_eval", "gw_batch_autotune", "gw_batch_synchronize",
     "gw_density", "gw_sigma_inf", "gw_set_mu", "gw_particle_number", "gw_find_mu", "gw_diis_create",
     "gw_diis_destroy", "gw_diis_push", "gw_diis_extrapolate", "gw_scgw_bytes", "gw_scgw", "gw_diis_push_residual",
-    "gw_commutator_residual",
+    "gw_commutator_residual", "gw_gf2_self_energy", "gw_gf2_exchange",
 ]
 GW_BATCH_SERIAL, GW_BATCH_STREAMS, GW_BATCH_GRAPH = 0, 1, 2
 BATCH_MODES = {"serial": GW_BATCH_SERIAL, "streams": GW_BATCH_STREAMS, "graph": GW_BATCH_GRAPH}
@@ -60,7 +60,7 @@ class gw_job(ctypes.Structure):
         ("alpha", ctypes.c_double), ("tol", ctypes.c_double), ("itermax", ctypes.c_int),
         ("static_part", ctypes.c_int), ("diis_size", ctypes.c_int), ("diis_start", ctypes.c_int),
         ("n_electrons", ctypes.c_double), ("mu_lo", ctypes.c_double), ("mu_hi", ctypes.c_double),
-        ("mu_tol", ctypes.c_double), ("diis_kind", ctypes.c_int),
+        ("mu_tol", ctypes.c_double), ("diis_kind", ctypes.c_int), ("method", ctypes.c_int),
     ]
 
 
@@ -69,7 +69,7 @@ class gw_scgw_options(ctypes.Structure):
         ("alpha", ctypes.c_double), ("tol", ctypes.c_double), ("itermax", ctypes.c_int),
         ("static_part", ctypes.c_int), ("diis_size", ctypes.c_int), ("diis_start", ctypes.c_int),
         ("n_electrons", ctypes.c_double), ("mu_lo", ctypes.c_double), ("mu_hi", ctypes.c_double),
-        ("mu_tol", ctypes.c_double), ("diis_kind", ctypes.c_int),
+        ("mu_tol", ctypes.c_double), ("diis_kind", ctypes.c_int), ("method", ctypes.c_int),
     ]
 
 
@@ -147,6 +147,8 @@ def lib():
     L.gw_diis_create.argtypes = [ctypes.POINTER(vp), ctypes.c_longlong, ctypes.c_longlong, i, vp]
     L.gw_diis_push_residual.argtypes = [vp, vp, vp]
     L.gw_commutator_residual.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.gw_gf2_self_energy.argtypes = [vp, vp, vp]
+    L.gw_gf2_exchange.argtypes = [vp, vp, vp]
     L.gw_diis_destroy.argtypes = [vp]
     L.gw_diis_push.argtypes = [vp, vp, vp]
     L.gw_diis_extrapolate.argtypes = [vp, vp, ctypes.POINTER(d), ctypes.POINTER(i)]
@@ -413,7 +415,7 @@ class gw_server:
 
     def submit(self, cfg: gw_config, H, V, G0, Sigma_out=None, G_out=None, alpha=0.7, tol=1e-8,
                itermax=20, static_part=False, diis_size=0, diis_start=2, n_electrons=0.0, mu_lo=-5.0,
-               mu_hi=5.0, mu_tol=1e-10, diis_kind="diis") -> int:
+               mu_hi=5.0, mu_tol=1e-10, diis_kind="diis", method="gw") -> int:
         nk = cfg.nk[0] * cfg.nk[1] * cfg.nk[2]
         nao, naux, ntau = cfg.nao, cfg.naux, cfg.ntau
         job = gw_job(cfg, _host(H, (nk, nao, nao), "H"), _host(V, (nk, nk, naux, nao, nao), "V"),
@@ -422,7 +424,7 @@ class gw_server:
                      None if G_out is None else _host(G_out, (nk, ntau, nao, nao), "G_out", True),
                      float(alpha), float(tol), int(itermax), int(bool(static_part)), int(diis_size),
                      int(diis_start), float(n_electrons), float(mu_lo), float(mu_hi), float(mu_tol),
-                     DIIS_KINDS[diis_kind] if isinstance(diis_kind, str) else int(diis_kind))
+                     _code(DIIS_KINDS, diis_kind), _code(METHODS, method))
         jid = ctypes.c_uint64()
         _check(lib().gw_submit(self._h, ctypes.byref(job), ctypes.byref(jid)))
         self._keep[jid.value] = (H, V, G0, Sigma_out, G_out)
@@ -585,13 +587,28 @@ class gw_diis:
 
 
 DIIS_KINDS = {"diis": 0, "cdiis": 1}
+METHODS = {"gw": 0, "gf2": 1}
+
+
+def _code(table, x):
+    return table[x] if isinstance(x, str) else int(x)
 
 
 def scgw_options(alpha=0.5, tol=1e-8, itermax=20, static_part=True, diis_size=0, diis_start=2, n_electrons=0.0,
-                 mu_lo=-5.0, mu_hi=5.0, mu_tol=1e-10, diis_kind="diis") -> gw_scgw_options:
+                 mu_lo=-5.0, mu_hi=5.0, mu_tol=1e-10, diis_kind="diis", method="gw") -> gw_scgw_options:
     return gw_scgw_options(float(alpha), float(tol), int(itermax), int(bool(static_part)), int(diis_size),
                            int(diis_start), float(n_electrons), float(mu_lo), float(mu_hi), float(mu_tol),
-                           DIIS_KINDS[diis_kind] if isinstance(diis_kind, str) else int(diis_kind))
+                           _code(DIIS_KINDS, diis_kind), _code(METHODS, method))
+
+
+def gw_gf2_self_energy(ctx: gw_ctx, G, Sig):
+    s = ctx.shapes()
+    _check(lib().gw_gf2_self_energy(ctx.handle, _ptr(G, s["G"]), _ptr(Sig, s["Sig"])))
+
+
+def gw_gf2_exchange(ctx: gw_ctx, G, SigX):
+    s = ctx.shapes()
+    _check(lib().gw_gf2_exchange(ctx.handle, _ptr(G, s["G"]), _ptr(SigX, s["Sig"])))
 
 
 def gw_commutator_residual(ctx: gw_ctx, H, SigInf, Sig, G, e):

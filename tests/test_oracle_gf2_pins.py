@@ -86,3 +86,19 @@ def test_hermitian(nk3):
     w, v, g = case(nk3, 3, 5, 4, 4.0, 11)
     sig = F.gf2_self_energy(v, g, nk3, 2.0)
     assert np.abs(sig - sig.conj().swapaxes(-1, -2)).max() < 1e-13 * np.abs(sig).max()
+
+
+def test_gf2_loop_reaches_its_fixed_point():
+    """The loop with the second-order self-energy: at convergence Sigma^inf and Sigma~ are those
+    of G (Eq. sigma2), G holds n_electrons and solves the Dyson equation with them."""
+    w = I.Workload("gf2loop", (2, 1, 1), 3, 6, 12, 12, 5.0, 0.0, 3.0, 21, solid=True)
+    h, v, g = I.make_inputs(w)
+    v = 0.4 * v
+    r = O.scgw_full(h, v, g, w.nk3, w.beta, 0.0, alpha=0.7, tol=1e-10, itermax=60, n_electrons=2.0,
+                    mu_tol=1e-13, diis_size=4, method="gf2")
+    assert r["hist"][-1] < 1e-10
+    gam = O.density_matrix(r["G"], w.beta)
+    assert abs(O.particle_number(gam, 2.0) - 2.0) < 1e-9
+    assert np.abs(O.sigma_inf(v, gam, w.nk3, 2.0) - r["SigInf"]).max() < 1e-8
+    assert np.abs(F.gf2_self_energy(v, r["G"], w.nk3, 2.0) - r["Sig"]).max() < 1e-8
+    assert np.abs(O.dyson_G(h + r["SigInf"], r["Sig"], r["mu"], w.beta) - r["G"]).max() < 1e-12
