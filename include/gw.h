@@ -260,9 +260,9 @@ int gw_synchronize(gw_ctx* ctx);
  *       V^{k k1}_ip(Q) V^{k3 k2}_mk(Q) G^{k1}_pq(tau) G^{k2}_kl(tau) G^{k3}_nm(beta - tau),
  * k3 = k1 + k2 - k, s = spin_factor. The direct (first) term is the GW self-energy contraction
  * with P0 in place of P~ (gw_polarization then gw_self_energy, in the context's precision); the
- * exchange term runs in FP64 (naux^2 nao^3 complex MACs twice per (k, k1, k2, tau)) through a
- * device workspace of at most about 2 GiB (fewer tau nodes per batch with cfg.tau_chunk),
- * allocated on first use. Writes Sig_dev [nk][ntau][nao][nao];
+ * exchange term runs in FP64, contracted over Q and Q' first (2 nao^4 naux + nao^5 complex MACs
+ * per (k, k1, k2, tau)), through a device workspace of at most about 2 GiB (fewer tau nodes per
+ * batch with cfg.tau_chunk), allocated on first use. Writes Sig_dev [nk][ntau][nao][nao];
  * uses the context's P0 buffer. gw_gf2_exchange writes the exchange term alone,
  * (1/N_k^2) sum ... V^{k2 k}_lj(Q') V^{k1 k3}_qn(Q') ..., so that Sigma = direct - exchange.
  */

@@ -846,17 +846,20 @@ int gw_commutator_residual(gw_ctx* ctx, const gw_c128* H_dev, const gw_c128* Sig
 // Exchange term of Eq. sigma2 for every k and tau node, added to S with weight alpha:
 //   S^k(t) += alpha sum_{k1 k2} X, X_ij = sum_{Q R q m l} A_iq(Q) D_qm(R) B_ml(Q) V^{k2 k}_lj(R),
 //   A(Q) = V^{k k1}(Q) G^{k1}(t), D(R) = V^{k1 k3}(R) G^{k3}(beta - t), B(Q) = V^{k3 k2}(Q) G^{k2}(t),
-//   k3 = k1 + k2 - k. Per batch of tau nodes: A, D, B (one V.G product each), then
-//   E[t][Q][i][R][m] = sum_q A D (batched over Q), H[t][R][i][l] = sum_{Q m} E B, and
-//   X = sum_{R l} H V^{k2 k}; naux^2 nao^3 complex MACs twice per (k, k1, k2, t).
+//   k3 = k1 + k2 - k. Contracted over the auxiliary indices first:
+//   Y[(i q)][(m l)] = sum_Q A_iq(Q) B_ml(Q),  W[(q m)][(l j)] = sum_R D_qm(R) V^{k2 k}_lj(R),
+//   X_ij = sum_{q m l} Y[(i q)][(m l)] W[(q m)][(l j)],
+// 2 nao^4 naux + nao^5 complex MACs per (k, k1, k2, t) (2 naux^2 nao^3 the other way round). The
+// last product is split over q into partial sums (its output is only nao x nao) and reduced in
+// a fixed order.
 static int gf2_exchange(gw_ctx* c, const double2* G, double2* S, double alpha) {
   const int nk = c->nk, nao = c->nao, naux = c->naux, T = c->ntau;
-  const long long n2 = c->nao2, pair = c->pair;
-  const double per_t = (double)pair * (4.0 + naux) * sizeof(double2);   // A, D, B, H and E per node
+  const long long n2 = c->nao2, pair = c->pair, n3 = n2 * nao, n4 = n2 * n2;
+  const double per_t = (3.0 * pair + 2.0 * n4 + n3) * sizeof(double2);   // A, D, B, Y, W, partials
   int nt = (int)std::min<double>(T, std::max(1.0, std::floor(2147483648.0 / per_t)));
-  nt = std::max(1, std::min(nt, 65535 / naux));              // batch count of the E product
+  nt = std::max(1, std::min(nt, 65535 / nao));               // batch count of the split last product
   if (c->cfg.tau_chunk > 0) nt = std::min(nt, c->cfg.tau_chunk);
-  const size_t need = (size_t)nt * pair * (4 + naux);
+  const size_t need = (size_t)nt * (3 * pair + 2 * n4 + n3);
   if (c->gf2_n < need) {
     if (c->gf2_ws) {
       cudaStreamSynchronize(c->stream);
@@ -873,8 +876,9 @@ static int gf2_exchange(gw_ctx* c, const double2* G, double2* S, double alpha) {
   double2* A = c->gf2_ws;
   double2* D = A + (size_t)nt * pair;
   double2* B = D + (size_t)nt * pair;
-  double2* H = B + (size_t)nt * pair;
-  double2* E = H + (size_t)nt * pair;
+  double2* Y = B + (size_t)nt * pair;
+  double2* W = Y + (size_t)nt * n4;
+  double2* part = W + (size_t)nt * n4;
   // out[t][Q][i][b] = sum_a V[Q][i][a] Gt[a][b], Gt = g0 + t * gstep
   auto vg = [&](const double2* Vb, const double2* g0, long long gstep, int m, double2* out) {
     ZGemm g;
@@ -896,6 +900,28 @@ static int gf2_exchange(gw_ctx* c, const double2* G, double2* S, double alpha) {
     g.slot = SLOT_GF2_FP64;
     return zgemm_fp64(g, c->stream);
   };
+  // out[t][(a b)][(c d)] = sum_Q X[t][Q][a][b] Z[t][Q][c][d]   (Z's batch stride may be 0)
+  auto outer_q = [&](const double2* X, const double2* Z, long long zstep, int m, double2* out) {
+    ZGemm g;
+    g.M = (int)n2;
+    g.N = (int)n2;
+    g.K = naux;
+    g.nbatch = m;
+    g.A = X;
+    g.va.rs_in = 1;
+    g.va.ks_in = n2;
+    g.ba.bs_in = pair;
+    g.B = Z;
+    g.vb.rs_in = 1;
+    g.vb.ks_in = n2;
+    g.bb.bs_in = zstep;
+    g.C = out;
+    g.vc.rs_in = n2;
+    g.vc.ks_in = 1;
+    g.bc.bs_in = n4;
+    g.slot = SLOT_GF2_FP64;
+    return zgemm_fp64(g, c->stream);
+  };
   for (int k = 0; k < nk; ++k)
     for (int k1 = 0; k1 < nk; ++k1)
       for (int k2 = 0; k2 < nk; ++k2) {
@@ -905,85 +931,34 @@ static int gf2_exchange(gw_ctx* c, const double2* G, double2* S, double alpha) {
           GW_TRY(vg(c->V + ((long long)k * nk + k1) * pair, G + ((long long)k1 * T + t0) * n2, n2, m, A));
           GW_TRY(vg(c->V + ((long long)k1 * nk + k3) * pair, G + ((long long)k3 * T + (T - 1 - t0)) * n2, -n2, m, D));
           GW_TRY(vg(c->V + ((long long)k3 * nk + k2) * pair, G + ((long long)k2 * T + t0) * n2, n2, m, B));
-          {  // E[t][Q][i][(R, m)] = sum_q A[t][Q][i][q] D[t][R][q][m]
+          GW_TRY(outer_q(A, B, pair, m, Y));                                            // Y = sum_Q A B
+          GW_TRY(outer_q(D, c->V + ((long long)k2 * nk + k) * pair, 0, m, W));          // W = sum_R D V
+          {  // part[t][q][i][j] = sum_{(m l)} Y[t][(i q)][(m l)] W[t][(q m)][(l j)], batch (t, q)
             ZGemm g;
             g.M = nao;
-            g.N = naux * nao;
-            g.K = nao;
-            g.nbatch = m * naux;
-            g.bin = naux;
-            g.A = A;
-            g.va.rs_in = nao;
+            g.N = nao;
+            g.K = (int)n2;
+            g.nbatch = m * nao;
+            g.bin = nao;
+            g.A = Y;
+            g.va.rs_in = n3;
             g.va.ks_in = 1;
             g.ba.bs_in = n2;
-            g.ba.bs_out = pair;
-            g.B = D;
-            g.vb.rin = nao;
+            g.ba.bs_out = n4;
+            g.B = W;
             g.vb.rs_in = 1;
-            g.vb.rs_out = n2;
             g.vb.ks_in = nao;
-            g.bb.bs_out = pair;
-            g.C = E;
-            g.vc.rs_in = (long long)naux * nao;
-            g.vc.ks_in = 1;
-            g.bc.bs_in = pair;
-            g.bc.bs_out = (long long)naux * pair;
-            g.slot = SLOT_GF2_FP64;
-            GW_TRY(zgemm_fp64(g, c->stream));
-          }
-          {  // H[t][R][i][l] = sum_{Q, m} E[t][Q][i][R][m] B[t][Q][m][l]; row (R, i), k (Q, m)
-            ZGemm g;
-            g.M = naux * nao;
-            g.N = nao;
-            g.K = naux * nao;
-            g.nbatch = m;
-            g.A = E;
-            g.va.rin = nao;
-            g.va.rs_out = nao;
-            g.va.rs_in = (long long)naux * nao;
-            g.va.kin = nao;
-            g.va.ks_out = pair;
-            g.va.ks_in = 1;
-            g.ba.bs_in = (long long)naux * pair;
-            g.B = B;
-            g.vb.rs_in = 1;
-            g.vb.kin = nao;
-            g.vb.ks_out = n2;
-            g.vb.ks_in = nao;
-            g.bb.bs_in = pair;
-            g.C = H;
-            g.vc.rs_in = nao;
-            g.vc.ks_in = 1;
-            g.bc.bs_in = pair;
-            g.slot = SLOT_GF2_FP64;
-            GW_TRY(zgemm_fp64(g, c->stream));
-          }
-          {  // S^k(t) += alpha sum_{R, l} H[t][R][i][l] V^{k2 k}[R][l][j]
-            ZGemm g;
-            g.M = nao;
-            g.N = nao;
-            g.K = naux * nao;
-            g.nbatch = m;
-            g.A = H;
-            g.va.rs_in = nao;
-            g.va.kin = nao;
-            g.va.ks_out = n2;
-            g.va.ks_in = 1;
-            g.ba.bs_in = pair;
-            g.B = c->V + ((long long)k2 * nk + k) * pair;
-            g.vb.rs_in = 1;
-            g.vb.kin = nao;
-            g.vb.ks_out = n2;
-            g.vb.ks_in = nao;
-            g.C = S + ((long long)k * T + t0) * n2;
+            g.bb.bs_in = n3;
+            g.bb.bs_out = n4;
+            g.C = part;
             g.vc.rs_in = nao;
             g.vc.ks_in = 1;
             g.bc.bs_in = n2;
-            g.alpha = alpha;
-            g.accumulate = 1;
+            g.bc.bs_out = n3;
             g.slot = SLOT_GF2_FP64;
             GW_TRY(zgemm_fp64(g, c->stream));
           }
+          GW_TRY(reduce_partials_fp64(part, S + ((long long)k * T + t0) * n2, m, (int)n2, nao, alpha, c->stream));
         }
       }
   return GW_OK;

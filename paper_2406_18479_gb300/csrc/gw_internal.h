@@ -102,6 +102,9 @@ int hartree_fp64(const double2* V, const double2* gamma, double2* rho, double2* 
 //   exchange: out^k += scale sum_{k'Q b} (V^{kk'}(Q) gamma^{k'})_ib V^{k'k}_bj(Q), for nao <= kExchangeMaxNao,
 //             through part [nk][nk][exchange_chunks][nao][nao]
 constexpr int kExchangeMaxNao = 52;
+// out[o][e] += scale sum_{p < nparts} part[(o nparts + p)][e], e < n2, summed in the order of p
+int reduce_partials_fp64(const double2* part, double2* out, int nouter, int n2, int nparts, double scale,
+                         void* stream);
 int exchange_chunks(int nk, int naux);
 int exchange_fp64(const double2* V, const double2* gamma, double2* part, double2* out, int nk, int naux, int nao,
                   double scale, void* stream);

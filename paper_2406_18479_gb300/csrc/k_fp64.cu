@@ -593,15 +593,16 @@ __global__ void __launch_bounds__(kExThreads) exchange_partial_kernel(const doub
   }
 }
 
-// out^k_ij += scale sum_{k', c} part[(k nk + k') qc + c]_ij, summed in that fixed order
-__global__ void exchange_reduce_kernel(const double2* __restrict__ part, double2* __restrict__ out, int nk, int n2,
-                                       int qc, double scale) {
-  const long long total = (long long)nk * n2;
+// out[o][e] += scale sum_{p < nparts} part[o nparts + p][e], summed in the order of p (the exchange
+// of Eq. sigma_inf: o = k, p = (k', c); the GF2 exchange: o = tau node, p = orbital q)
+__global__ void exchange_reduce_kernel(const double2* __restrict__ part, double2* __restrict__ out, int nouter,
+                                       int n2, int nparts, double scale) {
+  const long long total = (long long)nouter * n2;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-    const long long k = e / n2, r = e % n2;
-    const double2* p = part + k * nk * qc * n2 + r;
+    const long long o = e / n2, r = e % n2;
+    const double2* p = part + o * nparts * n2 + r;
     double2 s = make_double2(0.0, 0.0);
-    for (int u = 0; u < nk * qc; ++u) {
+    for (int u = 0; u < nparts; ++u) {
       const double2 v = p[(long long)u * n2];
       s.x += v.x;
       s.y += v.y;
@@ -801,6 +802,17 @@ int hartree_fp64(const double2* V, const double2* gamma, double2* rho, double2* 
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "hartree launch: %s", cudaGetErrorString(e));
 }
 
+int reduce_partials_fp64(const double2* part, double2* out, int nouter, int n2, int nparts, double scale,
+                         void* stream) {
+  prof_begin(SLOT_ELEMENTWISE, (cudaStream_t)stream);
+  exchange_reduce_kernel<<<grid_for((long long)nouter * n2, 256), 256, 0, (cudaStream_t)stream>>>(part, out, nouter,
+                                                                                                n2, nparts, scale);
+  prof_end(SLOT_ELEMENTWISE, (cudaStream_t)stream, 2.0 * nouter * (double)n2 * nparts,
+           16.0 * nouter * (double)n2 * (nparts + 2));
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "reduce_partials launch: %s", cudaGetErrorString(e));
+}
+
 int exchange_chunks(int nk, int naux) {
   // enough blocks for every SM several times over: 4 x 152 at least, when naux allows
   const int want = (608 + nk * nk - 1) / (nk * nk);
@@ -822,8 +834,8 @@ int exchange_fp64(const double2* V, const double2* gamma, double2* part, double2
   prof_begin(SLOT_STATIC_FP64, (cudaStream_t)stream);
   exchange_partial_kernel<<<nk * nk * qc, kExThreads, smem, (cudaStream_t)stream>>>(V, gamma, part, nk, naux, nao,
                                                                                      qc);
-  exchange_reduce_kernel<<<grid_for((long long)nk * n2, 256), 256, 0, (cudaStream_t)stream>>>(part, out, nk, n2, qc,
-                                                                                             scale);
+  exchange_reduce_kernel<<<grid_for((long long)nk * n2, 256), 256, 0, (cudaStream_t)stream>>>(part, out, nk, n2,
+                                                                                             nk * qc, scale);
   prof_end(SLOT_STATIC_FP64, (cudaStream_t)stream, 16.0 * (double)nk * nk * naux * n2 * nao,
            32.0 * (double)nk * nk * naux * n2);
   const cudaError_t e = cudaGetLastError();
