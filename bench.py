@@ -552,6 +552,124 @@ def run_serving(args, rank, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def _event_ms(stream, fn, steps):
+    """Average CUDA-event time of fn() over steps calls on stream, after one untimed call."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_loop(args, rank, local_rank):
+    """One JSON line for the self-consistency loop of Sec. 2.4 on the bench workload: iterations/s
+    of gw_scgw (static part, GW self-energy, DIIS over five vectors, Dyson) and the cost of each
+    piece beside the self-energy evaluation (rank 0; other ranks exit)."""
+    import torch
+    from paper_2406_18479_gb300 import gw, inputs as I
+    if rank != 0:
+        return
+    torch.cuda.set_device(local_rank)
+    w = I.WORKLOADS[args.workload]
+    h, v, g = I.make_inputs(w)
+    V, G0, H = (torch.from_numpy(x).cuda() for x in (v, g, h))
+    ctx = gw.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision=args.precision, tau_chunk=args.tau_chunk)
+    gw.gw_set_coulomb(ctx, V)
+    st = ctx.stream
+    Sig = torch.empty(ctx.shapes()["Sig"], dtype=torch.complex128, device="cuda")
+    Sinf = torch.empty((w.nk, w.nao, w.nao), dtype=torch.complex128, device="cuda")
+    Gw = torch.empty_like(G0)
+    e = torch.empty((w.nk, ctx.nwf, w.nao, w.nao), dtype=torch.complex128, device="cuda")
+    pieces = {}
+    with ClockSampler(local_rank) as clk:
+        pieces["sigma_eval"] = _event_ms(st, lambda: gw.gw_sigma_eval(ctx, G0, Sig), 2)
+        pieces["sigma_inf"] = _event_ms(st, lambda: gw.gw_sigma_inf(ctx, G0, Sinf), 3)
+        pieces["dyson"] = _event_ms(st, lambda: gw.gw_dyson_G(ctx, H, Sig, Gw), 3)
+        pieces["commutator_residual"] = _event_ms(st, lambda: gw.gw_commutator_residual(ctx, H, Sinf, Sig, G0, e), 3)
+        gw.gw_dyson_G(ctx, H, Sig, Gw)
+        n1 = gw.gw_particle_number(ctx, Gw)
+        t0 = time.perf_counter()
+        gw.gw_find_mu(ctx, H, Sig, n1, -1.0, 1.0, 1e-10, Gw)
+        pieces["find_mu"] = (time.perf_counter() - t0) * 1e3
+        gw.gw_set_mu(ctx, w.mu)
+        n = w.nk * w.nao * w.nao * (1 + w.ntau)
+        d = gw.gw_diis(n, 5, stream=st)
+        pairs = [(torch.randn(n, dtype=torch.complex128, device="cuda"),
+                  torch.randn(n, dtype=torch.complex128, device="cuda")) for _ in range(6)]
+        out = torch.empty(n, dtype=torch.complex128, device="cuda")
+        t0 = time.perf_counter()
+        for a, b in pairs:
+            d.push(a, b)
+            d.extrapolate(out)
+        torch.cuda.synchronize()
+        pieces["diis_push_extrapolate"] = (time.perf_counter() - t0) * 1e3 / len(pairs)
+        d.destroy()
+        iters = max(2, args.steps)
+        opt = gw.scgw_options(alpha=0.5, tol=0.0, itermax=iters, static_part=True, diis_size=5)
+        Gl = G0.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, r = gw.gw_scgw(ctx, H, Gl, Sig, Sinf, opt)
+        loop_s = time.perf_counter() - t0
+    ctx.destroy()
+    line = {"metric": "scGW iterations/s (static part, GW self-energy, DIIS, Dyson; Sec. 2.4)",
+            "value": r["iterations"] / loop_s, "unit": "iterations/s", "n_gpus": 1, "steps": iters,
+            "warmup": 1, "ms_per_step": loop_s * 1e3 / r["iterations"], "higher_is_better": True,
+            "dtype": args.precision, "data": "synthetic (seeded H(k), V, G0 shaped like the paper's Si example)",
+            "config": {"workload": w.name, "precision": args.precision, "diis_size": 5, "static_part": True},
+            "pieces_ms": pieces, "loop_status": rc, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def gf2_exchange_flops(nao, naux, ntau, nk=1):
+    """FP64 flops of the GF2 exchange as contracted: (2 nao^4 naux + nao^5) complex MACs per
+    (k, k1, k2, tau), 8 real flops each."""
+    return 8.0 * nk ** 3 * ntau * (2.0 * nao ** 4 * naux + nao ** 5)
+
+
+def run_gf2(args, rank, local_rank):
+    """One JSON line for the second-order self-energy (Eq. sigma2) on a molecule (nk = 1,
+    naux = 4 nao, 80 tau nodes, beta = 100): evaluations/s, with the FP64 exchange's rate
+    against the FP64 pipe (rank 0; other ranks exit)."""
+    import torch
+    from paper_2406_18479_gb300 import gw, inputs as I
+    if rank != 0:
+        return
+    torch.cuda.set_device(local_rank)
+    w = I.molecule(f"molecule_nao{args.gf2_nao}", args.gf2_nao, ntau=80, beta=100.0, seed=4)
+    h, v, g = I.make_inputs(w)
+    V, G0 = torch.from_numpy(v).cuda(), torch.from_numpy(g).cuda()
+    ctx = gw.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision=args.precision)
+    gw.gw_set_coulomb(ctx, V)
+    st = ctx.stream
+    S = torch.empty(ctx.shapes()["Sig"], dtype=torch.complex128, device="cuda")
+    steps = max(1, args.steps)
+    with ClockSampler(local_rank) as clk:
+        ms = _event_ms(st, lambda: gw.gw_gf2_self_energy(ctx, G0, S), steps)
+        ms_x = _event_ms(st, lambda: gw.gw_gf2_exchange(ctx, G0, S), steps)
+        ms_gw = _event_ms(st, lambda: gw.gw_sigma_eval(ctx, G0, S), steps)
+    ctx.destroy()
+    fx = gf2_exchange_flops(w.nao, w.naux, w.ntau)
+    achieved = fx / (ms_x * 1e-3) / 1e12
+    line = {"metric": "GF2 self-energy evaluations/s (Eq. sigma2)", "value": 1e3 / ms, "unit": "sigma_evals/s",
+            "n_gpus": 1, "steps": steps, "warmup": 1, "ms_per_step": ms, "higher_is_better": True,
+            "dtype": {"fp64": "c128 (f64)", "bf16x3": "direct term bf16x3 slices, exchange f64"}[args.precision],
+            "data": "synthetic (seeded molecule)",
+            "config": {"workload": w.name, "nao": w.nao, "naux": w.naux, "ntau": w.ntau, "beta": w.beta,
+                       "precision": args.precision},
+            "exchange_ms": ms_x, "gw_sigma_eval_ms": ms_gw,
+            "roofline": {"kernel": "gf2_exchange_fp64", "bound": "alu", "achieved": achieved,
+                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                         "traffic": None, "peak_source": "FP64 pipe, GB300 nominal 1.25 TFLOP/s"},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -575,13 +693,18 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="measure only the 48-molecule batch (loop vs streams vs graph) and print its own line")
     ap.add_argument("--batch-streams", type=int, default=8)
+    ap.add_argument("--loop", action="store_true",
+                    help="measure only the self-consistency loop (gw_scgw and its pieces) and print its own line")
+    ap.add_argument("--gf2", action="store_true",
+                    help="measure only the second-order self-energy on a molecule and print its own line")
+    ap.add_argument("--gf2-nao", type=int, default=26)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.precision is None:
         args.precision = "bf16x3"
     if args.steps is None:
-        args.steps = 2 if args.precision == "fp64" else (3 if args.batched else 10)
+        args.steps = 2 if args.precision == "fp64" else (3 if (args.batched or args.loop or args.gf2) else 10)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -591,6 +714,10 @@ def main():
         run_batched(args, rank, local_rank)
     elif args.serving:
         run_serving(args, rank, local_rank)
+    elif args.loop:
+        run_loop(args, rank, local_rank)
+    elif args.gf2:
+        run_gf2(args, rank, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 
