@@ -18,6 +18,11 @@
  *   Sig  [nk][ntau][nao][nao]
  * k is the flat index (n1*N2 + n2)*N3 + n3 of the Gamma-centred mesh
  * k = 2 pi (n1/N1, n2/N2, n3/N3); k +- q is taken modulo the mesh.
+ * With gw_config.v_packed = 1, V holds only the pairs k1 <= k2,
+ *   Vp   [nk (nk + 1) / 2][naux][nao][nao]  in the order (0,0), (0,1), .., (0,nk-1), (1,1), ..,
+ * and the library takes V^{k2 k1}_ij(Q) = conj V^{k1 k2}_ji(Q) (the k1 <-> k2 symmetry of the
+ * density-fitted Coulomb factor, Eq. CoulombDF with real auxiliary functions): about half the
+ * memory of V for solids.
  *
  * Pointers named *_dev are device pointers owned by the caller (for example
  * torch tensors); the library never frees them and reads or writes them only
@@ -84,6 +89,10 @@ typedef struct {
   int precision;        /* gw_precision */
   int tau_chunk;        /* tau nodes per batch in the contractions; 0 = automatic */
   int v_slices;         /* mixed precisions: GW_V_AUTO, GW_V_ALL_PAIRS or GW_V_PER_Q */
+  int v_packed;         /* 1: V holds the pairs k1 <= k2 only (layout above). FP64 keeps a full
+                           working copy in the context; the mixed precisions unpack the blocks
+                           they slice (all pairs once, through a transient buffer, or the nk
+                           blocks of one q at a time) and keep no FP64 copy */
 } gw_config;
 
 /* Library version string. */
@@ -145,10 +154,11 @@ int gw_set_grids(gw_ctx* ctx, const double* tau_host, const gw_c128* Fb_host, co
                  const double* omega_f_host);
 
 /*
- * Borrows the Coulomb factor V (layout above, Eq. CoulombDF). The caller keeps
- * V_dev alive and unchanged until gw_destroy or the next gw_set_coulomb. In the
+ * Borrows the Coulomb factor V (layout above, Eq. CoulombDF; packed when cfg.v_packed). The
+ * caller keeps V_dev alive and unchanged until gw_destroy or the next gw_set_coulomb. In the
  * mixed precisions this call also cuts V into its bf16 slices (a device workspace), or,
- * with per-q slices, only records V.
+ * with per-q slices, only records V. A packed V is unpacked here into the context's FP64
+ * copy (FP64 precision) or, for all-pair slices, into a transient buffer.
  */
 int gw_set_coulomb(gw_ctx* ctx, const gw_c128* V_dev);
 

@@ -138,7 +138,10 @@ struct gw_ctx {
   int* status = nullptr;                  // device flags: [0] singular matrix
   double* maxdiff = nullptr;
   int* nonfinite = nullptr;
-  const double2* V = nullptr;
+  const double2* V = nullptr;             // full-layout V: the caller's, or the unpacked copy Vfull
+  const double2* Vp = nullptr;            // the caller's packed V (cfg.v_packed)
+  double2* Vfull = nullptr;               // FP64 precision with a packed V: the full working copy
+  bool coulomb = false;                   // gw_set_coulomb has been called
   size_t bytes = 0;
   MixedState* mixed = nullptr;
   // static part and loop helpers
@@ -203,7 +206,7 @@ void free_ctx(gw_ctx* c) {
   mixed_destroy(c->mixed);
   void* ptrs[] = {c->Fb, c->Bb, c->Ff, c->Bf, c->wf, c->tabs, c->mq_dev, c->wlist, c->work, c->P0t, c->Pw,
                   c->Pt, c->dyson_ws, c->status, c->maxdiff, c->nonfinite, c->wbeta, c->gamma, c->rho,
-                  c->xinf, c->scal, c->gw_w, c->heff, c->gf2_ws};
+                  c->xinf, c->scal, c->gw_w, c->heff, c->gf2_ws, c->Vfull};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -433,7 +436,7 @@ bool config_ok(const gw_config* cfg) {
   return !(cfg->nk[0] < 1 || cfg->nk[1] < 1 || cfg->nk[2] < 1 || nk > 4096 || cfg->nao < 1 || cfg->nao > 512 ||
            cfg->naux < 1 || cfg->naux > 4096 || cfg->ntau < 1 || cfg->ntau > 512 || !(cfg->beta > 0) ||
            cfg->precision < GW_FP64 || cfg->precision > GW_MIXED_FP16S || cfg->v_slices < GW_V_AUTO ||
-           cfg->v_slices > GW_V_PER_Q);
+           cfg->v_slices > GW_V_PER_Q || cfg->v_packed < 0 || cfg->v_packed > 1);
 }
 
 // Weights w_j with p(beta) = sum_j w_j f(tau_j) for the polynomial p of degree n - 1 through the
@@ -520,6 +523,7 @@ int ctx_build(gw_ctx* c, const gw_config* cfg) {
     c->nt = std::min(nt, c->ntau);
     if (cfg->precision == GW_FP64) {
       if ((rc = dev_alloc(c, &c->work, (size_t)c->nt * 2 * nk * c->pair)) != GW_OK) break;
+      if (cfg->v_packed && (rc = dev_alloc(c, &c->Vfull, (size_t)nk * nk * c->pair)) != GW_OK) break;
     }
     if ((rc = dev_alloc(c, &c->P0t, (size_t)nk * c->ntau * c->naux2)) != GW_OK) break;
     if ((rc = dev_alloc(c, &c->Pw, (size_t)nk * c->nwb * c->naux2)) != GW_OK) break;
@@ -554,6 +558,7 @@ int ctx_build(gw_ctx* c, const gw_config* cfg) {
       d.nk = nk; d.nao = c->nao; d.naux = c->naux; d.ntau = c->ntau; d.precision = cfg->precision;
       d.tau_chunk = cfg->tau_chunk;
       d.v_slices = cfg->v_slices;
+      d.v_packed = cfg->v_packed;
       d.mq = c->mq;
       if ((rc = mixed_create(&c->mixed, d, c->stream, c->status, &c->bytes, c->dry)) != GW_OK) break;
     }
@@ -574,7 +579,8 @@ size_t job_device_bytes(const gw_config* cfg) {
   const size_t nk = (size_t)cfg->nk[0] * cfg->nk[1] * cfg->nk[2], nao2 = (size_t)cfg->nao * cfg->nao;
   // V, H, G and the Sigma output of the job, and the loop's buffers with its default options
   gw_scgw_options o{};
-  return c.bytes + sizeof(gw_c128) * (nk * nk * cfg->naux * nao2 + nk * nao2 + 2 * nk * cfg->ntau * nao2) +
+  const size_t vblocks = cfg->v_packed ? (size_t)packed_pairs((int)nk) : nk * nk;
+  return c.bytes + sizeof(gw_c128) * (vblocks * cfg->naux * nao2 + nk * nao2 + 2 * nk * cfg->ntau * nao2) +
          scgw_device_bytes(cfg, &o);
 }
 
@@ -659,15 +665,32 @@ int gw_set_grids(gw_ctx* ctx, const double* tau_host, const gw_c128* Fb_host, co
 int gw_set_coulomb(gw_ctx* ctx, const gw_c128* V_dev) {
   ProfScope _ps(ctx ? &ctx->prof : nullptr);
   if (!ctx || !V_dev) return fail(GW_EINVAL, "gw_set_coulomb: null argument");
-  ctx->V = reinterpret_cast<const double2*>(V_dev);
-  if (ctx->mixed) return mixed_set_coulomb(ctx->mixed, ctx->V);
+  const double2* V = reinterpret_cast<const double2*>(V_dev);
+  ctx->coulomb = false;
+  if (ctx->cfg.v_packed) {
+    ctx->Vp = V;
+    if (!ctx->mixed) {   // FP64: one full working copy
+      VPairs L;
+      L.all = 1;
+      GW_TRY(unpack_v_fp64(V, ctx->nk, ctx->nao, ctx->pair, L, ctx->nk * ctx->nk, ctx->Vfull, ctx->stream));
+      ctx->V = ctx->Vfull;
+    } else {
+      ctx->V = nullptr;
+      GW_TRY(mixed_set_coulomb(ctx->mixed, nullptr, V));
+    }
+  } else {
+    ctx->V = V;
+    ctx->Vp = nullptr;
+    if (ctx->mixed) GW_TRY(mixed_set_coulomb(ctx->mixed, V));
+  }
+  ctx->coulomb = true;
   return GW_OK;
 }
 
 int gw_polarization(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* P0t_dev) {
   ProfScope _ps(ctx ? &ctx->prof : nullptr);
   if (!ctx || !G_dev || !P0t_dev) return fail(GW_EINVAL, "gw_polarization: null argument");
-  if (!ctx->V) return fail(GW_EINVAL, "gw_polarization: call gw_set_coulomb first");
+  if (!ctx->coulomb) return fail(GW_EINVAL, "gw_polarization: call gw_set_coulomb first");
   const double2* G = reinterpret_cast<const double2*>(G_dev);
   double2* P = reinterpret_cast<double2*>(P0t_dev);
   // only canonical (q, tau) are contracted; the rest is P0^q(beta - tau) = P0^{-q}(tau)^T
@@ -710,7 +733,7 @@ int gw_screened_interaction(gw_ctx* ctx, const gw_c128* P0t_dev, gw_c128* Pt_dev
 int gw_self_energy(gw_ctx* ctx, const gw_c128* G_dev, const gw_c128* Pt_dev, gw_c128* Sig_dev) {
   ProfScope _ps(ctx ? &ctx->prof : nullptr);
   if (!ctx || !G_dev || !Pt_dev || !Sig_dev) return fail(GW_EINVAL, "gw_self_energy: null argument");
-  if (!ctx->V) return fail(GW_EINVAL, "gw_self_energy: call gw_set_coulomb first");
+  if (!ctx->coulomb) return fail(GW_EINVAL, "gw_self_energy: call gw_set_coulomb first");
   const double2* G = reinterpret_cast<const double2*>(G_dev);
   const double2* P = reinterpret_cast<const double2*>(Pt_dev);
   double2* S = reinterpret_cast<double2*>(Sig_dev);
@@ -749,14 +772,20 @@ int gw_density(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* gamma_dev) {
 int gw_sigma_inf(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* SigInf_dev) {
   ProfScope _ps(ctx ? &ctx->prof : nullptr);
   if (!ctx || !G_dev || !SigInf_dev) return fail(GW_EINVAL, "gw_sigma_inf: null argument");
-  if (!ctx->V) return fail(GW_EINVAL, "gw_sigma_inf: call gw_set_coulomb first");
+  if (!ctx->coulomb) return fail(GW_EINVAL, "gw_sigma_inf: call gw_set_coulomb first");
   const int nk = ctx->nk, nao = ctx->nao, naux = ctx->naux;
   double2* S = reinterpret_cast<double2*>(SigInf_dev);
   GW_TRY(density_fp64(reinterpret_cast<const double2*>(G_dev), ctx->wbeta, ctx->gamma, nk, ctx->ntau, nao, ctx->stream));
   // Hartree: (s / N_k) sum_Q V^{kk}_ij(Q) rho_Q
-  GW_TRY(hartree_fp64(ctx->V, ctx->gamma, ctx->rho, S, nk, naux, nao, ctx->cfg.spin_factor / nk, ctx->stream));
+  // the full-layout V when there is one, else the packed one (mixed precisions with cfg.v_packed)
+  const double2* Vs = ctx->V ? ctx->V : ctx->Vp;
+  const int packed = ctx->V ? 0 : 1;
+  GW_TRY(hartree_fp64(Vs, ctx->gamma, ctx->rho, S, nk, naux, nao, ctx->cfg.spin_factor / nk, packed, ctx->stream));
   // exchange: -(1 / N_k) sum_{k'} sum_{Q b} X^{k'}_{Q i b} V^{k'k}_bj(Q), X^{k'}_{Q i b} = sum_a V^{kk'}_ia(Q) gamma^{k'}_ab
-  if (nao <= kExchangeMaxNao) return exchange_fp64(ctx->V, ctx->gamma, ctx->xinf, S, nk, naux, nao, -1.0 / nk, ctx->stream);
+  if (nao <= kExchangeMaxNao)
+    return exchange_fp64(Vs, ctx->gamma, ctx->xinf, S, nk, naux, nao, -1.0 / nk, packed, ctx->stream);
+  if (packed)
+    return fail(GW_ENOTIMPL, "gw_sigma_inf: nao above %d with a packed V needs FP64 precision", kExchangeMaxNao);
   for (int k = 0; k < nk; ++k) {
     ZGemm a;
     a.M = naux * nao;
@@ -859,7 +888,8 @@ static int gf2_exchange(gw_ctx* c, const double2* G, double2* S, double alpha) {
   int nt = (int)std::min<double>(T, std::max(1.0, std::floor(2147483648.0 / per_t)));
   nt = std::max(1, std::min(nt, 65535 / nao));               // batch count of the split last product
   if (c->cfg.tau_chunk > 0) nt = std::min(nt, c->cfg.tau_chunk);
-  const size_t need = (size_t)nt * (3 * pair + 2 * n4 + n3);
+  const bool unpack = c->V == nullptr;    // packed V without a full copy: four blocks per (k, k1, k2)
+  const size_t need = (size_t)nt * (3 * pair + 2 * n4 + n3) + (unpack ? 4 * (size_t)pair : 0);
   if (c->gf2_n < need) {
     if (c->gf2_ws) {
       cudaStreamSynchronize(c->stream);
@@ -879,6 +909,7 @@ static int gf2_exchange(gw_ctx* c, const double2* G, double2* S, double alpha) {
   double2* Y = B + (size_t)nt * pair;
   double2* W = Y + (size_t)nt * n4;
   double2* part = W + (size_t)nt * n4;
+  double2* vblk = part + (size_t)nt * n3;   // the unpacked blocks (k k1), (k1 k3), (k3 k2), (k2 k)
   // out[t][Q][i][b] = sum_a V[Q][i][a] Gt[a][b], Gt = g0 + t * gstep
   auto vg = [&](const double2* Vb, const double2* g0, long long gstep, int m, double2* out) {
     ZGemm g;
@@ -926,13 +957,26 @@ static int gf2_exchange(gw_ctx* c, const double2* G, double2* S, double alpha) {
     for (int k1 = 0; k1 < nk; ++k1)
       for (int k2 = 0; k2 < nk; ++k2) {
         const int k3 = kshift(c->cfg.nk, kshift(c->cfg.nk, k1, k2, +1), k, -1);
+        const int pa[4] = {k, k1, k3, k2}, pb[4] = {k1, k3, k2, k};
+        const double2* vb[4];
+        if (unpack) {
+          VPairs L;
+          for (int i = 0; i < 4; ++i) {
+            L.k1[i] = pa[i];
+            L.k2[i] = pb[i];
+            vb[i] = vblk + i * pair;
+          }
+          GW_TRY(unpack_v_fp64(c->Vp, nk, nao, pair, L, 4, vblk, c->stream));
+        } else {
+          for (int i = 0; i < 4; ++i) vb[i] = c->V + ((long long)pa[i] * nk + pb[i]) * pair;
+        }
         for (int t0 = 0; t0 < T; t0 += nt) {
           const int m = std::min(nt, T - t0);
-          GW_TRY(vg(c->V + ((long long)k * nk + k1) * pair, G + ((long long)k1 * T + t0) * n2, n2, m, A));
-          GW_TRY(vg(c->V + ((long long)k1 * nk + k3) * pair, G + ((long long)k3 * T + (T - 1 - t0)) * n2, -n2, m, D));
-          GW_TRY(vg(c->V + ((long long)k3 * nk + k2) * pair, G + ((long long)k2 * T + t0) * n2, n2, m, B));
+          GW_TRY(vg(vb[0], G + ((long long)k1 * T + t0) * n2, n2, m, A));
+          GW_TRY(vg(vb[1], G + ((long long)k3 * T + (T - 1 - t0)) * n2, -n2, m, D));
+          GW_TRY(vg(vb[2], G + ((long long)k2 * T + t0) * n2, n2, m, B));
           GW_TRY(outer_q(A, B, pair, m, Y));                                            // Y = sum_Q A B
-          GW_TRY(outer_q(D, c->V + ((long long)k2 * nk + k) * pair, 0, m, W));          // W = sum_R D V
+          GW_TRY(outer_q(D, vb[3], 0, m, W));                                           // W = sum_R D V
           {  // part[t][q][i][j] = sum_{(m l)} Y[t][(i q)][(m l)] W[t][(q m)][(l j)], batch (t, q)
             ZGemm g;
             g.M = nao;
@@ -967,7 +1011,7 @@ static int gf2_exchange(gw_ctx* c, const double2* G, double2* S, double alpha) {
 int gw_gf2_exchange(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* SigX_dev) {
   ProfScope _ps(ctx ? &ctx->prof : nullptr);
   if (!ctx || !G_dev || !SigX_dev) return fail(GW_EINVAL, "gw_gf2_exchange: null argument");
-  if (!ctx->V) return fail(GW_EINVAL, "gw_gf2_exchange: call gw_set_coulomb first");
+  if (!ctx->coulomb) return fail(GW_EINVAL, "gw_gf2_exchange: call gw_set_coulomb first");
   double2* S = reinterpret_cast<double2*>(SigX_dev);
   if (cudaMemsetAsync(S, 0, (size_t)ctx->nk * ctx->ntau * ctx->nao2 * sizeof(double2), ctx->stream) != cudaSuccess)
     return cuda_check("gw_gf2_exchange memset");
@@ -977,7 +1021,7 @@ int gw_gf2_exchange(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* SigX_dev) {
 int gw_gf2_self_energy(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* Sig_dev) {
   ProfScope _ps(ctx ? &ctx->prof : nullptr);
   if (!ctx || !G_dev || !Sig_dev) return fail(GW_EINVAL, "gw_gf2_self_energy: null argument");
-  if (!ctx->V) return fail(GW_EINVAL, "gw_gf2_self_energy: call gw_set_coulomb first");
+  if (!ctx->coulomb) return fail(GW_EINVAL, "gw_gf2_self_energy: call gw_set_coulomb first");
   // direct term: the GW self-energy contraction with P0 in place of P~
   GW_TRY(gw_polarization(ctx, G_dev, reinterpret_cast<gw_c128*>(ctx->P0t)));
   GW_TRY(gw_self_energy(ctx, G_dev, reinterpret_cast<const gw_c128*>(ctx->P0t), Sig_dev));

@@ -98,7 +98,7 @@ int mirror_fill(double2* X, int nk, int T, int n, const int* mq_dev, void* strea
 constexpr int kDotBlocks = 512;
 int density_fp64(const double2* G, const double* w, double2* gamma, int nk, int ntau, int nao, void* stream);
 int hartree_fp64(const double2* V, const double2* gamma, double2* rho, double2* out, int nk, int naux, int nao,
-                 double scale, void* stream);
+                 double scale, int packed, void* stream);
 //   exchange: out^k += scale sum_{k'Q b} (V^{kk'}(Q) gamma^{k'})_ib V^{k'k}_bj(Q), for nao <= kExchangeMaxNao,
 //             through part [nk][nk][exchange_chunks][nao][nao]
 constexpr int kExchangeMaxNao = 52;
@@ -107,7 +107,20 @@ int reduce_partials_fp64(const double2* part, double2* out, int nouter, int n2, 
                          void* stream);
 int exchange_chunks(int nk, int naux);
 int exchange_fp64(const double2* V, const double2* gamma, double2* part, double2* out, int nk, int naux, int nao,
-                  double scale, void* stream);
+                  double scale, int packed, void* stream);
+
+// The packed Coulomb factor (gw_config.v_packed): blocks k1 <= k2 only, in row order of the upper
+// triangle; V^{k2 k1}_ij(Q) = conj V^{k1 k2}_ji(Q). unpack_v_fp64 writes full-layout blocks
+// dst[b] = V^{k1 k2} for a list of pairs: decoded from full-layout offsets tab[b] (a device
+// table), every pair in order (all), or up to four given pairs.
+struct VPairs {
+  const long long* tab = nullptr;
+  int all = 0;
+  int k1[4] = {0, 0, 0, 0}, k2[4] = {0, 0, 0, 0};
+};
+inline long long packed_pairs(int nk) { return (long long)nk * (nk + 1) / 2; }
+int unpack_v_fp64(const double2* Vp, int nk, int nao, long long pair, const VPairs& L, int nblocks, double2* dst,
+                  void* stream);
 int trace_fp64(const double2* gamma, int nk, int nao, double* out_dev, void* stream);
 int add_fp64(const double2* a, const double2* b, double2* c, long long n, void* stream);
 int dot_re_fp64(const double2* x, const double2* y, long long n, double* partial_dev, double* out_dev, void* stream);

@@ -9,7 +9,7 @@ namespace gwi {
 
 struct MixedDims {
   int nk3[3] = {1, 1, 1};
-  int nk = 1, nao = 0, naux = 0, ntau = 0, precision = 0, tau_chunk = 0, v_slices = 0;
+  int nk = 1, nao = 0, naux = 0, ntau = 0, precision = 0, tau_chunk = 0, v_slices = 0, v_packed = 0;
   std::vector<int> mq;    // index of -q for every q
 };
 
@@ -20,7 +20,8 @@ struct MixedState;
 int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int* status, size_t* bytes,
                  bool dry = false);
 void mixed_destroy(MixedState* s);
-int mixed_set_coulomb(MixedState* s, const double2* V);
+// V: the full-layout Coulomb factor, or null with Vp the packed one (pairs k1 <= k2)
+int mixed_set_coulomb(MixedState* s, const double2* V, const double2* Vp = nullptr);
 int mixed_polarization(MixedState* s, const double2* G, double2* P0t, double spin_factor);
 int mixed_self_energy(MixedState* s, const double2* G, const double2* Pt, double2* Sig);
 

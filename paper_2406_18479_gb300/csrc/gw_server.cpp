@@ -82,7 +82,7 @@ int run_job(Job* j) {
   const gw_config& c = s.cfg;
   const long long nk = (long long)c.nk[0] * c.nk[1] * c.nk[2];
   const long long nao2 = (long long)c.nao * c.nao;
-  const size_t bV = sizeof(gw_c128) * nk * nk * c.naux * nao2;
+  const size_t bV = sizeof(gw_c128) * (c.v_packed ? (size_t)packed_pairs((int)nk) : (size_t)(nk * nk)) * c.naux * nao2;
   const size_t bH = sizeof(gw_c128) * nk * nao2;
   const size_t bG = sizeof(gw_c128) * nk * c.ntau * nao2;
   cudaStream_t st = nullptr;

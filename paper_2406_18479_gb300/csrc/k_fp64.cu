@@ -496,8 +496,65 @@ __global__ void density_kernel(const double2* G, const double* w, double2* gamma
 }
 
 // rho_Q = sum_{k'} sum_ab gamma^{k'}_ab V^{k'k'}_ba(Q); one block per Q
+// Packed Coulomb factor: only the pairs k1 <= k2, in the order (0,0), (0,1), .., (0,nk-1), (1,1), ..;
+// V^{k2 k1}_ij(Q) = conj V^{k1 k2}_ji(Q). Block of the pair (a, b), a <= b:
+__device__ __forceinline__ long long packed_block(int a, int b, int nk) {
+  return (long long)a * nk - (long long)a * (a - 1) / 2 + (b - a);
+}
+
+// Offset of element (Q, i, j) of V^{k1 k2} and whether it is conjugated: the full layout, or the
+// packed one (the transposed element of the stored pair for k1 > k2).
+__device__ __forceinline__ long long v_elem(int k1, int k2, int Q, int i, int j, int nk, int nao, long long pair,
+                                            int packed, bool* conj) {
+  const long long n2 = (long long)nao * nao;
+  if (!packed) {
+    *conj = false;
+    return ((long long)k1 * nk + k2) * pair + Q * n2 + (long long)i * nao + j;
+  }
+  if (k1 <= k2) {
+    *conj = false;
+    return packed_block(k1, k2, nk) * pair + Q * n2 + (long long)i * nao + j;
+  }
+  *conj = true;
+  return packed_block(k2, k1, nk) * pair + Q * n2 + (long long)j * nao + i;
+}
+
+__device__ __forceinline__ double2 v_load(const double2* V, int k1, int k2, int Q, int i, int j, int nk, int nao,
+                                          long long pair, int packed) {
+  bool cj;
+  const double2 v = V[v_elem(k1, k2, Q, i, j, nk, nao, pair, packed, &cj)];
+  return cj ? make_double2(v.x, -v.y) : v;
+}
+
+// dst[b] = V^{k1 k2} (full layout [naux][nao][nao]) from the packed V, for the blocks b of a list:
+// pairs decoded from full-layout offsets tab[b] = (k1 nk + k2) pair, or every pair in order
+// (all = 1), or up to four given pairs.
+__global__ void unpack_v_kernel(const double2* __restrict__ Vp, int nk, int nao, long long pair, VPairs L,
+                                int nblocks, double2* __restrict__ dst) {
+  const long long n2 = (long long)nao * nao;
+  for (int b = blockIdx.y; b < nblocks; b += gridDim.y) {
+    int k1, k2;
+    if (L.tab) {
+      const long long kk = L.tab[b] / pair;
+      k1 = (int)(kk / nk);
+      k2 = (int)(kk % nk);
+    } else if (L.all) {
+      k1 = b / nk;
+      k2 = b % nk;
+    } else {
+      k1 = L.k1[b];
+      k2 = L.k2[b];
+    }
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < pair;
+         e += (long long)gridDim.x * blockDim.x) {
+      const int Q = (int)(e / n2), r = (int)(e % n2), i = r / nao, j = r % nao;
+      dst[(long long)b * pair + e] = v_load(Vp, k1, k2, Q, i, j, nk, nao, pair, 1);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) hartree_rho_kernel(const double2* V, const double2* gamma, double2* rho, int nk,
-                                                          int naux, int nao) {
+                                                          int naux, int nao, int packed) {
   const int Q = blockIdx.x;
   const long long nao2 = (long long)nao * nao, pair = (long long)naux * nao2;
   double2 acc = make_double2(0.0, 0.0);
@@ -505,7 +562,8 @@ __global__ void __launch_bounds__(256) hartree_rho_kernel(const double2* V, cons
     const int kp = (int)(e / nao2);
     const int a = (int)((e % nao2) / nao), b = (int)(e % nao);
     const double2 g = gamma[(long long)kp * nao2 + (long long)a * nao + b];
-    const double2 v = V[((long long)kp * nk + kp) * pair + (long long)Q * nao2 + (long long)b * nao + a];
+    const long long blk = packed ? packed_block(kp, kp, nk) : (long long)kp * nk + kp;
+    const double2 v = V[blk * pair + (long long)Q * nao2 + (long long)b * nao + a];
     cmac(acc, g, v);
   }
   __shared__ double sx[256], sy[256];
@@ -524,12 +582,12 @@ __global__ void __launch_bounds__(256) hartree_rho_kernel(const double2* V, cons
 
 // out^k_ij = scale sum_Q V^{kk}_ij(Q) rho_Q
 __global__ void hartree_j_kernel(const double2* V, const double2* rho, double2* out, int nk, int naux, int nao,
-                                 double scale) {
+                                 double scale, int packed) {
   const long long nao2 = (long long)nao * nao, pair = (long long)naux * nao2;
   const long long total = (long long)nk * nao2;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     const long long k = e / nao2, r = e % nao2;
-    const double2* v = V + (k * nk + k) * pair + r;
+    const double2* v = V + (packed ? packed_block((int)k, (int)k, nk) : k * nk + k) * pair + r;
     double2 acc = make_double2(0.0, 0.0);
     for (int Q = 0; Q < naux; ++Q) cmac(acc, v[(long long)Q * nao2], rho[Q]);
     out[e] = make_double2(scale * acc.x, scale * acc.y);
@@ -546,7 +604,7 @@ constexpr int kExMaxPerThread = 11;    // nao^2 <= 256 * 11: nao <= kExchangeMax
 __global__ void __launch_bounds__(kExThreads) exchange_partial_kernel(const double2* __restrict__ V,
                                                                       const double2* __restrict__ gamma,
                                                                       double2* __restrict__ part, int nk, int naux,
-                                                                      int nao, int qc) {
+                                                                      int nao, int qc, int packed) {
   extern __shared__ double2 ex_sm[];
   const int n2 = nao * nao;
   double2* g = ex_sm;
@@ -556,8 +614,6 @@ __global__ void __launch_bounds__(kExThreads) exchange_partial_kernel(const doub
   const int c = blockIdx.x % qc, kp = (blockIdx.x / qc) % nk, k = blockIdx.x / (qc * nk);
   const int q0 = (int)((long long)naux * c / qc), q1 = (int)((long long)naux * (c + 1) / qc);
   const long long pair = (long long)naux * n2;
-  const double2* Va = V + ((long long)k * nk + kp) * pair;
-  const double2* Vb = V + ((long long)kp * nk + k) * pair;
   for (int e = threadIdx.x; e < n2; e += kExThreads) g[e] = gamma[(long long)kp * n2 + e];
   double2 acc[kExMaxPerThread];
 #pragma unroll
@@ -565,8 +621,9 @@ __global__ void __launch_bounds__(kExThreads) exchange_partial_kernel(const doub
   for (int Q = q0; Q < q1; ++Q) {
     __syncthreads();
     for (int e = threadIdx.x; e < n2; e += kExThreads) {
-      v1[e] = Va[(long long)Q * n2 + e];
-      v2[e] = Vb[(long long)Q * n2 + e];
+      const int i = e / nao, j = e - i * nao;
+      v1[e] = v_load(V, k, kp, Q, i, j, nk, nao, pair, packed);
+      v2[e] = v_load(V, kp, k, Q, i, j, nk, nao, pair, packed);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < n2; e += kExThreads) {
@@ -792,11 +849,11 @@ int density_fp64(const double2* G, const double* w, double2* gamma, int nk, int 
 }
 
 int hartree_fp64(const double2* V, const double2* gamma, double2* rho, double2* out, int nk, int naux, int nao,
-                 double scale, void* stream) {
+                 double scale, int packed, void* stream) {
   const long long n = (long long)nk * nao * nao;
   prof_begin(SLOT_STATIC_FP64, (cudaStream_t)stream);
-  hartree_rho_kernel<<<naux, 256, 0, (cudaStream_t)stream>>>(V, gamma, rho, nk, naux, nao);
-  hartree_j_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(V, rho, out, nk, naux, nao, scale);
+  hartree_rho_kernel<<<naux, 256, 0, (cudaStream_t)stream>>>(V, gamma, rho, nk, naux, nao, packed);
+  hartree_j_kernel<<<grid_for(n, 256), 256, 0, (cudaStream_t)stream>>>(V, rho, out, nk, naux, nao, scale, packed);
   prof_end(SLOT_STATIC_FP64, (cudaStream_t)stream, 16.0 * n * naux, 32.0 * n * naux);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "hartree launch: %s", cudaGetErrorString(e));
@@ -820,7 +877,7 @@ int exchange_chunks(int nk, int naux) {
 }
 
 int exchange_fp64(const double2* V, const double2* gamma, double2* part, double2* out, int nk, int naux, int nao,
-                  double scale, void* stream) {
+                  double scale, int packed, void* stream) {
   if (nao > kExchangeMaxNao) return fail(GW_EINVAL, "exchange_fp64: nao=%d above %d", nao, kExchangeMaxNao);
   static const bool attr = [] {
     const bool ok = cudaFuncSetAttribute(exchange_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -833,13 +890,26 @@ int exchange_fp64(const double2* V, const double2* gamma, double2* part, double2
   const size_t smem = 4 * (size_t)n2 * sizeof(double2);
   prof_begin(SLOT_STATIC_FP64, (cudaStream_t)stream);
   exchange_partial_kernel<<<nk * nk * qc, kExThreads, smem, (cudaStream_t)stream>>>(V, gamma, part, nk, naux, nao,
-                                                                                     qc);
+                                                                                     qc, packed);
   exchange_reduce_kernel<<<grid_for((long long)nk * n2, 256), 256, 0, (cudaStream_t)stream>>>(part, out, nk, n2,
                                                                                              nk * qc, scale);
   prof_end(SLOT_STATIC_FP64, (cudaStream_t)stream, 16.0 * (double)nk * nk * naux * n2 * nao,
            32.0 * (double)nk * nk * naux * n2);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "exchange launch: %s", cudaGetErrorString(e));
+}
+
+int unpack_v_fp64(const double2* Vp, int nk, int nao, long long pair, const VPairs& L, int nblocks, double2* dst,
+                  void* stream) {
+  if (nblocks <= 0) return GW_OK;
+  if (!L.tab && !L.all && nblocks > 4) return fail(GW_EINVAL, "unpack_v: at most four listed pairs");
+  const int gx = (int)std::min<long long>((pair + 255) / 256, 1024);
+  prof_begin(SLOT_ELEMENTWISE, (cudaStream_t)stream);
+  unpack_v_kernel<<<dim3(gx, std::min(nblocks, 65535)), 256, 0, (cudaStream_t)stream>>>(Vp, nk, nao, pair, L, nblocks,
+                                                                                        dst);
+  prof_end(SLOT_ELEMENTWISE, (cudaStream_t)stream, 0.0, 32.0 * (double)pair * nblocks);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "unpack_v launch: %s", cudaGetErrorString(e));
 }
 
 int trace_fp64(const double2* gamma, int nk, int nao, double* out_dev, void* stream) {

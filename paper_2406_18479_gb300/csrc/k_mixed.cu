@@ -872,6 +872,8 @@ struct MixedState {
   int nt = 1;                   // tau nodes per batch
   long long nao2 = 0, naux2 = 0, pair = 0;
   const double2* V = nullptr;
+  const double2* Vp = nullptr;  // packed V (pairs k1 <= k2), when given instead of V
+  double2* vscratch = nullptr;  // per-q mode with a packed V: the nk full-layout blocks of one table
   Planes vrow, vcol, gf, gm;    // V rows (Q,i) over orbitals; V rows (j,b) over Q'; G^T forward / mirrored tau
   bool per_q = false;           // V slices staged per q (vq, vcq) instead of held for all pairs
   Planes vq[2], vcq;
@@ -1190,7 +1192,10 @@ int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int*
         if ((rc = alloc_planes(s, &s->vq[i], (long long)nk * naux * nao, s->Kc_vg, s->Kpad_vg, 2, bytes))) break;
       if (rc) break;
       if ((rc = alloc_planes(s, &s->vcq, (long long)nk * s->nao2, s->Kc_r, s->Kpad_r, 2, bytes))) break;
+      if (d.v_packed && (rc = m_alloc(s, &s->vscratch, (size_t)nk * s->pair, bytes))) break;
     } else {
+      // a packed V is unpacked for the slicing through a transient buffer of all pairs
+      if (d.v_packed) *bytes += (size_t)nk * nk * s->pair * sizeof(double2);
       if ((rc = alloc_planes(s, &s->vrow, vpairs * naux * nao, s->Kc_vg, s->Kpad_vg, 2, bytes))) break;
       if ((rc = alloc_planes(s, &s->vcol, vpairs * s->nao2, s->Kc_r, s->Kpad_r, 2, bytes))) break;
     }
@@ -1250,13 +1255,46 @@ void mixed_destroy(MixedState* s) {
   delete s;
 }
 
-int mixed_set_coulomb(MixedState* s, const double2* V) {
+int mixed_set_coulomb(MixedState* s, const double2* V, const double2* Vp) {
   s->V = V;
+  s->Vp = Vp;
   if (s->per_q) return GW_OK;               // sliced per q, when used
   const int nk = s->d.nk;
+  double2* tmp = nullptr;
+  if (Vp) {
+    if (cudaMalloc(reinterpret_cast<void**>(&tmp), (size_t)nk * nk * s->pair * sizeof(double2)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(GW_ENOMEM, "mixed: no room to unpack V");
+    }
+    VPairs L;
+    L.all = 1;
+    int rc = unpack_v_fp64(Vp, nk, s->d.nao, s->pair, L, nk * nk, tmp, s->stream);
+    if (rc == GW_OK) rc = stage_vrow(s, tmp, nk * nk, nullptr, s->vrow);
+    if (rc == GW_OK) rc = stage_vcol(s, tmp, nk * nk, nullptr, s->vcol);
+    cudaStreamSynchronize(s->stream);
+    cudaFree(tmp);
+    return rc;
+  }
   GW_TRY_INTERNAL(stage_vrow(s, V, nk * nk, nullptr, s->vrow));
   return stage_vcol(s, V, nk * nk, nullptr, s->vcol);
 }
+
+namespace {
+
+// Per-q V slices of one pair table: from V through the table, or from the blocks unpacked
+// out of a packed V into the scratch.
+int stage_q(MixedState* s, int table, int q, bool col, const Planes& P) {
+  const int nk = s->d.nk;
+  if (s->Vp) {
+    VPairs L;
+    L.tab = tab(s, table, q);
+    GW_TRY_INTERNAL(unpack_v_fp64(s->Vp, nk, s->d.nao, s->pair, L, nk, s->vscratch, s->stream));
+    return col ? stage_vcol(s, s->vscratch, nk, nullptr, P) : stage_vrow(s, s->vscratch, nk, nullptr, P);
+  }
+  return col ? stage_vcol(s, s->V, nk, tab(s, table, q), P) : stage_vrow(s, s->V, nk, tab(s, table, q), P);
+}
+
+}  // namespace
 
 int mixed_polarization(MixedState* s, const double2* G, double2* P0t, double spin_factor) {
   GW_TRY_INTERNAL(slice_g(s, G));
@@ -1265,8 +1303,8 @@ int mixed_polarization(MixedState* s, const double2* G, double2* P0t, double spi
     const int mq = s->d.mq[q];
     const int tend = mq < q ? 0 : (mq == q ? (s->d.ntau + 1) / 2 : s->d.ntau);
     if (tend > 0 && s->per_q) {
-      GW_TRY_INTERNAL(stage_vrow(s, s->V, s->d.nk, tab(s, E_KKPQ, q), s->vq[0]));
-      GW_TRY_INTERNAL(stage_vrow(s, s->V, s->d.nk, tab(s, E_KPQK, q), s->vq[1]));
+      GW_TRY_INTERNAL(stage_q(s, E_KKPQ, q, false, s->vq[0]));
+      GW_TRY_INTERNAL(stage_q(s, E_KPQK, q, false, s->vq[1]));
     }
     // equal batches of at most nt nodes (no short last batch that would leave the GPU half idle)
     const int nb = (tend + s->nt - 1) / s->nt;
@@ -1285,8 +1323,8 @@ int mixed_self_energy(MixedState* s, const double2* G, const double2* Pt, double
   const int nb = (s->d.ntau + s->nt - 1) / s->nt;      // equal batches of at most nt nodes
   for (int q = 0; q < s->d.nk; ++q) {
     if (s->per_q) {
-      GW_TRY_INTERNAL(stage_vrow(s, s->V, s->d.nk, tab(s, E_KKMQ, q), s->vq[0]));
-      GW_TRY_INTERNAL(stage_vcol(s, s->V, s->d.nk, tab(s, E_KMQK, q), s->vcq));
+      GW_TRY_INTERNAL(stage_q(s, E_KKMQ, q, false, s->vq[0]));
+      GW_TRY_INTERNAL(stage_q(s, E_KMQK, q, true, s->vcq));
     }
     for (int i = 0; i < nb; ++i) {
       const int t0 = (int)((long long)s->d.ntau * i / nb), t1 = (int)((long long)s->d.ntau * (i + 1) / nb);

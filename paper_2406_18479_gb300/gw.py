@@ -50,6 +50,7 @@ class gw_config(ctypes.Structure):
         ("nk", ctypes.c_int * 3), ("nao", ctypes.c_int), ("naux", ctypes.c_int), ("ntau", ctypes.c_int),
         ("beta", ctypes.c_double), ("mu", ctypes.c_double), ("spin_factor", ctypes.c_double),
         ("precision", ctypes.c_int), ("tau_chunk", ctypes.c_int), ("v_slices", ctypes.c_int),
+        ("v_packed", ctypes.c_int),
     ]
 
 
@@ -201,7 +202,7 @@ class gw_ctx:
     """Owner of one gw_ctx* (gw_create ... gw_destroy)."""
 
     def __init__(self, nk3, nao, naux, ntau, beta, mu=0.0, spin_factor=2.0, precision="fp64",
-                 tau_chunk=0, v_slices=0, stream=None):
+                 tau_chunk=0, v_slices=0, stream=None, v_packed=False):
         import torch
         self.nk3 = tuple(int(x) for x in nk3)
         self.nk = int(np.prod(self.nk3))
@@ -210,8 +211,9 @@ class gw_ctx:
         self.nwb = gw_sample_count(ntau, 0)
         self.nwf = gw_sample_count(ntau, 1)
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.v_packed = int(v_packed)
         cfg = gw_config((ctypes.c_int * 3)(*self.nk3), self.nao, self.naux, self.ntau, self.beta,
-                        self.mu, float(spin_factor), prec, int(tau_chunk), int(v_slices))
+                        self.mu, float(spin_factor), prec, int(tau_chunk), int(v_slices), self.v_packed)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = ctypes.c_void_p()
         _check(lib().gw_create(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(self.stream.cuda_stream)))
@@ -226,7 +228,8 @@ class gw_ctx:
 
     def shapes(self):
         nk, nao, naux, ntau = self.nk, self.nao, self.naux, self.ntau
-        return {"V": (nk, nk, naux, nao, nao), "G": (nk, ntau, nao, nao), "H": (nk, nao, nao),
+        v = (nk * (nk + 1) // 2, naux, nao, nao) if self.v_packed else (nk, nk, naux, nao, nao)
+        return {"V": v, "G": (nk, ntau, nao, nao), "H": (nk, nao, nao),
                 "Pt": (nk, ntau, naux, naux), "Pw": (nk, self.nwb, naux, naux),
                 "Sig": (nk, ntau, nao, nao)}
 
@@ -373,10 +376,10 @@ def gw_polarization_noalloc(nk3, nao, naux, ntau, spin_factor, V, G, P0t, stream
 
 
 def make_config(nk3, nao, naux, ntau, beta, mu=0.0, spin_factor=2.0, precision="fp64", tau_chunk=0,
-                v_slices=0):
+                v_slices=0, v_packed=False):
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     return gw_config((ctypes.c_int * 3)(*[int(x) for x in nk3]), int(nao), int(naux), int(ntau), float(beta),
-                     float(mu), float(spin_factor), prec, int(tau_chunk), int(v_slices))
+                     float(mu), float(spin_factor), prec, int(tau_chunk), int(v_slices), int(bool(v_packed)))
 
 
 def gw_job_bytes(cfg: gw_config) -> int:
@@ -418,7 +421,8 @@ class gw_server:
                mu_hi=5.0, mu_tol=1e-10, diis_kind="diis", method="gw") -> int:
         nk = cfg.nk[0] * cfg.nk[1] * cfg.nk[2]
         nao, naux, ntau = cfg.nao, cfg.naux, cfg.ntau
-        job = gw_job(cfg, _host(H, (nk, nao, nao), "H"), _host(V, (nk, nk, naux, nao, nao), "V"),
+        vshape = (nk * (nk + 1) // 2, naux, nao, nao) if cfg.v_packed else (nk, nk, naux, nao, nao)
+        job = gw_job(cfg, _host(H, (nk, nao, nao), "H"), _host(V, vshape, "V"),
                      _host(G0, (nk, ntau, nao, nao), "G0"),
                      None if Sigma_out is None else _host(Sigma_out, (nk, ntau, nao, nao), "Sigma_out", True),
                      None if G_out is None else _host(G_out, (nk, ntau, nao, nao), "G_out", True),

@@ -196,3 +196,9 @@ def serving_stream(n: int = 200, seed: int = 5):
                          seed=seed * 1000 + i, solid=True)
         out.append((gap, w))
     return out
+
+
+def pack_v(v: np.ndarray) -> np.ndarray:
+    """The pairs k1 <= k2 of V[k1][k2] in row order of the upper triangle (the packed layout)."""
+    nk = v.shape[0]
+    return np.ascontiguousarray(np.stack([v[a, b] for a in range(nk) for b in range(a, nk)]))
