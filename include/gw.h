@@ -425,13 +425,15 @@ int gw_batch_autotune(gw_batch* batch, const gw_c128* const* G_dev, gw_c128* con
 int gw_batch_synchronize(gw_batch* batch);
 
 /*
- * Request loop for scGW jobs (self-consistency loop of Sec. 2.4 at fixed mu).
+ * Request loop for scGW jobs (the self-consistency loop of Sec. 2.4, gw_scgw).
  *
- * A job runs, on its own CUDA stream and device buffers:
+ * A job runs gw_scgw on its own context, CUDA stream and device buffers, with the options
+ * in gw_job: with the loop options all zero, at fixed mu without the static part,
  *   it = 1:  Sigma = Sigma[G0]                              (gw_sigma_eval)
- *   it > 1:  Sigma <- alpha Sigma[G] + (1 - alpha) Sigma     (gw_mix, Sec. 5.3)
+ *   it > 1:  Sigma <- alpha Sigma[G] + (1 - alpha) Sigma     (iteration mixing, Sec. 5.3)
  *   then     G = Dyson(H, Sigma)                            (gw_dyson_G, Eq. dyson)
- * and stops when max |dSigma| < tol (it > 1) or after itermax evaluations.
+ * and stops when max |dSigma| < tol (it > 1) or after itermax evaluations; the options add
+ * the static part, the mu search, DIIS or CDIIS, and GF2 in place of GW.
  *
  * gw_server_create starts max_slots worker threads on the current device. A
  * submitted job waits in arrival order until a slot is free and its device
@@ -445,7 +447,7 @@ typedef struct gw_server gw_server;
 typedef struct {
   gw_config cfg;              /* sizes, beta, mu, spin factor, precision, tau chunk */
   const gw_c128* H_host;      /* [nk][nao][nao] */
-  const gw_c128* V_host;      /* [nk][nk][naux][nao][nao] */
+  const gw_c128* V_host;      /* [nk][nk][naux][nao][nao], or packed with cfg.v_packed */
   const gw_c128* G0_host;     /* [nk][ntau][nao][nao], the starting Green's function */
   gw_c128* Sigma_out_host;    /* [nk][ntau][nao][nao] final Sigma, or NULL */
   gw_c128* G_out_host;        /* [nk][ntau][nao][nao] final G, or NULL */
