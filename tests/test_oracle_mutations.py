@@ -189,3 +189,32 @@ def test_planted_gf2_mistake_is_caught(monkeypatch, kw, pin):
             GP.test_one_spin_orbital_has_no_second_order_term(3)
         else:
             GP.test_against_four_index_brute_force((2, 1, 1))
+
+
+# ---- k-space interpolation --------------------------------------------------------------------
+
+@pytest.mark.parametrize("mistake", ["forward_sign", "no_boundary_split"])
+def test_planted_kinterp_mistake_is_caught(monkeypatch, mistake):
+    import itertools
+    import test_oracle_kinterp_pins as KP
+    from oracle import kinterp
+
+    real_vectors = kinterp.lattice_vectors
+    if mistake == "forward_sign":
+        def interp(X, nk3, f_new):           # e^{+i k R} in the forward transform
+            fk = kinterp.mesh_fractions(nk3)
+            out = np.zeros((len(f_new),) + X.shape[1:], complex)
+            for R, w in real_vectors(nk3):
+                XR = np.tensordot(np.exp(+2j * np.pi * fk @ R), X, axes=(0, 0)) / fk.shape[0]
+                out += w * np.exp(2j * np.pi * np.asarray(f_new) @ R)[(slice(None),) + (None,) * (X.ndim - 1)] * XR
+            return out
+        monkeypatch.setattr(kinterp, "k_interpolate", interp)
+        with pytest.raises(AssertionError):
+            KP.test_one_sided_hopping_is_reproduced((3, 3, 1))
+    else:
+        def vectors(nk3):
+            axes = [list(range(-(n // 2), (n - 1) // 2 + 1)) for n in nk3]   # boundary taken once, at -N/2
+            return [(np.array(c), 1.0) for c in itertools.product(*axes)]
+        monkeypatch.setattr(kinterp, "lattice_vectors", vectors)
+        with pytest.raises(AssertionError):
+            KP.test_nearest_neighbour_hamiltonian((2, 2, 2))
