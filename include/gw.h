@@ -306,6 +306,21 @@ int gw_sigma_inf(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* SigInf_dev);
 int gw_commutator_residual(gw_ctx* ctx, const gw_c128* H_dev, const gw_c128* SigInf_dev, const gw_c128* Sig_dev,
                            const gw_c128* G_dev, gw_c128* e_dev);
 
+/*
+ * Wannier-like k-space interpolation (Sec. 2.5, without the maximally localised basis):
+ *   X(R) = (1/N_k) sum_k X(k) e^{-i k R},   X(k') = sum_R w_R X(R) e^{i k' R},
+ * k on the nk3 Gamma-centred mesh (flat order as everywhere), k' = 2 pi f' for the nkf
+ * fractional coordinates f_host [nkf][3] (host, any values). R runs over the lattice vectors
+ * nearest the origin, R_d in [-N_d/2, N_d/2]; for even N_d the two boundary vectors share one
+ * term (w = 1/2 each, weights multiply over directions), so the interpolation is exact on the
+ * mesh. X_dev [nk][nelem] -> Xf_dev [nkf][nelem] (any per-k block: Sigma~ [ntau][nao][nao],
+ * Sigma^inf [nao][nao], ...), FP64, on cuda_stream (stream-ordered; no context needed). The
+ * paper interpolates Sigma^inf and Sigma~ this way and evaluates H on the finer k set directly,
+ * then solves the Dyson equation there (gw_dyson_G on a context whose nk equals nkf).
+ */
+int gw_k_interpolate(const int nk3[3], const gw_c128* X_dev, long long nelem, int nkf, const double* f_host,
+                     gw_c128* Xf_dev, void* cuda_stream);
+
 /* Sets the chemical potential used by gw_dyson_G. */
 int gw_set_mu(gw_ctx* ctx, double mu);
 

@@ -33,7 +33,7 @@ ABI_SYMBOLS = [
     "gw_batch_set_coulomb", "gw_batch_sigma_eval", "gw_batch_autotune", "gw_batch_synchronize",
     "gw_density", "gw_sigma_inf", "gw_set_mu", "gw_particle_number", "gw_find_mu", "gw_diis_create",
     "gw_diis_destroy", "gw_diis_push", "gw_diis_extrapolate", "gw_scgw_bytes", "gw_scgw", "gw_diis_push_residual",
-    "gw_commutator_residual", "gw_gf2_self_energy", "gw_gf2_exchange",
+    "gw_commutator_residual", "gw_gf2_self_energy", "gw_gf2_exchange", "gw_k_interpolate",
 ]
 GW_BATCH_SERIAL, GW_BATCH_STREAMS, GW_BATCH_GRAPH = 0, 1, 2
 BATCH_MODES = {"serial": GW_BATCH_SERIAL, "streams": GW_BATCH_STREAMS, "graph": GW_BATCH_GRAPH}
@@ -150,6 +150,7 @@ def lib():
     L.gw_commutator_residual.argtypes = [vp, vp, vp, vp, vp, vp]
     L.gw_gf2_self_energy.argtypes = [vp, vp, vp]
     L.gw_gf2_exchange.argtypes = [vp, vp, vp]
+    L.gw_k_interpolate.argtypes = [ctypes.POINTER(i), vp, ctypes.c_longlong, i, ctypes.POINTER(d), vp, vp]
     L.gw_diis_destroy.argtypes = [vp]
     L.gw_diis_push.argtypes = [vp, vp, vp]
     L.gw_diis_extrapolate.argtypes = [vp, vp, ctypes.POINTER(d), ctypes.POINTER(i)]
@@ -643,3 +644,17 @@ def gw_scgw(ctx: gw_ctx, H, G, Sigma=None, SigInf=None, opt: gw_scgw_options = N
         ctx.mu = r.mu
     return rc, {"iterations": r.iterations, "max_abs_dsigma": r.max_abs_dsigma, "mu": r.mu,
                 "n_electrons": r.n_electrons}
+
+
+def gw_k_interpolate(nk3, X, f, Xf, stream=None):
+    """X [nk][...] on the nk3 mesh -> Xf [len(f)][...] at the fractional k coordinates f [nkf][3]."""
+    import torch
+    nk = int(np.prod(nk3))
+    if X.shape[0] != nk or Xf.shape[0] != len(f) or tuple(X.shape[1:]) != tuple(Xf.shape[1:]):
+        raise GWError(GW_EINVAL, "gw_k_interpolate: shapes do not match")
+    fa = np.ascontiguousarray(np.asarray(f, dtype=np.float64).reshape(-1, 3))
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(lib().gw_k_interpolate((ctypes.c_int * 3)(*[int(x) for x in nk3]), _ptr(X),
+                                  ctypes.c_longlong(X[0].numel() if nk else 0), int(len(fa)),
+                                  fa.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(Xf),
+                                  ctypes.c_void_p(st.cuda_stream)))
