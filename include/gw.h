@@ -386,7 +386,8 @@ typedef struct {
   double mu_lo, mu_hi, mu_tol;   /* bracket and tolerance of that search */
   int diis_kind;              /* 0: residual F_i - Sigma_{i-1}; 1: commutator (gw_commutator_residual
                                  of G_{i-1} and F_i) */
-  int method;                 /* dynamic self-energy: 0 GW (gw_sigma_eval), 1 GF2 (gw_gf2_self_energy) */
+  int method;                 /* dynamic self-energy: 0 GW (gw_sigma_eval), 1 GF2 (gw_gf2_self_energy),
+                                 2 none (Hartree-Fock: Sigma~ = 0, use with static_part = 1) */
 } gw_scgw_options;
 
 typedef struct {

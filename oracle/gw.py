@@ -287,8 +287,8 @@ def scgw_full(H, V, G0, nk3, beta, mu, spin_factor=2.0, alpha=0.5, tol=1e-6, ite
     """The self-consistency loop of Sec. 2.4 with its four steps per iteration n:
 
       (1) the static part Sigma^inf[G_{n-1}] (Eq. sigma_inf; left out when static is False) and
-          the dynamic part Sigma~[G_{n-1}] (Eq. sigma_gw, or Eq. sigma2 with method "gf2") --
-          together the output F_n;
+          the dynamic part Sigma~[G_{n-1}] (Eq. sigma_gw, Eq. sigma2 with method "gf2", zero with
+          method "hf") -- together the output F_n;
       (2) acceleration (Sec. 5.3): Sigma_1 = F_1; afterwards iteration mixing
           Sigma_n = alpha F_n + (1 - alpha) Sigma_{n-1}, or, with diis_size > 0, Pulay's
           extrapolation over the newest diis_size pairs (Sigma_{i-1}, F_i) from iteration
@@ -312,6 +312,8 @@ def scgw_full(H, V, G0, nk3, beta, mu, spin_factor=2.0, alpha=0.5, tol=1e-6, ite
         if method == "gf2":
             from .gf2 import gf2_self_energy
             sdyn = gf2_self_energy(V, G, nk3, spin_factor)
+        elif method == "hf":
+            sdyn = np.zeros_like(G)                 # Hartree-Fock: the static part alone
         else:
             sdyn = sigma_eval(V, G, nk3, beta, spin_factor)["Sig"]
         out = np.concatenate([sinf.ravel(), sdyn.ravel()])

@@ -1,4 +1,5 @@
-// The self-consistency loop of Sec. 2.4 on one context: static and dynamic (GW or GF2) self-energy,
+// The self-consistency loop of Sec. 2.4 on one context: static and dynamic (GW, GF2, or none for
+// Hartree-Fock) self-energy,
 // acceleration (iteration mixing, or DIIS with the difference or the commutator residual,
 // Sec. 5.3), the chemical-potential search and
 // the Dyson update, until max |Sigma_n - Sigma_{n-1}| < tol.
@@ -45,7 +46,7 @@ int gw_scgw(gw_ctx* ctx, const gw_c128* H_dev, gw_c128* G_dev, gw_c128* Sigma_de
   if (!ctx || !H_dev || !G_dev || !o || !res) return fail(GW_EINVAL, "gw_scgw: null argument");
   if (!(o->alpha > 0.0 && o->alpha < 2.0) || !(o->tol >= 0.0) || o->itermax < 1 || o->diis_size < 0 ||
       o->diis_size > 16 || (o->diis_size > 0 && o->diis_start < 2) || o->diis_kind < 0 || o->diis_kind > 1 ||
-      o->method < 0 || o->method > 1 ||
+      o->method < 0 || o->method > 2 ||
       (o->n_electrons > 0.0 && !(o->mu_lo < o->mu_hi && o->mu_tol > 0.0)))
     return fail(GW_EINVAL, "gw_scgw: options out of range");
   const CtxInfo ci = ctx_info(ctx);
@@ -86,8 +87,12 @@ int gw_scgw(gw_ctx* ctx, const gw_c128* H_dev, gw_c128* G_dev, gw_c128* Sigma_de
     for (it = 1; it <= o->itermax; ++it) {
       // (1) the output F_n of G_{n-1}
       if (o->static_part && (rc = gw_sigma_inf(ctx, G_dev, reinterpret_cast<gw_c128*>(F))) != GW_OK) break;
-      rc = o->method == 1 ? gw_gf2_self_energy(ctx, G_dev, reinterpret_cast<gw_c128*>(F + nst))
-                          : gw_sigma_eval(ctx, G_dev, reinterpret_cast<gw_c128*>(F + nst));
+      if (o->method == 2)        // Hartree-Fock: no dynamic part
+        rc = cudaMemsetAsync(F + nst, 0, ndyn * cb, st) == cudaSuccess ? GW_OK : fail(GW_ECUDA, "gw_scgw: memset");
+      else if (o->method == 1)
+        rc = gw_gf2_self_energy(ctx, G_dev, reinterpret_cast<gw_c128*>(F + nst));
+      else
+        rc = gw_sigma_eval(ctx, G_dev, reinterpret_cast<gw_c128*>(F + nst));
       if (rc != GW_OK) break;
       // (2) Sigma_n from F_n and the history
       if (it == 1) {

@@ -592,7 +592,7 @@ class gw_diis:
 
 
 DIIS_KINDS = {"diis": 0, "cdiis": 1}
-METHODS = {"gw": 0, "gf2": 1}
+METHODS = {"gw": 0, "gf2": 1, "hf": 2}
 
 
 def _code(table, x):

@@ -282,7 +282,7 @@ def test_scgw_rejects_bad_options(G):
     ctx = G.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision="fp64")
     G.gw_set_coulomb(ctx, dev(v))
     for bad in (dict(alpha=2.0), dict(itermax=0), dict(diis_size=17), dict(diis_size=2, diis_start=1),
-                dict(n_electrons=3.0, mu_lo=1.0, mu_hi=0.0), dict(diis_size=2, diis_kind=2)):
+                dict(n_electrons=3.0, mu_lo=1.0, mu_hi=0.0), dict(diis_size=2, diis_kind=2), dict(method=3)):
         with pytest.raises(G.GWError) as e:
             G.gw_scgw(ctx, dev(h), dev(g), None, None, G.scgw_options(**bad))
         assert e.value.code == G.GW_EINVAL
@@ -329,3 +329,25 @@ def test_diis_with_explicit_residuals(G):
         d.push(dev(outs[0]), dev(outs[1]))            # difference residuals need n_residual = 0
     assert e.value.code == G.GW_EINVAL
     d.destroy()
+
+
+def test_hartree_fock_loop_matches_oracle(G):
+    w, h, v, g = loop_case()
+    ref = O.scgw_full(h, v, g, w.nk3, w.beta, 0.0, alpha=0.7, tol=1e-11, itermax=200, n_electrons=3.0,
+                      mu_lo=-4.0, mu_hi=4.0, mu_tol=1e-13, diis_size=5, method="hf")
+    ctx = G.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision="fp64")
+    vd = dev(v)
+    G.gw_set_coulomb(ctx, vd)
+    Gd = dev(g)
+    S = torch.empty(ctx.shapes()["Sig"], dtype=torch.complex128, device="cuda")
+    Sinf = torch.empty((w.nk, w.nao, w.nao), dtype=torch.complex128, device="cuda")
+    opt = G.scgw_options(alpha=0.7, tol=1e-11, itermax=200, diis_size=5, n_electrons=3.0, mu_lo=-4.0, mu_hi=4.0,
+                         mu_tol=1e-13, method="hf")
+    rc, r = G.gw_scgw(ctx, dev(h), Gd, S, Sinf, opt)
+    assert rc == G.GW_OK
+    assert abs(r["iterations"] - ref["iterations"]) <= 1
+    assert abs(r["mu"] - ref["mu"]) < 1e-9
+    assert not torch.any(S)
+    assert np.abs(host(Sinf) - ref["SigInf"]).max() < 1e-9
+    assert np.abs(host(Gd) - ref["G"]).max() < 1e-9
+    ctx.destroy()

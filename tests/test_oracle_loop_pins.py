@@ -175,3 +175,18 @@ def test_cdiis_loop_reaches_the_same_fixed_point():
     assert b["iterations"] < a["iterations"]
     e = O.commutator_residual(h, b["SigInf"], b["Sig"], b["G"], w.beta)
     assert np.abs(e).max() < 1e-8
+
+
+def test_hartree_fock_loop_fixed_point_is_a_fermi_matrix():
+    """With Sigma~ = 0 the converged G is non-interacting in H + Sigma^inf: its density matrix is
+    U f(eps - mu) U^dagger of that matrix, Sigma^inf is the one of this density, and N = n."""
+    w, h, v, g = loop_case()
+    r = O.scgw_full(h, v, g, w.nk3, w.beta, 0.0, alpha=0.7, tol=1e-11, itermax=200, n_electrons=3.0,
+                    mu_tol=1e-13, diis_size=5, method="hf")
+    assert r["hist"][-1] < 1e-11 and not np.any(r["Sig"])
+    gam = O.density_matrix(r["G"], w.beta)
+    for k in range(w.nk):
+        e, u = np.linalg.eigh(h[k] + r["SigInf"][k])
+        assert np.abs(gam[k] - (u * fermi(e - r["mu"], w.beta)) @ u.conj().T).max() < 1e-9
+    assert np.abs(O.sigma_inf(v, gam, w.nk3, 2.0) - r["SigInf"]).max() < 1e-9
+    assert abs(O.particle_number(gam, 2.0) - 3.0) < 1e-9
