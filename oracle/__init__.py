@@ -13,10 +13,11 @@ can be checked against the paper by eye:
             the static part (Eq. sigma_inf), the mu search, DIIS/CDIIS and the full loop
   gf2.py    the second-order self-energy (Eq. sigma2)
   kinterp.py  the Wannier-like k-space interpolation (Sec. 2.5)
+  ir.py     intermediate-representation tau grids and transforms (the paper's Lambda = 1e4 grids)
 
 Parity status: every function is pinned (tests/test_oracle_pins.py,
 tests/test_oracle_loop_pins.py, tests/test_oracle_gf2_pins.py,
-tests/test_oracle_kinterp_pins.py) against
+tests/test_oracle_kinterp_pins.py, tests/test_oracle_ir_pins.py) against
 closed forms, brute force with 4-index integrals, the pole-pair sum and
 invariants. No function is "parity unpinned".
 """
