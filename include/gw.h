@@ -138,6 +138,25 @@ int gw_destroy(gw_ctx* ctx);
 size_t gw_workspace_bytes(const gw_ctx* ctx);
 
 /*
+ * Intermediate-representation (IR) grids for gw_set_grids (the paper runs on IR grids with
+ * Lambda = beta omega_max = 1e4; its grid files are not available and are built here, on the
+ * host): the basis u_l(tau) = sqrt(2/beta) U_l(2 tau / beta - 1) of the singular value
+ * expansion of the logistic kernel exp(-Lambda y (x + 1) / 2) / (1 + exp(-Lambda y)), the
+ * L = *ntau_out functions with s_l / s_0 > eps; tau nodes at the L roots of U_L (mirror
+ * symmetric); Matsubara samples where the transform of u_L changes sign, mirrored and trimmed
+ * or padded to gw_sample_count(L, stat) (padding by the smallest ||F||_F ||F^+||_F);
+ * F = u^(samples) U_tau^{-1} maps node values to Matsubara values, B is its least-squares
+ * left inverse. Both statistics share the tau nodes. Output layouts as gw_set_grids takes
+ * them, for T = L, nb = gw_sample_count(T, 0), nf = gw_sample_count(T, 1): tau [T],
+ * Fb [nb][T], Bb [T][nb], Ff [nf][T], Bf [T][nf], omega_b [nb], omega_f [nf] (host buffers of
+ * at least those sizes for T = cap; omega_* may be NULL). tau_host = NULL: only *ntau_out.
+ * 1 <= lambda <= 1e6, 1e-15 <= eps <= 1e-2; GW_EINVAL if L > cap. Seconds of host time at
+ * Lambda = 1e4 (one SVD per call).
+ */
+int gw_ir_grids(double beta, double lambda, double eps, int cap, int* ntau_out, double* tau_host, gw_c128* Fb_host,
+                gw_c128* Bb_host, gw_c128* Ff_host, gw_c128* Bf_host, double* omega_b_host, double* omega_f_host);
+
+/*
  * Replaces the context's grids (built by gw_create from the Chebyshev interpolant, see
  * gw_grid_build) with the caller's, for example transforms of another basis (the paper's
  * grid files, Sec. 2.3 and Eq. P0t_to_P0w). Host arrays, copied; sizes as gw_create made

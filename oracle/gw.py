@@ -127,16 +127,20 @@ def sigma_eval(V, G, nk3, beta, spin_factor=2.0):
     return {"P0t": P0t, "P0w": P0w, "Pw": Pw, "Pt": Pt, "Sig": Sig}
 
 
-def dyson_G(H, Sig, mu, beta):
+def dyson_G(H, Sig, mu, beta, fermionic=None):
     """Dyson equation, Eq. (dyson), with S = I and Sigma^inf = 0:
 
       G^k(i w_n) = [(i w_n + mu) I - H^k - Sigma^k(i w_n)]^{-1},
 
-    Sigma(i w_n) = F^f Sigma(tau), G(tau) = B^f G(i w_n) on the fermionic grid.
+    Sigma(i w_n) = F^f Sigma(tau), G(tau) = B^f G(i w_n) on the fermionic grid: the Chebyshev
+    one, or fermionic = (w_n, F^f, B^f) given (another tau grid, e.g. an IR grid).
     """
     nk, ntau, nao, _ = Sig.shape
-    m, Ff, Bf = grids.transform_matrices(ntau, beta, 1)
-    wn = (2 * m + 1) * np.pi / beta
+    if fermionic is None:
+        m, Ff, Bf = grids.transform_matrices(ntau, beta, 1)
+        wn = (2 * m + 1) * np.pi / beta
+    else:
+        wn, Ff, Bf = fermionic
     Sw = to_matsubara(Sig, Ff)
     Gw = np.empty_like(Sw)
     eye = np.eye(nao)

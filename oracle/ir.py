@@ -17,7 +17,8 @@ side of smaller magnitude, mirrored (fermionic n -> -n-1, bosonic n -> -n), and 
 the top, or padded (one point at a time: a gap's log-midpoint or half again beyond the last,
 whichever gives the smallest ||F||_F ||F^+||_F) to the count of the library's symmetric sets (ntau, or
 ntau + 1 when the parity differs). F = u^(samples) U_tau^{-1} maps node values to Matsubara
-values, B is its least-squares left inverse.
+values, B is its least-squares left inverse; for bosons F[nw-1-n][L-1-t] = F[n][t] (and the same
+for B) is imposed exactly.
 """
 from __future__ import annotations
 
@@ -180,5 +181,9 @@ def ir_grid(beta, lam, eps, stat):
         m = full(sel)
     m = np.array(m)
     F = transform(m)
+    if stat == 0:        # F[nw-1-n][L-1-t] = F[n][t] exactly (it holds to rounding amplified by U_tau^-1)
+        F = 0.5 * (F + F[::-1, ::-1])
     B = np.linalg.pinv(F, rcond=1e-14)
+    if stat == 0:
+        B = 0.5 * (B + B[::-1, ::-1])
     return tau, m, F, B

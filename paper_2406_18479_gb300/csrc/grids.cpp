@@ -90,7 +90,7 @@ static void gauss_legendre20(double* x, double* w) {
 }
 
 // Householder QR least-squares left inverse of A (m x n, m >= n, row-major).
-static bool lsq_left_inverse(const std::vector<cd>& A_in, int m, int n, std::vector<cd>& Binv) {
+bool lsq_left_inverse(const std::vector<cd>& A_in, int m, int n, std::vector<cd>& Binv) {
   std::vector<cd> A = A_in;                  // m x n
   std::vector<cd> Qt(m * (size_t)m, 0.0);    // accumulates Q^H, m x m
   for (int i = 0; i < m; ++i) Qt[(size_t)i * m + i] = 1.0;

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdint>
 #include <string>
+#include <complex>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -13,6 +14,8 @@ namespace gwi {
 
 // ---- host utilities (grids.cpp, errors in gw_api.cu)
 int sample_count(int ntau, int stat);
+// Householder QR least-squares left inverse of A (m x n, m >= n, row-major complex): B A = I
+bool lsq_left_inverse(const std::vector<std::complex<double>>& A, int m, int n, std::vector<std::complex<double>>& B);
 std::vector<int64_t> matsubara_indices(int n, int stat);
 int grid_build(int ntau, double beta, int stat, double* tau, int64_t* idx, gw_c128* F, gw_c128* B);
 int fail(int code, const char* fmt, ...);

@@ -33,7 +33,7 @@ ABI_SYMBOLS = [
     "gw_batch_set_coulomb", "gw_batch_sigma_eval", "gw_batch_autotune", "gw_batch_synchronize",
     "gw_density", "gw_sigma_inf", "gw_set_mu", "gw_particle_number", "gw_find_mu", "gw_diis_create",
     "gw_diis_destroy", "gw_diis_push", "gw_diis_extrapolate", "gw_scgw_bytes", "gw_scgw", "gw_diis_push_residual",
-    "gw_commutator_residual", "gw_gf2_self_energy", "gw_gf2_exchange", "gw_k_interpolate",
+    "gw_commutator_residual", "gw_gf2_self_energy", "gw_gf2_exchange", "gw_k_interpolate", "gw_ir_grids",
 ]
 GW_BATCH_SERIAL, GW_BATCH_STREAMS, GW_BATCH_GRAPH = 0, 1, 2
 BATCH_MODES = {"serial": GW_BATCH_SERIAL, "streams": GW_BATCH_STREAMS, "graph": GW_BATCH_GRAPH}
@@ -150,6 +150,7 @@ def lib():
     L.gw_commutator_residual.argtypes = [vp, vp, vp, vp, vp, vp]
     L.gw_gf2_self_energy.argtypes = [vp, vp, vp]
     L.gw_gf2_exchange.argtypes = [vp, vp, vp]
+    L.gw_ir_grids.argtypes = [d, d, d, i, ctypes.POINTER(i), vp, vp, vp, vp, vp, vp, vp]
     L.gw_k_interpolate.argtypes = [ctypes.POINTER(i), vp, ctypes.c_longlong, i, ctypes.POINTER(d), vp, vp]
     L.gw_diis_destroy.argtypes = [vp]
     L.gw_diis_push.argtypes = [vp, vp, vp]
@@ -658,3 +659,21 @@ def gw_k_interpolate(nk3, X, f, Xf, stream=None):
                                   ctypes.c_longlong(X[0].numel() if nk else 0), int(len(fa)),
                                   fa.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), _ptr(Xf),
                                   ctypes.c_void_p(st.cuda_stream)))
+
+
+def gw_ir_grids(beta, lam=1e4, eps=1e-10):
+    """IR grids (see include/gw.h): (tau, Fb, Bb, Ff, Bf, omega_f, omega_b) in the argument order of
+    gw_set_grids(ctx, tau, Fb, Bb, Ff, Bf, omega_f, omega_b); len(tau) is the ntau of the context."""
+    n = ctypes.c_int(0)
+    _check(lib().gw_ir_grids(float(beta), float(lam), float(eps), 0, ctypes.byref(n), None, None, None, None, None,
+                             None, None))
+    T = n.value
+    nb, nf = gw_sample_count(T, 0), gw_sample_count(T, 1)
+    tau = np.zeros(T)
+    Fb, Bb = np.zeros((nb, T), complex), np.zeros((T, nb), complex)
+    Ff, Bf = np.zeros((nf, T), complex), np.zeros((T, nf), complex)
+    wb, wf = np.zeros(nb), np.zeros(nf)
+    p = lambda a: ctypes.c_void_p(a.ctypes.data)
+    _check(lib().gw_ir_grids(float(beta), float(lam), float(eps), T, ctypes.byref(n), p(tau), p(Fb), p(Bb), p(Ff),
+                             p(Bf), p(wb), p(wf)))
+    return tau, Fb, Bb, Ff, Bf, wf, wb
