@@ -79,7 +79,7 @@ const char* prof_slot_name(int slot) {
   static const char* names[SLOT_COUNT] = {
       "vg_fp64", "p0_gemm_fp64", "r_gemm_fp64", "sigma_gemm_fp64", "transform_fp64", "inverse_fp64",
       "elementwise", "slice_planes", "vg_gemm_tc", "p0_gemm_tc", "r_gemm_tc", "sigma_gemm_tc", "reduce",
-      "static_fp64", "gf2_exchange_fp64"};
+      "static_fp64", "gf2_exchange_fp64", "gf2_outer_tc"};
   return (slot >= 0 && slot < SLOT_COUNT) ? names[slot] : "";
 }
 
@@ -975,9 +975,16 @@ static int gf2_exchange(gw_ctx* c, const double2* G, double2* S, double alpha) {
           GW_TRY(vg(vb[0], G + ((long long)k1 * T + t0) * n2, n2, m, A));
           GW_TRY(vg(vb[1], G + ((long long)k3 * T + (T - 1 - t0)) * n2, -n2, m, D));
           GW_TRY(vg(vb[2], G + ((long long)k2 * T + t0) * n2, n2, m, B));
-          GW_TRY(outer_q(A, B, pair, m, Y));                                            // Y = sum_Q A B
-          GW_TRY(outer_q(D, vb[3], 0, m, W));                                           // W = sum_R D V
-          {  // part[t][q][i][j] = sum_{(m l)} Y[t][(i q)][(m l)] W[t][(q m)][(l j)], batch (t, q)
+          if (c->mixed) {   // the two nao^4 naux products on the tensor cores
+            GW_TRY(mixed_outer_q(c->mixed, A, pair, B, pair, m, (int)n2, Y, n4));
+            GW_TRY(mixed_outer_q(c->mixed, D, pair, vb[3], 0, m, (int)n2, W, n4));
+          } else {
+            GW_TRY(outer_q(A, B, pair, m, Y));                                          // Y = sum_Q A B
+            GW_TRY(outer_q(D, vb[3], 0, m, W));                                         // W = sum_R D V
+          }
+          if (c->mixed) {
+            GW_TRY(mixed_gf2_last(c->mixed, Y, W, m, nao, part));
+          } else {  // part[t][q][i][j] = sum_{(m l)} Y[t][(i q)][(m l)] W[t][(q m)][(l j)], batch (t, q)
             ZGemm g;
             g.M = nao;
             g.N = nao;

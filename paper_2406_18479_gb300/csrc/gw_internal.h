@@ -34,7 +34,7 @@ size_t job_device_bytes(const gw_config* cfg);
 enum ProfSlot {
   SLOT_VG_FP64 = 0, SLOT_P0_FP64, SLOT_R_FP64, SLOT_SIGMA_FP64, SLOT_TRANSFORM_FP64, SLOT_INVERSE_FP64,
   SLOT_ELEMENTWISE, SLOT_LIMBS, SLOT_VG_MIXED, SLOT_P0_TC, SLOT_R_TC, SLOT_SIGMA_MIXED, SLOT_REDUCE,
-  SLOT_STATIC_FP64, SLOT_GF2_FP64, SLOT_COUNT
+  SLOT_STATIC_FP64, SLOT_GF2_FP64, SLOT_GF2_TC, SLOT_COUNT
 };
 const char* prof_slot_name(int slot);
 void prof_begin(int slot, cudaStream_t s);

@@ -24,5 +24,12 @@ void mixed_destroy(MixedState* s);
 int mixed_set_coulomb(MixedState* s, const double2* V, const double2* Vp = nullptr);
 int mixed_polarization(MixedState* s, const double2* G, double2* P0t, double spin_factor);
 int mixed_self_energy(MixedState* s, const double2* G, const double2* Pt, double2* Sig);
+// out[b][(a c)][(d e)] = sum_Q X[b][Q][a][c] Z[b][Q][d][e] on the tensor cores (FP64 output), for nb
+// batches of n2 = nao^2 rows, K = naux; z_bs = 0: one Z for every batch.
+int mixed_outer_q(MixedState* s, const double2* X, long long x_bs, const double2* Z, long long z_bs, int nb,
+                  int n2, double2* out, long long out_bs);
+// part[b][q][i][j] = sum_{m l} Y[b][(i q)][(m l)] W[b][(q m)][(l j)] on the tensor cores (FP64 output):
+// the last product of the GF2 exchange, split over q, for nb batches.
+int mixed_gf2_last(MixedState* s, const double2* Y, const double2* W, int nb, int nao, double2* part);
 
 }  // namespace gwi

@@ -885,6 +885,10 @@ struct MixedState {
   long long* rowtabs = nullptr;
   int* status = nullptr;
   int Kc_vg = 0, Kpad_vg = 0, Kc_p0 = 0, Kpad_p0 = 0, Kc_r = 0, Kpad_r = 0, Kc_s = 0, Kpad_s = 0;
+  __nv_bfloat16* oq_mem = nullptr;   // planes of mixed_outer_q (allocated on first use), oq_rows rows each
+  long long oq_rows = 0;
+  __nv_bfloat16* ol_mem = nullptr;   // planes of mixed_gf2_last (allocated on first use)
+  size_t ol_elems = 0;
   std::vector<void*> allocs;
   bool dry = false;   // size-only: count bytes, allocate nothing
 };
@@ -1295,6 +1299,108 @@ int stage_q(MixedState* s, int table, int q, bool col, const Planes& P) {
 }
 
 }  // namespace
+
+namespace {
+
+// (re)allocates a lazily sized plane buffer of at least elems bf16 values
+int ensure_mem(MixedState* s, __nv_bfloat16** mem, size_t* have, size_t elems) {
+  if (*have >= elems) return GW_OK;
+  if (*mem) {
+    cudaStreamSynchronize(s->stream);
+    cudaFree(*mem);
+    s->allocs.erase(std::find(s->allocs.begin(), s->allocs.end(), (void*)*mem));
+    *mem = nullptr;
+    *have = 0;
+  }
+  size_t bytes = 0;
+  GW_TRY_INTERNAL(m_alloc(s, mem, elems, &bytes));
+  *have = elems;
+  return GW_OK;
+}
+
+}  // namespace
+
+int mixed_gf2_last(MixedState* s, const double2* Y, const double2* W, int nb, int nao, double2* part) {
+  const int n2 = nao * nao;
+  int Kc = 0, Kpad = 0;
+  chunking(n2, &Kc, &Kpad);
+  const long long rows = (long long)nb * n2;              // (t, q, i) for A, (t, q, j) for B
+  const Planes shape = view(nullptr, rows, Kc, Kpad, 2);
+  GW_TRY_INTERNAL(ensure_mem(s, &s->ol_mem, &s->ol_elems, 2 * shape.elems()));
+  const Planes ys = view(s->ol_mem, rows, Kc, Kpad, 2);
+  const Planes ws = view(s->ol_mem + shape.elems(), rows, Kc, Kpad, 2);
+  const long long n3 = (long long)n2 * nao, n4 = (long long)n2 * n2;
+  {  // rows r = (q, i) of Y[t][(i q)][(m l)]: element (r, k) at (i nao + q) n2 + k
+    ZView v;
+    v.rin = nao;
+    v.rs_out = n2;
+    v.rs_in = (long long)nao * n2;
+    v.ks_in = 1;
+    GW_TRY_INTERNAL(slice(s, Y, v, n4, 0, 1 << 30, nb, n2, n2, ys, n2));
+  }
+  {  // rows r = (q, j) of W[t][(q m)][(l j)], k = (m, l): element at q n3 + m n2 + l nao + j
+    ZView v;
+    v.rin = nao;
+    v.rs_out = n3;
+    v.rs_in = 1;
+    v.kin = nao;
+    v.ks_out = n2;
+    v.ks_in = nao;
+    GW_TRY_INTERNAL(slice(s, W, v, n4, 0, 1 << 30, nb, n2, n2, ws, n2));
+  }
+  OzParams p;                     // part[t][q][i][j] = sum_{(m l)} Y_q[i][(m l)] W_q[(m l)][j], batch (t, q)
+  p.M = nao;
+  p.N = nao;
+  p.nbatch = nb * nao;
+  p.a_bs_in = nao;
+  p.b_bs_in = nao;
+  p.C = part;
+  p.vc.rs_in = nao;
+  p.vc.ks_in = 1;
+  p.bc.bs_in = n2;
+  p.status = s->status;
+  p.ws = s->ws;
+  return launch_oz(ys, ws, p, SLOT_GF2_TC, s->stream);
+}
+
+int mixed_outer_q(MixedState* s, const double2* X, long long x_bs, const double2* Z, long long z_bs, int nb,
+                  int n2, double2* out, long long out_bs) {
+  const int naux = s->d.naux;
+  const long long rows = (long long)nb * n2;
+  const Planes shape = view(nullptr, rows, s->Kc_r, s->Kpad_r, 2);
+  if (s->oq_rows < rows) {
+    if (s->oq_mem) {
+      cudaStreamSynchronize(s->stream);
+      cudaFree(s->oq_mem);
+      s->allocs.erase(std::find(s->allocs.begin(), s->allocs.end(), (void*)s->oq_mem));
+      s->oq_mem = nullptr;
+      s->oq_rows = 0;
+    }
+    size_t bytes = 0;
+    GW_TRY_INTERNAL(m_alloc(s, &s->oq_mem, 2 * shape.elems(), &bytes));
+    s->oq_rows = rows;
+  }
+  const Planes xs = view(s->oq_mem, rows, s->Kc_r, s->Kpad_r, 2);
+  const Planes zs = view(s->oq_mem + shape.elems(), z_bs ? rows : n2, s->Kc_r, s->Kpad_r, 2);
+  ZView v;                                  // rows r = (a b), k = Q: element r + Q n2
+  v.rs_in = 1;
+  v.ks_in = n2;
+  GW_TRY_INTERNAL(slice(s, X, v, x_bs, 0, 1 << 30, nb, n2, naux, xs, n2));
+  GW_TRY_INTERNAL(slice(s, Z, v, z_bs, 0, 1 << 30, z_bs ? nb : 1, n2, naux, zs, n2));
+  OzParams p;
+  p.M = n2;
+  p.N = n2;
+  p.nbatch = nb;
+  p.a_bs_in = n2;
+  p.b_bs_in = z_bs ? n2 : 0;
+  p.C = out;
+  p.vc.rs_in = n2;
+  p.vc.ks_in = 1;
+  p.bc.bs_in = out_bs;
+  p.status = s->status;
+  p.ws = s->ws;
+  return launch_oz(xs, zs, p, SLOT_GF2_TC, s->stream);
+}
 
 int mixed_polarization(MixedState* s, const double2* G, double2* P0t, double spin_factor) {
   GW_TRY_INTERNAL(slice_g(s, G));
