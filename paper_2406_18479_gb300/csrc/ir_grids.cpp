@@ -80,11 +80,10 @@ void spherical_bessel(double k, double* j) {
     j[1] = std::sin(ak) / (ak * ak) - std::cos(ak) / ak;
     for (int m = 1; m + 1 < kNgl; ++m) j[m + 1] = (2 * m + 1) / ak * j[m] - j[m - 1];
   } else {
-    const int top = kNgl + 30 + (int)ak;
-    double f1 = 0.0, f0 = 1e-280;
-    std::vector<double> f(top + 2, 0.0);
-    f[top + 1] = f1;
-    f[top] = f0;
+    const int top = kNgl + 30 + (int)ak;           // ak <= kNgl: top + 2 <= 64
+    double f[64] = {0.0};
+    f[top + 1] = 0.0;
+    f[top] = 1e-280;
     for (int m = top; m >= 1; --m) {
       f[m - 1] = (2 * m + 1) / ak * f[m] - f[m + 1];
       if (std::fabs(f[m - 1]) > 1e250) {   // rescale
