@@ -127,13 +127,14 @@ def sigma_eval(V, G, nk3, beta, spin_factor=2.0):
     return {"P0t": P0t, "P0w": P0w, "Pw": Pw, "Pt": Pt, "Sig": Sig}
 
 
-def dyson_G(H, Sig, mu, beta, fermionic=None):
-    """Dyson equation, Eq. (dyson), with S = I and Sigma^inf = 0:
+def dyson_G(H, Sig, mu, beta, fermionic=None, S=None):
+    """Dyson equation, Eq. (dyson), with Sigma^inf = 0 (it enters through H):
 
-      G^k(i w_n) = [(i w_n + mu) I - H^k - Sigma^k(i w_n)]^{-1},
+      G^k(i w_n) = [(i w_n + mu) S^k - H^k - Sigma^k(i w_n)]^{-1},
 
-    Sigma(i w_n) = F^f Sigma(tau), G(tau) = B^f G(i w_n) on the fermionic grid: the Chebyshev
-    one, or fermionic = (w_n, F^f, B^f) given (another tau grid, e.g. an IR grid).
+    S = I unless the overlap S [nk][nao][nao] is given. Sigma(i w_n) = F^f Sigma(tau),
+    G(tau) = B^f G(i w_n) on the fermionic grid: the Chebyshev one, or fermionic = (w_n, F^f, B^f)
+    given (another tau grid, e.g. an IR grid).
     """
     nk, ntau, nao, _ = Sig.shape
     if fermionic is None:
@@ -145,8 +146,9 @@ def dyson_G(H, Sig, mu, beta, fermionic=None):
     Gw = np.empty_like(Sw)
     eye = np.eye(nao)
     for k in range(nk):
+        ov = eye if S is None else S[k]
         for n in range(len(wn)):
-            Gw[k, n] = np.linalg.inv((1j * wn[n] + mu) * eye - H[k] - Sw[k, n])
+            Gw[k, n] = np.linalg.inv((1j * wn[n] + mu) * ov - H[k] - Sw[k, n])
     return to_tau(Gw, Bf)
 
 
@@ -216,24 +218,26 @@ def sigma_inf(V, gamma, nk3, spin_factor=2.0):
     return out
 
 
-def particle_number(gamma, spin_factor=2.0):
-    """Electrons per cell, (s/N_k) sum_k Tr gamma^k."""
+def particle_number(gamma, spin_factor=2.0, S=None):
+    """Electrons per cell, (s/N_k) sum_k Re Tr gamma^k S^k (S = I unless given)."""
     nk = gamma.shape[0]
-    return float(np.real(spin_factor * np.einsum("kii->", gamma) / nk))
+    if S is None:
+        return float(np.real(spin_factor * np.einsum("kii->", gamma) / nk))
+    return float(np.real(spin_factor * np.einsum("kij,kji->", gamma, S) / nk))
 
 
-def dyson_G_static(H, sig_inf, Sig, mu, beta):
-    """Eq. (dyson) with the static part: [(i w_n + mu) I - H^k - Sigma^inf,k - Sigma~^k(i w_n)]^{-1};
+def dyson_G_static(H, sig_inf, Sig, mu, beta, S=None):
+    """Eq. (dyson) with the static part: [(i w_n + mu) S^k - H^k - Sigma^inf,k - Sigma~^k(i w_n)]^{-1};
     the static part enters exactly like H, so this is dyson_G with H + Sigma^inf."""
-    return dyson_G(H if sig_inf is None else H + sig_inf, Sig, mu, beta)
+    return dyson_G(H if sig_inf is None else H + sig_inf, Sig, mu, beta, S=S)
 
 
-def find_mu(H, sig_inf, Sig, beta, n_target, spin_factor=2.0, lo=-5.0, hi=5.0, tol=1e-10, maxit=200):
-    """Chemical potential with (s/N_k) sum_k Tr gamma^k = n_target (Sec. 2.4, step 3), by bisection
-    on the particle number of the Dyson solution, which grows with mu. Returns (mu, G)."""
+def find_mu(H, sig_inf, Sig, beta, n_target, spin_factor=2.0, lo=-5.0, hi=5.0, tol=1e-10, maxit=200, S=None):
+    """Chemical potential with (s/N_k) sum_k Tr gamma^k S^k = n_target (Sec. 2.4, step 3), by
+    bisection on the particle number of the Dyson solution, which grows with mu. Returns (mu, G)."""
     def number(mu):
-        G = dyson_G_static(H, sig_inf, Sig, mu, beta)
-        return particle_number(density_matrix(G, beta), spin_factor), G
+        G = dyson_G_static(H, sig_inf, Sig, mu, beta, S)
+        return particle_number(density_matrix(G, beta), spin_factor, S), G
     n_lo, _ = number(lo)
     n_hi, _ = number(hi)
     if not (n_lo <= n_target <= n_hi):
@@ -273,21 +277,25 @@ def diis_extrapolate(outputs, inputs):
     return sum(ci * o for ci, o in zip(c, outputs)), c
 
 
-def commutator_residual(H, sig_inf, Sig, G, beta):
+def commutator_residual(H, sig_inf, Sig, G, beta, S=None):
     """Error vector of the commutator variant of DIIS (Sec. 5.3, after Pulay's SCF commutator
-    F D S - S D F with S = I): e^k(i w_n) = [G^k(i w_n), H^k + Sigma^inf,k + Sigma~^k(i w_n)],
-    with G(i w) = F^f G(tau) and Sigma~(i w) = F^f Sigma~(tau). A G that solves the Dyson
-    equation with this very (Sigma^inf, Sigma~) commutes with it, so e vanishes at self-consistency."""
+    F D S - S D F): with F^k(i w_n) = H^k + Sigma^inf,k + Sigma~^k(i w_n),
+      e^k(i w_n) = S^k G^k(i w_n) F^k(i w_n) - F^k(i w_n) G^k(i w_n) S^k   (= [G, F] for S = I),
+    G(i w) = F^f G(tau), Sigma~(i w) = F^f Sigma~(tau). A G that solves the Dyson equation with this
+    very (Sigma^inf, Sigma~) and S makes it vanish, so e vanishes at self-consistency."""
     nk, ntau, nao, _ = G.shape
     _, Ff, _ = grids.transform_matrices(ntau, beta, 1)
     Gw = to_matsubara(G, Ff)
     Fw = to_matsubara(Sig, Ff) + (H + (0 if sig_inf is None else sig_inf))[:, None]
-    return Gw @ Fw - Fw @ Gw
+    if S is None:
+        return Gw @ Fw - Fw @ Gw
+    Sk = S[:, None]
+    return Sk @ Gw @ Fw - Fw @ Gw @ Sk
 
 
 def scgw_full(H, V, G0, nk3, beta, mu, spin_factor=2.0, alpha=0.5, tol=1e-6, itermax=10, static=True,
               n_electrons=None, mu_lo=-5.0, mu_hi=5.0, mu_tol=1e-10, diis_size=0, diis_start=2, diis_kind="diis",
-              method="gw"):
+              method="gw", S=None):
     """The self-consistency loop of Sec. 2.4 with its four steps per iteration n:
 
       (1) the static part Sigma^inf[G_{n-1}] (Eq. sigma_inf; left out when static is False) and
@@ -303,8 +311,9 @@ def scgw_full(H, V, G0, nk3, beta, mu, spin_factor=2.0, alpha=0.5, tol=1e-6, ite
       (4) G_n = Dyson(H + Sigma^inf_n, Sigma~_n, mu).
 
     The pair (Sigma^inf, Sigma~) is one vector for mixing, DIIS and the stopping test
-    max |Sigma_n - Sigma_{n-1}| < tol. Returns a dict with Sig (dynamic), SigInf, G, mu,
-    iterations and hist (the max |dSigma| of iterations 2, 3, ...)."""
+    max |Sigma_n - Sigma_{n-1}| < tol; S is the overlap of Eq. (dyson) (identity when None).
+    Returns a dict with Sig (dynamic), SigInf, G, mu, iterations and hist (the max |dSigma| of
+    iterations 2, 3, ...)."""
     nk, ntau, nao, _ = G0.shape
     G = G0
     prev = None                         # (SigInf, Sig) of the previous iteration
@@ -327,7 +336,7 @@ def scgw_full(H, V, G0, nk3, beta, mu, spin_factor=2.0, alpha=0.5, tol=1e-6, ite
             if diis_size > 0:
                 if diis_kind == "cdiis":
                     ins.append(commutator_residual(H, out[:nk * nao * nao].reshape(nk, nao, nao),
-                                                   out[nk * nao * nao:].reshape(G0.shape), G, beta).ravel())
+                                                   out[nk * nao * nao:].reshape(G0.shape), G, beta, S).ravel())
                 else:
                     ins.append(out - prev)
                 outs.append(out)
@@ -342,9 +351,9 @@ def scgw_full(H, V, G0, nk3, beta, mu, spin_factor=2.0, alpha=0.5, tol=1e-6, ite
         sinf = cur[:nk * nao * nao].reshape(nk, nao, nao)
         sdyn = cur[nk * nao * nao:].reshape(G0.shape)
         if n_electrons is not None:
-            mu, G = find_mu(H, sinf, sdyn, beta, n_electrons, spin_factor, lo=mu_lo, hi=mu_hi, tol=mu_tol)
+            mu, G = find_mu(H, sinf, sdyn, beta, n_electrons, spin_factor, lo=mu_lo, hi=mu_hi, tol=mu_tol, S=S)
         else:
-            G = dyson_G_static(H, sinf, sdyn, mu, beta)
+            G = dyson_G_static(H, sinf, sdyn, mu, beta, S)
         if hist and hist[-1] < tol:
             break
     return {"Sig": sdyn, "SigInf": sinf, "G": G, "mu": mu, "iterations": it, "hist": hist}

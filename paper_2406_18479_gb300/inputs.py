@@ -202,3 +202,10 @@ def pack_v(v: np.ndarray) -> np.ndarray:
     """The pairs k1 <= k2 of V[k1][k2] in row order of the upper triangle (the packed layout)."""
     nk = v.shape[0]
     return np.ascontiguousarray(np.stack([v[a, b] for a in range(nk) for b in range(a, nk)]))
+
+
+def overlap(w: Workload, rng: np.random.Generator, spread: float = 0.3) -> np.ndarray:
+    """S(k), Hermitian positive definite: eigenvalues uniform in [1 - spread, 1 + spread] in a
+    random basis per k (a non-orthogonal orbital basis)."""
+    return np.stack([_hermitian_with_spectrum(rng.uniform(1.0 - spread, 1.0 + spread, w.nao), rng)
+                     for _ in range(w.nk)])

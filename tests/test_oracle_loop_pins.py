@@ -190,3 +190,47 @@ def test_hartree_fock_loop_fixed_point_is_a_fermi_matrix():
         assert np.abs(gam[k] - (u * fermi(e - r["mu"], w.beta)) @ u.conj().T).max() < 1e-9
     assert np.abs(O.sigma_inf(v, gam, w.nk3, 2.0) - r["SigInf"]).max() < 1e-9
     assert abs(O.particle_number(gam, 2.0) - 3.0) < 1e-9
+
+
+def overlap_case():
+    w = I.Workload("s", (2, 1, 1), 4, 6, 16, 16, 5.0, 0.0, 4.0, 31, solid=True)
+    h, v, g = I.make_inputs(w)
+    S = I.overlap(w, np.random.default_rng(3))
+    rng = np.random.default_rng(4)
+    sig = 0.05 * (rng.standard_normal(g.shape) + 1j * rng.standard_normal(g.shape))
+    return w, h, v, g, S, 0.5 * (sig + sig.conj().swapaxes(-1, -2))
+
+
+def test_dyson_with_overlap_is_the_orthogonalised_problem():
+    """With S = L L^dagger, (i w + mu) S - H - Sigma = L [(i w + mu) - L^-1 (H + Sigma) L^-dagger] L^dagger,
+    so G = L^-dagger G' L^-1 with G' the S = I solution for the transformed H and Sigma; the
+    particle number Tr(gamma S) is Tr(gamma') of the orthogonalised problem."""
+    w, h, v, g, S, sig = overlap_case()
+    G = O.dyson_G(h, sig, 0.2, w.beta, S=S)
+    L = np.linalg.cholesky(S)
+    Li = np.linalg.inv(L)
+    hp = Li @ h @ Li.conj().swapaxes(-1, -2)
+    sp = Li[:, None] @ sig @ Li.conj().swapaxes(-1, -2)[:, None]
+    Gp = O.dyson_G(hp, sp, 0.2, w.beta)
+    back = Li.conj().swapaxes(-1, -2)[:, None] @ Gp @ Li[:, None]
+    assert np.abs(G - back).max() < 1e-12 * np.abs(G).max()
+    n = O.particle_number(O.density_matrix(G, w.beta), 2.0, S)
+    assert abs(n - O.particle_number(O.density_matrix(Gp, w.beta), 2.0)) < 1e-11
+
+
+def test_commutator_with_overlap_vanishes_for_a_dyson_solution():
+    w, h, v, g, S, sig = overlap_case()
+    sinf = O.sigma_inf(v, O.density_matrix(g, w.beta), w.nk3, 2.0)
+    G = O.dyson_G(h + sinf, sig, -0.1, w.beta, S=S)
+    assert np.abs(O.commutator_residual(h, sinf, sig, G, w.beta, S)).max() < 1e-11
+    assert np.abs(O.commutator_residual(h, sinf, sig, G, w.beta)).max() > 1e-3      # S = I does not hold
+
+
+def test_loop_with_overlap_reaches_its_fixed_point():
+    w, h, v, g, S, sig = overlap_case()
+    r = O.scgw_full(h, 0.3 * v, g, w.nk3, w.beta, 0.0, alpha=0.6, tol=1e-10, itermax=80, n_electrons=3.0,
+                    mu_tol=1e-13, diis_size=5, diis_kind="cdiis", S=S)
+    assert r["hist"][-1] < 1e-10
+    gam = O.density_matrix(r["G"], w.beta)
+    assert abs(O.particle_number(gam, 2.0, S) - 3.0) < 1e-9
+    assert np.abs(O.dyson_G(h + r["SigInf"], r["Sig"], r["mu"], w.beta, S=S) - r["G"]).max() < 1e-12
