@@ -231,6 +231,15 @@ int gw_sigma_eval(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* Sig_dev);
 int gw_dyson_G(gw_ctx* ctx, const gw_c128* H_dev, const gw_c128* Sig_dev, gw_c128* G_dev);
 
 /*
+ * Overlap S^k of a non-orthogonal orbital basis, Eq. dyson: S_dev [nk][nao][nao] Hermitian positive
+ * definite, borrowed (kept alive and unchanged by the caller), or NULL for S = I (the default).
+ * With an overlap, gw_dyson_G solves G^k(i w_n) = [(i w_n + mu) S^k - H^k - Sigma^k(i w_n)]^{-1},
+ * gw_particle_number counts (s/N_k) sum_k Re Tr gamma^k S^k, gw_find_mu uses both, and
+ * gw_commutator_residual returns S G F - F G S (Pulay's F D S - S D F up to sign).
+ */
+int gw_set_overlap(gw_ctx* ctx, const gw_c128* S_dev);
+
+/*
  * Iteration mixing (Sec. 5.3): Sig_inout <- alpha Sig_new + (1 - alpha) Sig_inout, and
  * *max_abs_diff_host = max |Sig_inout(after) - Sig_inout(before)| over all elements.
  * Synchronizes the stream to return the norm. Returns GW_ENOTFINITE if the
@@ -316,10 +325,11 @@ int gw_density(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* gamma_dev);
 int gw_sigma_inf(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* SigInf_dev);
 
 /*
- * Error vector of the commutator variant of DIIS (Sec. 5.3; Pulay's SCF commutator with an
- * orthonormal basis): e^k(i w_n) = [G^k(i w_n), H^k + Sigma^inf,k + Sigma~^k(i w_n)] on the
- * fermionic samples, G(i w) = F^f G(tau), Sigma~(i w) = F^f Sigma~(tau). It vanishes when G
- * solves the Dyson equation with this (Sigma^inf, Sigma~). SigInf_dev may be NULL (zero).
+ * Error vector of the commutator variant of DIIS (Sec. 5.3; Pulay's SCF commutator
+ * F D S - S D F): with F = H^k + Sigma^inf,k + Sigma~^k(i w_n) on the fermionic samples,
+ * e^k(i w_n) = [G^k(i w_n), F] = G F - F G, or S G F - F G S with an overlap (gw_set_overlap);
+ * G(i w) = F^f G(tau), Sigma~(i w) = F^f Sigma~(tau). It vanishes when G solves the Dyson
+ * equation with this (Sigma^inf, Sigma~) (and S). SigInf_dev may be NULL (zero).
  * Writes e_dev [nk][nw_f][nao][nao] (nw_f from gw_grid_build, statistics 1).
  */
 int gw_commutator_residual(gw_ctx* ctx, const gw_c128* H_dev, const gw_c128* SigInf_dev, const gw_c128* Sig_dev,
@@ -343,7 +353,7 @@ int gw_k_interpolate(const int nk3[3], const gw_c128* X_dev, long long nelem, in
 /* Sets the chemical potential used by gw_dyson_G. */
 int gw_set_mu(gw_ctx* ctx, double mu);
 
-/* Electrons per cell (s/N_k) sum_k Tr gamma^k of G (synchronous). */
+/* Electrons per cell (s/N_k) sum_k Re Tr gamma^k S^k of G (S = I without an overlap; synchronous). */
 int gw_particle_number(gw_ctx* ctx, const gw_c128* G_dev, double* n_host);
 
 /*
@@ -497,6 +507,7 @@ typedef struct {
   double mu_lo, mu_hi, mu_tol;
   int diis_kind;
   int method;
+  const gw_c128* S_host;      /* [nk][nao][nao] overlap of Eq. dyson, or NULL for S = I */
 } gw_job;
 
 typedef struct {

@@ -151,6 +151,8 @@ struct gw_ctx {
   double2* xinf = nullptr;                // exchange intermediate of one k, [nk][naux][nao][nao]
   double2* gw_w = nullptr;                // G on the fermionic samples, [nk][nwf][nao][nao]
   double2* heff = nullptr;                // H + Sigma^inf, [nk][nao][nao]
+  const double2* S = nullptr;             // overlap of Eq. dyson (borrowed; null: identity)
+  double2* cw_tmp = nullptr;              // commutator with an overlap: one product, [nk][nwf][nao][nao]
   double2* gf2_ws = nullptr;              // GF2 exchange intermediates (allocated on first use)
   size_t gf2_n = 0;
   double* scal = nullptr;                 // reduction partials and results
@@ -206,7 +208,7 @@ void free_ctx(gw_ctx* c) {
   mixed_destroy(c->mixed);
   void* ptrs[] = {c->Fb, c->Bb, c->Ff, c->Bf, c->wf, c->tabs, c->mq_dev, c->wlist, c->work, c->P0t, c->Pw,
                   c->Pt, c->dyson_ws, c->status, c->maxdiff, c->nonfinite, c->wbeta, c->gamma, c->rho,
-                  c->xinf, c->scal, c->gw_w, c->heff, c->gf2_ws, c->Vfull};
+                  c->xinf, c->scal, c->gw_w, c->heff, c->gf2_ws, c->Vfull, c->cw_tmp};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -577,10 +579,11 @@ size_t job_device_bytes(const gw_config* cfg) {
   c.dry = true;
   if (ctx_build(&c, cfg) != GW_OK) return 0;
   const size_t nk = (size_t)cfg->nk[0] * cfg->nk[1] * cfg->nk[2], nao2 = (size_t)cfg->nao * cfg->nao;
-  // V, H, G and the Sigma output of the job, and the loop's buffers with its default options
+  // V, H (and an overlap of its size), G and the Sigma output of the job, and the loop's buffers
+  // with its default options
   gw_scgw_options o{};
   const size_t vblocks = cfg->v_packed ? (size_t)packed_pairs((int)nk) : nk * nk;
-  return c.bytes + sizeof(gw_c128) * (vblocks * cfg->naux * nao2 + nk * nao2 + 2 * nk * cfg->ntau * nao2) +
+  return c.bytes + sizeof(gw_c128) * (vblocks * cfg->naux * nao2 + 2 * nk * nao2 + 2 * nk * cfg->ntau * nao2) +
          scgw_device_bytes(cfg, &o);
 }
 
@@ -756,7 +759,8 @@ int gw_dyson_G(gw_ctx* ctx, const gw_c128* H_dev, const gw_c128* Sig_dev, gw_c12
   const double2* S = reinterpret_cast<const double2*>(Sig_dev);
   double2* G = reinterpret_cast<double2*>(G_dev);
   GW_TRY(transform(ctx, 1, true, S, ctx->dyson_ws, ctx->nk, ctx->nao2));
-  GW_TRY(build_g_dyson_fp64(ctx->dyson_ws, H, ctx->wf, ctx->cfg.mu, ctx->nk, ctx->nwf, ctx->nao, ctx->stream));
+  GW_TRY(build_g_dyson_fp64(ctx->dyson_ws, H, ctx->S, ctx->wf, ctx->cfg.mu, ctx->nk, ctx->nwf, ctx->nao,
+                            ctx->stream));
   GW_TRY(batched_inverse_fp64(ctx->dyson_ws, ctx->nao, ctx->nao2, ctx->nk * ctx->nwf, ctx->status, ctx->stream));
   GW_TRY(transform(ctx, 1, false, ctx->dyson_ws, G, ctx->nk, ctx->nao2));
   return GW_OK;
@@ -847,28 +851,55 @@ int gw_commutator_residual(gw_ctx* ctx, const gw_c128* H_dev, const gw_c128* Sig
   double2* Fw = ctx->dyson_ws;
   GW_TRY(transform(ctx, 1, true, reinterpret_cast<const double2*>(G_dev), ctx->gw_w, nk, ctx->nao2));
   GW_TRY(transform(ctx, 1, true, reinterpret_cast<const double2*>(Sig_dev), Fw, nk, ctx->nao2));
-  // Fw <- (i w_n + mu) I - H - Sigma~(i w_n); the multiple of I commutes exactly, so
-  // e = Fw G - G Fw = [G, H + Sigma~]
-  GW_TRY(build_g_dyson_fp64(Fw, H, ctx->wf, ctx->cfg.mu, nk, nw, nao, ctx->stream));
-  for (int pass = 0; pass < 2; ++pass) {
+  // Fw <- (i w_n + mu) S - H - Sigma~(i w_n). Without an overlap the multiple of I commutes exactly
+  // and e = Fw G - G Fw = [G, H + Sigma~]; with one, e = Fw G S - S G Fw = S G F - F G S.
+  GW_TRY(build_g_dyson_fp64(Fw, H, ctx->S, ctx->wf, ctx->cfg.mu, nk, nw, nao, ctx->stream));
+  double2* e = reinterpret_cast<double2*>(e_dev);
+  // C = alpha X Y (+ C), X and Y per (k, n) or, for the overlap, per k (batch b = k nw + n)
+  auto mul = [&](const double2* X, bool x_per_k, const double2* Y, bool y_per_k, double2* C, double alpha,
+                 int acc) {
     ZGemm g;
     g.M = g.N = g.K = nao;
     g.nbatch = nk * nw;
-    g.A = pass == 0 ? Fw : ctx->gw_w;
-    g.B = pass == 0 ? ctx->gw_w : Fw;
-    g.C = reinterpret_cast<double2*>(e_dev);
-    g.ba.bs_in = g.bb.bs_in = g.bc.bs_in = ctx->nao2;
+    g.bin = nw;
+    g.A = X;
+    g.B = Y;
+    g.C = C;
+    g.ba.bs_in = x_per_k ? 0 : ctx->nao2;
+    g.ba.bs_out = x_per_k ? ctx->nao2 : (long long)nw * ctx->nao2;
+    g.bb.bs_in = y_per_k ? 0 : ctx->nao2;
+    g.bb.bs_out = y_per_k ? ctx->nao2 : (long long)nw * ctx->nao2;
+    g.bc.bs_in = ctx->nao2;
+    g.bc.bs_out = (long long)nw * ctx->nao2;
     g.va.rs_in = nao;                  // A(m, k) = X[m][k]
     g.va.ks_in = 1;
     g.vb.rs_in = 1;                    // B(n, k) = Y[k][n]
     g.vb.ks_in = nao;
     g.vc.rs_in = nao;
     g.vc.ks_in = 1;
-    g.alpha = pass == 0 ? 1.0 : -1.0;
-    g.accumulate = pass;
+    g.alpha = alpha;
+    g.accumulate = acc;
     g.slot = SLOT_STATIC_FP64;
-    GW_TRY(zgemm_fp64(g, ctx->stream));
+    return zgemm_fp64(g, ctx->stream);
+  };
+  if (!ctx->S) {
+    GW_TRY(mul(Fw, false, ctx->gw_w, false, e, 1.0, 0));
+    return mul(ctx->gw_w, false, Fw, false, e, -1.0, 1);
   }
+  if (!ctx->cw_tmp &&
+      cudaMalloc(reinterpret_cast<void**>(&ctx->cw_tmp), (size_t)nk * nw * ctx->nao2 * sizeof(double2)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GW_ENOMEM, "gw_commutator_residual: no room for the overlap products");
+  }
+  GW_TRY(mul(Fw, false, ctx->gw_w, false, ctx->cw_tmp, 1.0, 0));        // Fw G
+  GW_TRY(mul(ctx->cw_tmp, false, ctx->S, true, e, 1.0, 0));             // e = Fw G S
+  GW_TRY(mul(ctx->gw_w, false, Fw, false, ctx->cw_tmp, 1.0, 0));        // G Fw
+  return mul(ctx->S, true, ctx->cw_tmp, false, e, -1.0, 1);             // e -= S G Fw
+}
+
+int gw_set_overlap(gw_ctx* ctx, const gw_c128* S_dev) {
+  if (!ctx) return fail(GW_EINVAL, "gw_set_overlap: null context");
+  ctx->S = reinterpret_cast<const double2*>(S_dev);
   return GW_OK;
 }
 
@@ -1047,7 +1078,7 @@ int gw_particle_number(gw_ctx* ctx, const gw_c128* G_dev, double* n_host) {
   if (!ctx || !G_dev || !n_host) return fail(GW_EINVAL, "gw_particle_number: null argument");
   GW_TRY(density_fp64(reinterpret_cast<const double2*>(G_dev), ctx->wbeta, ctx->gamma, ctx->nk, ctx->ntau, ctx->nao,
                       ctx->stream));
-  GW_TRY(trace_fp64(ctx->gamma, ctx->nk, ctx->nao, ctx->scal, ctx->stream));
+  GW_TRY(trace_fp64(ctx->gamma, ctx->S, ctx->nk, ctx->nao, ctx->scal, ctx->stream));
   double tr = 0.0;
   if (cudaMemcpyAsync(&tr, ctx->scal, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
       cudaStreamSynchronize(ctx->stream) != cudaSuccess)

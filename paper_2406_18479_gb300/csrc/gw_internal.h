@@ -84,8 +84,8 @@ int batched_inverse_fp64(double2* base, int n, long long stride, int nbatch, int
 int add_identity_fp64(double2* base, int n, long long stride, int nbatch, double scale_m,
                       double shift, void* stream, const int* list = nullptr);
 
-// G Dyson build: A[k][n] = (i w_n + mu) I - H[k] - Sw[k][n]   (in place over Sw)
-int build_g_dyson_fp64(double2* sw, const double2* H, const double* wn, double mu, int nk, int nw,
+// G Dyson build: A[k][n] = (i w_n + mu) S[k] - H[k] - Sw[k][n] (S = I when null; in place over Sw)
+int build_g_dyson_fp64(double2* sw, const double2* H, const double2* S, const double* wn, double mu, int nk, int nw,
                        int nao, void* stream);
 
 // Index pairs related by P0^q(beta - tau) = P0^{-q}(tau)^T (and the same for the frequency
@@ -96,7 +96,7 @@ int mirror_fill(double2* X, int nk, int T, int n, const int* mq_dev, void* strea
 // Static part and loop helpers (Eq. sigma_inf, Sec. 2.4, Sec. 5.3), all FP64:
 //   density:  gamma^k = -sum_t w_t G^k(tau_t)          (w: weights of the interpolant at tau = beta)
 //   hartree:  out^k = scale sum_Q V^{kk}(Q) rho_Q, rho_Q = sum_{k'ab} gamma^{k'}_ab V^{k'k'}_ba(Q)
-//   trace:    *out = sum_k Re Tr gamma^k;  add: c = a + b
+//   trace:    *out = sum_k Re Tr gamma^k S^k (S = I when null);  add: c = a + b
 //   dot_re:   *out = Re <x, y> (kDotBlocks partial sums, in a fixed order);  lincomb: out = sum_i c_i v_i
 constexpr int kDotBlocks = 512;
 int density_fp64(const double2* G, const double* w, double2* gamma, int nk, int ntau, int nao, void* stream);
@@ -124,7 +124,7 @@ struct VPairs {
 inline long long packed_pairs(int nk) { return (long long)nk * (nk + 1) / 2; }
 int unpack_v_fp64(const double2* Vp, int nk, int nao, long long pair, const VPairs& L, int nblocks, double2* dst,
                   void* stream);
-int trace_fp64(const double2* gamma, int nk, int nao, double* out_dev, void* stream);
+int trace_fp64(const double2* gamma, const double2* S, int nk, int nao, double* out_dev, void* stream);
 int add_fp64(const double2* a, const double2* b, double2* c, long long n, void* stream);
 int dot_re_fp64(const double2* x, const double2* y, long long n, double* partial_dev, double* out_dev, void* stream);
 int lincomb_fp64(const double2* const* v, const double* c, int m, double2* out, long long n, void* stream);

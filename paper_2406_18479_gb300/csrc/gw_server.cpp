@@ -86,13 +86,13 @@ int run_job(Job* j) {
   const size_t bH = sizeof(gw_c128) * nk * nao2;
   const size_t bG = sizeof(gw_c128) * nk * c.ntau * nao2;
   cudaStream_t st = nullptr;
-  gw_c128 *V = nullptr, *H = nullptr, *G = nullptr, *S = nullptr;
+  gw_c128 *V = nullptr, *H = nullptr, *G = nullptr, *S = nullptr, *Ov = nullptr;
   gw_ctx* ctx = nullptr;
   int rc = GW_OK;
   auto cleanup = [&]() {
     if (ctx) gw_destroy(ctx);
     if (st) cudaStreamSynchronize(st);
-    for (void* p : {(void*)V, (void*)H, (void*)G, (void*)S})
+    for (void* p : {(void*)V, (void*)H, (void*)G, (void*)S, (void*)Ov})
       if (p) cudaFree(p);
     if (st) cudaStreamDestroy(st);
   };
@@ -102,7 +102,8 @@ int run_job(Job* j) {
       break;
     }
     if (cudaMalloc((void**)&V, bV) != cudaSuccess || cudaMalloc((void**)&H, bH) != cudaSuccess ||
-        cudaMalloc((void**)&G, bG) != cudaSuccess || cudaMalloc((void**)&S, bG) != cudaSuccess) {
+        cudaMalloc((void**)&G, bG) != cudaSuccess || cudaMalloc((void**)&S, bG) != cudaSuccess ||
+        (s.S_host && cudaMalloc((void**)&Ov, bH) != cudaSuccess)) {
       rc = fail(GW_ENOMEM, "job %llu: device allocation failed", (unsigned long long)j->id);
       break;
     }
@@ -111,6 +112,10 @@ int run_job(Job* j) {
     cudaMemcpyAsync(G, s.G0_host, bG, cudaMemcpyHostToDevice, st);
     if ((rc = gw_create(&ctx, &c, st)) != GW_OK) break;
     if ((rc = gw_set_coulomb(ctx, V)) != GW_OK) break;
+    if (Ov) {
+      cudaMemcpyAsync(Ov, s.S_host, bH, cudaMemcpyHostToDevice, st);
+      if ((rc = gw_set_overlap(ctx, Ov)) != GW_OK) break;
+    }
     const gw_scgw_options o = job_options(s);
     gw_scgw_result r{};
     rc = gw_scgw(ctx, H, G, S, nullptr, &o, &r);

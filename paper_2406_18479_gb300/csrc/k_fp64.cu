@@ -405,7 +405,7 @@ __global__ void add_identity_kernel(double2* base, int n, long long stride, int 
   }
 }
 
-__global__ void build_g_dyson_kernel(double2* sw, const double2* H, const double* wn, double mu,
+__global__ void build_g_dyson_kernel(double2* sw, const double2* H, const double2* S, const double* wn, double mu,
                                      int nk, int nw, int nao) {
   const long long nn = (long long)nao * nao;
   const long long total = nn * nw * nk;
@@ -417,7 +417,11 @@ __global__ void build_g_dyson_kernel(double2* sw, const double2* H, const double
     const double2 h = H[(long long)k * nn + r];
     double2 s = sw[e];
     double2 v = make_double2(-h.x - s.x, -h.y - s.y);
-    if (r / nao == r % nao) {
+    if (S) {   // (mu + i w_n) S^k
+      const double2 o = S[(long long)k * nn + r];
+      v.x += mu * o.x - wn[n] * o.y;
+      v.y += mu * o.y + wn[n] * o.x;
+    } else if (r / nao == r % nao) {
       v.x += mu;
       v.y += wn[n];
     }
@@ -670,11 +674,21 @@ __global__ void exchange_reduce_kernel(const double2* __restrict__ part, double2
 }
 
 // *out = sum_k sum_i Re gamma^k_ii (one block)
-__global__ void __launch_bounds__(256) trace_kernel(const double2* gamma, int nk, int nao, double* out) {
+__global__ void __launch_bounds__(256) trace_kernel(const double2* gamma, const double2* S, int nk, int nao,
+                                                    double* out) {
   double acc = 0.0;
-  for (long long e = threadIdx.x; e < (long long)nk * nao; e += blockDim.x) {
-    const long long k = e / nao, i = e % nao;
-    acc += gamma[(k * nao + i) * nao + i].x;
+  if (!S) {
+    for (long long e = threadIdx.x; e < (long long)nk * nao; e += blockDim.x) {
+      const long long k = e / nao, i = e % nao;
+      acc += gamma[(k * nao + i) * nao + i].x;
+    }
+  } else {   // sum_k Re Tr gamma^k S^k = sum_{k i j} Re gamma^k_ij S^k_ji
+    const long long nn = (long long)nao * nao;
+    for (long long e = threadIdx.x; e < (long long)nk * nn; e += blockDim.x) {
+      const long long k = e / nn, r = e % nn, i = r / nao, j = r % nao;
+      const double2 a = gamma[e], b = S[k * nn + j * nao + i];
+      acc += a.x * b.x - a.y * b.y;
+    }
   }
   __shared__ double sh[256];
   sh[threadIdx.x] = acc;
@@ -806,11 +820,11 @@ int add_identity_fp64(double2* base, int n, long long stride, int nbatch, double
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "add_identity launch: %s", cudaGetErrorString(e));
 }
 
-int build_g_dyson_fp64(double2* sw, const double2* H, const double* wn, double mu, int nk, int nw,
+int build_g_dyson_fp64(double2* sw, const double2* H, const double2* S, const double* wn, double mu, int nk, int nw,
                        int nao, void* stream) {
   const long long total = (long long)nao * nao * nw * nk;
   prof_begin(SLOT_ELEMENTWISE, (cudaStream_t)stream);
-  build_g_dyson_kernel<<<grid_for(total, 256), 256, 0, (cudaStream_t)stream>>>(sw, H, wn, mu, nk, nw,
+  build_g_dyson_kernel<<<grid_for(total, 256), 256, 0, (cudaStream_t)stream>>>(sw, H, S, wn, mu, nk, nw,
                                                                                nao);
   prof_end(SLOT_ELEMENTWISE, (cudaStream_t)stream, 4.0 * total, 32.0 * total);
   const cudaError_t e = cudaGetLastError();
@@ -912,9 +926,9 @@ int unpack_v_fp64(const double2* Vp, int nk, int nao, long long pair, const VPai
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "unpack_v launch: %s", cudaGetErrorString(e));
 }
 
-int trace_fp64(const double2* gamma, int nk, int nao, double* out_dev, void* stream) {
+int trace_fp64(const double2* gamma, const double2* S, int nk, int nao, double* out_dev, void* stream) {
   prof_begin(SLOT_ELEMENTWISE, (cudaStream_t)stream);
-  trace_kernel<<<1, 256, 0, (cudaStream_t)stream>>>(gamma, nk, nao, out_dev);
+  trace_kernel<<<1, 256, 0, (cudaStream_t)stream>>>(gamma, S, nk, nao, out_dev);
   prof_end(SLOT_ELEMENTWISE, (cudaStream_t)stream, (double)nk * nao, 16.0 * nk * nao);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "trace launch: %s", cudaGetErrorString(e));

@@ -33,7 +33,7 @@ ABI_SYMBOLS = [
     "gw_batch_set_coulomb", "gw_batch_sigma_eval", "gw_batch_autotune", "gw_batch_synchronize",
     "gw_density", "gw_sigma_inf", "gw_set_mu", "gw_particle_number", "gw_find_mu", "gw_diis_create",
     "gw_diis_destroy", "gw_diis_push", "gw_diis_extrapolate", "gw_scgw_bytes", "gw_scgw", "gw_diis_push_residual",
-    "gw_commutator_residual", "gw_gf2_self_energy", "gw_gf2_exchange", "gw_k_interpolate", "gw_ir_grids",
+    "gw_commutator_residual", "gw_gf2_self_energy", "gw_gf2_exchange", "gw_k_interpolate", "gw_ir_grids", "gw_set_overlap",
 ]
 GW_BATCH_SERIAL, GW_BATCH_STREAMS, GW_BATCH_GRAPH = 0, 1, 2
 BATCH_MODES = {"serial": GW_BATCH_SERIAL, "streams": GW_BATCH_STREAMS, "graph": GW_BATCH_GRAPH}
@@ -62,6 +62,7 @@ class gw_job(ctypes.Structure):
         ("static_part", ctypes.c_int), ("diis_size", ctypes.c_int), ("diis_start", ctypes.c_int),
         ("n_electrons", ctypes.c_double), ("mu_lo", ctypes.c_double), ("mu_hi", ctypes.c_double),
         ("mu_tol", ctypes.c_double), ("diis_kind", ctypes.c_int), ("method", ctypes.c_int),
+        ("S_host", ctypes.c_void_p),
     ]
 
 
@@ -150,6 +151,7 @@ def lib():
     L.gw_commutator_residual.argtypes = [vp, vp, vp, vp, vp, vp]
     L.gw_gf2_self_energy.argtypes = [vp, vp, vp]
     L.gw_gf2_exchange.argtypes = [vp, vp, vp]
+    L.gw_set_overlap.argtypes = [vp, vp]
     L.gw_ir_grids.argtypes = [d, d, d, i, ctypes.POINTER(i), vp, vp, vp, vp, vp, vp, vp]
     L.gw_k_interpolate.argtypes = [ctypes.POINTER(i), vp, ctypes.c_longlong, i, ctypes.POINTER(d), vp, vp]
     L.gw_diis_destroy.argtypes = [vp]
@@ -420,7 +422,7 @@ class gw_server:
 
     def submit(self, cfg: gw_config, H, V, G0, Sigma_out=None, G_out=None, alpha=0.7, tol=1e-8,
                itermax=20, static_part=False, diis_size=0, diis_start=2, n_electrons=0.0, mu_lo=-5.0,
-               mu_hi=5.0, mu_tol=1e-10, diis_kind="diis", method="gw") -> int:
+               mu_hi=5.0, mu_tol=1e-10, diis_kind="diis", method="gw", S=None) -> int:
         nk = cfg.nk[0] * cfg.nk[1] * cfg.nk[2]
         nao, naux, ntau = cfg.nao, cfg.naux, cfg.ntau
         vshape = (nk * (nk + 1) // 2, naux, nao, nao) if cfg.v_packed else (nk, nk, naux, nao, nao)
@@ -430,10 +432,11 @@ class gw_server:
                      None if G_out is None else _host(G_out, (nk, ntau, nao, nao), "G_out", True),
                      float(alpha), float(tol), int(itermax), int(bool(static_part)), int(diis_size),
                      int(diis_start), float(n_electrons), float(mu_lo), float(mu_hi), float(mu_tol),
-                     _code(DIIS_KINDS, diis_kind), _code(METHODS, method))
+                     _code(DIIS_KINDS, diis_kind), _code(METHODS, method),
+                     None if S is None else _host(S, (nk, nao, nao), "S"))
         jid = ctypes.c_uint64()
         _check(lib().gw_submit(self._h, ctypes.byref(job), ctypes.byref(jid)))
-        self._keep[jid.value] = (H, V, G0, Sigma_out, G_out)
+        self._keep[jid.value] = (H, V, G0, Sigma_out, G_out, S)
         return jid.value
 
     def poll(self, job_id: int, timeout_us: int = -1):
@@ -677,3 +680,9 @@ def gw_ir_grids(beta, lam=1e4, eps=1e-10):
     _check(lib().gw_ir_grids(float(beta), float(lam), float(eps), T, ctypes.byref(n), p(tau), p(Fb), p(Bb), p(Ff),
                              p(Bf), p(wb), p(wf)))
     return tau, Fb, Bb, Ff, Bf, wf, wb
+
+
+def gw_set_overlap(ctx: gw_ctx, S=None):
+    """Overlap S [nk][nao][nao] of Eq. dyson (borrowed), or None for S = I."""
+    _check(lib().gw_set_overlap(ctx.handle, None if S is None else _ptr(S, (ctx.nk, ctx.nao, ctx.nao))))
+    ctx._keep_s = S

@@ -351,3 +351,64 @@ def test_hartree_fock_loop_matches_oracle(G):
     assert np.abs(host(Sinf) - ref["SigInf"]).max() < 1e-9
     assert np.abs(host(Gd) - ref["G"]).max() < 1e-9
     ctx.destroy()
+
+
+def overlap_case():
+    w = I.Workload("s", (2, 1, 1), 4, 6, 16, 16, 5.0, 0.0, 4.0, 31, solid=True)
+    h, v, g = I.make_inputs(w)
+    S = I.overlap(w, np.random.default_rng(3))
+    return w, h, v, g, S, hermitian_noise(g.shape, 0.05, 4)
+
+
+def test_overlap_dyson_number_mu_commutator(G):
+    w, h, v, g, S, sig = overlap_case()
+    ctx = G.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, mu=0.2, precision="fp64")
+    Sd = dev(S)
+    G.gw_set_overlap(ctx, Sd)
+    Gd = torch.empty(ctx.shapes()["G"], dtype=torch.complex128, device="cuda")
+    G.gw_dyson_G(ctx, dev(h), dev(sig), Gd)
+    ref = O.dyson_G(h, sig, 0.2, w.beta, S=S)
+    assert rel(host(Gd), ref) < 1e-10
+    n = G.gw_particle_number(ctx, Gd)
+    assert abs(n - O.particle_number(O.density_matrix(ref, w.beta), 2.0, S)) < 1e-11
+    mu = G.gw_find_mu(ctx, dev(h), dev(sig), 3.0, -4.0, 4.0, 1e-12, Gd)
+    mu_ref, G_ref = O.find_mu(h, None, sig, w.beta, 3.0, 2.0, lo=-4.0, hi=4.0, tol=1e-12, S=S)
+    assert abs(mu - mu_ref) < 1e-9 and rel(host(Gd), G_ref) < 1e-8
+    sinf = hermitian_noise((w.nk, w.nao, w.nao), 0.1, 5)
+    e = torch.empty((w.nk, ctx.nwf, w.nao, w.nao), dtype=torch.complex128, device="cuda")
+    G.gw_commutator_residual(ctx, dev(h), dev(sinf), dev(sig), dev(g), e)
+    assert rel(host(e), O.commutator_residual(h, sinf, sig, g, w.beta, S)) < 1e-12
+    G.gw_set_overlap(ctx, None)                   # back to S = I
+    G.gw_set_mu(ctx, 0.2)
+    G.gw_dyson_G(ctx, dev(h), dev(sig), Gd)
+    assert rel(host(Gd), O.dyson_G(h, sig, 0.2, w.beta)) < 1e-10
+    ctx.destroy()
+
+
+def test_overlap_loop_and_job(G):
+    w, h, v, g, S, _ = overlap_case()
+    v = 0.3 * v
+    ref = O.scgw_full(h, v, g, w.nk3, w.beta, 0.0, alpha=0.6, tol=1e-10, itermax=80, n_electrons=3.0,
+                      mu_lo=-4.0, mu_hi=4.0, mu_tol=1e-12, diis_size=5, diis_kind="cdiis", S=S)
+    ctx = G.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision="fp64")
+    vd = dev(v)
+    G.gw_set_coulomb(ctx, vd)
+    Sd = dev(S)
+    G.gw_set_overlap(ctx, Sd)
+    Gd = dev(g)
+    Sig = torch.empty(ctx.shapes()["Sig"], dtype=torch.complex128, device="cuda")
+    opt = G.scgw_options(alpha=0.6, tol=1e-10, itermax=80, diis_size=5, n_electrons=3.0, mu_lo=-4.0, mu_hi=4.0,
+                         mu_tol=1e-12, diis_kind="cdiis")
+    rc, r = G.gw_scgw(ctx, dev(h), Gd, Sig, None, opt)
+    assert rc == G.GW_OK and abs(r["iterations"] - ref["iterations"]) <= 1
+    assert abs(r["mu"] - ref["mu"]) < 1e-9 and np.abs(host(Gd) - ref["G"]).max() < 1e-9
+    ctx.destroy()
+    cfg = G.make_config(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision="fp64")
+    srv = G.gw_server(8 << 30, 1)
+    Gout = np.empty(g.shape, complex)
+    jid = srv.submit(cfg, h, v, g, None, Gout, alpha=0.6, tol=1e-10, itermax=80, static_part=True, diis_size=5,
+                     n_electrons=3.0, mu_lo=-4.0, mu_hi=4.0, mu_tol=1e-12, diis_kind="cdiis", S=S)
+    rc, res = srv.poll(jid, -1)
+    srv.destroy()
+    assert rc == G.GW_OK and res["status"] == G.GW_OK
+    assert np.abs(Gout - ref["G"]).max() < 1e-9

@@ -100,9 +100,10 @@ def test_job_bytes_equal_context_workspace(cuda, precision):
     cfg = gw.make_config(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision=precision)
     ctx = gw.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision=precision)
     nk, nao2 = 4, 25
-    # V, H, G, the Sigma output; the loop's Sigma_{n-1} and F_n (static + dynamic), H + Sigma^inf, flags
+    # V, H, an overlap, G, the Sigma output; the loop's Sigma_{n-1} and F_n (static + dynamic),
+    # H + Sigma^inf, flags
     nall = nk * nao2 * (1 + w.ntau)
-    buffers = 16 * (nk * nk * w.naux * nao2 + nk * nao2 + 2 * nk * w.ntau * nao2) + 16 * (2 * nall + nk * nao2) + 256
+    buffers = 16 * (nk * nk * w.naux * nao2 + 2 * nk * nao2 + 2 * nk * w.ntau * nao2) + 16 * (2 * nall + nk * nao2) + 256
     assert gw.gw_job_bytes(cfg) == ctx.workspace_bytes() + buffers
     assert gw.gw_scgw_bytes(cfg, gw.scgw_options()) == 16 * (2 * nall + nk * nao2) + 256
     five = gw.gw_scgw_bytes(cfg, gw.scgw_options(diis_size=5))
