@@ -331,9 +331,19 @@ def run_ours(args, rank, world, local_rank):
     w = I.Workload(base.name, base.nk3, base.nao, base.naux, base.ntau, base.nomega, base.beta, base.mu,
                    base.decay, base.seed + rank, base.solid)
     h, v, g = I.make_inputs(w)
-    V = torch.from_numpy(v).cuda()
+    grid = None
+    if args.ir_lambda > 0:
+        # the same system on an IR grid (the tau node count follows from Lambda and eps)
+        grid = gw.gw_ir_grids(w.beta, args.ir_lambda, args.ir_eps)
+        w = I.Workload(f"{w.name}_ir{args.ir_lambda:g}", w.nk3, w.nao, w.naux, len(grid[0]), len(grid[0]), w.beta,
+                       w.mu, w.decay, w.seed, w.solid)
+        g = I.g0_tau(h, w.mu, w.beta, grid[0])
+    V = torch.from_numpy(I.pack_v(v) if args.v_packed else v).cuda()
     G = torch.from_numpy(g).cuda()
-    ctx = gw.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision=args.precision, tau_chunk=args.tau_chunk)
+    ctx = gw.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision=args.precision, tau_chunk=args.tau_chunk,
+                       v_packed=args.v_packed)
+    if grid is not None:
+        gw.gw_set_grids(ctx, *grid)
     Sig = torch.empty(ctx.shapes()["Sig"], dtype=torch.complex128, device="cuda")
     gw.gw_set_coulomb(ctx, V)
     stream = ctx.stream
@@ -380,7 +390,9 @@ def run_ours(args, rank, world, local_rank):
     # ---- optional FP64 comparison (one evaluation) for the mixed precisions
     fp64 = None
     if args.precision != "fp64" and args.fp64_compare:
-        c64 = gw.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision="fp64")
+        c64 = gw.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision="fp64", v_packed=args.v_packed)
+        if grid is not None:
+            gw.gw_set_grids(c64, *grid)
         S64 = torch.empty_like(Sig)
         gw.gw_set_coulomb(c64, V)
         torch.cuda.synchronize()
@@ -443,6 +455,9 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": w.name, "nk": w.nk, "nao": w.nao, "naux": w.naux, "ntau": w.ntau,
                    "nomega": nwb, "beta": w.beta, "precision": args.precision, "tau_chunk": args.tau_chunk,
                    "l2": "inputs larger than L2 (V 1.58 GB, P 1.73 GB per pass)",
+                   "grid": (f"IR Lambda={args.ir_lambda:g} eps={args.ir_eps:g}" if grid is not None
+                            else "Chebyshev"),
+                   "v_layout": "packed k1<=k2" if args.v_packed else "all pairs",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "tflops_algorithmic": flops * world * steps / (t_max / 1e3) / 1e12,
         "roofline": {"kernel": dname, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
@@ -457,7 +472,7 @@ def run_ours(args, rank, world, local_rank):
         line["fp64"] = fp64
     if serving is not None:
         line["serving"] = serving
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and grid is None:
         val, sample, spent = oracle_sample(w, h, v, g, budget_s=args.ref_budget)
         line["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
                                 "sample": sample}
@@ -710,6 +725,11 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="measure only the 48-molecule batch (loop vs streams vs graph) and print its own line")
     ap.add_argument("--batch-streams", type=int, default=8)
+    ap.add_argument("--v-packed", action="store_true",
+                    help="pass V packed (pairs k1 <= k2 only) to the library")
+    ap.add_argument("--ir-lambda", type=float, default=0.0,
+                    help="run the workload on an IR grid with this Lambda (0: the workload's Chebyshev grid)")
+    ap.add_argument("--ir-eps", type=float, default=1e-10)
     ap.add_argument("--loop", action="store_true",
                     help="measure only the self-consistency loop (gw_scgw and its pieces) and print its own line")
     ap.add_argument("--gf2", action="store_true",
