@@ -56,20 +56,20 @@ def run():
     return h, v, g, out
 
 
-def test_c3_polarization_sampled(run):
+def test_solid_4x4x4_polarization_sampled(run):
     h, v, g, out = run
     ref = O.polarization(v, g, W.nk3, 2.0, q_list=out["q_s"], t_list=out["t_s"])
     assert rel(out["P0_s"], ref) < TOL
 
 
-def test_c3_screened_interaction_from_gpu_p0(run):
+def test_solid_4x4x4_screened_interaction_from_gpu_p0(run):
     h, v, g, out = run
     _, F, B = grids.transform_matrices(W.ntau, W.beta, 0)
     _, _, pt = O.screened_interaction(out["P0_q"], F, B)
     assert rel(out["Pt_q"], pt) < 1e-10
 
 
-def test_c3_self_energy_sampled_from_gpu_pt(run):
+def test_solid_4x4x4_self_energy_sampled_from_gpu_pt(run):
     h, v, g, out = run
     ref = O.self_energy(v, g, out["Pt"], W.nk3, k_list=out["k_s"], t_list=out["kt_t"])
     assert rel(out["Sig_s"], ref) < TOL
