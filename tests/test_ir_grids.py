@@ -59,3 +59,14 @@ def test_bad_arguments(lib):
     for args in ((-1.0, 100.0, 1e-10), (10.0, 0.5, 1e-10), (10.0, 100.0, 1e-20)):
         with pytest.raises(gw.GWError):
             lib.gw_ir_grids(*args)
+
+
+@pytest.mark.parametrize("lam,eps", [(1.0, 1e-10), (10.0, 1e-6), (1000.0, 1e-12), (300.0, 1e-4)])
+def test_sweep_of_lambda_and_eps(lib, lam, eps):
+    """Propagators with poles inside [-omega_max, omega_max] transform to within 20 eps."""
+    beta = 50.0
+    tau, Fb, Bb, Ff, Bf, wf, wb = lib.gw_ir_grids(beta, lam, eps)
+    for stat, F, w in ((0, Fb, wb), (1, Ff, wf)):
+        for e in (-0.9 * lam / beta, 0.37 * lam / beta, 0.7 * lam / beta):
+            ref = 1.0 / (1j * w - e)
+            assert np.abs(F @ g0(e, tau, beta, stat) - ref).max() < 20 * eps * np.abs(ref).max()
