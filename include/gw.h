@@ -417,6 +417,9 @@ typedef struct {
                                  of G_{i-1} and F_i) */
   int method;                 /* dynamic self-energy: 0 GW (gw_sigma_eval), 1 GF2 (gw_gf2_self_energy),
                                  2 none (Hartree-Fock: Sigma~ = 0, use with static_part = 1) */
+  int resume;                 /* 1: Sigma_dev (and SigInf_dev with the static part) hold Sigma_{n-1}
+                                 of a loop being continued and G_dev the G built from it; the first
+                                 iteration then mixes with it (the DIIS subspace starts empty) */
 } gw_scgw_options;
 
 typedef struct {
@@ -429,6 +432,20 @@ typedef struct {
 size_t gw_scgw_bytes(const gw_config* cfg, const gw_scgw_options* opt);
 int gw_scgw(gw_ctx* ctx, const gw_c128* H_dev, gw_c128* G_dev, gw_c128* Sigma_dev, gw_c128* SigInf_dev,
             const gw_scgw_options* opt, gw_scgw_result* res);
+
+/*
+ * Checkpoint files (host memory): a one-line JSON header with the sizes of cfg, beta, the spin
+ * factor, mu and the iteration, and the names and element counts of narrays complex arrays,
+ * followed by their raw little-endian complex128 values. Names: 1..64 of [A-Za-z0-9_].
+ * gw_checkpoint_read fills the arrays it is asked for by name (each must be stored with exactly
+ * that count; others are skipped) and the header fields (cfg_out keeps its precision, tau_chunk,
+ * v_slices and v_packed); GW_EINVAL for a missing, malformed or truncated file. A loop is
+ * continued from saved G, Sigma~ and Sigma^inf through gw_scgw's resume option.
+ */
+int gw_checkpoint_write(const char* path, const gw_config* cfg, double mu, int iteration, int narrays,
+                        const char* const* names, const gw_c128* const* data_host, const long long* counts);
+int gw_checkpoint_read(const char* path, gw_config* cfg_out, double* mu, int* iteration, int narrays,
+                       const char* const* names, gw_c128* const* data_host, const long long* counts);
 
 /*
  * Batched self-energy evaluation of many independent systems (molecules or k-meshes of

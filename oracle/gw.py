@@ -295,7 +295,7 @@ def commutator_residual(H, sig_inf, Sig, G, beta, S=None):
 
 def scgw_full(H, V, G0, nk3, beta, mu, spin_factor=2.0, alpha=0.5, tol=1e-6, itermax=10, static=True,
               n_electrons=None, mu_lo=-5.0, mu_hi=5.0, mu_tol=1e-10, diis_size=0, diis_start=2, diis_kind="diis",
-              method="gw", S=None):
+              method="gw", S=None, resume=None):
     """The self-consistency loop of Sec. 2.4 with its four steps per iteration n:
 
       (1) the static part Sigma^inf[G_{n-1}] (Eq. sigma_inf; left out when static is False) and
@@ -312,11 +312,16 @@ def scgw_full(H, V, G0, nk3, beta, mu, spin_factor=2.0, alpha=0.5, tol=1e-6, ite
 
     The pair (Sigma^inf, Sigma~) is one vector for mixing, DIIS and the stopping test
     max |Sigma_n - Sigma_{n-1}| < tol; S is the overlap of Eq. (dyson) (identity when None).
+    resume = (SigInf, Sig): continue a loop whose last Sigma_{n-1} these are (G0 the G built from
+    them): the first iteration then mixes with them instead of taking F_1 as it is.
     Returns a dict with Sig (dynamic), SigInf, G, mu, iterations and hist (the max |dSigma| of
     iterations 2, 3, ...)."""
     nk, ntau, nao, _ = G0.shape
     G = G0
     prev = None                         # (SigInf, Sig) of the previous iteration
+    if resume is not None:
+        prev = np.concatenate([(resume[0] if static else np.zeros((nk, nao, nao), complex)).ravel(),
+                               resume[1].ravel()])
     ins, outs = [], []                  # residuals and outputs of the DIIS subspace
     hist = []
     it = 0

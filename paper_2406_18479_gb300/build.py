@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libgw_gb300.so")
-SOURCES = ["gw_api.cu", "k_fp64.cu", "k_mixed.cu", "noalloc.cu", "grids.cpp", "gw_server.cpp", "gw_batch.cpp", "gw_diis.cpp", "gw_scgw.cpp", "kinterp.cpp", "ir_grids.cpp"]
+SOURCES = ["gw_api.cu", "k_fp64.cu", "k_mixed.cu", "noalloc.cu", "grids.cpp", "gw_server.cpp", "gw_batch.cpp", "gw_diis.cpp", "gw_scgw.cpp", "kinterp.cpp", "ir_grids.cpp", "checkpoint.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
          "-I" + CSRC]

@@ -46,7 +46,8 @@ int gw_scgw(gw_ctx* ctx, const gw_c128* H_dev, gw_c128* G_dev, gw_c128* Sigma_de
   if (!ctx || !H_dev || !G_dev || !o || !res) return fail(GW_EINVAL, "gw_scgw: null argument");
   if (!(o->alpha > 0.0 && o->alpha < 2.0) || !(o->tol >= 0.0) || o->itermax < 1 || o->diis_size < 0 ||
       o->diis_size > 16 || (o->diis_size > 0 && o->diis_start < 2) || o->diis_kind < 0 || o->diis_kind > 1 ||
-      o->method < 0 || o->method > 2 ||
+      o->method < 0 || o->method > 2 || o->resume < 0 || o->resume > 1 ||
+      (o->resume && (!Sigma_dev || (o->static_part && !SigInf_dev))) ||
       (o->n_electrons > 0.0 && !(o->mu_lo < o->mu_hi && o->mu_tol > 0.0)))
     return fail(GW_EINVAL, "gw_scgw: options out of range");
   const CtxInfo ci = ctx_info(ctx);
@@ -84,6 +85,10 @@ int gw_scgw(gw_ctx* ctx, const gw_c128* H_dev, gw_c128* G_dev, gw_c128* Sigma_de
       cudaMemsetAsync(S, 0, nst * cb, st);
       cudaMemsetAsync(F, 0, nst * cb, st);
     }
+    if (o->resume) {   // Sigma_{n-1} of the loop being continued
+      cudaMemcpyAsync(S + nst, Sigma_dev, ndyn * cb, cudaMemcpyDeviceToDevice, st);
+      if (o->static_part) cudaMemcpyAsync(S, SigInf_dev, nst * cb, cudaMemcpyDeviceToDevice, st);
+    }
     for (it = 1; it <= o->itermax; ++it) {
       // (1) the output F_n of G_{n-1}
       if (o->static_part && (rc = gw_sigma_inf(ctx, G_dev, reinterpret_cast<gw_c128*>(F))) != GW_OK) break;
@@ -95,7 +100,7 @@ int gw_scgw(gw_ctx* ctx, const gw_c128* H_dev, gw_c128* G_dev, gw_c128* Sigma_de
         rc = gw_sigma_eval(ctx, G_dev, reinterpret_cast<gw_c128*>(F + nst));
       if (rc != GW_OK) break;
       // (2) Sigma_n from F_n and the history
-      if (it == 1) {
+      if (it == 1 && !o->resume) {
         if (cudaMemcpyAsync(S, F, nall * cb, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
           rc = fail(GW_ECUDA, "gw_scgw: copy");
           break;
@@ -146,7 +151,7 @@ int gw_scgw(gw_ctx* ctx, const gw_c128* H_dev, gw_c128* G_dev, gw_c128* Sigma_de
       else
         rc = gw_dyson_G(ctx, H, Sd, G_dev);
       if (rc != GW_OK) break;
-      if (it > 1 && d < o->tol) {
+      if ((it > 1 || o->resume) && d < o->tol) {
         converged = true;
         break;
       }

@@ -33,7 +33,7 @@ ABI_SYMBOLS = [
     "gw_batch_set_coulomb", "gw_batch_sigma_eval", "gw_batch_autotune", "gw_batch_synchronize",
     "gw_density", "gw_sigma_inf", "gw_set_mu", "gw_particle_number", "gw_find_mu", "gw_diis_create",
     "gw_diis_destroy", "gw_diis_push", "gw_diis_extrapolate", "gw_scgw_bytes", "gw_scgw", "gw_diis_push_residual",
-    "gw_commutator_residual", "gw_gf2_self_energy", "gw_gf2_exchange", "gw_k_interpolate", "gw_ir_grids", "gw_set_overlap",
+    "gw_commutator_residual", "gw_gf2_self_energy", "gw_gf2_exchange", "gw_k_interpolate", "gw_ir_grids", "gw_set_overlap", "gw_checkpoint_write", "gw_checkpoint_read",
 ]
 GW_BATCH_SERIAL, GW_BATCH_STREAMS, GW_BATCH_GRAPH = 0, 1, 2
 BATCH_MODES = {"serial": GW_BATCH_SERIAL, "streams": GW_BATCH_STREAMS, "graph": GW_BATCH_GRAPH}
@@ -72,6 +72,7 @@ class gw_scgw_options(ctypes.Structure):
         ("static_part", ctypes.c_int), ("diis_size", ctypes.c_int), ("diis_start", ctypes.c_int),
         ("n_electrons", ctypes.c_double), ("mu_lo", ctypes.c_double), ("mu_hi", ctypes.c_double),
         ("mu_tol", ctypes.c_double), ("diis_kind", ctypes.c_int), ("method", ctypes.c_int),
+        ("resume", ctypes.c_int),
     ]
 
 
@@ -152,6 +153,9 @@ def lib():
     L.gw_gf2_self_energy.argtypes = [vp, vp, vp]
     L.gw_gf2_exchange.argtypes = [vp, vp, vp]
     L.gw_set_overlap.argtypes = [vp, vp]
+    L.gw_checkpoint_write.argtypes = [ctypes.c_char_p, ctypes.POINTER(gw_config), d, i, i, vp, vp, vp]
+    L.gw_checkpoint_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(gw_config), ctypes.POINTER(d),
+                                     ctypes.POINTER(i), i, vp, vp, vp]
     L.gw_ir_grids.argtypes = [d, d, d, i, ctypes.POINTER(i), vp, vp, vp, vp, vp, vp, vp]
     L.gw_k_interpolate.argtypes = [ctypes.POINTER(i), vp, ctypes.c_longlong, i, ctypes.POINTER(d), vp, vp]
     L.gw_diis_destroy.argtypes = [vp]
@@ -604,10 +608,10 @@ def _code(table, x):
 
 
 def scgw_options(alpha=0.5, tol=1e-8, itermax=20, static_part=True, diis_size=0, diis_start=2, n_electrons=0.0,
-                 mu_lo=-5.0, mu_hi=5.0, mu_tol=1e-10, diis_kind="diis", method="gw") -> gw_scgw_options:
+                 mu_lo=-5.0, mu_hi=5.0, mu_tol=1e-10, diis_kind="diis", method="gw", resume=False) -> gw_scgw_options:
     return gw_scgw_options(float(alpha), float(tol), int(itermax), int(bool(static_part)), int(diis_size),
                            int(diis_start), float(n_electrons), float(mu_lo), float(mu_hi), float(mu_tol),
-                           _code(DIIS_KINDS, diis_kind), _code(METHODS, method))
+                           _code(DIIS_KINDS, diis_kind), _code(METHODS, method), int(bool(resume)))
 
 
 def gw_gf2_self_energy(ctx: gw_ctx, G, Sig):
@@ -686,3 +690,30 @@ def gw_set_overlap(ctx: gw_ctx, S=None):
     """Overlap S [nk][nao][nao] of Eq. dyson (borrowed), or None for S = I."""
     _check(lib().gw_set_overlap(ctx.handle, None if S is None else _ptr(S, (ctx.nk, ctx.nao, ctx.nao))))
     ctx._keep_s = S
+
+
+def gw_checkpoint_write(path, cfg: gw_config, mu, iteration, arrays: dict):
+    """arrays: name -> complex128 numpy array (host); see include/gw.h for the format."""
+    items = [(k, np.ascontiguousarray(v, dtype=np.complex128)) for k, v in arrays.items()]
+    n = len(items)
+    names = (ctypes.c_char_p * max(n, 1))(*[k.encode() for k, _ in items])
+    data = (ctypes.c_void_p * max(n, 1))(*[a.ctypes.data for _, a in items])
+    counts = (ctypes.c_longlong * max(n, 1))(*[a.size for _, a in items])
+    _check(lib().gw_checkpoint_write(str(path).encode(), ctypes.byref(cfg), float(mu), int(iteration), n,
+                                     ctypes.cast(names, ctypes.c_void_p), ctypes.cast(data, ctypes.c_void_p),
+                                     ctypes.cast(counts, ctypes.c_void_p)))
+
+
+def gw_checkpoint_read(path, shapes: dict, cfg: gw_config = None):
+    """shapes: name -> shape of the arrays to read. Returns (cfg, mu, iteration, {name: array})."""
+    cfg = cfg if cfg is not None else make_config((1, 1, 1), 1, 1, 1, 1.0)
+    out = {k: np.zeros(tuple(v), complex) for k, v in shapes.items()}
+    n = len(out)
+    names = (ctypes.c_char_p * max(n, 1))(*[k.encode() for k in out])
+    data = (ctypes.c_void_p * max(n, 1))(*[a.ctypes.data for a in out.values()])
+    counts = (ctypes.c_longlong * max(n, 1))(*[a.size for a in out.values()])
+    mu, it = ctypes.c_double(), ctypes.c_int()
+    _check(lib().gw_checkpoint_read(str(path).encode(), ctypes.byref(cfg), ctypes.byref(mu), ctypes.byref(it), n,
+                                    ctypes.cast(names, ctypes.c_void_p), ctypes.cast(data, ctypes.c_void_p),
+                                    ctypes.cast(counts, ctypes.c_void_p)))
+    return cfg, mu.value, it.value, out

@@ -234,3 +234,15 @@ def test_loop_with_overlap_reaches_its_fixed_point():
     gam = O.density_matrix(r["G"], w.beta)
     assert abs(O.particle_number(gam, 2.0, S) - 3.0) < 1e-9
     assert np.abs(O.dyson_G(h + r["SigInf"], r["Sig"], r["mu"], w.beta, S=S) - r["G"]).max() < 1e-12
+
+
+def test_resumed_loop_continues_exactly():
+    """2n iterations in one go equal n iterations, then n more resumed from the saved (Sigma, G)
+    (mixing only: the DIIS history is not part of the saved state)."""
+    w, h, v, g = loop_case()
+    kw = dict(alpha=0.6, tol=0.0, n_electrons=3.0, mu_tol=1e-13)
+    full = O.scgw_full(h, v, g, w.nk3, w.beta, 0.0, itermax=6, **kw)
+    half = O.scgw_full(h, v, g, w.nk3, w.beta, 0.0, itermax=3, **kw)
+    rest = O.scgw_full(h, v, half["G"], w.nk3, w.beta, half["mu"], itermax=3, resume=(half["SigInf"], half["Sig"]), **kw)
+    assert np.array_equal(rest["Sig"], full["Sig"]) and np.array_equal(rest["G"], full["G"])
+    assert rest["hist"] == full["hist"][2:]
