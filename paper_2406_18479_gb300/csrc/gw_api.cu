@@ -692,6 +692,7 @@ int gw_set_coulomb(gw_ctx* ctx, const gw_c128* V_dev) {
 
 int gw_polarization(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* P0t_dev) {
   ProfScope _ps(ctx ? &ctx->prof : nullptr);
+  NvtxRange _nr("gw_polarization");
   if (!ctx || !G_dev || !P0t_dev) return fail(GW_EINVAL, "gw_polarization: null argument");
   if (!ctx->coulomb) return fail(GW_EINVAL, "gw_polarization: call gw_set_coulomb first");
   const double2* G = reinterpret_cast<const double2*>(G_dev);
@@ -723,18 +724,21 @@ int gw_to_tau(gw_ctx* ctx, int stat, const gw_c128* in_dev, gw_c128* out_dev, in
 
 int gw_aux_dyson(gw_ctx* ctx, const gw_c128* P0w_dev, gw_c128* Pw_dev) {
   ProfScope _ps(ctx ? &ctx->prof : nullptr);
+  NvtxRange _nr("gw_aux_dyson");
   if (!ctx || !P0w_dev || !Pw_dev) return fail(GW_EINVAL, "gw_aux_dyson: null argument");
   return aux_dyson(ctx, reinterpret_cast<const double2*>(P0w_dev), reinterpret_cast<double2*>(Pw_dev));
 }
 
 int gw_screened_interaction(gw_ctx* ctx, const gw_c128* P0t_dev, gw_c128* Pt_dev) {
   ProfScope _ps(ctx ? &ctx->prof : nullptr);
+  NvtxRange _nr("gw_screened_interaction");
   if (!ctx || !P0t_dev || !Pt_dev) return fail(GW_EINVAL, "gw_screened_interaction: null argument");
   return screened(ctx, reinterpret_cast<const double2*>(P0t_dev), reinterpret_cast<double2*>(Pt_dev));
 }
 
 int gw_self_energy(gw_ctx* ctx, const gw_c128* G_dev, const gw_c128* Pt_dev, gw_c128* Sig_dev) {
   ProfScope _ps(ctx ? &ctx->prof : nullptr);
+  NvtxRange _nr("gw_self_energy");
   if (!ctx || !G_dev || !Pt_dev || !Sig_dev) return fail(GW_EINVAL, "gw_self_energy: null argument");
   if (!ctx->coulomb) return fail(GW_EINVAL, "gw_self_energy: call gw_set_coulomb first");
   const double2* G = reinterpret_cast<const double2*>(G_dev);
@@ -746,6 +750,7 @@ int gw_self_energy(gw_ctx* ctx, const gw_c128* G_dev, const gw_c128* Pt_dev, gw_
 
 int gw_sigma_eval(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* Sig_dev) {
   ProfScope _ps(ctx ? &ctx->prof : nullptr);
+  NvtxRange _nr("gw_sigma_eval");
   if (!ctx || !G_dev || !Sig_dev) return fail(GW_EINVAL, "gw_sigma_eval: null argument");
   GW_TRY(gw_polarization(ctx, G_dev, reinterpret_cast<gw_c128*>(ctx->P0t)));
   GW_TRY(screened_sym(ctx, ctx->P0t, ctx->Pt));
@@ -754,6 +759,7 @@ int gw_sigma_eval(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* Sig_dev) {
 
 int gw_dyson_G(gw_ctx* ctx, const gw_c128* H_dev, const gw_c128* Sig_dev, gw_c128* G_dev) {
   ProfScope _ps(ctx ? &ctx->prof : nullptr);
+  NvtxRange _nr("gw_dyson_G");
   if (!ctx || !H_dev || !Sig_dev || !G_dev) return fail(GW_EINVAL, "gw_dyson_G: null argument");
   const double2* H = reinterpret_cast<const double2*>(H_dev);
   const double2* S = reinterpret_cast<const double2*>(Sig_dev);
@@ -768,6 +774,7 @@ int gw_dyson_G(gw_ctx* ctx, const gw_c128* H_dev, const gw_c128* Sig_dev, gw_c12
 
 int gw_density(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* gamma_dev) {
   ProfScope _ps(ctx ? &ctx->prof : nullptr);
+  NvtxRange _nr("gw_density");
   if (!ctx || !G_dev || !gamma_dev) return fail(GW_EINVAL, "gw_density: null argument");
   return density_fp64(reinterpret_cast<const double2*>(G_dev), ctx->wbeta, reinterpret_cast<double2*>(gamma_dev),
                       ctx->nk, ctx->ntau, ctx->nao, ctx->stream);
@@ -775,6 +782,7 @@ int gw_density(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* gamma_dev) {
 
 int gw_sigma_inf(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* SigInf_dev) {
   ProfScope _ps(ctx ? &ctx->prof : nullptr);
+  NvtxRange _nr("gw_sigma_inf");
   if (!ctx || !G_dev || !SigInf_dev) return fail(GW_EINVAL, "gw_sigma_inf: null argument");
   if (!ctx->coulomb) return fail(GW_EINVAL, "gw_sigma_inf: call gw_set_coulomb first");
   const int nk = ctx->nk, nao = ctx->nao, naux = ctx->naux;
@@ -840,6 +848,7 @@ int gw_sigma_inf(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* SigInf_dev) {
 int gw_commutator_residual(gw_ctx* ctx, const gw_c128* H_dev, const gw_c128* SigInf_dev, const gw_c128* Sig_dev,
                            const gw_c128* G_dev, gw_c128* e_dev) {
   ProfScope _ps(ctx ? &ctx->prof : nullptr);
+  NvtxRange _nr("gw_commutator_residual");
   if (!ctx || !H_dev || !Sig_dev || !G_dev || !e_dev) return fail(GW_EINVAL, "gw_commutator_residual: null argument");
   const int nk = ctx->nk, nao = ctx->nao, nw = ctx->nwf;
   const double2* H = reinterpret_cast<const double2*>(H_dev);
@@ -1048,6 +1057,7 @@ static int gf2_exchange(gw_ctx* c, const double2* G, double2* S, double alpha) {
 
 int gw_gf2_exchange(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* SigX_dev) {
   ProfScope _ps(ctx ? &ctx->prof : nullptr);
+  NvtxRange _nr("gw_gf2_exchange");
   if (!ctx || !G_dev || !SigX_dev) return fail(GW_EINVAL, "gw_gf2_exchange: null argument");
   if (!ctx->coulomb) return fail(GW_EINVAL, "gw_gf2_exchange: call gw_set_coulomb first");
   double2* S = reinterpret_cast<double2*>(SigX_dev);
@@ -1058,6 +1068,7 @@ int gw_gf2_exchange(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* SigX_dev) {
 
 int gw_gf2_self_energy(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* Sig_dev) {
   ProfScope _ps(ctx ? &ctx->prof : nullptr);
+  NvtxRange _nr("gw_gf2_self_energy");
   if (!ctx || !G_dev || !Sig_dev) return fail(GW_EINVAL, "gw_gf2_self_energy: null argument");
   if (!ctx->coulomb) return fail(GW_EINVAL, "gw_gf2_self_energy: call gw_set_coulomb first");
   // direct term: the GW self-energy contraction with P0 in place of P~
@@ -1075,6 +1086,7 @@ int gw_set_mu(gw_ctx* ctx, double mu) {
 
 int gw_particle_number(gw_ctx* ctx, const gw_c128* G_dev, double* n_host) {
   ProfScope _ps(ctx ? &ctx->prof : nullptr);
+  NvtxRange _nr("gw_particle_number");
   if (!ctx || !G_dev || !n_host) return fail(GW_EINVAL, "gw_particle_number: null argument");
   GW_TRY(density_fp64(reinterpret_cast<const double2*>(G_dev), ctx->wbeta, ctx->gamma, ctx->nk, ctx->ntau, ctx->nao,
                       ctx->stream));
@@ -1089,6 +1101,7 @@ int gw_particle_number(gw_ctx* ctx, const gw_c128* G_dev, double* n_host) {
 
 int gw_find_mu(gw_ctx* ctx, const gw_c128* Heff_dev, const gw_c128* Sig_dev, double n_target, double mu_lo,
                double mu_hi, double tol, gw_c128* G_dev, double* mu_host) {
+  NvtxRange _nr("gw_find_mu");
   if (!ctx || !Heff_dev || !Sig_dev || !G_dev || !mu_host || !(mu_lo < mu_hi) || !(tol > 0))
     return fail(GW_EINVAL, "gw_find_mu: bad argument");
   auto number = [&](double mu, double* n) {

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <vector_types.h>
 
 #include "gw.h"
@@ -19,6 +20,15 @@ bool lsq_left_inverse(const std::vector<std::complex<double>>& A, int m, int n, 
 std::vector<int64_t> matsubara_indices(int n, int stat);
 int grid_build(int ntau, double beta, int stat, double* tau, int64_t* idx, gw_c128* F, gw_c128* B);
 int fail(int code, const char* fmt, ...);
+
+// NVTX range over a scope (a no-op unless a tracing tool is attached): the ABI's stages show up
+// by name on a timeline
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Device bytes of one scGW job: its context's workspaces (counted by running the
 // context build in size-only mode) plus V, H, G and two Sigma buffers. 0 for an

@@ -90,6 +90,7 @@ int gw_scgw(gw_ctx* ctx, const gw_c128* H_dev, gw_c128* G_dev, gw_c128* Sigma_de
       if (o->static_part) cudaMemcpyAsync(S, SigInf_dev, nst * cb, cudaMemcpyDeviceToDevice, st);
     }
     for (it = 1; it <= o->itermax; ++it) {
+      NvtxRange _nr("gw_scgw iteration");
       // (1) the output F_n of G_{n-1}
       if (o->static_part && (rc = gw_sigma_inf(ctx, G_dev, reinterpret_cast<gw_c128*>(F))) != GW_OK) break;
       if (o->method == 2)        // Hartree-Fock: no dynamic part
