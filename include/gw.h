@@ -287,6 +287,23 @@ int gw_polarization_noalloc(const int nk3[3], int nao, int naux, int ntau, doubl
                             const gw_c128* V_dev, const gw_c128* G_dev, gw_c128* P0t_dev,
                             void* cuda_stream);
 
+/*
+ * Checks the guard zones (256 bytes of 0xA5 after every workspace allocation of the context):
+ * GW_ECUDA if any was overwritten, i.e. some kernel wrote past the end of a workspace. Synchronous.
+ */
+int gw_check_guards(gw_ctx* ctx);
+/* Test hook: changes one byte of the index-th guard zone of the context (inside that allocation),
+ * as a write past the end of the workspace would, so that gw_check_guards must report it. */
+int gw_debug_mark_guard(gw_ctx* ctx, int index);
+
+/*
+ * Failure detection self-test (no counterpart in the paper): one thread waits, with the same
+ * bounded mbarrier wait the tensor-core GEMM uses, on a phase that nothing completes. The wait
+ * gives up after limit_s seconds (1e-3..10), records its code (*code_out = 99) and the kernel
+ * returns: the call returns GW_EDEVTIMEOUT and the device stays usable. Synchronous.
+ */
+int gw_selftest_bounded_wait(double limit_s, int* code_out, void* cuda_stream);
+
 /* Waits for all work queued on the context's stream. */
 int gw_synchronize(gw_ctx* ctx);
 

@@ -156,6 +156,7 @@ struct gw_ctx {
   double2* gf2_ws = nullptr;              // GF2 exchange intermediates (allocated on first use)
   size_t gf2_n = 0;
   double* scal = nullptr;                 // reduction partials and results
+  std::vector<unsigned char*> guards;     // guard zones of the workspaces allocated by dev_alloc
   Prof prof;
 };
 
@@ -173,17 +174,21 @@ int kshift(const int nk3[3], int k, int q, int sign) {
 template <class T>
 int dev_alloc(gw_ctx* c, T** p, size_t count) {
   if (count == 0) count = 1;
+  const size_t bytes = count * sizeof(T);
   if (c->dry) {
     *p = nullptr;
-    c->bytes += count * sizeof(T);
+    c->bytes += bytes + kGuardBytes;
     return GW_OK;
   }
-  const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+  const cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes + kGuardBytes);
   if (e != cudaSuccess) {
     *p = nullptr;
-    return fail(GW_ENOMEM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+    return fail(GW_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
   }
-  c->bytes += count * sizeof(T);
+  unsigned char* guard = reinterpret_cast<unsigned char*>(*p) + bytes;
+  cudaMemset(guard, kGuardByte, kGuardBytes);
+  c->guards.push_back(guard);
+  c->bytes += bytes + kGuardBytes;
   return GW_OK;
 }
 
@@ -904,6 +909,31 @@ int gw_commutator_residual(gw_ctx* ctx, const gw_c128* H_dev, const gw_c128* Sig
   GW_TRY(mul(ctx->cw_tmp, false, ctx->S, true, e, 1.0, 0));             // e = Fw G S
   GW_TRY(mul(ctx->gw_w, false, Fw, false, ctx->cw_tmp, 1.0, 0));        // G Fw
   return mul(ctx->S, true, ctx->cw_tmp, false, e, -1.0, 1);             // e -= S G Fw
+}
+
+int gw_check_guards(gw_ctx* ctx) {
+  if (!ctx) return fail(GW_EINVAL, "gw_check_guards: null context");
+  std::vector<unsigned char*> all = ctx->guards;
+  if (ctx->mixed) mixed_guards(ctx->mixed, &all);
+  int first = -1;
+  const int bad = check_guards(all.data(), (int)all.size(), &first, ctx->stream);
+  if (bad < 0) return fail(GW_ECUDA, "gw_check_guards: the check did not run");
+  if (bad > 0) return fail(GW_ECUDA, "gw_check_guards: %d of %zu workspace guards overwritten (first: %d)", bad,
+                           all.size(), first);
+  return GW_OK;
+}
+
+int gw_debug_mark_guard(gw_ctx* ctx, int index) {
+  if (!ctx || index < 0 || index >= (int)ctx->guards.size()) return fail(GW_EINVAL, "gw_debug_mark_guard: bad index");
+  // one byte inside the allocation's own guard zone: what a write past the workspace would leave
+  return cudaMemset(ctx->guards[index] + kGuardBytes / 2, 0, 1) == cudaSuccess ? GW_OK
+                                                                            : fail(GW_ECUDA, "gw_debug_mark_guard");
+}
+
+int gw_selftest_bounded_wait(double limit_s, int* code_out, void* cuda_stream) {
+  if (!code_out || !(limit_s >= 1e-3 && limit_s <= 10.0)) return fail(GW_EINVAL, "gw_selftest_bounded_wait: bad argument");
+  *code_out = 0;
+  return mixed_wait_selftest(limit_s, code_out, (cudaStream_t)cuda_stream);
 }
 
 int gw_set_overlap(gw_ctx* ctx, const gw_c128* S_dev) {

@@ -21,6 +21,13 @@ std::vector<int64_t> matsubara_indices(int n, int stat);
 int grid_build(int ntau, double beta, int stat, double* tau, int64_t* idx, gw_c128* F, gw_c128* B);
 int fail(int code, const char* fmt, ...);
 
+// Guard zones: every workspace allocation carries kGuardBytes of kGuardByte after its end, checked
+// by gw_check_guards; an out-of-bounds write past a workspace shows up there.
+constexpr size_t kGuardBytes = 256;
+constexpr unsigned char kGuardByte = 0xA5;
+// number of guards of [guards, guards + n) that differ from the pattern; *first <- index of the first
+int check_guards(unsigned char* const* guards, int n, int* first, void* stream);
+
 // NVTX range over a scope (a no-op unless a tracing tool is attached): the ABI's stages show up
 // by name on a timeline
 struct NvtxRange {

@@ -20,6 +20,8 @@ struct MixedState;
 int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int* status, size_t* bytes,
                  bool dry = false);
 void mixed_destroy(MixedState* s);
+// appends the guard zones of the state's workspaces
+void mixed_guards(const MixedState* s, std::vector<unsigned char*>* out);
 // V: the full-layout Coulomb factor, or null with Vp the packed one (pairs k1 <= k2)
 int mixed_set_coulomb(MixedState* s, const double2* V, const double2* Vp = nullptr);
 int mixed_polarization(MixedState* s, const double2* G, double2* P0t, double spin_factor);
@@ -31,5 +33,7 @@ int mixed_outer_q(MixedState* s, const double2* X, long long x_bs, const double2
 // part[b][q][i][j] = sum_{m l} Y[b][(i q)][(m l)] W[b][(q m)][(l j)] on the tensor cores (FP64 output):
 // the last product of the GF2 exchange, split over q, for nb batches.
 int mixed_gf2_last(MixedState* s, const double2* Y, const double2* W, int nb, int nao, double2* part);
+// launches the bounded-wait self-test (see gw_selftest_bounded_wait); *code receives the wait's code
+int mixed_wait_selftest(double limit_s, int* code, cudaStream_t st);
 
 }  // namespace gwi

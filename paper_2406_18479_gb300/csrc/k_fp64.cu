@@ -884,6 +884,41 @@ int reduce_partials_fp64(const double2* part, double2* out, int nouter, int n2, 
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "reduce_partials launch: %s", cudaGetErrorString(e));
 }
 
+__global__ void check_guards_kernel(unsigned char* const* guards, int n, int* count, int* first) {
+  for (int g = blockIdx.x; g < n; g += gridDim.x) {
+    int bad = 0;
+    for (int i = threadIdx.x; i < (int)kGuardBytes; i += blockDim.x) bad |= guards[g][i] != kGuardByte;
+    if (__syncthreads_or(bad) && threadIdx.x == 0) {
+      atomicAdd(count, 1);
+      atomicMin(first, g);
+    }
+  }
+}
+
+int check_guards(unsigned char* const* guards, int n, int* first, void* stream) {
+  if (n <= 0) return 0;
+  unsigned char** dg = nullptr;
+  int* flags = nullptr;
+  if (cudaMalloc(reinterpret_cast<void**>(&dg), n * sizeof(void*)) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&flags), 2 * sizeof(int)) != cudaSuccess) {
+    cudaFree(dg);
+    cudaGetLastError();
+    return -1;
+  }
+  int h[2] = {0, 1 << 30};
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaMemcpyAsync(dg, guards, n * sizeof(void*), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(flags, h, sizeof h, cudaMemcpyHostToDevice, st);
+  check_guards_kernel<<<std::min(n, 1024), 128, 0, st>>>(dg, n, flags, flags + 1);
+  cudaMemcpyAsync(h, flags, sizeof h, cudaMemcpyDeviceToHost, st);
+  const bool ok = cudaStreamSynchronize(st) == cudaSuccess;
+  cudaFree(dg);
+  cudaFree(flags);
+  if (!ok) return -1;
+  *first = h[1];
+  return h[0];
+}
+
 int exchange_chunks(int nk, int naux) {
   // enough blocks for every SM several times over: 4 x 152 at least, when naux allows
   const int want = (608 + nk * nk - 1) / (nk * nk);

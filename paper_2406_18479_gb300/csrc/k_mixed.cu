@@ -325,13 +325,13 @@ constexpr uint64_t kWaitLimitNs = 4000000000ull;   // 4 s: far beyond any legiti
 
 // Bounded wait. Returns false when the CTA is aborting or the limit passed (and then raises abort).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status,
-                                          int code) {
+                                          int code, uint64_t limit_ns = kWaitLimitNs) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = globaltimer();
   while (true) {
     if (mbar_try(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (globaltimer() - t0 > kWaitLimitNs) {
+    if (globaltimer() - t0 > limit_ns) {
       *abort_flag = 1;
       atomicExch(status + 1, code);
       return false;
@@ -729,6 +729,24 @@ __global__ void __launch_bounds__(352, 1)
   }
 }
 
+// Self-test of the bounded wait: one thread waits, with the production routine, on an mbarrier
+// phase that nothing completes (no arrivals); the wait must give up after limit_ns, write its code
+// to status[1] and let the kernel return.
+__global__ void wait_selftest_kernel(uint64_t limit_ns, int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const bool ok = mbar_wait(&bar, 0, &abort_flag, status, 99, limit_ns);
+    if (ok) atomicExch(status, 1);        // would mean the phase completed: not expected
+  }
+}
+
 // ------------------------------------------------------------------------------------------------
 // host side
 
@@ -890,6 +908,7 @@ struct MixedState {
   __nv_bfloat16* ol_mem = nullptr;   // planes of mixed_gf2_last (allocated on first use)
   size_t ol_elems = 0;
   std::vector<void*> allocs;
+  std::vector<unsigned char*> guards;   // guard zone of each allocation, in the order of allocs
   bool dry = false;   // size-only: count bytes, allocate nothing
 };
 
@@ -898,17 +917,21 @@ namespace {
 template <class T>
 int m_alloc(MixedState* s, T** p, size_t count, size_t* bytes) {
   if (count == 0) count = 1;
+  const size_t nb = count * sizeof(T);
   if (s->dry) {
     *p = nullptr;
-    *bytes += count * sizeof(T);
+    *bytes += nb + kGuardBytes;
     return GW_OK;
   }
-  if (cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T)) != cudaSuccess) {
+  if (cudaMalloc(reinterpret_cast<void**>(p), nb + kGuardBytes) != cudaSuccess) {
     *p = nullptr;
-    return fail(GW_ENOMEM, "mixed workspace: cudaMalloc of %zu bytes failed", count * sizeof(T));
+    return fail(GW_ENOMEM, "mixed workspace: cudaMalloc of %zu bytes failed", nb);
   }
+  unsigned char* guard = reinterpret_cast<unsigned char*>(*p) + nb;
+  cudaMemset(guard, kGuardByte, kGuardBytes);
   s->allocs.push_back(*p);
-  *bytes += count * sizeof(T);
+  s->guards.push_back(guard);
+  *bytes += nb + kGuardBytes;
   return GW_OK;
 }
 
@@ -1253,6 +1276,10 @@ int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int*
   return GW_OK;
 }
 
+void mixed_guards(const MixedState* s, std::vector<unsigned char*>* out) {
+  out->insert(out->end(), s->guards.begin(), s->guards.end());
+}
+
 void mixed_destroy(MixedState* s) {
   if (!s) return;
   for (void* p : s->allocs) cudaFree(p);
@@ -1300,6 +1327,25 @@ int stage_q(MixedState* s, int table, int q, bool col, const Planes& P) {
 
 }  // namespace
 
+int mixed_wait_selftest(double limit_s, int* code, cudaStream_t st) {
+  int* status = nullptr;
+  if (cudaMalloc(reinterpret_cast<void**>(&status), 2 * sizeof(int)) != cudaSuccess)
+    return fail(GW_ENOMEM, "wait self-test: allocation failed");
+  int h[2] = {0, 0};
+  cudaMemsetAsync(status, 0, 2 * sizeof(int), st);
+  wait_selftest_kernel<<<1, 32, 0, st>>>((uint64_t)(limit_s * 1e9), status);
+  int rc = GW_OK;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(h, status, sizeof h, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    rc = fail(GW_ECUDA, "wait self-test: launch or copy failed");
+  cudaFree(status);
+  if (rc != GW_OK) return rc;
+  *code = h[1];
+  if (h[0]) return fail(GW_ECUDA, "wait self-test: a phase that nothing completes was seen complete");
+  return h[1] ? fail(GW_EDEVTIMEOUT, "a device-side wait gave up (code %d)", h[1]) : GW_OK;
+}
+
 namespace {
 
 // (re)allocates a lazily sized plane buffer of at least elems bf16 values
@@ -1308,7 +1354,9 @@ int ensure_mem(MixedState* s, __nv_bfloat16** mem, size_t* have, size_t elems) {
   if (*mem) {
     cudaStreamSynchronize(s->stream);
     cudaFree(*mem);
-    s->allocs.erase(std::find(s->allocs.begin(), s->allocs.end(), (void*)*mem));
+    const size_t at = std::find(s->allocs.begin(), s->allocs.end(), (void*)*mem) - s->allocs.begin();
+    s->allocs.erase(s->allocs.begin() + at);
+    s->guards.erase(s->guards.begin() + at);
     *mem = nullptr;
     *have = 0;
   }
@@ -1372,7 +1420,9 @@ int mixed_outer_q(MixedState* s, const double2* X, long long x_bs, const double2
     if (s->oq_mem) {
       cudaStreamSynchronize(s->stream);
       cudaFree(s->oq_mem);
-      s->allocs.erase(std::find(s->allocs.begin(), s->allocs.end(), (void*)s->oq_mem));
+      const size_t at = std::find(s->allocs.begin(), s->allocs.end(), (void*)s->oq_mem) - s->allocs.begin();
+      s->allocs.erase(s->allocs.begin() + at);
+      s->guards.erase(s->guards.begin() + at);
       s->oq_mem = nullptr;
       s->oq_rows = 0;
     }

@@ -33,7 +33,7 @@ ABI_SYMBOLS = [
     "gw_batch_set_coulomb", "gw_batch_sigma_eval", "gw_batch_autotune", "gw_batch_synchronize",
     "gw_density", "gw_sigma_inf", "gw_set_mu", "gw_particle_number", "gw_find_mu", "gw_diis_create",
     "gw_diis_destroy", "gw_diis_push", "gw_diis_extrapolate", "gw_scgw_bytes", "gw_scgw", "gw_diis_push_residual",
-    "gw_commutator_residual", "gw_gf2_self_energy", "gw_gf2_exchange", "gw_k_interpolate", "gw_ir_grids", "gw_set_overlap", "gw_checkpoint_write", "gw_checkpoint_read",
+    "gw_commutator_residual", "gw_gf2_self_energy", "gw_gf2_exchange", "gw_k_interpolate", "gw_ir_grids", "gw_set_overlap", "gw_checkpoint_write", "gw_checkpoint_read", "gw_selftest_bounded_wait", "gw_check_guards", "gw_debug_mark_guard",
 ]
 GW_BATCH_SERIAL, GW_BATCH_STREAMS, GW_BATCH_GRAPH = 0, 1, 2
 BATCH_MODES = {"serial": GW_BATCH_SERIAL, "streams": GW_BATCH_STREAMS, "graph": GW_BATCH_GRAPH}
@@ -153,6 +153,9 @@ def lib():
     L.gw_gf2_self_energy.argtypes = [vp, vp, vp]
     L.gw_gf2_exchange.argtypes = [vp, vp, vp]
     L.gw_set_overlap.argtypes = [vp, vp]
+    L.gw_selftest_bounded_wait.argtypes = [d, ctypes.POINTER(i), vp]
+    L.gw_check_guards.argtypes = [vp]
+    L.gw_debug_mark_guard.argtypes = [vp, i]
     L.gw_checkpoint_write.argtypes = [ctypes.c_char_p, ctypes.POINTER(gw_config), d, i, i, vp, vp, vp]
     L.gw_checkpoint_read.argtypes = [ctypes.c_char_p, ctypes.POINTER(gw_config), ctypes.POINTER(d),
                                      ctypes.POINTER(i), i, vp, vp, vp]
@@ -717,3 +720,22 @@ def gw_checkpoint_read(path, shapes: dict, cfg: gw_config = None):
                                     ctypes.cast(names, ctypes.c_void_p), ctypes.cast(data, ctypes.c_void_p),
                                     ctypes.cast(counts, ctypes.c_void_p)))
     return cfg, mu.value, it.value, out
+
+
+def gw_selftest_bounded_wait(limit_s=0.2, stream=None):
+    """(status, code) of the bounded-wait self-test: GW_EDEVTIMEOUT and 99 when the wait gave up."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    code = ctypes.c_int(0)
+    rc = lib().gw_selftest_bounded_wait(float(limit_s), ctypes.byref(code), ctypes.c_void_p(st.cuda_stream))
+    return rc, code.value
+
+
+def gw_check_guards(ctx: gw_ctx):
+    """Raises GWError if a kernel wrote past the end of one of the context's workspaces."""
+    _check(lib().gw_check_guards(ctx.handle))
+
+
+def gw_debug_mark_guard(ctx: gw_ctx, index: int = 0):
+    """Test hook: change one byte of a guard zone so that gw_check_guards must report it."""
+    _check(lib().gw_debug_mark_guard(ctx.handle, int(index)))

@@ -90,7 +90,8 @@ def test_serving_job_and_bytes(G):
     cp = G.make_config(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision="bf16x3", v_slices=2, v_packed=True)
     vbytes = 16 * w.naux * w.nao ** 2
     # the job's V shrinks from nk^2 to nk (nk + 1) / 2 blocks; the per-q scratch adds nk blocks
-    assert G.gw_job_bytes(cf) - G.gw_job_bytes(cp) == vbytes * (w.nk * w.nk - w.nk * (w.nk + 1) // 2 - w.nk)
+    # (and the scratch's 256-byte guard zone)
+    assert G.gw_job_bytes(cf) - G.gw_job_bytes(cp) == vbytes * (w.nk * w.nk - w.nk * (w.nk + 1) // 2 - w.nk) - 256
     srv = G.gw_server(8 << 30, 2)
     out = []
     for cfg, vv in ((cf, v), (cp, I.pack_v(v))):
