@@ -186,7 +186,7 @@ int dev_alloc(gw_ctx* c, T** p, size_t count) {
     return fail(GW_ENOMEM, "cudaMalloc of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
   }
   unsigned char* guard = reinterpret_cast<unsigned char*>(*p) + bytes;
-  cudaMemset(guard, kGuardByte, kGuardBytes);
+  cudaMemsetAsync(guard, kGuardByte, kGuardBytes, c->stream);   // ordered before the context's work
   c->guards.push_back(guard);
   c->bytes += bytes + kGuardBytes;
   return GW_OK;

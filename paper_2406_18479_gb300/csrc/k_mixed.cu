@@ -928,7 +928,7 @@ int m_alloc(MixedState* s, T** p, size_t count, size_t* bytes) {
     return fail(GW_ENOMEM, "mixed workspace: cudaMalloc of %zu bytes failed", nb);
   }
   unsigned char* guard = reinterpret_cast<unsigned char*>(*p) + nb;
-  cudaMemset(guard, kGuardByte, kGuardBytes);
+  cudaMemsetAsync(guard, kGuardByte, kGuardBytes, s->stream);   // ordered before the state's work
   s->allocs.push_back(*p);
   s->guards.push_back(guard);
   *bytes += nb + kGuardBytes;
