@@ -4,7 +4,11 @@
  * The library evaluates the dynamical GW self-energy of fully self-consistent
  * finite-temperature GW with density-fitted Coulomb integrals
  * (arXiv 2406.18479, Sec. 2.3, Eqs. tilde_P0_tau, P0t_to_P0w, tilde_P_omega,
- * tilde_W_DF2, sigma_gw) and the Dyson update of G (Sec. 2.5, Eq. dyson).
+ * tilde_W_DF2, sigma_gw) and the Dyson update of G (Sec. 2.5, Eq. dyson), and the
+ * rest of the self-consistency loop around them (Sec. 2.4: the static part,
+ * Eq. sigma_inf; the chemical potential; mixing, DIIS and CDIIS, Sec. 5.3), the
+ * second-order self-energy (Eq. sigma2), Hartree-Fock, IR and Chebyshev grids and
+ * the k-space interpolation of Sec. 2.5.
  *
  * Conventions shared by every call
  * --------------------------------
