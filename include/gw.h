@@ -37,6 +37,12 @@
  * Every call returns a gw_status. On failure the call leaves its outputs
  * undefined and gw_last_error() returns a thread-local message. Nothing is
  * thrown across the ABI.
+ *
+ * Threads: a context, a DIIS subspace or a batch is used by one thread at a time
+ * (its calls are ordered on its stream); different objects may be used from
+ * different threads at once. The server's calls (gw_submit, gw_poll, ...) may come
+ * from any thread. Host-only calls (gw_grid_build, gw_ir_grids, gw_checkpoint_*,
+ * gw_sample_count, the *_bytes queries) need no device.
  */
 #ifndef GW_GB300_H
 #define GW_GB300_H
