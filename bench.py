@@ -353,17 +353,19 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- device-resident timed region
     gw.gw_profile_enable(ctx, True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # one event before the first step and one after every step: the total and the per-step spread
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
+        evs[0].record(stream)
+        for i in range(args.steps):
             gw.gw_sigma_eval(ctx, G, Sig)
-        e1.record(stream)
+            evs[i + 1].record(stream)
         torch.cuda.synchronize()
     barrier()
-    ms = e0.elapsed_time(e1)
+    ms = evs[0].elapsed_time(evs[-1])
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
     launches = gw.gw_launch_count(ctx)
     prof = gw.gw_profile_read(ctx)
     gw.gw_profile_enable(ctx, False)
@@ -460,6 +462,8 @@ def run_ours(args, rank, world, local_rank):
                    "v_layout": "packed k1<=k2" if args.v_packed else "all pairs",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "tflops_algorithmic": flops * world * steps / (t_max / 1e3) / 1e12,
+        "step_ms": {"median": float(np.median(step_ms)), "p99": float(np.percentile(step_ms, 99)),
+                    "min": float(np.min(step_ms)), "max": float(np.max(step_ms))},
         "roofline": {"kernel": dname, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_note},
         "kernels": kernels,
