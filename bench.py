@@ -4,10 +4,12 @@
 One step is one self-energy evaluation -- P0(tau) (Eq. tilde_P0_tau), the
 tau -> i Omega transform, the auxiliary Dyson equation (Eq. tilde_P_omega),
 the transform back, and Sigma(tau) (Eqs. sigma_gw, tilde_W_DF2) -- over every
-k and tau of the Si-like 3x3x3 solid (nk=27, nao=26, naux=200, ntau=100,
-beta=100), with V, G and all workspaces resident in HBM.
+k and tau of the 4x4x4 solid (nk=64, nao=52, naux=400, ntau=120, beta=200;
+4295 TFLOP per evaluation), with V, G and all workspaces resident in HBM.
+The Si-like 3x3x3 solid (nk=27, nao=26, naux=200) runs with
+--workload solid_3x3x3_nao26.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x3|fp64]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x4|fp64]
     python bench.py --impl reference      # the FP64 CPU oracle on a bounded sample
     python bench.py --serving [--serving-jobs N] [--precision P]   # scGW job stream alone
     python bench.py --batched [--precision P] [--steps K]          # 48 molecules: loop vs graph
@@ -35,8 +37,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("GW Σ evals/s & TFLOP/s vs peak, mixed vs FP64 at max|ΔΣ|≤1e-6 Ha; p50/p99")
 UNIT = "sigma_evals/s"
-WORKLOAD = "solid_3x3x3_nao26"
-FP64_PEAK_TFLOPS = 1.25      # GB300 nominal FP64 (no FP64 tensor path is faster on this part)
+WORKLOAD = "solid_4x4x4_nao52"
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 nominal FP64, used only if the live measurement fails
+# a full FP64 evaluation is compared only up to this many algorithmic TFLOP (about 2 minutes of
+# FP64 work); above it the FP64 comparison runs on a sample of momentum transfers q
+FP64_FULL_MAX_TFLOP = 100.0
 
 
 def canonical_fraction(nk3, n):
@@ -57,6 +62,42 @@ def algorithmic_flops(nk3, nao, naux, ntau, nwb):
     transforms = 2 * 8.0 * nk * nwb * ntau * naux ** 2
     dyson = (8.0 * nk * nwb * naux ** 3 + 2.0 * nk * nwb * naux ** 2) * canonical_fraction(nk3, nwb)
     return contraction * canonical_fraction(nk3, ntau) + contraction + transforms + dyson
+
+
+def stage_flops(nk3, nao, naux, ntau):
+    """Algorithmic flops (8 per complex multiply-add) of one evaluation per tensor-core GEMM class,
+    as computed: P0 and its V.G products at canonical (q, tau), the Sigma side at every (q, tau)."""
+    nk = int(np.prod(nk3))
+    cf = canonical_fraction(nk3, ntau)
+    per = 8.0 * nk * nk * ntau
+    return {"vg_gemm_tc": per * (2.0 * naux * nao ** 3 * cf + naux * nao ** 3),
+            "p0_gemm_tc": per * cf * naux ** 2 * nao ** 2,
+            "r_gemm_tc": per * naux ** 2 * nao ** 2,
+            "sigma_gemm_tc": per * naux * nao ** 3}
+
+
+def fp64_peak_tflops():
+    """Measured FP64 rate of this GPU: torch complex128 matmul (cuBLAS ZGEMM) of 4096^3, best
+    of 5, 8 real flops per complex multiply-add. cuBLAS serves only as the yardstick here."""
+    import torch
+    try:
+        a = torch.randn(4096, 4096, dtype=torch.complex128, device="cuda")
+        b = torch.randn_like(a)
+        torch.matmul(a, b)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        del a, b
+        return 8.0 * 4096 ** 3 / (best * 1e-3) / 1e12, "complex128 matmul 4096^3 on this GPU (measured)"
+    except Exception as e:  # noqa: BLE001 - the nominal figure stands in, labelled as such
+        return FP64_NOMINAL_TFLOPS, f"GB300 nominal (measurement failed: {e})"
 
 
 def measured_peaks():
@@ -163,11 +204,20 @@ def oracle_sample(w, h, v, g, budget_s=15.0):
     return 1.0 / per_eval, sample, time.perf_counter() - start
 
 
-def blas_threads():
-    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
-        if os.environ.get(var):
-            return int(os.environ[var])
-    return os.cpu_count()
+class CpuMeter:
+    """Cores a block of host work actually kept busy: process CPU time over wall time."""
+
+    def __enter__(self):
+        self.c0, self.w0 = time.process_time(), time.perf_counter()
+        return self
+
+    def __exit__(self, *a):
+        self.cpu = time.process_time() - self.c0
+        self.wall = time.perf_counter() - self.w0
+
+    @property
+    def cores(self):
+        return round(self.cpu / max(self.wall, 1e-9), 1)
 
 
 def source_hash(rec):
@@ -225,9 +275,10 @@ def run_reference(args, rank):
     for _ in range(args.warmup):
         oracle_sample(w, h, v, g, budget_s=2.0)
     t_all = time.perf_counter()
-    for _ in range(args.steps):
-        val, sample, _ = oracle_sample(w, h, v, g, budget_s=args.ref_budget)
-        vals.append(val)
+    with CpuMeter() as cpu:
+        for _ in range(args.steps):
+            val, sample, _ = oracle_sample(w, h, v, g, budget_s=args.ref_budget)
+            vals.append(val)
     wall = time.perf_counter() - t_all
     value = float(np.median(vals))
     line = {
@@ -236,8 +287,9 @@ def run_reference(args, rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic (seeded)",
         "config": {"workload": w.name, "nk": w.nk, "nao": w.nao, "naux": w.naux, "ntau": w.ntau,
                    "beta": w.beta, "l2": "n/a (CPU)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-                         "sample": sample + "; numpy loops, BLAS threads as reported"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu.cores, "kind": "oracle",
+                         "sample": sample + f"; numpy with its BLAS, cores = CPU time / wall time of the "
+                                            f"timed samples ({os.cpu_count()} available)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": wall,
     }
@@ -313,6 +365,70 @@ def serving_measure(precision, n_jobs, slots=4, budget_gb=160.0, max_tflop=None,
     }
 
 
+def fp64_compare(w, V, G, Sig_mixed, ctx, grid, args, t_mixed_ms):
+    """Mixed against the GPU FP64 path. A full FP64 evaluation up to FP64_FULL_MAX_TFLOP of work;
+    above it, a sample of momentum transfers (Eq. sigma_gw sums over q, gw_sigma_eval_q gives the
+    part of one q): q = 0, whose -q is itself, so that its cost is the average per-q cost of a
+    full evaluation (P0 at half the tau nodes by the mirror relation, Sigma at all). Reports the
+    largest |dSigma_q| over the sample, and two extrapolations to the full sum over nk values of q:
+    sqrt(nk) x that (errors of independent q adding like a random walk) and nk x that (the triangle
+    inequality, a bound)."""
+    import torch
+    from paper_2406_18479_gb300 import gw
+
+    def make64():
+        c = gw.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision="fp64", v_packed=args.v_packed)
+        if grid is not None:
+            gw.gw_set_grids(c, *grid)
+        gw.gw_set_coulomb(c, V)
+        return c
+
+    def timed(stream, fn):
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        fn()
+        a1.record(stream)
+        torch.cuda.synchronize()
+        return a0.elapsed_time(a1)
+
+    if algorithmic_flops(w.nk3, w.nao, w.naux, w.ntau, gw.gw_sample_count(w.ntau, 0)) <= FP64_FULL_MAX_TFLOP * 1e12:
+        gw.gw_sigma_eval(ctx, G, Sig_mixed)
+        torch.cuda.synchronize()
+        mixed = Sig_mixed.cpu()
+        ctx.destroy()
+        torch.cuda.empty_cache()
+        c64 = make64()
+        S64 = torch.empty_like(Sig_mixed)
+        ms64 = timed(c64.stream, lambda: gw.gw_sigma_eval(c64, G, S64))
+        ref = S64.cpu()
+        c64.destroy()
+        return {"method": "full evaluation", "ms_per_eval": ms64, "speedup_mixed_over_fp64": ms64 / t_mixed_ms,
+                "max_abs_dSigma_Ha": float((mixed - ref).abs().max()),
+                "max_abs_Sigma_Ha": float(ref.abs().max())}
+    q = 0
+    gw.gw_sigma_eval_q(ctx, G, Sig_mixed, q, q + 1)
+    torch.cuda.synchronize()
+    mixed = Sig_mixed.cpu()
+    ctx.destroy()
+    torch.cuda.empty_cache()
+    c64 = make64()
+    S64 = torch.empty_like(Sig_mixed)
+    ms_q = timed(c64.stream, lambda: gw.gw_sigma_eval_q(c64, G, S64, q, q + 1))
+    ref = S64.cpu()
+    c64.destroy()
+    d = float((mixed - ref).abs().max())
+    ms64 = ms_q * w.nk
+    return {"method": f"sample of q: q = {q} (the part of Sigma from one momentum transfer, Eq. sigma_gw)",
+            "q": [q], "ms_per_q_fp64": ms_q,
+            "ms_per_eval": ms64, "ms_per_eval_note": "extrapolated: nk x the FP64 time of q = 0",
+            "speedup_mixed_over_fp64": ms64 / t_mixed_ms,
+            "max_abs_dSigma_q_Ha": d, "max_abs_Sigma_q_Ha": float(ref.abs().max()),
+            "max_abs_dSigma_Ha_estimate": d * float(np.sqrt(w.nk)),
+            "max_abs_dSigma_Ha_bound": d * w.nk,
+            "estimate_note": "sqrt(nk) x the sampled q (independent per-q errors); bound: nk x it"}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2406_18479_gb300 import gw, inputs as I
@@ -330,6 +446,7 @@ def run_ours(args, rank, world, local_rank):
     base = I.WORKLOADS[args.workload]
     w = I.Workload(base.name, base.nk3, base.nao, base.naux, base.ntau, base.nomega, base.beta, base.mu,
                    base.decay, base.seed + rank, base.solid)
+    t_in = time.perf_counter()
     h, v, g = I.make_inputs(w)
     grid = None
     if args.ir_lambda > 0:
@@ -340,21 +457,33 @@ def run_ours(args, rank, world, local_rank):
         g = I.g0_tau(h, w.mu, w.beta, grid[0])
     V = torch.from_numpy(I.pack_v(v) if args.v_packed else v).cuda()
     G = torch.from_numpy(g).cuda()
+    v_bytes = V.numel() * 16
+    keep_v = rank == 0 and world == 1 and not args.no_cpu_baseline and grid is None
+    if not keep_v:
+        del v
+    input_s = time.perf_counter() - t_in
     ctx = gw.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision=args.precision, tau_chunk=args.tau_chunk,
-                       v_packed=args.v_packed)
+                       v_packed=args.v_packed, slice_pass=args.slice_pass)
     if grid is not None:
         gw.gw_set_grids(ctx, *grid)
     Sig = torch.empty(ctx.shapes()["Sig"], dtype=torch.complex128, device="cuda")
     gw.gw_set_coulomb(ctx, V)
     stream = ctx.stream
-    for _ in range(args.warmup):
+    # warm-up; the last warm-up evaluation is profiled per launch (CUDA events on the stream) for the
+    # kernel shares and the roofline, so that the timed evaluations run without instrumentation
+    for i in range(args.warmup):
+        if i == args.warmup - 1:
+            gw.gw_profile_enable(ctx, True)
         gw.gw_sigma_eval(ctx, G, Sig)
     gw.gw_synchronize(ctx)
+    prof = gw.gw_profile_read(ctx)
+    gw.gw_profile_enable(ctx, False)
+    gw.gw_synchronize(ctx)
 
-    # ---- device-resident timed region
-    gw.gw_profile_enable(ctx, True)
+    # ---- device-resident timed region (no per-launch instrumentation)
     # one event before the first step and one after every step: the total and the per-step spread
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    launches0 = gw.gw_launch_count(ctx)
     barrier()
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
@@ -366,16 +495,13 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     ms = evs[0].elapsed_time(evs[-1])
     step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
-    launches = gw.gw_launch_count(ctx)
-    prof = gw.gw_profile_read(ctx)
-    gw.gw_profile_enable(ctx, False)
-    gw.gw_synchronize(ctx)
+    launches = gw.gw_launch_count(ctx) - launches0
     t_max = max_over_ranks(ms, dist)
 
-    # ---- end to end through the public API with host buffers (pinned)
+    # ---- end to end through the public API with host buffers (pinned): about a minute of steps
     G_host = torch.from_numpy(g).pin_memory()
     S_host = torch.empty(Sig.shape, dtype=Sig.dtype).pin_memory()
-    k_e2e = max(1, args.steps)
+    k_e2e = max(1, min(args.steps, int(np.ceil(60000.0 / max(t_max / args.steps, 1e-3)))))
     barrier()
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -389,51 +515,59 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(f0.elapsed_time(f1), dist)
 
-    # ---- optional FP64 comparison (one evaluation) for the mixed precisions
+    # ---- FP64 comparison for the mixed precisions (full, or on a sample of q); frees ctx
     fp64 = None
     if args.precision != "fp64" and args.fp64_compare:
-        c64 = gw.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision="fp64", v_packed=args.v_packed)
-        if grid is not None:
-            gw.gw_set_grids(c64, *grid)
-        S64 = torch.empty_like(Sig)
-        gw.gw_set_coulomb(c64, V)
-        torch.cuda.synchronize()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(c64.stream)
-        gw.gw_sigma_eval(c64, G, S64)
-        a1.record(c64.stream)
-        torch.cuda.synchronize()
-        ms64 = a0.elapsed_time(a1)
-        gw.gw_sigma_eval(ctx, G, Sig)
-        torch.cuda.synchronize()
-        dsig = float((Sig - S64).abs().max().item())
-        fp64 = {"ms_per_eval": ms64, "speedup_mixed_over_fp64": ms64 / (t_max / args.steps),
-                "max_abs_dSigma_Ha": dsig, "max_abs_Sigma_Ha": float(S64.abs().max().item())}
-        c64.destroy()
+        fp64 = fp64_compare(w, V, G, Sig, ctx, grid, args, t_max / args.steps)
+    else:
+        ctx.destroy()
+    del V
+    torch.cuda.empty_cache()
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
 
+    fp64_peak, fp64_peak_note = fp64_peak_tflops()
     serving = None
     if world == 1 and args.serving_jobs > 0:
         serving = serving_measure(args.precision, args.serving_jobs)
+        if args.precision != "fp64" and args.fp64_compare:
+            # mixed and FP64 on the same jobs: those of the sample at most this many TFLOP per
+            # evaluation, so that the FP64 pass takes seconds
+            lim = args.serving_fp64_max_tflop
+            serving["vs_fp64"] = {"max_tflop_per_eval": lim,
+                                  args.precision: serving_measure(args.precision, args.serving_jobs, max_tflop=lim),
+                                  "fp64": serving_measure("fp64", args.serving_jobs, max_tflop=lim)}
 
     nwb = gw.gw_sample_count(w.ntau, 0)
     flops = algorithmic_flops(w.nk3, w.nao, w.naux, w.ntau, nwb)
     steps = args.steps
     value = world * steps / (t_max / 1e3)
     peaks, peak_src = measured_peaks()
-    # dominant kernel by device time
-    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])
-    dname, d = dom
+    bf16_peak = peaks["bf16_tflops_sustained"]
+    alg = stage_flops(w.nk3, w.nao, w.naux, w.ntau)
+    prof_total = sum(y["ms"] for y in prof.values())
+    kernels = {}
+    for k, x in prof.items():
+        e = {"launches": x["launches"], "ms": round(x["ms"], 3), "share": round(x["ms"] / prof_total, 4)}
+        if k.endswith("_tc") and x["ms"] > 0:
+            ex = x["flops"] / (x["ms"] * 1e-3) / 1e12
+            e["executed_bf16_tflops"] = round(ex, 1)
+            e["tensor_pipe_frac_of_sustained_peak"] = round(ex / bf16_peak, 4)
+            if k in alg:
+                e["algorithmic_tflops"] = round(alg[k] / (x["ms"] * 1e-3) / 1e12, 2)
+        kernels[k] = e
+    # dominant kernel by device time (of the profiled evaluation)
+    dname, d = max(prof.items(), key=lambda kv: kv[1]["ms"])
     per_launch_ms = d["ms"] / d["launches"]
     if dname.endswith("_tc"):
         bound, unit = "tensor", "TFLOP/s"
         achieved = d["flops"] / d["launches"] / (per_launch_ms * 1e-3) / 1e12
-        peak = peaks["bf16_tflops_sustained"]
-        peak_note = f"bf16 dense sustained ({peak_src})"
+        peak = bf16_peak
+        peak_note = (f"bf16 dense sustained ({peak_src}); achieved counts the executed bf16 flops "
+                     f"(10 slice products of 4 real MMAs per complex multiply-add)")
     elif dname in ("slice_planes", "elementwise", "reduce"):
         bound, unit = "hbm", "GB/s"
         achieved = d["bytes"] / d["launches"] / (per_launch_ms * 1e-3) / 1e9
@@ -442,46 +576,49 @@ def run_ours(args, rank, world, local_rank):
     else:
         bound, unit = "alu", "TFLOP/s"
         achieved = d["flops"] / d["launches"] / (per_launch_ms * 1e-3) / 1e12
-        peak = FP64_PEAK_TFLOPS
-        peak_note = "FP64 pipe, GB300 nominal 1.25 TFLOP/s (cuBLAS ZGEMM measured 1.10)"
+        peak, peak_note = fp64_peak, "FP64: " + fp64_peak_note
     traffic = ncu_traffic(dname, d["bytes"] / d["launches"])
     clocks = clk.summary()
-    kernels = {k: {"launches": x["launches"], "ms": round(x["ms"], 3),
-                   "share": round(x["ms"] / sum(y["ms"] for y in prof.values()), 4)} for k, x in prof.items()}
+    p_bytes = w.nk * w.ntau * w.naux ** 2 * 16
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps, "warmup": args.warmup,
         "ms_per_step": t_max / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "c128 (f64)",
-                  "bf16x3": "bf16 (four exact slices per operand), f32 accumulate, f64 transforms/Dyson"}[args.precision],
+                  "bf16x4": "bf16 (four exact slices per operand), f32 accumulate, f64 transforms/Dyson"}[args.precision],
         "data": "synthetic (seeded H(k), V, G0 shaped like the paper's Si example)",
         "config": {"workload": w.name, "nk": w.nk, "nao": w.nao, "naux": w.naux, "ntau": w.ntau,
                    "nomega": nwb, "beta": w.beta, "precision": args.precision, "tau_chunk": args.tau_chunk,
-                   "l2": "inputs larger than L2 (V 1.58 GB, P 1.73 GB per pass)",
+                   "slice_output": "separate slicing pass" if args.slice_pass else "from the producing GEMM where the sizes allow",
+                   "l2": f"inputs larger than L2 (V {v_bytes / 1e9:.1f} GB, P {p_bytes / 1e9:.1f} GB per pass)",
                    "grid": (f"IR Lambda={args.ir_lambda:g} eps={args.ir_eps:g}" if grid is not None
                             else "Chebyshev"),
                    "v_layout": "packed k1<=k2" if args.v_packed else "all pairs",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "tflops_algorithmic": flops * world * steps / (t_max / 1e3) / 1e12,
+        "tflop_per_eval_algorithmic": flops / 1e12,
         "step_ms": {"median": float(np.median(step_ms)), "p99": float(np.percentile(step_ms, 99)),
                     "min": float(np.min(step_ms)), "max": float(np.max(step_ms))},
         "roofline": {"kernel": dname, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_note},
         "kernels": kernels,
+        "kernels_note": "one profiled warm-up evaluation (CUDA events per launch); the timed steps ran without",
+        "fp64_peak_tflops": {"value": fp64_peak, "source": fp64_peak_note},
         "gpu_launches": launches,
-        "e2e": {"value": world * k_e2e / (e2e_ms / 1e3), "unit": UNIT,
+        "e2e": {"value": world * k_e2e / (e2e_ms / 1e3), "unit": UNIT, "steps": k_e2e,
                 "h2d_bytes_per_step": int(G.numel() * 16), "d2h_bytes_per_step": int(Sig.numel() * 16)},
         "clocks": clocks,
+        "input_generation_s": input_s,
     }
     if fp64 is not None:
         line["fp64"] = fp64
     if serving is not None:
         line["serving"] = serving
-    if world == 1 and not args.no_cpu_baseline and grid is None:
-        val, sample, spent = oracle_sample(w, h, v, g, budget_s=args.ref_budget)
-        line["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": blas_threads(), "kind": "oracle",
-                                "sample": sample}
+    if keep_v:
+        with CpuMeter() as cpu:
+            val, sample, spent = oracle_sample(w, h, v, g, budget_s=args.ref_budget)
+        line["cpu_baseline"] = {"value": val, "unit": UNIT, "cores": cpu.cores, "kind": "oracle",
+                                "sample": sample + f"; cores = CPU time / wall time ({os.cpu_count()} available)"}
     print(json.dumps(line), flush=True)
-    ctx.destroy()
     if dist is not None:
         dist.destroy_process_group()
 
@@ -687,11 +824,12 @@ def run_gf2(args, rank, local_rank):
         peaks, peak_src = measured_peaks()
         bound, peak, peak_note = "tensor", peaks["bf16_tflops_sustained"], f"bf16 dense sustained ({peak_src})"
     else:
-        bound, peak, peak_note = "alu", FP64_PEAK_TFLOPS, "FP64 pipe, GB300 nominal 1.25 TFLOP/s"
+        peak, peak_note = fp64_peak_tflops()
+        bound, peak_note = "alu", "FP64: " + peak_note
     line = {"metric": "GF2 self-energy evaluations/s (Eq. sigma2)", "value": 1e3 / ms, "unit": "sigma_evals/s",
             "n_gpus": 1, "steps": steps, "warmup": 1, "ms_per_step": ms, "higher_is_better": True,
             "dtype": {"fp64": "c128 (f64)",
-                      "bf16x3": "bf16 slices for the direct term and the exchange's nao^4 naux products, "
+                      "bf16x4": "bf16 slices for the direct term and the exchange's nao^4 naux products, "
                                 "f64 for the rest"}[args.precision],
             "data": "synthetic (seeded molecule)",
             "config": {"workload": w.name, "nao": w.nao, "naux": w.naux, "ntau": w.ntau, "beta": w.beta,
@@ -712,13 +850,16 @@ def main():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["bf16x3", "fp64"], default=None)
+    ap.add_argument("--precision", choices=["bf16x4", "bf16x3", "fp64"], default=None,
+                    help="bf16x4: four bf16 slices per operand (bf16x3 is its former name)")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-fp64-compare", dest="fp64_compare", action="store_false",
                     help="skip the one FP64 evaluation that gives the mixed/FP64 speed-up and max|dSigma|")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-budget", type=float, default=15.0)
     ap.add_argument("--tau-chunk", type=int, default=0, help="tau nodes per contraction batch (0: automatic)")
+    ap.add_argument("--slice-pass", action="store_true",
+                    help="slice every GEMM operand in a separate pass (no slice-output epilogues)")
     ap.add_argument("--serving-jobs", type=int, default=12,
                     help="jobs of the scGW stream measured beside the main line (0: none)")
     ap.add_argument("--serving", action="store_true",
@@ -726,6 +867,8 @@ def main():
     ap.add_argument("--serving-max-tflop", type=float, default=None,
                     help="leave out stream jobs above this many TFLOP per evaluation")
     ap.add_argument("--serving-slots", type=int, default=4)
+    ap.add_argument("--serving-fp64-max-tflop", type=float, default=0.5,
+                    help="jobs of the serving sample compared in mixed and FP64: at most this many TFLOP per evaluation")
     ap.add_argument("--batched", action="store_true",
                     help="measure only the 48-molecule batch (loop vs streams vs graph) and print its own line")
     ap.add_argument("--batch-streams", type=int, default=8)
@@ -742,8 +885,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.precision is None:
-        args.precision = "bf16x3"
+    if args.precision is None or args.precision == "bf16x3":
+        args.precision = "bf16x4"
     if args.steps is None:
         args.steps = 2 if args.precision == "fp64" else (3 if (args.batched or args.loop or args.gf2) else 10)
     rank = int(os.environ.get("RANK", "0"))

@@ -71,14 +71,17 @@ typedef enum {
 
 typedef enum {
   GW_FP64 = 0,          /* every contraction in FP64 */
-  GW_MIXED_BF16X3 = 1,  /* V.G.V contractions on tcgen05 tensor cores: each operand row is cut,
+  GW_MIXED_BF16X4 = 1,  /* V.G.V contractions on tcgen05 tensor cores: each operand row is cut,
                            per chunk of at most 256 k, into four bf16 slices on one power-of-two
                            alignment; slice products of order 0 and 1 sum exactly in their own
                            FP32 accumulators, orders 2-3 share a third, higher orders are dropped
                            (2^-32 relative); transforms, Dyson solves and the Sigma accumulation
                            stay FP64 */
-  GW_MIXED_FP16S = 2    /* reserved: gw_create returns GW_ENOTIMPL */
+  GW_MIXED_BF16X3 = 1   /* former name of GW_MIXED_BF16X4 (the scheme always had four slices) */
 } gw_precision;
+/* Value 2 (a single FP16 operand per tile with a power-of-two scale) is not a precision of this
+ * library: its error, about 1e-4 of max|Sigma|, is five orders of magnitude above the 1e-6 Ha
+ * target; gw_create rejects it with GW_EINVAL. */
 
 /*
  * Where the mixed precisions keep the bf16 slices of V: for all nk^2 (k1, k2) pairs, made
@@ -103,6 +106,11 @@ typedef struct {
                            working copy in the context; the mixed precisions unpack the blocks
                            they slice (all pairs once, through a transient buffer, or the nk
                            blocks of one q at a time) and keep no FP64 copy */
+  int slice_pass;       /* mixed precisions: 0 = the V.G products and R write the next
+                           contraction's bf16 slices from their epilogue where the sizes allow
+                           (nao % 4 == 0, nao <= 56, naux % 40 == 0), 1 = always through FP64-range
+                           intermediates and a separate slicing pass. Both meet the same error
+                           bound; their results differ by rounding order (the chunks differ). */
 } gw_config;
 
 /* Library version string. */
@@ -233,6 +241,24 @@ int gw_self_energy(gw_ctx* ctx, const gw_c128* G_dev, const gw_c128* Pt_dev, gw_
 int gw_sigma_eval(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* Sig_dev);
 
 /*
+ * The part of one evaluation that comes from the momentum transfers q in [q_begin, q_end).
+ * Eq. sigma_gw is a sum over q, and P0^q (Eq. tilde_P0_tau), P~^q (Eq. tilde_P_omega) and the
+ * transforms are computed per q, so the partial sums of disjoint ranges add up to the full
+ * Sigma (up to rounding order): this is the unit by which the path shards over GPUs (each
+ * rank a range, one sum of Sig over ranks), and the unit of sampled accuracy checks.
+ *   Sig_dev [nk][ntau][nao][nao] is overwritten with
+ *   -(1/N_k) sum_{q in range} sum_QQ'ab V^{k,k-q}_ia(Q) G^{k-q}_ab(tau) P~^q_QQ'(tau) V^{k-q,k}_bj(Q').
+ * A q whose -q lies in the range uses the symmetry P0^q(beta - tau) = P0^{-q}(tau)^T as
+ * gw_sigma_eval does; a q whose -q lies outside is computed at every tau node and frequency.
+ * [0, nk) gives the result of gw_sigma_eval bit for bit. P0t_dev and Pt_dev (optional, null to
+ * skip; device, [q_end - q_begin][ntau][naux][naux], caller-owned) receive P0^q(tau) and
+ * P~^q(tau) of the range. GW_EINVAL for a range outside [0, nk) or with q_begin > q_end (an
+ * empty range writes Sig = 0).
+ */
+int gw_sigma_eval_q(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* Sig_dev, int q_begin, int q_end,
+                    gw_c128* P0t_dev, gw_c128* Pt_dev);
+
+/*
  * Dyson equation, Eq. dyson (Sec. 2.5) with S = I and Sigma^inf = 0:
  *   G^k(i w_n) = [(i w_n + mu) I - H^k - Sigma^k(i w_n)]^{-1},
  * with Sigma(i w) = F^f Sigma(tau) and G(tau) = B^f G(i w) on the fermionic grid.
@@ -273,25 +299,29 @@ int gw_profile_read(gw_ctx* ctx, int slot, char* name, int name_cap, long long* 
                     double* total_ms, double* flops, double* bytes);
 
 /*
- * P0(tau) of gw_polarization (FP64) for callers that cannot allocate device
- * memory when they call: code inside a CUDA-graph capture, where cudaMalloc
- * cannot be recorded, or a host whose device memory budget is already handed
- * out to its own pools. This entry point has no counterpart in the paper; it
- * is an allocation-free form of step (a).
+ * P0(tau) of gw_polarization (FP64) for callers that cannot allocate device memory when they
+ * call. Some hosts reserve all the device memory they will use at start-up and hand it to
+ * their own pools (a serving runtime sized to the GPU's HBM), so a later cudaMalloc fails or
+ * would break their accounting; some embedding runtimes forbid allocation after
+ * initialisation; and some latency-critical loops cannot afford the device-wide
+ * synchronisation that cudaMalloc and cudaFree may imply. This entry point has no counterpart
+ * in the paper; it is an allocation-free form of step (a).
  *
- * Needs no context: sizes, spin factor, V_dev, G_dev and the output P0t_dev
- * (layouts as above) are passed directly; work is queued on cuda_stream
- * (a cudaStream_t, NULL = legacy default stream). The V.G intermediates live
- * in one fixed 64 MiB device array inside the library, which every GPU that
- * loads the library holds until the process exits. The call rejects, with
- * GW_EINVAL and a message, problems whose one (tau, k) unit needs more than
- * that array (2 * naux * nao^2 complex elements > 4 Mi).
+ * Needs no context: sizes, spin factor, V_dev, G_dev and the output P0t_dev (layouts as above,
+ * device memory of the current device, owned by the caller) are passed directly; work is
+ * queued on cuda_stream (a cudaStream_t, NULL = legacy default stream). GW_EINVAL when a pointer
+ * is null or not device memory of the current device. The V.G intermediates live in one fixed
+ * 64 MiB device array inside the library, which every GPU that loads the library holds until
+ * the process exits. The call rejects, with GW_EINVAL and a message, problems whose one
+ * (tau, k) unit needs more than that array (2 * naux * nao^2 complex elements > 4 Mi); larger
+ * problems split the k sum into chunks that fit and accumulate them into P0t_dev.
  *
- * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture. All calls share the
- * one array, so calls whose work overlaps on the GPU (different streams or
- * threads without ordering) race on it; order them on one stream. Nothing in
- * the array needs to start at zero; P0t_dev is overwritten.
+ * The first call on a device looks up the array's device address (once per device, then kept
+ * for the process): make that first call before any stream capture, and do not reset the
+ * device between calls (a reset would move the array). All calls share the one array and
+ * nothing in it needs to start at zero, so calls whose work overlaps on the GPU (different
+ * streams or threads without ordering) race on it; order them on one stream. P0t_dev is
+ * overwritten.
  */
 int gw_polarization_noalloc(const int nk3[3], int nao, int naux, int ntau, double spin_factor,
                             const gw_c128* V_dev, const gw_c128* G_dev, gw_c128* P0t_dev,

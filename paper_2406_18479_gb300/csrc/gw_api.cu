@@ -134,6 +134,7 @@ struct gw_ctx {
   std::vector<int> mq;                    // index of -q for every q
   int* mq_dev = nullptr;
   int* wlist = nullptr;                   // canonical (q, n) matrices of P~(i Omega), as q * nwb + n
+  int* wlist_q = nullptr;                 // (q, n) matrices of a q range (gw_sigma_eval_q)
   int nwlist = 0;
   int* status = nullptr;                  // device flags: [0] singular matrix
   double* maxdiff = nullptr;
@@ -211,7 +212,7 @@ int cuda_check(const char* what) {
 void free_ctx(gw_ctx* c) {
   if (!c) return;
   mixed_destroy(c->mixed);
-  void* ptrs[] = {c->Fb, c->Bb, c->Ff, c->Bf, c->wf, c->tabs, c->mq_dev, c->wlist, c->work, c->P0t, c->Pw,
+  void* ptrs[] = {c->Fb, c->Bb, c->Ff, c->Bf, c->wf, c->tabs, c->mq_dev, c->wlist, c->wlist_q, c->work, c->P0t, c->Pw,
                   c->Pt, c->dyson_ws, c->status, c->maxdiff, c->nonfinite, c->wbeta, c->gamma, c->rho,
                   c->xinf, c->scal, c->gw_w, c->heff, c->gf2_ws, c->Vfull, c->cw_tmp};
   for (void* p : ptrs)
@@ -244,11 +245,16 @@ int upload_grid(gw_ctx* c, int stat, double2** F, double2** B, int* nw_out) {
 // the rest follows from P0^q(beta - tau) = P0^{-q}(tau)^T (mirror_fill).
 int canonical_end(const gw_ctx* c, int q, int T) { return c->mq[q] < q ? 0 : (c->mq[q] == q ? (T + 1) / 2 : T); }
 
-int polarization_fp64(gw_ctx* c, const double2* G, double2* P0t) {
+// The same within a q range [q0, q1): a q whose -q lies outside the range takes every index.
+int canonical_end(const gw_ctx* c, int q, int T, int q0, int q1) {
+  return (c->mq[q] < q0 || c->mq[q] >= q1) ? T : canonical_end(c, q, T);
+}
+
+int polarization_fp64(gw_ctx* c, const double2* G, double2* P0t, int q0, int q1) {
   const int nk = c->nk, nao = c->nao, naux = c->naux, ntau = c->ntau;
   const long long nao2 = c->nao2, pair = c->pair;
-  for (int q = 0; q < nk; ++q) {
-    const int tend = canonical_end(c, q, ntau);
+  for (int q = q0; q < q1; ++q) {
+    const int tend = canonical_end(c, q, ntau, q0, q1);
     for (int t0 = 0; t0 < tend; t0 += c->nt) {
       const int nt = std::min(c->nt, tend - t0);
       double2* Abuf = c->work;
@@ -291,12 +297,12 @@ int polarization_fp64(gw_ctx* c, const double2* G, double2* P0t) {
   return GW_OK;
 }
 
-int self_energy_fp64(gw_ctx* c, const double2* G, const double2* Pt, double2* Sig) {
+int self_energy_fp64(gw_ctx* c, const double2* G, const double2* Pt, double2* Sig, int q0, int q1) {
   const int nk = c->nk, nao = c->nao, naux = c->naux, ntau = c->ntau;
   const long long nao2 = c->nao2, pair = c->pair;
   if (cudaMemsetAsync(Sig, 0, (size_t)nk * ntau * nao2 * sizeof(double2), c->stream) != cudaSuccess)
     return cuda_check("memset Sigma");
-  for (int q = 0; q < nk; ++q) {
+  for (int q = q0; q < q1; ++q) {
     for (int t0 = 0; t0 < ntau; t0 += c->nt) {
       const int nt = std::min(c->nt, ntau - t0);
       double2* Rbuf = c->work;
@@ -399,20 +405,39 @@ int screened(gw_ctx* c, const double2* P0t, double2* Pt) {
 // writes it). Then P0^q(i W_n) = P0^{-q}(-i W_n)^T, the aux Dyson equation commutes with the
 // transpose, and P~ inherits both relations: only canonical (q, n) and (q, t) are computed,
 // the rest is filled by transposition. The frequency samples are symmetric (index j <-> nw-1-j).
-int screened_sym(gw_ctx* c, const double2* P0t, double2* Pt) {
+//
+// With a q range [q0, q1) only the q of the range are transformed and solved; a q whose -q lies
+// outside the range takes every frequency and tau node (its mirror partner is not computed).
+int screened_sym(gw_ctx* c, const double2* P0t, double2* Pt, int q0 = 0, int q1 = -1) {
+  if (q1 < 0) q1 = c->nk;
   const long long n2 = c->naux2;
-  for (int q = 0; q < c->nk; ++q) {
-    if (c->mq[q] < q) continue;
+  const bool full = q0 == 0 && q1 == c->nk;
+  for (int q = q0; q < q1; ++q) {
+    if (canonical_end(c, q, c->nwb, q0, q1) == 0) continue;
     GW_TRY(transform_q(c, 0, true, P0t, c->Pw, q, 0, c->nwb, n2));
   }
-  // all canonical (q, n) matrices in one launch each
-  GW_TRY(add_identity_fp64(c->Pw, c->naux, n2, c->nwlist, -1.0, 1.0, c->stream, c->wlist));   // I - P0
-  GW_TRY(batched_inverse_fp64(c->Pw, c->naux, n2, c->nwlist, c->status, c->stream, c->wlist));
-  GW_TRY(add_identity_fp64(c->Pw, c->naux, n2, c->nwlist, 1.0, -1.0, c->stream, c->wlist));    // (I - P0)^-1 - I
-  GW_TRY(mirror_fill(c->Pw, c->nk, c->nwb, c->naux, c->mq_dev, c->stream));
-  for (int q = 0; q < c->nk; ++q)
-    GW_TRY(transform_q(c, 0, false, c->Pw, Pt, q, 0, canonical_end(c, q, c->ntau), n2));
-  return mirror_fill(Pt, c->nk, c->ntau, c->naux, c->mq_dev, c->stream);
+  // all canonical (q, n) matrices of the range in one launch each
+  int nlist = c->nwlist;
+  const int* list = c->wlist;
+  if (!full) {
+    std::vector<int> wl;
+    for (int q = q0; q < q1; ++q)
+      for (int n = 0; n < canonical_end(c, q, c->nwb, q0, q1); ++n) wl.push_back(q * c->nwb + n);
+    nlist = (int)wl.size();
+    if (nlist > 0 && cudaMemcpyAsync(c->wlist_q, wl.data(), wl.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                     c->stream) != cudaSuccess)
+      return cuda_check("q-range frequency list");
+    list = c->wlist_q;
+  }
+  if (nlist > 0) {
+    GW_TRY(add_identity_fp64(c->Pw, c->naux, n2, nlist, -1.0, 1.0, c->stream, list));   // I - P0
+    GW_TRY(batched_inverse_fp64(c->Pw, c->naux, n2, nlist, c->status, c->stream, list));
+    GW_TRY(add_identity_fp64(c->Pw, c->naux, n2, nlist, 1.0, -1.0, c->stream, list));    // (I - P0)^-1 - I
+  }
+  GW_TRY(mirror_fill(c->Pw, c->nk, c->nwb, c->naux, c->mq_dev, c->stream, q0, q1));
+  for (int q = q0; q < q1; ++q)
+    GW_TRY(transform_q(c, 0, false, c->Pw, Pt, q, 0, canonical_end(c, q, c->ntau, q0, q1), n2));
+  return mirror_fill(Pt, c->nk, c->ntau, c->naux, c->mq_dev, c->stream, q0, q1);
 }
 
 }  // namespace
@@ -442,8 +467,9 @@ bool config_ok(const gw_config* cfg) {
   const long long nk = (long long)cfg->nk[0] * cfg->nk[1] * cfg->nk[2];
   return !(cfg->nk[0] < 1 || cfg->nk[1] < 1 || cfg->nk[2] < 1 || nk > 4096 || cfg->nao < 1 || cfg->nao > 512 ||
            cfg->naux < 1 || cfg->naux > 4096 || cfg->ntau < 1 || cfg->ntau > 512 || !(cfg->beta > 0) ||
-           cfg->precision < GW_FP64 || cfg->precision > GW_MIXED_FP16S || cfg->v_slices < GW_V_AUTO ||
-           cfg->v_slices > GW_V_PER_Q || cfg->v_packed < 0 || cfg->v_packed > 1);
+           cfg->precision < GW_FP64 || cfg->precision > GW_MIXED_BF16X4 || cfg->v_slices < GW_V_AUTO ||
+           cfg->v_slices > GW_V_PER_Q || cfg->v_packed < 0 || cfg->v_packed > 1 || cfg->slice_pass < 0 ||
+           cfg->slice_pass > 1);
 }
 
 // Weights w_j with p(beta) = sum_j w_j f(tau_j) for the polynomial p of degree n - 1 through the
@@ -523,6 +549,8 @@ int ctx_build(gw_ctx* c, const gw_config* cfg) {
       c->nwlist = (int)wl.size();
       if ((rc = dev_alloc(c, &c->wlist, wl.size())) != GW_OK) break;
       upload(c, c->wlist, wl.data(), wl.size() * sizeof(int));
+      // the (q, n) list of a q range (gw_sigma_eval_q): at most every (q, n)
+      if ((rc = dev_alloc(c, &c->wlist_q, (size_t)nk * c->nwb)) != GW_OK) break;
     }
     // tau chunk: intermediates of 2 * nk * pair complex per tau node, capped at 4 GiB
     const double per_t = 2.0 * nk * (double)c->pair * sizeof(double2);
@@ -566,6 +594,7 @@ int ctx_build(gw_ctx* c, const gw_config* cfg) {
       d.tau_chunk = cfg->tau_chunk;
       d.v_slices = cfg->v_slices;
       d.v_packed = cfg->v_packed;
+      d.fuse = cfg->slice_pass == 0;
       d.mq = c->mq;
       if ((rc = mixed_create(&c->mixed, d, c->stream, c->status, &c->bytes, c->dry)) != GW_OK) break;
     }
@@ -600,7 +629,6 @@ int gw_create(gw_ctx** out, const gw_config* cfg, void* cuda_stream) {
   if (!out || !cfg) return fail(GW_EINVAL, "gw_create: null argument");
   *out = nullptr;
   if (!config_ok(cfg)) return fail(GW_EINVAL, "gw_create: configuration out of range");
-  if (cfg->precision == GW_MIXED_FP16S) return fail(GW_ENOTIMPL, "gw_create: GW_MIXED_FP16S is not implemented");
   gw_ctx* c = new gw_ctx();
   c->stream = (cudaStream_t)cuda_stream;
   const int rc = ctx_build(c, cfg);
@@ -704,9 +732,9 @@ int gw_polarization(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* P0t_dev) {
   double2* P = reinterpret_cast<double2*>(P0t_dev);
   // only canonical (q, tau) are contracted; the rest is P0^q(beta - tau) = P0^{-q}(tau)^T
   if (ctx->mixed)
-    GW_TRY(mixed_polarization(ctx->mixed, G, P, ctx->cfg.spin_factor));
+    GW_TRY(mixed_polarization(ctx->mixed, G, P, ctx->cfg.spin_factor, 0, ctx->nk));
   else
-    GW_TRY(polarization_fp64(ctx, G, P));
+    GW_TRY(polarization_fp64(ctx, G, P, 0, ctx->nk));
   return mirror_fill(P, ctx->nk, ctx->ntau, ctx->naux, ctx->mq_dev, ctx->stream);
 }
 
@@ -749,8 +777,8 @@ int gw_self_energy(gw_ctx* ctx, const gw_c128* G_dev, const gw_c128* Pt_dev, gw_
   const double2* G = reinterpret_cast<const double2*>(G_dev);
   const double2* P = reinterpret_cast<const double2*>(Pt_dev);
   double2* S = reinterpret_cast<double2*>(Sig_dev);
-  if (ctx->mixed) return mixed_self_energy(ctx->mixed, G, P, S);
-  return self_energy_fp64(ctx, G, P, S);
+  if (ctx->mixed) return mixed_self_energy(ctx->mixed, G, P, S, 0, ctx->nk);
+  return self_energy_fp64(ctx, G, P, S, 0, ctx->nk);
 }
 
 int gw_sigma_eval(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* Sig_dev) {
@@ -760,6 +788,33 @@ int gw_sigma_eval(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* Sig_dev) {
   GW_TRY(gw_polarization(ctx, G_dev, reinterpret_cast<gw_c128*>(ctx->P0t)));
   GW_TRY(screened_sym(ctx, ctx->P0t, ctx->Pt));
   return gw_self_energy(ctx, G_dev, reinterpret_cast<const gw_c128*>(ctx->Pt), Sig_dev);
+}
+
+int gw_sigma_eval_q(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* Sig_dev, int q_begin, int q_end,
+                    gw_c128* P0t_dev, gw_c128* Pt_dev) {
+  ProfScope _ps(ctx ? &ctx->prof : nullptr);
+  NvtxRange _nr("gw_sigma_eval_q");
+  if (!ctx || !G_dev || !Sig_dev) return fail(GW_EINVAL, "gw_sigma_eval_q: null argument");
+  if (q_begin < 0 || q_end > ctx->nk || q_begin > q_end)
+    return fail(GW_EINVAL, "gw_sigma_eval_q: range [%d, %d) is not within [0, %d)", q_begin, q_end, ctx->nk);
+  if (!ctx->coulomb) return fail(GW_EINVAL, "gw_sigma_eval_q: call gw_set_coulomb first");
+  const double2* G = reinterpret_cast<const double2*>(G_dev);
+  double2* S = reinterpret_cast<double2*>(Sig_dev);
+  if (ctx->mixed)
+    GW_TRY(mixed_polarization(ctx->mixed, G, ctx->P0t, ctx->cfg.spin_factor, q_begin, q_end));
+  else
+    GW_TRY(polarization_fp64(ctx, G, ctx->P0t, q_begin, q_end));
+  GW_TRY(mirror_fill(ctx->P0t, ctx->nk, ctx->ntau, ctx->naux, ctx->mq_dev, ctx->stream, q_begin, q_end));
+  GW_TRY(screened_sym(ctx, ctx->P0t, ctx->Pt, q_begin, q_end));
+  // the range's blocks, for a caller that checks the stages
+  const size_t blk = (size_t)(q_end - q_begin) * ctx->ntau * ctx->naux2 * sizeof(double2);
+  const size_t off = (size_t)q_begin * ctx->ntau * ctx->naux2;
+  if (P0t_dev && blk && cudaMemcpyAsync(P0t_dev, ctx->P0t + off, blk, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+    return cuda_check("gw_sigma_eval_q: P0 copy");
+  if (Pt_dev && blk && cudaMemcpyAsync(Pt_dev, ctx->Pt + off, blk, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+    return cuda_check("gw_sigma_eval_q: P~ copy");
+  if (ctx->mixed) return mixed_self_energy(ctx->mixed, G, ctx->Pt, S, q_begin, q_end);
+  return self_energy_fp64(ctx, G, ctx->Pt, S, q_begin, q_end);
 }
 
 int gw_dyson_G(gw_ctx* ctx, const gw_c128* H_dev, const gw_c128* Sig_dev, gw_c128* G_dev) {

@@ -108,7 +108,9 @@ int build_g_dyson_fp64(double2* sw, const double2* H, const double2* S, const do
 // Index pairs related by P0^q(beta - tau) = P0^{-q}(tau)^T (and the same for the frequency
 // samples, which are symmetric): X[q][t] <- X[mq[q]][T-1-t]^T for every (q, t) that is not
 // canonical; canonical (q, t): q < mq[q], or q == mq[q] and t <= T-1-t. X is [nk][T][n][n].
-int mirror_fill(double2* X, int nk, int T, int n, const int* mq_dev, void* stream);
+// With a range [q0, q1) (q1 < 0: nk) only q in the range whose -q is also in it are filled
+// (a q whose -q lies outside was computed at every node).
+int mirror_fill(double2* X, int nk, int T, int n, const int* mq_dev, void* stream, int q0 = 0, int q1 = -1);
 
 // Static part and loop helpers (Eq. sigma_inf, Sec. 2.4, Sec. 5.3), all FP64:
 //   density:  gamma^k = -sum_t w_t G^k(tau_t)          (w: weights of the interpolant at tau = beta)

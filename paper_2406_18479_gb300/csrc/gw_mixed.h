@@ -10,6 +10,7 @@ namespace gwi {
 struct MixedDims {
   int nk3[3] = {1, 1, 1};
   int nk = 1, nao = 0, naux = 0, ntau = 0, precision = 0, tau_chunk = 0, v_slices = 0, v_packed = 0;
+  int fuse = 1;           // 1: slice-output epilogues where the sizes allow (nao % 4 == 0, nao <= 56, naux % 40 == 0)
   std::vector<int> mq;    // index of -q for every q
 };
 
@@ -24,8 +25,10 @@ void mixed_destroy(MixedState* s);
 void mixed_guards(const MixedState* s, std::vector<unsigned char*>* out);
 // V: the full-layout Coulomb factor, or null with Vp the packed one (pairs k1 <= k2)
 int mixed_set_coulomb(MixedState* s, const double2* V, const double2* Vp = nullptr);
-int mixed_polarization(MixedState* s, const double2* G, double2* P0t, double spin_factor);
-int mixed_self_energy(MixedState* s, const double2* G, const double2* Pt, double2* Sig);
+// P0 of the q in [q0, q1): canonical tau nodes of the q whose -q is in the range too, every node
+// of the others. Sigma from the q in [q0, q1) (Sig is overwritten with that partial sum).
+int mixed_polarization(MixedState* s, const double2* G, double2* P0t, double spin_factor, int q0, int q1);
+int mixed_self_energy(MixedState* s, const double2* G, const double2* Pt, double2* Sig, int q0, int q1);
 // out[b][(a c)][(d e)] = sum_Q X[b][Q][a][c] Z[b][Q][d][e] on the tensor cores (FP64 output), for nb
 // batches of n2 = nao^2 rows, K = naux; z_bs = 0: one Z for every batch.
 int mixed_outer_q(MixedState* s, const double2* X, long long x_bs, const double2* Z, long long z_bs, int nb,

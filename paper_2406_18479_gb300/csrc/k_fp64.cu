@@ -452,7 +452,8 @@ __global__ void mix_kernel(const double2* s_new, double2* s_inout, double alpha,
 
 // X[q][t] = X[mq[q]][T-1-t]^T for the (q, t) that are not canonical, where
 // canonical means q < mq[q], or q == mq[q] and t <= T-1-t. One 32x32 tile per block.
-__global__ void __launch_bounds__(256) mirror_fill_kernel(double2* X, int nk, int T, int n, const int* mq) {
+__global__ void __launch_bounds__(256) mirror_fill_kernel(double2* X, int nk, int T, int n, const int* mq, int q0,
+                                                          int q1) {
   __shared__ double2 tile[32][33];
   const int tiles_1d = (n + 31) / 32;
   long long b = blockIdx.x;
@@ -463,6 +464,8 @@ __global__ void __launch_bounds__(256) mirror_fill_kernel(double2* X, int nk, in
   const int t = (int)(b % T);
   const int q = (int)(b / T);
   const int p = mq[q];
+  // q outside [q0, q1), or its partner -q outside (then every node of q was computed): nothing to fill
+  if (q < q0 || q >= q1 || p < q0 || p >= q1) return;
   const bool canonical = q < p || (q == p && t <= T - 1 - t);
   if (canonical) return;
   const long long nn = (long long)n * n;
@@ -831,13 +834,14 @@ int build_g_dyson_fp64(double2* sw, const double2* H, const double2* S, const do
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "build_g_dyson launch: %s", cudaGetErrorString(e));
 }
 
-int mirror_fill(double2* X, int nk, int T, int n, const int* mq_dev, void* stream) {
+int mirror_fill(double2* X, int nk, int T, int n, const int* mq_dev, void* stream, int q0, int q1) {
+  if (q1 < 0) q1 = nk;
   const long long tiles_1d = (n + 31) / 32;
   const long long blocks = (long long)nk * T * tiles_1d * tiles_1d;
-  if (blocks == 0) return GW_OK;
+  if (blocks == 0 || q1 <= q0) return GW_OK;
   if (blocks > 2147483647LL) return fail(GW_EINVAL, "mirror_fill: too many blocks");
   prof_begin(SLOT_ELEMENTWISE, (cudaStream_t)stream);
-  mirror_fill_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(X, nk, T, n, mq_dev);
+  mirror_fill_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(X, nk, T, n, mq_dev, q0, q1);
   prof_end(SLOT_ELEMENTWISE, (cudaStream_t)stream, 0.0, 16.0 * (double)nk * T * n * n);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "mirror_fill launch: %s", cudaGetErrorString(e));

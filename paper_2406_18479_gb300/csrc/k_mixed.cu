@@ -270,6 +270,25 @@ struct OzParams {
   float4* cw = nullptr;               // per-CTA newest chunk values, same shape
   FastDiv cdiv;                       // division by vc.kin
   int* status = nullptr;              // status[1] <- error code of a device-side wait that gave up
+  // column blocks: tile nt covers output columns [nt * nstride, nt * nstride + nstride) of N
+  // (B rows from nt * nstride), nstride <= BN; 0: nstride = BN
+  int nstride = 0;
+  // Slice output (so = 1): instead of C, the tile's final values are written as the bf16 slice
+  // groups of the next contraction's operand (planes [group][k-step][row][64] at so_dst, so_rows
+  // rows, so_ksteps k-steps of 16). Output (m, n) of batch (bo, bi), with m = m_hi so_mdiv + m_lo
+  // and n = n_hi so_ndiv + n_lo, goes to
+  //   row   = bo so_row_bs_out + bi so_row_bs_in + m_hi so_rm + n_hi so_rn,
+  //   chunk = bo so_ch_bs_out + bi so_ch_bs_in + (n_lo / so_cb) so_ch_cb + m_lo / 4,
+  //   k     = chunk (4 so_cb) + 4 (n_lo % so_cb) + m_lo % 4,
+  // so that one chunk (4 consecutive rows m_lo x so_cb consecutive columns n_lo) lies in one
+  // tile and shares one slice alignment, the largest |value| of the chunk. so_xhalf: a chunk
+  // spans both column halves of the tile (their maxima are exchanged). Requires so_mdiv % 4 == 0,
+  // so_cb % 4 == 0, 4-aligned column ranges, and no block-diagonal batching.
+  int so = 0, so_xhalf = 0;
+  __nv_bfloat16* so_dst = nullptr;
+  long long so_rows = 0;
+  int so_ksteps = 0, so_cb = 0, so_ch_cb = 0, so_mdiv = 1, so_ndiv = 1 << 30;
+  long long so_rm = 0, so_rn = 0, so_row_bs_in = 0, so_row_bs_out = 0, so_ch_bs_in = 0, so_ch_bs_out = 0;
 };
 
 // Error-free FP32 sum: s + e = a + b exactly.
@@ -417,7 +436,12 @@ struct OzShape {
   static constexpr int kThreads = 352;                 // producer, MMA, 8 epilogue warps, negation warp
   static constexpr int kOrderCols = 2 * kBN;           // [im | re] of one order
   static constexpr int kTmemCols = 512;
-  static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + 256;
+  // slice output: maxima exchanged between column halves (two tiles in flight x 4 lane quarters x
+  // 2 halves x 32 lanes) and per-warp line staging (8 warps x 8 line groups x 272 bytes)
+  static constexpr int kXmaxBytes = 2 * 4 * 2 * 32 * 4;
+  static constexpr int kLineBytes = 272;
+  static constexpr int kStageOutBytes = 8 * 8 * kLineBytes;
+  static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + 256 + kXmaxBytes + kStageOutBytes;
   static_assert(3 * kOrderCols <= kTmemCols, "three orders must fit in TMEM");
   static_assert(kStageBytes % 1024 == 0, "stages must keep the 1024-byte swizzle alignment");
   static_assert(kSmem <= 232448, "stages exceed shared memory");
@@ -462,6 +486,9 @@ __global__ void __launch_bounds__(352, 1)
   uint64_t* drain_bar = acc_full + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 3);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  uint64_t* xbar = acc_full + 5;                   // slice output: column-half maxima written
+  uint32_t* xmax = reinterpret_cast<uint32_t*>(smem + (size_t)S::kStages * S::kStageBytes + 256);
+  uint8_t* stage_out = reinterpret_cast<uint8_t*>(xmax) + S::kXmaxBytes;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -473,6 +500,7 @@ __global__ void __launch_bounds__(352, 1)
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, 8);                 // one arrival per epilogue warp
     mbar_init(drain_bar, 1);
+    mbar_init(xbar, 8);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -488,6 +516,7 @@ __global__ void __launch_bounds__(352, 1)
   const uint32_t tmem = *tmem_slot;
   const int tiles_per_batch = p.mtiles * p.ntiles;
   const int total_tiles = p.nbatch * tiles_per_batch;
+  const int nstride = p.nstride > 0 ? p.nstride : BN;
   const int nchunks = (p.nsteps + p.steps_per_chunk - 1) / p.steps_per_chunk;
 
   if (warp == 0) {
@@ -498,7 +527,7 @@ __global__ void __launch_bounds__(352, 1)
         const int b = tile / tiles_per_batch, mt = (tile % tiles_per_batch) / p.ntiles, nt = tile % p.ntiles;
         const int bo = b / p.bin, bi = b % p.bin;
         const int arow = (int)(p.a_row0 + (p.a_tab ? p.a_tab[bi] : bi * p.a_bs_in) + bo * p.a_bs_out) + mt * kBM;
-        const int brow = (int)(p.b_row0 + (p.b_tab ? p.b_tab[bi] : bi * p.b_bs_in) + bo * p.b_bs_out) + nt * BN;
+        const int brow = (int)(p.b_row0 + (p.b_tab ? p.b_tab[bi] : bi * p.b_bs_in) + bo * p.b_bs_out) + nt * nstride;
         for (int s = 0; s < p.nsteps; ++s, ++step) {
           const int st = step % S::kStages;
           const uint32_t ph = (step / S::kStages) & 1;
@@ -614,6 +643,7 @@ __global__ void __launch_bounds__(352, 1)
     float4* ws = p.ws + (size_t)blockIdx.x * BN * kBM + lrow;
     float4* cw = p.cw + (size_t)blockIdx.x * BN * kBM + lrow;
     uint32_t chunk = 0;
+    uint32_t so_tile = 0;                            // slice-output tiles with a column-half exchange
     for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
       const int b = tile / tiles_per_batch, mt = (tile % tiles_per_batch) / p.ntiles, nt = tile % p.ntiles;
       int row = mt * kBM + lrow;
@@ -633,13 +663,17 @@ __global__ void __launch_bounds__(352, 1)
       const int bo = ob / p.bin, bi = ob % p.bin;
       double2* C = p.C + (p.bc.tab ? p.bc.tab[bi] : (long long)bi * p.bc.bs_in) + (long long)bo * p.bc.bs_out;
       const long long roff = row_ok ? s_view_row(p.vc, row) : 0;
-      // output column of tile column cl: nt * BN + cl - dcol0 (valid if in [0, min(N, ncols)))
+      // output column of tile column cl: nt * nstride + cl - dcol0 (valid if in [0, min(N, ncols)))
       auto col_ok = [&](int cl) {
-        const int n = nt * BN + cl - dcol0;
-        return row_ok && cl - dcol0 >= 0 && cl - dcol0 < ncols && n < p.N;
+        const int n = nt * nstride + cl - dcol0;
+        return row_ok && cl - dcol0 >= 0 && cl - dcol0 < ncols && cl < nstride && n < p.N;
       };
       auto out_write = [&](int cl, float rh, float rl, float ih, float il) {
-        const int n = nt * BN + cl - dcol0;
+        if (p.so) {                                   // kept for the slice output below
+          cw[(size_t)cl * kBM] = make_float4(rh, rl, ih, il);
+          return;
+        }
+        const int n = nt * nstride + cl - dcol0;
         const int nq = fdiv(n, p.cdiv);
         double2* dst = C + roff + (long long)nq * p.vc.ks_out + (long long)(n - nq * p.vc.kin) * p.vc.ks_in;
         if (p.out_df) {
@@ -656,10 +690,144 @@ __global__ void __launch_bounds__(352, 1)
         }
       };
       bool ok = true;
+      // ---- slice output helpers. A chunk of the next contraction is 4 consecutive rows (this
+      //      lane and its 3 neighbours) x so_cb columns; its alignment 2^E comes from the largest
+      //      |hi| of its re and im parts, as in slice_kernel.
+      const int m_so = mt * kBM + lrow;               // producer row within the batch
+      const bool mok = m_so < p.M;
+      uint32_t so_mx = 0;                             // largest |hi| of this thread's values (bits)
+      // alignment of this lane group's chunk from the thread maxima; returns true for a chunk
+      // taken as zero (largest value below 2^-90: its slices would be subnormal)
+      auto so_alignment = [&](uint32_t mx, float* magic) -> bool {
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+        if (p.so_xhalf) {
+          // the chunk's other columns belong to the warp with the same lanes and the other half
+          const uint32_t par = so_tile & 1;
+          xmax[((par * 4 + quarter) * 2 + half) * 32 + lane] = mx;
+          __syncwarp();
+          int w = 1;
+          if (lane == 0) {
+            mbar_arrive(xbar);
+            w = mbar_wait(xbar, par, abort_flag, p.status, 16);
+          }
+          w = __shfl_sync(0xffffffffu, w, 0);
+          __syncwarp();
+          if (w) mx = max(mx, xmax[((par * 4 + quarter) * 2 + (half ^ 1)) * 32 + lane]);
+          else ok = false;
+          ++so_tile;
+        }
+        const int eb = (int)((mx >> 23) & 0xFF);
+        const int E = eb - 126;                       // every |value| / 2^E < 1
+#pragma unroll
+        for (int sl = 0; sl < 4; ++sl) magic[sl] = ldexpf(3.0f, E + 15 - 8 * sl);   // 1.5 * 2^23 * q_sl
+        return eb == 0 || E < -90;
+      };
+      // line staging of this warp's 8 lane groups: [re | im] x 4 slices x 16 values (+16 bytes of
+      // padding, so that the 2-byte stores of one instruction fall in distinct banks)
+      uint8_t* line = stage_out + ((size_t)(warp - 2) * 8 + (lane >> 2)) * S::kLineBytes;
+      // slices of 4 columns c0..c0+3 of this row (double-float values f) -> one 16-wide line of the
+      // consumer's planes, written by the 4 lanes of the group (128 bytes per part)
+      auto so_line = [&](int c0, const float4* f, bool zero, const float* magic) {
+        const int n0 = nt * nstride + c0;
+        const bool gok = ok && mok && c0 < nstride && n0 < p.N;   // the same for all 4 columns and lanes
+        __nv_bfloat16* lb = reinterpret_cast<__nv_bfloat16*>(line);
+        const int j4 = lane & 3;
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          float sr[4] = {0.f, 0.f, 0.f, 0.f}, si[4] = {0.f, 0.f, 0.f, 0.f};
+          if (gok && !zero) {
+            df_slices(f[cc].x, f[cc].y, magic, sr);
+            df_slices(f[cc].z, f[cc].w, magic, si);
+          }
+#pragma unroll
+          for (int sl = 0; sl < 4; ++sl) {
+            lb[sl * 16 + cc * 4 + j4] = __float2bfloat16_rn(sr[sl]);        // exact: digit x 2^(E-7-8 sl)
+            lb[64 + sl * 16 + cc * 4 + j4] = __float2bfloat16_rn(si[sl]);
+          }
+        }
+        __syncwarp();
+        if (gok) {
+          const int m_hi = m_so / p.so_mdiv, m_lo = m_so - m_hi * p.so_mdiv;
+          const int n_hi = n0 / p.so_ndiv, n_lo = n0 - n_hi * p.so_ndiv;
+          const long long crow = bo * p.so_row_bs_out + bi * p.so_row_bs_in + (long long)m_hi * p.so_rm +
+                                 (long long)n_hi * p.so_rn;
+          const long long ch = bo * p.so_ch_bs_out + bi * p.so_ch_bs_in + (long long)(n_lo / p.so_cb) * p.so_ch_cb +
+                               m_lo / 4;
+          const long long kstep = ch * (p.so_cb / 4) + (n_lo % p.so_cb) / 4;
+          if (crow < 0 || crow >= p.so_rows || kstep < 0 || kstep >= p.so_ksteps) {
+            atomicExch(p.status + 1, 17);            // a layout outside the planes: recorded, not written
+          } else {
+#pragma unroll
+            for (int gr = 0; gr < 2; ++gr) {
+              const uint4* src = reinterpret_cast<const uint4*>(line + gr * 128);
+              uint4* dst =
+                  reinterpret_cast<uint4*>(p.so_dst + (((long long)gr * p.so_ksteps + kstep) * p.so_rows + crow) * 64);
+              dst[j4] = src[j4];
+              dst[j4 + 4] = src[j4 + 4];
+            }
+          }
+        }
+        __syncwarp();
+      };
       for (int c = 0; c < nchunks; ++c, ++chunk) {
         if (!mbar_wait(acc_full, chunk & 1, abort_flag, p.status, 14)) { ok = false; break; }
         tc_fence_after();
         const bool single = nchunks == 1;
+        if (p.so && single) {
+          // ---- slice output of a one-chunk contraction straight from TMEM: pass 1 finds the row
+          //      maximum, pass 2 slices 4 columns at a time; TMEM is released after pass 2
+          uint32_t mx = 0;
+#pragma unroll 1
+          for (int g = 0; g < kCols / G; ++g) {
+            const int cb = half * kCols + g * G;
+            float v[3][2][G];
+            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cb;
+#pragma unroll
+            for (int o = 0; o < 3; ++o) {
+              tmem_ldg<G>(taddr + o * S::kOrderCols, v[o][0]);
+              tmem_ldg<G>(taddr + o * S::kOrderCols + BN, v[o][1]);
+            }
+            tmem_wait_ld();
+#pragma unroll
+            for (int u = 0; u < G; ++u) {
+              if (!col_ok(cb + u)) continue;
+              float rh, rl, ih, il;
+              two_sum(v[0][1][u], v[1][1][u], rh, rl);
+              two_sum(v[0][0][u], v[1][0][u], ih, il);
+              mx = max(mx, max(__float_as_uint(rh) & 0x7FFFFFFFu, __float_as_uint(ih) & 0x7FFFFFFFu));
+            }
+          }
+          float magic[4];
+          const bool zero = so_alignment(mx, magic);
+#pragma unroll 1
+          for (int g4 = 0; g4 < kCols / 4; ++g4) {
+            const int c0 = half * kCols + 4 * g4;
+            float v[3][2][4];
+            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
+#pragma unroll
+            for (int o = 0; o < 3; ++o) {
+              tmem_ld4(taddr + o * S::kOrderCols, v[o][0]);
+              tmem_ld4(taddr + o * S::kOrderCols + BN, v[o][1]);
+            }
+            tmem_wait_ld();
+            float4 f[4];
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+              float rh, rl, ih, il;
+              two_sum(v[0][1][cc], v[1][1][cc], rh, rl);
+              rl = __fadd_rn(rl, v[2][1][cc]);
+              two_sum(v[0][0][cc], v[1][0][cc], ih, il);
+              il = __fadd_rn(il, v[2][0][cc]);
+              f[cc] = make_float4(rh, rl, ih, il);
+            }
+            so_line(c0, f, zero, magic);
+          }
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acc_empty);
+          continue;
+        }
         // ---- drain: TMEM -> chunk value (an exact FP32 pair per part) -> output or scratch
 #pragma unroll 1
         for (int g = 0; g < kCols / G; ++g) {
@@ -712,10 +880,33 @@ __global__ void __launch_bounds__(352, 1)
               if (!col_ok(cl)) continue;
               df_add(a[u].x, a[u].y, x[u].x, x[u].y);
               df_add(a[u].z, a[u].w, x[u].z, x[u].w);
+              if (last && p.so)
+                so_mx = max(so_mx, max(__float_as_uint(a[u].x) & 0x7FFFFFFFu, __float_as_uint(a[u].z) & 0x7FFFFFFFu));
               if (last) out_write(cl, a[u].x, a[u].y, a[u].z, a[u].w);
               else ws[(size_t)cl * kBM] = a[u];
             }
           }
+        }
+      }
+      if (p.so && nchunks > 1 && ok) {
+        // ---- slice output of a chunked contraction: the final values wait in cw; the next
+        //      group's loads are issued before the current group is sliced
+        float magic[4];
+        const bool zero = so_alignment(so_mx, magic);
+        auto load4 = [&](int c0, float4* f) {
+          const bool gok = mok && c0 < nstride && nt * nstride + c0 < p.N;
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) f[cc] = gok ? cw[(size_t)(c0 + cc) * kBM] : make_float4(0.f, 0.f, 0.f, 0.f);
+        };
+        float4 cur[4], nxt[4];
+        load4(half * kCols, cur);
+#pragma unroll 1
+        for (int g4 = 0; g4 < kCols / 4; ++g4) {
+          const int c0 = half * kCols + 4 * g4;
+          if (g4 + 1 < kCols / 4) load4(c0 + 4, nxt);
+          so_line(c0, cur, zero, magic);
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) cur[cc] = nxt[cc];
         }
       }
       if (!ok) break;
@@ -834,8 +1025,17 @@ int launch_oz_bn(const Planes& A, const Planes& B, OzParams p, int slot, cudaStr
   if (A.groups != 2 || B.groups != 2) return fail(GW_EINVAL, "oz_gemm: operands need two slice groups");
   p.nsteps = A.Kpad / kStepK;
   p.steps_per_chunk = A.Kc / kStepK;
+  if (p.nstride < 0 || p.nstride > S::kBN) return fail(GW_EINVAL, "oz_gemm: column stride above the tile width");
+  const int nstride = p.nstride > 0 ? p.nstride : S::kBN;
+  if (p.so) {
+    // a chunk is 4 rows (a lane group) by so_cb columns within one tile, or one column half
+    const bool halves_ok = p.so_xhalf ? p.so_cb >= nstride : (S::kBN / 2) % p.so_cb == 0;
+    if (p.dblock || !p.so_dst || p.so_mdiv % 4 || p.so_cb % 4 || p.so_cb <= 0 || p.M % 4 || p.N % 4 ||
+        nstride % 4 || !halves_ok || p.so_ksteps <= 0 || p.so_rows <= 0)
+      return fail(GW_EINVAL, "oz_gemm: slice output layout not supported");
+  }
   p.mtiles = (p.M + kBM - 1) / kBM;
-  p.ntiles = (p.N + S::kBN - 1) / S::kBN;
+  p.ntiles = (p.N + nstride - 1) / nstride;
   const long long total = (long long)p.nbatch * p.mtiles * p.ntiles;
   if (total == 0) return GW_OK;
   if (total > 2147483647LL) return fail(GW_EINVAL, "oz_gemm: too many tiles");
@@ -862,12 +1062,65 @@ int launch_oz_bn(const Planes& A, const Planes& B, OzParams p, int slot, cudaStr
 }
 
 // Tile width by the padding of N: 72 columns (MMA N = 144) when that covers N with fewer padded
-// columns than 80 (for example N = 200: 216 instead of 240), else 80. Block-diagonal launches
-// keep 80, the width their problem grouping was chosen for.
-int launch_oz(const Planes& A, const Planes& B, OzParams p, int slot, cudaStream_t st) {
-  const long long pad72 = (p.N + 71) / 72 * 72LL, pad80 = (p.N + 79) / 80 * 80LL;
-  if (!p.dblock && pad72 < pad80) return launch_oz_bn<72>(A, B, p, slot, st);
+// columns than 80 (for example N = 200: 216 instead of 240), else 80. The narrower 56 (MMA N = 112:
+// more MMA issues per output) is taken only where a launch asks for it (block-diagonal tiles).
+int oz_tile_width(long long N) {
+  const long long pad72 = (N + 71) / 72 * 72, pad80 = (N + 79) / 80 * 80;
+  return pad72 < pad80 ? 72 : 80;
+}
+
+int launch_oz(const Planes& A, const Planes& B, OzParams p, int slot, cudaStream_t st, int bn = 0) {
+  if (bn == 0) bn = oz_tile_width(p.N);
+  if (bn == 56) return launch_oz_bn<56>(A, B, p, slot, st);
+  if (bn == 72) return launch_oz_bn<72>(A, B, p, slot, st);
   return launch_oz_bn<80>(A, B, p, slot, st);
+}
+
+// Block-diagonal grouping of nao x nao problems: the tile width and the problems per tile that
+// make the most of each 128 x BN tile (g problems of nao x nao on its diagonal, g nao <= 128).
+void oz_block_diag(int nao, int* bn, int* grp) {
+  double best = -1.0;
+  for (int w : {80, 72, 56}) {
+    const int g = std::max(1, std::min(kBM, w) / nao);
+    const double use = (double)g * nao * nao / ((double)kBM * w);
+    if (use > best + 1e-12) best = use, *bn = w, *grp = g;
+  }
+}
+
+// Automatic tau batch (nodes per batch of the contractions). The largest batch whose
+// intermediates take at most 12 GiB, unless that leaves the P0 launches (batch x P0 tiles per
+// node) under two waves over the SMs: then, within 64 GiB, the batch whose P0 launches fill
+// their waves best (over the canonical tau ranges the launches take), the smaller on a tie.
+int auto_tau_batch(const MixedDims& d, double per_t) {
+  const int ntau = d.ntau;
+  const int nt12 = (int)std::min<double>(ntau, std::max(1.0, std::floor(12884901888.0 / per_t)));
+  const int sms = 152;                         // the GB300's SM count: the choice must not depend on the device
+  const long long p0_tiles = (long long)((d.naux + kBM - 1) / kBM) * ((d.naux + oz_tile_width(d.naux) - 1) /
+                                                                       oz_tile_width(d.naux));
+  if ((long long)nt12 * p0_tiles >= 2LL * sms) return nt12;
+  const int nt64 = (int)std::min<double>(ntau, std::max(1.0, std::floor(68719476736.0 / per_t)));
+  // canonical tau counts of the q (all nodes, half of them, or none)
+  std::vector<int> tends;
+  for (int q = 0; q < d.nk; ++q) {
+    const int mq = q < (int)d.mq.size() ? d.mq[q] : q;
+    tends.push_back(mq < q ? 0 : (mq == q ? (ntau + 1) / 2 : ntau));
+  }
+  int best = nt12;
+  double best_eff = -1.0;
+  for (int nt = nt12; nt <= nt64; ++nt) {
+    double work = 0.0, slots = 0.0;
+    for (int tend : tends) {
+      const int nb = (tend + nt - 1) / nt;
+      for (int i = 0; i < nb; ++i) {
+        const long long tiles = p0_tiles * ((long long)tend * (i + 1) / nb - (long long)tend * i / nb);
+        work += (double)tiles;
+        slots += (double)((tiles + sms - 1) / sms * sms);
+      }
+    }
+    const double eff = slots > 0.0 ? work / slots : 0.0;
+    if (eff > best_eff + 1e-9) best_eff = eff, best = nt;
+  }
+  return best;
 }
 
 }  // namespace
@@ -893,8 +1146,13 @@ struct MixedState {
   const double2* Vp = nullptr;  // packed V (pairs k1 <= k2), when given instead of V
   double2* vscratch = nullptr;  // per-q mode with a packed V: the nk full-layout blocks of one table
   Planes vrow, vcol, gf, gm;    // V rows (Q,i) over orbitals; V rows (j,b) over Q'; G^T forward / mirrored tau
+  Planes vrowt;                 // fused path, all pairs: V rows (i,Q) over orbitals (the Z operand)
   bool per_q = false;           // V slices staged per q (vq, vcq) instead of held for all pairs
-  Planes vq[2], vcq;
+  Planes vq[2], vcq;            // (fused path: vq[0] holds rows (i,Q) during the self-energy)
+  // Fused path: the V.G products and R write the slice groups of the next contraction straight
+  // from their epilogue (no FP64 or double-float intermediate, no separate slicing pass); the
+  // P0 and Sigma contractions then run over chunks that lie within one producer tile.
+  bool fused = false;
   __nv_bfloat16* xs_mem = nullptr;   // operand planes for the batched GEMMs (two buffers)
   __nv_bfloat16* ys_mem = nullptr;
   Planes ps;                    // P~ planes
@@ -1016,6 +1274,18 @@ int stage_vrow(MixedState* s, const double2* V, int nb, const long long* tab, co
   return slice(s, V, vr, s->pair, 0, 1 << 30, nb, naux * nao, nao, P, (long long)naux * nao, 0, tab);
 }
 
+// V slices with rows (i, Q) over the orbital a: row i * naux + Q reads V[Q][i][a] (the Z operand
+// of the fused path, whose output columns must run over Q)
+int stage_vrowt(MixedState* s, const double2* V, int nb, const long long* tab, const Planes& P) {
+  const int nao = s->d.nao, naux = s->d.naux;
+  ZView vr;
+  vr.rin = naux;
+  vr.rs_in = s->nao2;
+  vr.rs_out = nao;
+  vr.ks_in = 1;
+  return slice(s, V, vr, s->pair, 0, 1 << 30, nb, naux * nao, nao, P, (long long)naux * nao, 0, tab);
+}
+
 // V slices with rows (j, b) over Q': row j * nao + b reads V[Q'][b][j]
 int stage_vcol(MixedState* s, const double2* V, int nb, const long long* tab, const Planes& P) {
   const int nao = s->d.nao, naux = s->d.naux;
@@ -1032,10 +1302,20 @@ struct VOp {
   const Planes* P;
   int tab;
 };
-VOp v_op(const MixedState* s, int which) {
-  if (!s->per_q) return {which == T_VCOL_KMQK ? &s->vcol : &s->vrow, which};
+VOp v_op(const MixedState* s, int which, bool rows_iq = false) {
+  if (!s->per_q) return {which == T_VCOL_KMQK ? &s->vcol : (rows_iq ? &s->vrowt : &s->vrow), which};
   if (which == T_VCOL_KMQK) return {&s->vcq, T_LOC_VC};
   return {which == T_VKPQK ? &s->vq[1] : &s->vq[0], T_LOC_V};
+}
+
+// Slice output into operand planes P (the consumer's planes, chunks of 4 so_cb)
+void so_target(OzParams& p, const Planes& P, int cb, int ch_cb) {
+  p.so = 1;
+  p.so_dst = P.ptr;
+  p.so_rows = P.rows;
+  p.so_ksteps = P.Kpad / kStepK;
+  p.so_cb = cb;
+  p.so_ch_cb = ch_cb;
 }
 
 // out[t][k][Q][i][b] = sum_a V^{pair(k)}_ia(Q) G^{kg(k)}_ab(t) for t in [t0, t0+nt) (A and Z), or, with
@@ -1080,19 +1360,72 @@ int vg_gemm(MixedState* s, int pair_tab, int g_tab, const Planes& Gp, int q, int
   return launch_oz(*vo.P, Gp, p, SLOT_VG_MIXED, s->stream);
 }
 
+// Fused path, P0 operands. The contraction index of P0 runs over (k, d, b) in chunks of 4 b x all
+// d: element (k, d, b) at k-position (k (nao/4) + b/4) 4 nao + 4 d + b % 4, for both operands.
+//   X^Q_{db}(k,t) = sum_a G^{k+q}_ab(t) V^{k,k+q}_da(Q): rows (t, b) of G^T, one Q per tile (columns d)
+//   Y^{Q'}_{bd}(k,t) = sum_c V^{k+q,k}_bc(Q') G^k_cd(beta - t): rows (Q', b) of V, one t per tile (columns d)
+// so that a chunk is 4 consecutive rows b of one tile by all its nao columns.
+int p0_operands_fused(MixedState* s, int q, int t0, int nt, const Planes& xs, const Planes& ys) {
+  const int nk = s->d.nk, nao = s->d.nao, naux = s->d.naux;
+  {
+    const VOp vo = v_op(s, T_VKKPQ);
+    OzParams p;
+    p.nbatch = nk;                        // k
+    p.M = nt * nao;                       // (t, b)
+    p.N = naux * nao;                     // (Q, d)
+    p.nstride = nao;
+    p.a_tab = tab(s, T_GKPQ, q);
+    p.a_row0 = (long long)t0 * nao;
+    p.b_tab = tab(s, vo.tab, q);
+    so_target(p, xs, nao, nao / 4);
+    p.so_xhalf = 1;
+    p.so_mdiv = nao;                      // m = t nao + b
+    p.so_ndiv = nao;                      // n = Q nao + d
+    p.so_rm = naux;                       // row t naux + Q
+    p.so_rn = 1;
+    p.so_ch_bs_in = nao / 4;              // chunk k (nao/4) + b/4
+    p.status = s->status;
+    p.ws = s->ws;
+    GW_TRY_INTERNAL(launch_oz(s->gf, *vo.P, p, SLOT_VG_MIXED, s->stream, 56));
+  }
+  const VOp vo = v_op(s, T_VKPQK);
+  OzParams p;
+  p.nbatch = nk;
+  p.M = naux * nao;                       // (Q', b)
+  p.N = nt * nao;                         // (t, d)
+  p.nstride = nao;
+  p.a_tab = tab(s, vo.tab, q);
+  p.b_tab = tab(s, T_GK, q);
+  p.b_row0 = (long long)t0 * nao;
+  so_target(p, ys, nao, nao / 4);
+  p.so_xhalf = 1;
+  p.so_mdiv = nao;                        // m = Q' nao + b
+  p.so_ndiv = nao;                        // n = t nao + d
+  p.so_rm = 1;                            // row t naux + Q'
+  p.so_rn = naux;
+  p.so_ch_bs_in = nao / 4;
+  p.status = s->status;
+  p.ws = s->ws;
+  return launch_oz(*vo.P, s->gm, p, SLOT_VG_MIXED, s->stream, 56);
+}
+
 int polarization_chunk(MixedState* s, const double2* G, double2* P0t, double spin, int q, int t0, int nt) {
   const int nk = s->d.nk, nao = s->d.nao, naux = s->d.naux, ntau = s->d.ntau;
-  GW_TRY_INTERNAL(vg_gemm(s, T_VKKPQ, T_GKPQ, s->gf, q, t0, nt, false, s->x64));
-  GW_TRY_INTERNAL(vg_gemm(s, T_VKPQK, T_GK, s->gm, q, t0, nt, true, s->y64));
   const Planes xs = view(s->xs_mem, (long long)nt * naux, s->Kc_p0, s->Kpad_p0, 2);
   const Planes ys = view(s->ys_mem, (long long)nt * naux, s->Kc_p0, s->Kpad_p0, 2);
-  ZView v;                                 // rows Q, k = (k, d, b)
-  v.rs_in = s->nao2;
-  v.kin = (int)s->nao2;
-  v.ks_in = 1;
-  v.ks_out = s->pair;
-  GW_TRY_INTERNAL(slice(s, s->x64, v, (long long)nk * s->pair, 0, 1 << 30, nt, naux, nk * (int)s->nao2, xs, naux, 1));
-  GW_TRY_INTERNAL(slice(s, s->y64, v, (long long)nk * s->pair, 0, 1 << 30, nt, naux, nk * (int)s->nao2, ys, naux, 1));
+  if (s->fused) {
+    GW_TRY_INTERNAL(p0_operands_fused(s, q, t0, nt, xs, ys));
+  } else {
+    GW_TRY_INTERNAL(vg_gemm(s, T_VKKPQ, T_GKPQ, s->gf, q, t0, nt, false, s->x64));
+    GW_TRY_INTERNAL(vg_gemm(s, T_VKPQK, T_GK, s->gm, q, t0, nt, true, s->y64));
+    ZView v;                               // rows Q, k = (k, d, b)
+    v.rs_in = s->nao2;
+    v.kin = (int)s->nao2;
+    v.ks_in = 1;
+    v.ks_out = s->pair;
+    GW_TRY_INTERNAL(slice(s, s->x64, v, (long long)nk * s->pair, 0, 1 << 30, nt, naux, nk * (int)s->nao2, xs, naux, 1));
+    GW_TRY_INTERNAL(slice(s, s->y64, v, (long long)nk * s->pair, 0, 1 << 30, nt, naux, nk * (int)s->nao2, ys, naux, 1));
+  }
   OzParams p;
   p.M = naux;
   p.N = naux;
@@ -1119,6 +1452,8 @@ int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double
     GW_TRY_INTERNAL(slice(s, Pt + ((long long)q * ntau + t0) * s->naux2, v, s->naux2, 0, 1 << 30, nt, naux, naux,
                           s->ps, naux));
   }
+  const Planes xs = view(s->xs_mem, (long long)nt * nk * nao, s->Kc_s, s->Kpad_s, 2);
+  const Planes ys = view(s->ys_mem, (long long)nt * nk * nao, s->Kc_s, s->Kpad_s, 2);
   {  // R^Q_{bj}(k,t) = sum_Q' P~_QQ'(t) V^{k-q,k}_bj(Q')  -> y64[t][k][Q][j][b], computed as
      // rows (j, b) of V times columns Q of P~ so that the stores of a warp are contiguous
     OzParams p;
@@ -1137,13 +1472,41 @@ int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double
     p.status = s->status;
     p.ws = s->ws;
     p.out_df = 1;                           // double-float, sliced again for the Sigma contraction
-    GW_TRY_INTERNAL(launch_oz(*vo.P, s->ps, p, SLOT_R_TC, s->stream));
+    if (s->fused) {
+      // straight into the Sigma B operand: rows (t, k, j), k-position of (Q, b)
+      // ((Q/40) (nao/4) + b/4) 160 + 4 (Q % 40) + b % 4 (chunks of 4 b x 40 Q)
+      so_target(p, ys, 40, nao / 4);
+      p.so_mdiv = nao;                      // m = j nao + b
+      p.so_rm = 1;                          // row (t nk + k) nao + j
+      p.so_row_bs_in = nao;
+      p.so_row_bs_out = (long long)nk * nao;
+    }
+    // the fused chunks are halves of an 80-wide tile
+    GW_TRY_INTERNAL(launch_oz(*vo.P, s->ps, p, SLOT_R_TC, s->stream, s->fused ? 80 : 0));
   }
-  // Z^Q_{ib}(k,t) = sum_a V^{k,k-q}_ia(Q) G^{k-q}_ab(t) -> x64[t][k][Q][i][b]
-  GW_TRY_INTERNAL(vg_gemm(s, T_VKKMQ, T_GKMQ, s->gf, q, t0, nt, false, s->x64));
-  const Planes xs = view(s->xs_mem, (long long)nt * nk * nao, s->Kc_s, s->Kpad_s, 2);
-  const Planes ys = view(s->ys_mem, (long long)nt * nk * nao, s->Kc_s, s->Kpad_s, 2);
-  {
+  if (s->fused) {
+    // Z^Q_{ib}(k,t) = sum_a G^{k-q}_ab(t) V^{k,k-q}_ia(Q): rows (t, b) of G^T, columns (i, Q) of V,
+    // straight into the Sigma A operand (rows (t, k, i), the k-positions of R)
+    const VOp vo = v_op(s, T_VKKMQ, true);
+    OzParams p;
+    p.nbatch = nk;
+    p.M = nt * nao;                         // (t, b)
+    p.N = nao * naux;                       // (i, Q)
+    p.a_tab = tab(s, T_GKMQ, q);
+    p.a_row0 = (long long)t0 * nao;
+    p.b_tab = tab(s, vo.tab, q);
+    so_target(p, xs, 40, nao / 4);
+    p.so_mdiv = nao;                        // m = t nao + b
+    p.so_ndiv = naux;                       // n = i naux + Q
+    p.so_rm = (long long)nk * nao;          // row (t nk + k) nao + i
+    p.so_rn = 1;
+    p.so_row_bs_in = nao;
+    p.status = s->status;
+    p.ws = s->ws;
+    GW_TRY_INTERNAL(launch_oz(s->gf, *vo.P, p, SLOT_VG_MIXED, s->stream, 80));
+  } else {
+    // Z^Q_{ib}(k,t) = sum_a V^{k,k-q}_ia(Q) G^{k-q}_ab(t) -> x64[t][k][Q][i][b]
+    GW_TRY_INTERNAL(vg_gemm(s, T_VKKMQ, T_GKMQ, s->gf, q, t0, nt, false, s->x64));
     ZView vz;                               // rows i, k = (Q, b)
     vz.rs_in = nao;
     vz.kin = nao;
@@ -1154,9 +1517,10 @@ int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double
     GW_TRY_INTERNAL(slice(s, s->y64, vz, s->pair, 0, 1 << 30, nt * nk, nao, naux * nao, ys, nao, 1));
   }
   OzParams p;                               // Sigma^k_ij(t) += -(1/N_k) sum_{Q,b} Z_{Q,i,b} R_{Q,b,j}
-  // (t, k) problems of nao x nao are consecutive plane rows (t * nk + k) * nao; G of them share one
+  // (t, k) problems of nao x nao are consecutive plane rows (t * nk + k) * nao; grp of them share one
   // block-diagonal tile, so one MMA of N = grp * nao does the work of grp narrow ones
-  const int grp = std::max(1, std::min(kBM, 80) / nao);
+  int bn = 80, grp = 1;
+  oz_block_diag(nao, &bn, &grp);
   const int nprob = nt * nk;
   p.M = grp * nao;
   p.N = grp * nao;
@@ -1179,7 +1543,7 @@ int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double
   p.accumulate = 1;
   p.status = s->status;
   p.ws = s->ws;
-  return launch_oz(xs, ys, p, SLOT_SIGMA_MIXED, s->stream);
+  return launch_oz(xs, ys, p, SLOT_SIGMA_MIXED, s->stream, bn);
 }
 
 }  // namespace
@@ -1202,16 +1566,25 @@ int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int*
   chunking(nk * (int)s->nao2, &s->Kc_p0, &s->Kpad_p0);
   chunking(naux, &s->Kc_r, &s->Kpad_r);
   chunking(naux * nao, &s->Kc_s, &s->Kpad_s);
-  // tau batch: FP64 intermediates plus operand planes per tau node, capped at 12 GiB
-  const double per_t = 2.0 * nk * (double)s->pair * 16.0 +
+  // Fused path where the chunks fit producer tiles: 4 orbitals x nao (one 56-wide tile) for P0,
+  // 4 orbitals x 40 Q (one half of an 80-wide tile) for Sigma
+  s->fused = d.fuse && nao % 4 == 0 && nao <= 56 && naux % 40 == 0;
+  if (s->fused) {
+    s->Kc_p0 = 4 * nao;
+    s->Kpad_p0 = nk * (int)s->nao2;
+    s->Kc_s = 160;
+    s->Kpad_s = naux * nao;
+  }
+  // tau batch: FP64 intermediates (unfused) plus operand planes per tau node
+  const double per_t = (s->fused ? 0.0 : 2.0 * nk * (double)s->pair * 16.0) +
                        (8.0 + 8.0) * std::max((double)naux * s->Kpad_p0, (double)nk * nao * s->Kpad_s) * 2.0 +
                        (double)naux * s->Kpad_r * 8.0 * 2.0;
-  int nt = d.tau_chunk > 0 ? d.tau_chunk : (int)std::max(1.0, std::floor(12884901888.0 / per_t));
-  s->nt = std::min(nt, ntau);
+  s->nt = d.tau_chunk > 0 ? std::min(d.tau_chunk, ntau) : auto_tau_batch(d, per_t);
   int rc = GW_OK;
   do {
     // V slices for every pair when they take at most 24 GiB; else per q (4 nk pairs at a time)
-    const double full_v = 16.0 * nk * nk * ((double)naux * nao * s->Kpad_vg + (double)s->nao2 * s->Kpad_r);
+    const double full_v = 16.0 * nk * nk * ((s->fused ? 2.0 : 1.0) * naux * nao * s->Kpad_vg +
+                                            (double)s->nao2 * s->Kpad_r);
     s->per_q = d.v_slices == GW_V_PER_Q || (d.v_slices == GW_V_AUTO && full_v > 25769803776.0);
     const long long vpairs = s->per_q ? nk : (long long)nk * nk;
     if (s->per_q) {
@@ -1224,6 +1597,7 @@ int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int*
       // a packed V is unpacked for the slicing through a transient buffer of all pairs
       if (d.v_packed) *bytes += (size_t)nk * nk * s->pair * sizeof(double2);
       if ((rc = alloc_planes(s, &s->vrow, vpairs * naux * nao, s->Kc_vg, s->Kpad_vg, 2, bytes))) break;
+      if (s->fused && (rc = alloc_planes(s, &s->vrowt, vpairs * naux * nao, s->Kc_vg, s->Kpad_vg, 2, bytes))) break;
       if ((rc = alloc_planes(s, &s->vcol, vpairs * s->nao2, s->Kc_r, s->Kpad_r, 2, bytes))) break;
     }
     if ((rc = alloc_planes(s, &s->gf, (long long)nk * ntau * nao, s->Kc_vg, s->Kpad_vg, 2, bytes))) break;
@@ -1233,8 +1607,10 @@ int mixed_create(MixedState** out, const MixedDims& d, cudaStream_t stream, int*
     const size_t op_elems = 4 * std::max((size_t)s->nt * naux * s->Kpad_p0, (size_t)s->nt * nk * nao * s->Kpad_s);
     if ((rc = m_alloc(s, &s->xs_mem, 2 * op_elems, bytes))) break;
     if ((rc = m_alloc(s, &s->ys_mem, 2 * op_elems, bytes))) break;
-    if ((rc = m_alloc(s, &s->x64, (size_t)s->nt * nk * s->pair, bytes))) break;
-    if ((rc = m_alloc(s, &s->y64, (size_t)s->nt * nk * s->pair, bytes))) break;
+    if (!s->fused) {
+      if ((rc = m_alloc(s, &s->x64, (size_t)s->nt * nk * s->pair, bytes))) break;
+      if ((rc = m_alloc(s, &s->y64, (size_t)s->nt * nk * s->pair, bytes))) break;
+    }
     {
       int dev = 0, sms = 0;
       if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
@@ -1301,28 +1677,37 @@ int mixed_set_coulomb(MixedState* s, const double2* V, const double2* Vp) {
     L.all = 1;
     int rc = unpack_v_fp64(Vp, nk, s->d.nao, s->pair, L, nk * nk, tmp, s->stream);
     if (rc == GW_OK) rc = stage_vrow(s, tmp, nk * nk, nullptr, s->vrow);
+    if (rc == GW_OK && s->fused) rc = stage_vrowt(s, tmp, nk * nk, nullptr, s->vrowt);
     if (rc == GW_OK) rc = stage_vcol(s, tmp, nk * nk, nullptr, s->vcol);
     cudaStreamSynchronize(s->stream);
     cudaFree(tmp);
     return rc;
   }
   GW_TRY_INTERNAL(stage_vrow(s, V, nk * nk, nullptr, s->vrow));
+  if (s->fused) GW_TRY_INTERNAL(stage_vrowt(s, V, nk * nk, nullptr, s->vrowt));
   return stage_vcol(s, V, nk * nk, nullptr, s->vcol);
 }
 
 namespace {
 
 // Per-q V slices of one pair table: from V through the table, or from the blocks unpacked
-// out of a packed V into the scratch.
-int stage_q(MixedState* s, int table, int q, bool col, const Planes& P) {
+// out of a packed V into the scratch. layout: 0 rows (Q, i) over a, 1 rows (j, b) over Q',
+// 2 rows (i, Q) over a.
+enum { VL_ROW = 0, VL_COL = 1, VL_ROWT = 2 };
+int stage_q(MixedState* s, int table, int q, int layout, const Planes& P) {
   const int nk = s->d.nk;
+  const double2* src = s->V;
+  const long long* t = tab(s, table, q);
   if (s->Vp) {
     VPairs L;
-    L.tab = tab(s, table, q);
+    L.tab = t;
     GW_TRY_INTERNAL(unpack_v_fp64(s->Vp, nk, s->d.nao, s->pair, L, nk, s->vscratch, s->stream));
-    return col ? stage_vcol(s, s->vscratch, nk, nullptr, P) : stage_vrow(s, s->vscratch, nk, nullptr, P);
+    src = s->vscratch;
+    t = nullptr;
   }
-  return col ? stage_vcol(s, s->V, nk, tab(s, table, q), P) : stage_vrow(s, s->V, nk, tab(s, table, q), P);
+  if (layout == VL_COL) return stage_vcol(s, src, nk, t, P);
+  if (layout == VL_ROWT) return stage_vrowt(s, src, nk, t, P);
+  return stage_vrow(s, src, nk, t, P);
 }
 
 }  // namespace
@@ -1452,15 +1837,16 @@ int mixed_outer_q(MixedState* s, const double2* X, long long x_bs, const double2
   return launch_oz(xs, zs, p, SLOT_GF2_TC, s->stream);
 }
 
-int mixed_polarization(MixedState* s, const double2* G, double2* P0t, double spin_factor) {
+int mixed_polarization(MixedState* s, const double2* G, double2* P0t, double spin_factor, int q0, int q1) {
   GW_TRY_INTERNAL(slice_g(s, G));
-  for (int q = 0; q < s->d.nk; ++q) {
-    // canonical tau nodes only (the caller fills P0^q(beta - tau) = P0^{-q}(tau)^T)
+  for (int q = q0; q < q1; ++q) {
+    // canonical tau nodes only (the caller fills P0^q(beta - tau) = P0^{-q}(tau)^T); every node
+    // when -q lies outside the range
     const int mq = s->d.mq[q];
-    const int tend = mq < q ? 0 : (mq == q ? (s->d.ntau + 1) / 2 : s->d.ntau);
+    const int tend = (mq < q0 || mq >= q1) ? s->d.ntau : (mq < q ? 0 : (mq == q ? (s->d.ntau + 1) / 2 : s->d.ntau));
     if (tend > 0 && s->per_q) {
-      GW_TRY_INTERNAL(stage_q(s, E_KKPQ, q, false, s->vq[0]));
-      GW_TRY_INTERNAL(stage_q(s, E_KPQK, q, false, s->vq[1]));
+      GW_TRY_INTERNAL(stage_q(s, E_KKPQ, q, VL_ROW, s->vq[0]));
+      GW_TRY_INTERNAL(stage_q(s, E_KPQK, q, VL_ROW, s->vq[1]));
     }
     // equal batches of at most nt nodes (no short last batch that would leave the GPU half idle)
     const int nb = (tend + s->nt - 1) / s->nt;
@@ -1472,15 +1858,15 @@ int mixed_polarization(MixedState* s, const double2* G, double2* P0t, double spi
   return GW_OK;
 }
 
-int mixed_self_energy(MixedState* s, const double2* G, const double2* Pt, double2* Sig) {
+int mixed_self_energy(MixedState* s, const double2* G, const double2* Pt, double2* Sig, int q0, int q1) {
   if (cudaMemsetAsync(Sig, 0, (size_t)s->d.nk * s->d.ntau * s->nao2 * sizeof(double2), s->stream) != cudaSuccess)
     return fail(GW_ECUDA, "memset Sigma");
   GW_TRY_INTERNAL(slice_g(s, G));
   const int nb = (s->d.ntau + s->nt - 1) / s->nt;      // equal batches of at most nt nodes
-  for (int q = 0; q < s->d.nk; ++q) {
+  for (int q = q0; q < q1; ++q) {
     if (s->per_q) {
-      GW_TRY_INTERNAL(stage_q(s, E_KKMQ, q, false, s->vq[0]));
-      GW_TRY_INTERNAL(stage_q(s, E_KMQK, q, true, s->vcq));
+      GW_TRY_INTERNAL(stage_q(s, E_KKMQ, q, s->fused ? VL_ROWT : VL_ROW, s->vq[0]));
+      GW_TRY_INTERNAL(stage_q(s, E_KMQK, q, VL_COL, s->vcq));
     }
     for (int i = 0; i < nb; ++i) {
       const int t0 = (int)((long long)s->d.ntau * i / nb), t1 = (int)((long long)s->d.ntau * (i + 1) / nb);

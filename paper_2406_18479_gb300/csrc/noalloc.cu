@@ -1,18 +1,18 @@
 // P0(tau) without any device allocation: gw_polarization_noalloc.
 //
-// For callers that cannot allocate device memory at the time of the call:
-// code running inside a CUDA-graph capture (cudaMalloc is not capturable),
-// a host that hands the library a fixed memory budget already spent on its
-// own pools, or an embedding runtime that forbids allocation after start-up.
-// Those callers pass inputs and outputs only; the intermediates of the V.G
-// products live in one file-scope device array of fixed size.
+// For callers that cannot allocate device memory at the time of the call: a host that
+// reserved all its device memory at start-up for its own pools, an embedding runtime that
+// forbids allocation after initialisation, or a latency-critical loop that cannot take the
+// synchronisation cudaMalloc may imply. Those callers pass inputs and outputs only; the
+// intermediates of the V.G products live in one file-scope device array of fixed size.
 //
-// The computation is the FP64 path of gw_polarization (same kernels), with
-// the k sum split into chunks that fit the array and accumulated into P0t.
+// The computation is the FP64 path of gw_polarization (same kernels), with the k sum split
+// into chunks that fit the array and accumulated into P0t.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <mutex>
+#include <utility>
 
 #include "gw_internal.h"
 
@@ -28,11 +28,10 @@ constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
 double2* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (looked up once per device).
-int scratch_address(double2** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-    return fail(GW_ECUDA, "gw_polarization_noalloc: no usable current device");
+// Device address of the scratch array on device dev (looked up once per device and kept: the
+// address stays valid until the device is reset, which callers must not do between calls).
+int scratch_address(int dev, double2** out) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(GW_ECUDA, "gw_polarization_noalloc: no usable current device");
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;
@@ -42,6 +41,19 @@ int scratch_address(double2** out) {
     g_scratch_ptr[dev] = static_cast<double2*>(p);
   }
   *out = g_scratch_ptr[dev];
+  return GW_OK;
+}
+
+// GW_OK if p is device memory of device dev (a pointer from another device, host memory or an
+// unknown address would make the kernels fault)
+int check_device_ptr(const void* p, int dev, const char* what) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GW_EINVAL, "gw_polarization_noalloc: %s is not a CUDA pointer", what);
+  }
+  if (a.type != cudaMemoryTypeDevice || a.device != dev)
+    return fail(GW_EINVAL, "gw_polarization_noalloc: %s is not device memory of the current device %d", what, dev);
   return GW_OK;
 }
 
@@ -66,7 +78,9 @@ extern "C" int gw_polarization_noalloc(const int nk3[3], int nao, int naux, int 
   if (!nk3 || !V_dev || !G_dev || !P0t_dev) return fail(GW_EINVAL, "gw_polarization_noalloc: null argument");
   if (nk3[0] < 1 || nk3[1] < 1 || nk3[2] < 1 || nao < 1 || naux < 1 || ntau < 1)
     return fail(GW_EINVAL, "gw_polarization_noalloc: sizes must be positive");
-  const int nk = nk3[0] * nk3[1] * nk3[2];
+  const long long nk_ll = (long long)nk3[0] * nk3[1] * nk3[2];
+  if (nk_ll > 65535) return fail(GW_EINVAL, "gw_polarization_noalloc: nk = %lld above 65535", nk_ll);
+  const int nk = (int)nk_ll;
   const long long nao2 = (long long)nao * nao, pair = (long long)naux * nao2, naux2 = (long long)naux * naux;
   // one (tau, k) unit needs the A and B~ blocks of one k-point pair: 2 * naux * nao^2 elements
   if (2 * pair > kScratchElems)
@@ -74,10 +88,19 @@ extern "C" int gw_polarization_noalloc(const int nk3[3], int nao, int naux, int 
                 "gw_polarization_noalloc: 2*naux*nao^2 = %lld complex elements exceed the fixed scratch of %lld "
                 "(64 MiB); use gw_polarization with a context",
                 2 * pair, kScratchElems);
-  if (nk > 65535 || (long long)naux * nao > (1LL << 30))
-    return fail(GW_EINVAL, "gw_polarization_noalloc: problem too large");
+  if ((long long)naux * nao > (1LL << 30)) return fail(GW_EINVAL, "gw_polarization_noalloc: problem too large");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(GW_ECUDA, "gw_polarization_noalloc: no usable current device");
+  }
+  for (const auto& pw : {std::make_pair((const void*)V_dev, "V_dev"), std::make_pair((const void*)G_dev, "G_dev"),
+                         std::make_pair((const void*)P0t_dev, "P0t_dev")}) {
+    const int rc = check_device_ptr(pw.first, dev, pw.second);
+    if (rc != GW_OK) return rc;
+  }
   double2* scratch = nullptr;
-  const int rc0 = scratch_address(&scratch);
+  const int rc0 = scratch_address(dev, &scratch);
   if (rc0 != GW_OK) return rc0;
   cudaStream_t st = (cudaStream_t)cuda_stream;
   const double2* V = reinterpret_cast<const double2*>(V_dev);

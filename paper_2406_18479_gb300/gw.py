@@ -18,15 +18,16 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libgw_gb300.so")
 
 GW_OK, GW_EINVAL, GW_ENOMEM, GW_ECUDA, GW_ETIMEOUT, GW_EDEVTIMEOUT = 0, 1, 2, 3, 4, 5
 GW_ENOTFINITE, GW_ENOTCONV, GW_EAGAIN, GW_ENOTIMPL = 6, 7, 8, 9
-GW_FP64, GW_MIXED_BF16X3, GW_MIXED_FP16S = 0, 1, 2
+GW_FP64, GW_MIXED_BF16X4 = 0, 1
+GW_MIXED_BF16X3 = GW_MIXED_BF16X4          # former name (the scheme has four slices)
 GW_V_AUTO, GW_V_ALL_PAIRS, GW_V_PER_Q = 0, 1, 2
-PRECISIONS = {"fp64": GW_FP64, "bf16x3": GW_MIXED_BF16X3, "fp16s": GW_MIXED_FP16S}
+PRECISIONS = {"fp64": GW_FP64, "bf16x4": GW_MIXED_BF16X4, "bf16x3": GW_MIXED_BF16X4}
 
 # Every symbol declared in include/gw.h.
 ABI_SYMBOLS = [
     "gw_version", "gw_last_error", "gw_sample_count", "gw_grid_build", "gw_create", "gw_destroy",
     "gw_workspace_bytes", "gw_set_grids", "gw_set_coulomb", "gw_polarization", "gw_to_matsubara", "gw_to_tau",
-    "gw_aux_dyson", "gw_screened_interaction", "gw_self_energy", "gw_sigma_eval", "gw_dyson_G",
+    "gw_aux_dyson", "gw_screened_interaction", "gw_self_energy", "gw_sigma_eval", "gw_sigma_eval_q", "gw_dyson_G",
     "gw_mix", "gw_synchronize", "gw_profile_enable", "gw_launch_count", "gw_profile_slots",
     "gw_profile_read", "gw_polarization_noalloc", "gw_job_bytes", "gw_server_create",
     "gw_server_destroy", "gw_submit", "gw_poll", "gw_batch_create", "gw_batch_destroy",
@@ -50,7 +51,7 @@ class gw_config(ctypes.Structure):
         ("nk", ctypes.c_int * 3), ("nao", ctypes.c_int), ("naux", ctypes.c_int), ("ntau", ctypes.c_int),
         ("beta", ctypes.c_double), ("mu", ctypes.c_double), ("spin_factor", ctypes.c_double),
         ("precision", ctypes.c_int), ("tau_chunk", ctypes.c_int), ("v_slices", ctypes.c_int),
-        ("v_packed", ctypes.c_int),
+        ("v_packed", ctypes.c_int), ("slice_pass", ctypes.c_int),
     ]
 
 
@@ -121,6 +122,7 @@ def lib():
     L.gw_screened_interaction.argtypes = [vp, vp, vp]
     L.gw_self_energy.argtypes = [vp, vp, vp, vp]
     L.gw_sigma_eval.argtypes = [vp, vp, vp]
+    L.gw_sigma_eval_q.argtypes = [vp, vp, vp, i, i, vp, vp]
     L.gw_dyson_G.argtypes = [vp, vp, vp, vp]
     L.gw_mix.argtypes = [vp, vp, vp, d, ctypes.POINTER(d)]
     L.gw_synchronize.argtypes = [vp]
@@ -213,7 +215,7 @@ class gw_ctx:
     """Owner of one gw_ctx* (gw_create ... gw_destroy)."""
 
     def __init__(self, nk3, nao, naux, ntau, beta, mu=0.0, spin_factor=2.0, precision="fp64",
-                 tau_chunk=0, v_slices=0, stream=None, v_packed=False):
+                 tau_chunk=0, v_slices=0, stream=None, v_packed=False, slice_pass=False):
         import torch
         self.nk3 = tuple(int(x) for x in nk3)
         self.nk = int(np.prod(self.nk3))
@@ -224,7 +226,8 @@ class gw_ctx:
         prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
         self.v_packed = int(v_packed)
         cfg = gw_config((ctypes.c_int * 3)(*self.nk3), self.nao, self.naux, self.ntau, self.beta,
-                        self.mu, float(spin_factor), prec, int(tau_chunk), int(v_slices), self.v_packed)
+                        self.mu, float(spin_factor), prec, int(tau_chunk), int(v_slices), self.v_packed,
+                        int(bool(slice_pass)))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = ctypes.c_void_p()
         _check(lib().gw_create(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(self.stream.cuda_stream)))
@@ -328,6 +331,17 @@ def gw_sigma_eval(ctx: gw_ctx, G, Sig):
     _check(lib().gw_sigma_eval(ctx.handle, _ptr(G, s["G"]), _ptr(Sig, s["Sig"])))
 
 
+def gw_sigma_eval_q(ctx: gw_ctx, G, Sig, q_begin: int, q_end: int, P0t=None, Pt=None):
+    """Sig <- the part of one evaluation from the momentum transfers q in [q_begin, q_end);
+    P0t, Pt (optional, [q_end - q_begin][ntau][naux][naux]) receive the range's P0 and P~."""
+    s = ctx.shapes()
+    nq = int(q_end) - int(q_begin)
+    blk = (max(nq, 0),) + tuple(s["Pt"][1:])
+    _check(lib().gw_sigma_eval_q(ctx.handle, _ptr(G, s["G"]), _ptr(Sig, s["Sig"]), int(q_begin), int(q_end),
+                                 _ptr(P0t, blk) if P0t is not None else None,
+                                 _ptr(Pt, blk) if Pt is not None else None))
+
+
 def gw_dyson_G(ctx: gw_ctx, H, Sig, G):
     s = ctx.shapes()
     _check(lib().gw_dyson_G(ctx.handle, _ptr(H, s["H"]), _ptr(Sig, s["Sig"]), _ptr(G, s["G"])))
@@ -369,14 +383,22 @@ def gw_profile_read(ctx: gw_ctx) -> dict:
 
 
 def gw_polarization_noalloc(nk3, nao, naux, ntau, spin_factor, V, G, P0t, stream=None):
-    """P0(tau) without a context or any device allocation (see include/gw.h).
+    """P0(tau) without a context or any device allocation (see include/gw.h), for callers whose
+    device memory is already committed to their own pools or who may not allocate after start-up.
 
-    The first call on a device must come before any stream capture; calls that
-    overlap on the GPU share the library's one scratch array and race.
+    V, G and P0t must live on the current CUDA device (and the stream too). The first call on a
+    device must come before any stream capture; calls that overlap on the GPU share the
+    library's one scratch array and race.
     """
     import torch
     nk = int(np.prod(nk3))
     s = stream if stream is not None else torch.cuda.current_stream()
+    cur = torch.cuda.current_device()
+    for name, t in (("V", V), ("G", G), ("P0t", P0t)):
+        if isinstance(t, torch.Tensor) and t.is_cuda and t.device.index != cur:
+            raise GWError(GW_EINVAL, f"{name} is on cuda:{t.device.index}, the current device is cuda:{cur}")
+    if s.device.index != cur:
+        raise GWError(GW_EINVAL, f"the stream belongs to cuda:{s.device.index}, the current device is cuda:{cur}")
     arr = (ctypes.c_int * 3)(*[int(x) for x in nk3])
     _check(lib().gw_polarization_noalloc(arr, int(nao), int(naux), int(ntau), float(spin_factor),
                                          _ptr(V, (nk, nk, naux, nao, nao)), _ptr(G, (nk, ntau, nao, nao)),
@@ -387,10 +409,11 @@ def gw_polarization_noalloc(nk3, nao, naux, ntau, spin_factor, V, G, P0t, stream
 
 
 def make_config(nk3, nao, naux, ntau, beta, mu=0.0, spin_factor=2.0, precision="fp64", tau_chunk=0,
-                v_slices=0, v_packed=False):
+                v_slices=0, v_packed=False, slice_pass=False):
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     return gw_config((ctypes.c_int * 3)(*[int(x) for x in nk3]), int(nao), int(naux), int(ntau), float(beta),
-                     float(mu), float(spin_factor), prec, int(tau_chunk), int(v_slices), int(bool(v_packed)))
+                     float(mu), float(spin_factor), prec, int(tau_chunk), int(v_slices), int(bool(v_packed)),
+                     int(bool(slice_pass)))
 
 
 def gw_job_bytes(cfg: gw_config) -> int:

@@ -40,6 +40,7 @@ class Workload:
     decay: float = 8.0  # V^Q scale exp(-Q/decay)
     seed: int = 0
     solid: bool = False
+    vscale: float = 1.0  # overall amplitude of V (c_Q = vscale exp(-Q/decay))
 
     @property
     def nk(self) -> int:
@@ -118,10 +119,10 @@ def coulomb(w: Workload, rng: np.random.Generator, dtype=np.complex128) -> np.nd
     """V[k1][k2][Q][i][j] with V(k2,k1)^Q_ji = conj V(k1,k2)^Q_ij.
 
     Diagonal pairs are Hermitian in ij: c_Q (X + X^dagger)/2; pairs k1 < k2 are
-    c_Q X / sqrt(2); X_ij = (a + ib)/sqrt(2), a, b ~ N(0, 1); c_Q = exp(-Q/decay).
+    c_Q X / sqrt(2); X_ij = (a + ib)/sqrt(2), a, b ~ N(0, 1); c_Q = vscale exp(-Q/decay).
     """
     nk, nao, naux = w.nk, w.nao, w.naux
-    c = np.exp(-np.arange(naux) / w.decay)[:, None, None]
+    c = w.vscale * np.exp(-np.arange(naux) / w.decay)[:, None, None]
     v = np.empty((nk, nk, naux, nao, nao), dtype)
     for k1 in range(nk):
         for k2 in range(k1, nk):
@@ -177,10 +178,24 @@ def batched_molecules(n: int = 48, seed: int = 4):
     return [molecule(f"mol{i}_nao{int(a)}", int(a), seed=seed * 1000 + i) for i, a in enumerate(naos)]
 
 
+# Interaction strength of the serving stream: V scaled per job so that nao sum_Q c_Q^2, the size of
+# the exchange-like sums, is the same for every job (0.5^2 / (nao sum_Q exp(-2Q/decay)) times the
+# unit-variance V). The unit-variance V gives max|Sigma| of 10^2..10^3 Ha, where the fixed-mu
+# loop with mixing 0.5 diverges; at this strength max|Sigma| is of order 0.01 Ha and the loop
+# reaches max|dSigma| < 1e-6 within 10 evaluations (mixing halves the change per iteration).
+SERVING_STRENGTH = 0.5
+
+
+def serving_vscale(nao: int, naux: int, decay: float) -> float:
+    """V amplitude of a serving job: SERVING_STRENGTH / sqrt(nao sum_Q exp(-2 Q / decay))."""
+    return SERVING_STRENGTH / float(np.sqrt(nao * np.sum(np.exp(-2.0 * np.arange(naux) / decay))))
+
+
 def serving_stream(n: int = 200, seed: int = 5):
     """Seeded scGW job stream: [(gap, Workload)], gaps exponential with unit mean (Poisson arrivals;
     the caller divides by the rate). 70% molecules with nao on {10..120}; 30% solids on a 2x2x2 or
-    3x3x3 mesh with nao on {16..52}; naux = 4 nao, 80 tau nodes, beta = 100.
+    3x3x3 mesh with nao on {16..52}; naux = 4 nao, 80 tau nodes, beta = 100; V at the serving
+    strength (serving_vscale).
     """
     rng = np.random.default_rng(seed)
     out = []
@@ -194,6 +209,7 @@ def serving_stream(n: int = 200, seed: int = 5):
             nao = int(rng.integers(16, 53))
             w = Workload(f"job{i}_solid{m[0]}_nao{nao}", m, nao, 4 * nao, 80, 80, 100.0, decay=40.0,
                          seed=seed * 1000 + i, solid=True)
+        w = dataclasses.replace(w, vscale=serving_vscale(w.nao, w.naux, w.decay))
         out.append((gap, w))
     return out
 

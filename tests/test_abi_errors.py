@@ -1,5 +1,5 @@
 """Error paths and size queries of the C ABI that run on the host before any device work, so they
-are checked without a GPU: bad arguments give GW_EINVAL (or GW_ENOTIMPL) with a message, and the
+are checked without a GPU: bad arguments give GW_EINVAL with a message, and the
 device-byte queries of contexts, jobs and loops add up."""
 import ctypes
 
@@ -38,7 +38,7 @@ def test_null_and_out_of_range_arguments(L):
 
 
 @pytest.mark.parametrize("field,value", [("nao", 0), ("naux", 5000), ("ntau", 0), ("beta", -1.0), ("precision", 7),
-                                         ("v_slices", 3), ("v_packed", 2)])
+                                         ("precision", 2), ("v_slices", 3), ("v_packed", 2), ("slice_pass", 2)])
 def test_bad_configurations(L, field, value):
     cfg = gw.make_config((2, 1, 1), 3, 4, 5, 2.0)
     setattr(cfg, field, value)
@@ -47,10 +47,10 @@ def test_bad_configurations(L, field, value):
     assert gw.gw_job_bytes(cfg) == 0
 
 
-def test_fp16s_is_reserved(L):
-    cfg = gw.make_config((1, 1, 1), 3, 4, 5, 2.0, precision=2)
-    h = ctypes.c_void_p()
-    assert L.gw_create(ctypes.byref(h), ctypes.byref(cfg), None) == gw.GW_ENOTIMPL
+def test_precision_names():
+    """The four-slice scheme under its name and its former one; no FP16 precision exists."""
+    assert gw.PRECISIONS["bf16x4"] == gw.PRECISIONS["bf16x3"] == gw.GW_MIXED_BF16X4 == 1
+    assert "fp16s" not in gw.PRECISIONS
 
 
 def test_loop_bytes(L):

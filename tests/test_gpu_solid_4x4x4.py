@@ -4,8 +4,14 @@ size) and the tau batch is set to 15 nodes (300 P0 tiles per launch).
 
 The oracle recomputes samples from the same inputs: P0 at 2 q x 3 tau; P~ of one q from the
 GPU's own P0 of that q (steps a2-a4 at full size); Sigma at 4 k x 8 tau from the GPU's P~
-(step a5 at full size). Tolerance 1e-7 relative per sampled array. The FP64 path is not run
-here: one evaluation at this size takes about an hour of FP64 work.
+(step a5 at full size). Tolerance 1e-7 relative per sampled array.
+
+Accuracy in Ha: one FP64 evaluation at this size is about an hour of FP64 work, so the mixed
+path is compared with the GPU FP64 path on the part of Sigma from one momentum transfer
+(Eq. sigma_gw sums over q; gw_sigma_eval_q), q = 0, whose cost is the average per-q cost. The
+full Sigma sums 64 such parts; their rounding errors are independent, so the full error is
+about sqrt(64) times the part's (the test asserts that this estimate meets 1e-6 Ha, i.e. the
+part's error is at most 1.25e-7 Ha); the triangle inequality bounds it by 64 times the part's.
 """
 import numpy as np
 import pytest
@@ -42,6 +48,11 @@ def run():
     Sig = torch.empty(s["Sig"], dtype=torch.complex128, device="cuda")
     gw.gw_self_energy(ctx, Gd, Pt, Sig)
     gw.gw_synchronize(ctx)
+    # the part of Sigma from q = 0, mixed (this context) and FP64 (after this context is gone)
+    Sig_q = torch.empty_like(Sig)
+    gw.gw_sigma_eval_q(ctx, Gd, Sig_q, 0, 1)
+    gw.gw_synchronize(ctx)
+    sig_q_mixed = Sig_q.cpu().numpy()
     rng = np.random.default_rng(3)
     q_s = sorted(rng.choice(W.nk, 2, replace=False).tolist())
     t_s = sorted(rng.choice(W.ntau, 3, replace=False).tolist())
@@ -51,7 +62,16 @@ def run():
            "Pt_q": Pt[q_s[:1]].cpu().numpy(), "Pt": Pt.cpu().numpy(),
            "Sig_s": Sig[k_s][:, kt_t].cpu().numpy(), "q_s": q_s, "t_s": t_s, "k_s": k_s, "kt_t": kt_t}
     ctx.destroy()
-    del V, Gd, P0t, Pt, Sig
+    del P0t, Pt, Sig
+    torch.cuda.empty_cache()
+    c64 = gw.gw_create(W.nk3, W.nao, W.naux, W.ntau, W.beta, precision="fp64")
+    gw.gw_set_coulomb(c64, V)
+    gw.gw_sigma_eval_q(c64, Gd, Sig_q, 0, 1)
+    gw.gw_synchronize(c64)
+    out["sig_q_fp64"] = Sig_q.cpu().numpy()
+    out["sig_q_mixed"] = sig_q_mixed
+    c64.destroy()
+    del V, Gd, Sig_q
     torch.cuda.empty_cache()
     return h, v, g, out
 
@@ -73,3 +93,11 @@ def test_solid_4x4x4_self_energy_sampled_from_gpu_pt(run):
     h, v, g, out = run
     ref = O.self_energy(v, g, out["Pt"], W.nk3, k_list=out["k_s"], t_list=out["kt_t"])
     assert rel(out["Sig_s"], ref) < TOL
+
+
+def test_solid_4x4x4_sigma_part_of_q0_within_the_ha_target(run):
+    h, v, g, out = run
+    err = float(np.max(np.abs(out["sig_q_mixed"] - out["sig_q_fp64"])))
+    print(f"4x4x4 solid, q = 0: max|dSigma_q| = {err:.3e} Ha (max|Sigma_q| = {np.abs(out['sig_q_fp64']).max():.2f} Ha); "
+          f"full Sigma: estimate {np.sqrt(W.nk) * err:.2e} Ha, bound {W.nk * err:.2e} Ha")
+    assert err * np.sqrt(W.nk) <= 1e-6

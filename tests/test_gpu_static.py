@@ -252,9 +252,10 @@ def test_scgw_loop_mixed_precision(G):
                          mu_tol=1e-12)
     rc, r = G.gw_scgw(ctx, dev(h), Gd, S, None, opt)
     assert rc in (G.GW_OK, G.GW_ENOTCONV)
-    assert abs(r["mu"] - ref["mu"]) < 1e-5
-    assert np.abs(host(S) - ref["Sig"]).max() < 1e-5
-    assert np.abs(host(Gd) - ref["G"]).max() < 1e-5
+    # the fixed point in the mixed precision is the FP64 one to within the 1e-6 Ha target
+    assert abs(r["mu"] - ref["mu"]) < 1e-6
+    assert np.abs(host(S) - ref["Sig"]).max() < 1e-6
+    assert np.abs(host(Gd) - ref["G"]).max() < 1e-6
     ctx.destroy()
 
 
