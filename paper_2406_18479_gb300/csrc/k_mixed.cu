@@ -469,7 +469,7 @@ __device__ __forceinline__ void tmem_ldg(uint32_t taddr, float* v) {
   else tmem_ld4(taddr, v);
 }
 
-template <int BN_>
+template <int BN_, bool SO>
 __global__ void __launch_bounds__(352, 1)
     oz_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, const OzParams p) {
   using S = OzShape<BN_>;
@@ -669,7 +669,7 @@ __global__ void __launch_bounds__(352, 1)
         return row_ok && cl - dcol0 >= 0 && cl - dcol0 < ncols && cl < nstride && n < p.N;
       };
       auto out_write = [&](int cl, float rh, float rl, float ih, float il) {
-        if (p.so) {                                   // kept for the slice output below
+        if constexpr (SO) {                           // kept for the slice output below
           cw[(size_t)cl * kBM] = make_float4(rh, rl, ih, il);
           return;
         }
@@ -774,7 +774,7 @@ __global__ void __launch_bounds__(352, 1)
         if (!mbar_wait(acc_full, chunk & 1, abort_flag, p.status, 14)) { ok = false; break; }
         tc_fence_after();
         const bool single = nchunks == 1;
-        if (p.so && single) {
+        if (SO && single) {
           // ---- slice output of a one-chunk contraction straight from TMEM: pass 1 finds the row
           //      maximum, pass 2 slices 4 columns at a time; TMEM is released after pass 2
           uint32_t mx = 0;
@@ -880,7 +880,7 @@ __global__ void __launch_bounds__(352, 1)
               if (!col_ok(cl)) continue;
               df_add(a[u].x, a[u].y, x[u].x, x[u].y);
               df_add(a[u].z, a[u].w, x[u].z, x[u].w);
-              if (last && p.so)
+              if (SO && last)
                 so_mx = max(so_mx, max(__float_as_uint(a[u].x) & 0x7FFFFFFFu, __float_as_uint(a[u].z) & 0x7FFFFFFFu));
               if (last) out_write(cl, a[u].x, a[u].y, a[u].z, a[u].w);
               else ws[(size_t)cl * kBM] = a[u];
@@ -888,7 +888,7 @@ __global__ void __launch_bounds__(352, 1)
           }
         }
       }
-      if (p.so && nchunks > 1 && ok) {
+      if (SO && nchunks > 1 && ok) {
         // ---- slice output of a chunked contraction: the final values wait in cw; the next
         //      group's loads are issued before the current group is sliced
         float magic[4];
@@ -1047,13 +1047,17 @@ int launch_oz_bn(const Planes& A, const Planes& B, OzParams p, int slot, cudaStr
   GW_TRY_INTERNAL(make_map(B, S::kBN, &mb));
   // one-time setup; function-local statics initialise once even when contexts run on several threads
   static const bool attr = [] {
-    cudaFuncSetAttribute(oz_gemm_kernel<BN_>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
+    cudaFuncSetAttribute(oz_gemm_kernel<BN_, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
+    cudaFuncSetAttribute(oz_gemm_kernel<BN_, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
     return true;
   }();
   (void)attr;
   const int grid = (int)std::min<long long>(total, num_sms());
   prof_begin(slot, st);
-  oz_gemm_kernel<BN_><<<grid, S::kThreads, S::kSmem, st>>>(ma, mb, p);
+  if (p.so)
+    oz_gemm_kernel<BN_, true><<<grid, S::kThreads, S::kSmem, st>>>(ma, mb, p);
+  else
+    oz_gemm_kernel<BN_, false><<<grid, S::kThreads, S::kSmem, st>>>(ma, mb, p);
   // executed bf16 tensor flops: 10 slice products x 2 real MMAs of 128 x (2 BN) x 16 per k-step
   prof_end(slot, st, 2.0 * 20.0 * (double)total * kBM * (2 * S::kBN) * (double)p.nsteps * kStepK,
            (double)total * p.nsteps * S::kTxBytes);

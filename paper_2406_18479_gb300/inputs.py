@@ -58,6 +58,10 @@ WORKLOADS = {
     # a case small enough for full hardware-counter captures
     "solid_3x3x1_nao26": Workload("solid_3x3x1_nao26", (3, 3, 1), 26, 200, 25, 25, 100.0,
                                   decay=40.0, seed=6, solid=True),
+    # the 4x4x4 solid's orbital and auxiliary sizes on a 2x2x1 mesh and 16 tau nodes: the
+    # hardware-counter case of its kernels
+    "solid_2x2x1_nao52": Workload("solid_2x2x1_nao52", (2, 2, 1), 52, 400, 16, 16, 200.0,
+                                  decay=40.0, seed=8, solid=True),
 }
 
 
