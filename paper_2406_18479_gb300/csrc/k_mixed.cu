@@ -426,8 +426,8 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 // the next chunk's MMAs run.
 template <int BN_>
 struct OzShape {
-  static constexpr int kBN = BN_;                      // output columns per tile (72 or 80)
-  static constexpr int kStages = 3;
+  static constexpr int kBN = BN_;                      // output columns per tile (40, 56, 72 or 80)
+  static constexpr int kStages = kBN <= 40 ? 4 : 3;
   static constexpr int kRowBytes = 128;                // four slices x 16 k x bf16
   static constexpr int kAGroup = kBM * kRowBytes;      // bytes of one A group tile
   static constexpr int kBBlock = kBN * kRowBytes;      // bytes of one B group block
@@ -436,6 +436,10 @@ struct OzShape {
   static constexpr int kThreads = 352;                 // producer, MMA, 8 epilogue warps, negation warp
   static constexpr int kOrderCols = 2 * kBN;           // [im | re] of one order
   static constexpr int kTmemCols = 512;
+  // accumulator sets in TMEM: two where they fit (tiles up to 40 columns), so that the MMAs of
+  // the next chunk run while the epilogue drains the last one
+  static constexpr int kBufCols = 3 * kOrderCols;
+  static constexpr int kBufs = 2 * kBufCols <= kTmemCols ? 2 : 1;
   // slice output: maxima exchanged between column halves (two tiles in flight x 4 lane quarters x
   // 2 halves x 32 lanes) and per-warp line staging (8 warps x 8 line groups x 272 bytes)
   static constexpr int kXmaxBytes = 2 * 4 * 2 * 32 * 4;
@@ -481,12 +485,12 @@ __global__ void __launch_bounds__(352, 1)
   uint64_t* full = bars;                           // TMA landed
   uint64_t* empty = bars + S::kStages;             // MMAs done with the stage
   uint64_t* ready = bars + 2 * S::kStages;         // -Bi block written
-  uint64_t* acc_full = bars + 3 * S::kStages;
-  uint64_t* acc_empty = acc_full + 1;
-  uint64_t* drain_bar = acc_full + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 3);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  uint64_t* acc_full = bars + 3 * S::kStages;      // [2]: chunk done, per accumulator set
+  uint64_t* acc_empty = acc_full + 2;              // [2]: accumulator set drained
+  uint64_t* drain_bar = acc_full + 4;
   uint64_t* xbar = acc_full + 5;                   // slice output: column-half maxima written
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 6);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   uint32_t* xmax = reinterpret_cast<uint32_t*>(smem + (size_t)S::kStages * S::kStageBytes + 256);
   uint8_t* stage_out = reinterpret_cast<uint8_t*>(xmax) + S::kXmaxBytes;
 
@@ -497,8 +501,10 @@ __global__ void __launch_bounds__(352, 1)
       mbar_init(&empty[s], 1);
       mbar_init(&ready[s], 1);
     }
-    mbar_init(acc_full, 1);
-    mbar_init(acc_empty, 8);                 // one arrival per epilogue warp
+    for (int b = 0; b < S::kBufs; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 8);           // one arrival per epilogue warp
+    }
     mbar_init(drain_bar, 1);
     mbar_init(xbar, 8);
     *abort_flag = 0;
@@ -563,8 +569,9 @@ __global__ void __launch_bounds__(352, 1)
       for (int tile = blockIdx.x; tile < total_tiles && ok; tile += gridDim.x) {
         for (int s = 0; s < p.nsteps && ok; ++s, ++step) {
           const bool chunk_start = (s % p.steps_per_chunk) == 0;
+          const uint32_t buf = chunk % S::kBufs;
           if (chunk_start) {
-            if (!mbar_wait(acc_empty, (chunk & 1) ^ 1, abort_flag, p.status, 12)) { ok = false; break; }
+            if (!mbar_wait(&acc_empty[buf], ((chunk / S::kBufs) & 1) ^ 1, abort_flag, p.status, 12)) { ok = false; break; }
             tc_fence_after();
           }
           const int st = step % S::kStages;
@@ -580,7 +587,7 @@ __global__ void __launch_bounds__(352, 1)
             for (int jj = 0; jj < 4; ++jj) {
               if (i + jj > 3) continue;
               const int acc = (i + jj == 0) ? 0 : (i + jj == 1 ? 1 : 2);
-              const uint32_t d = tmem + (uint32_t)(acc * S::kOrderCols);
+              const uint32_t d = tmem + buf * S::kBufCols + (uint32_t)(acc * S::kOrderCols);
               // first write of each accumulator in a chunk: (0,0), (0,1) and (0,2) in loop order
               const bool first = chunk_start && i == 0 && jj == acc;
               const uint64_t ar = sa + (uint64_t)(2 * i);                          // +32 i bytes
@@ -593,7 +600,7 @@ __global__ void __launch_bounds__(352, 1)
           }
           mma_commit(&empty[st]);
           if ((s % p.steps_per_chunk) == p.steps_per_chunk - 1 || s == p.nsteps - 1) {
-            mma_commit(acc_full);
+            mma_commit(&acc_full[buf]);
             ++chunk;
           }
         }
@@ -771,9 +778,11 @@ __global__ void __launch_bounds__(352, 1)
         __syncwarp();
       };
       for (int c = 0; c < nchunks; ++c, ++chunk) {
-        if (!mbar_wait(acc_full, chunk & 1, abort_flag, p.status, 14)) { ok = false; break; }
+        const uint32_t buf = chunk % S::kBufs;
+        if (!mbar_wait(&acc_full[buf], (chunk / S::kBufs) & 1, abort_flag, p.status, 14)) { ok = false; break; }
         tc_fence_after();
         const bool single = nchunks == 1;
+        const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + buf * S::kBufCols;
         if (SO && single) {
           // ---- slice output of a one-chunk contraction straight from TMEM: pass 1 finds the row
           //      maximum, pass 2 slices 4 columns at a time; TMEM is released after pass 2
@@ -782,7 +791,7 @@ __global__ void __launch_bounds__(352, 1)
           for (int g = 0; g < kCols / G; ++g) {
             const int cb = half * kCols + g * G;
             float v[3][2][G];
-            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cb;
+            const uint32_t taddr = tbase + (uint32_t)cb;
 #pragma unroll
             for (int o = 0; o < 3; ++o) {
               tmem_ldg<G>(taddr + o * S::kOrderCols, v[o][0]);
@@ -804,7 +813,7 @@ __global__ void __launch_bounds__(352, 1)
           for (int g4 = 0; g4 < kCols / 4; ++g4) {
             const int c0 = half * kCols + 4 * g4;
             float v[3][2][4];
-            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
+            const uint32_t taddr = tbase + (uint32_t)c0;
 #pragma unroll
             for (int o = 0; o < 3; ++o) {
               tmem_ld4(taddr + o * S::kOrderCols, v[o][0]);
@@ -825,7 +834,7 @@ __global__ void __launch_bounds__(352, 1)
           }
           tc_fence_before();
           __syncwarp();
-          if (lane == 0) mbar_arrive(acc_empty);
+          if (lane == 0) mbar_arrive(&acc_empty[buf]);
           continue;
         }
         // ---- drain: TMEM -> chunk value (an exact FP32 pair per part) -> output or scratch
@@ -833,7 +842,7 @@ __global__ void __launch_bounds__(352, 1)
         for (int g = 0; g < kCols / G; ++g) {
           const int cb = half * kCols + g * G;
           float v[3][2][G];                           // [order][im, re][column]
-          const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)cb;
+          const uint32_t taddr = tbase + (uint32_t)cb;
 #pragma unroll
           for (int o = 0; o < 3; ++o) {
             tmem_ldg<G>(taddr + o * S::kOrderCols, v[o][0]);
@@ -844,7 +853,7 @@ __global__ void __launch_bounds__(352, 1)
             // this warp's accumulator columns are in registers: release TMEM
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(acc_empty);
+            if (lane == 0) mbar_arrive(&acc_empty[buf]);
           }
 #pragma unroll
           for (int u = 0; u < G; ++u) {
@@ -1066,8 +1075,12 @@ int launch_oz_bn(const Planes& A, const Planes& B, OzParams p, int slot, cudaStr
 }
 
 // Tile width by the padding of N: 72 columns (MMA N = 144) when that covers N with fewer padded
-// columns than 80 (for example N = 200: 216 instead of 240), else 80. The narrower 56 (MMA N = 112:
-// more MMA issues per output) is taken only where a launch asks for it (block-diagonal tiles).
+// columns than 80 (for example N = 200: 216 instead of 240), else 80. Narrower tiles are taken
+// only where a launch asks for them: 56 (block-diagonal tiles, column blocks of 52..56) and 40.
+// At 40 columns (MMA N = 80) two accumulator sets fit in TMEM and the next tile's MMAs overlap the
+// epilogue, but each MMA reads the 128-row A tile from shared memory for half the work, which
+// makes long contractions bound by shared-memory bandwidth (measured: P0 and R 25-50% slower);
+// it pays only for the one-chunk V.G product of the fused path, whose epilogue dominates.
 int oz_tile_width(long long N) {
   const long long pad72 = (N + 71) / 72 * 72, pad80 = (N + 79) / 80 * 80;
   return pad72 < pad80 ? 72 : 80;
@@ -1075,6 +1088,7 @@ int oz_tile_width(long long N) {
 
 int launch_oz(const Planes& A, const Planes& B, OzParams p, int slot, cudaStream_t st, int bn = 0) {
   if (bn == 0) bn = oz_tile_width(p.N);
+  if (bn == 40) return launch_oz_bn<40>(A, B, p, slot, st);
   if (bn == 56) return launch_oz_bn<56>(A, B, p, slot, st);
   if (bn == 72) return launch_oz_bn<72>(A, B, p, slot, st);
   return launch_oz_bn<80>(A, B, p, slot, st);
@@ -1478,7 +1492,8 @@ int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double
     p.out_df = 1;                           // double-float, sliced again for the Sigma contraction
     if (s->fused) {
       // straight into the Sigma B operand: rows (t, k, j), k-position of (Q, b)
-      // ((Q/40) (nao/4) + b/4) 160 + 4 (Q % 40) + b % 4 (chunks of 4 b x 40 Q)
+      // ((Q/40) (nao/4) + b/4) 160 + 4 (Q % 40) + b % 4 (chunks of 4 b x 40 Q: one column half
+      // of an 80-wide tile)
       so_target(p, ys, 40, nao / 4);
       p.so_mdiv = nao;                      // m = j nao + b
       p.so_rm = 1;                          // row (t nk + k) nao + j
@@ -1500,6 +1515,7 @@ int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double
     p.a_row0 = (long long)t0 * nao;
     p.b_tab = tab(s, vo.tab, q);
     so_target(p, xs, 40, nao / 4);
+    p.so_xhalf = 1;
     p.so_mdiv = nao;                        // m = t nao + b
     p.so_ndiv = naux;                       // n = i naux + Q
     p.so_rm = (long long)nk * nao;          // row (t nk + k) nao + i
@@ -1507,7 +1523,8 @@ int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double
     p.so_row_bs_in = nao;
     p.status = s->status;
     p.ws = s->ws;
-    GW_TRY_INTERNAL(launch_oz(s->gf, *vo.P, p, SLOT_VG_MIXED, s->stream, 80));
+    // 40-wide tiles: two accumulator sets, so the next tile's MMAs overlap this one's slice output
+    GW_TRY_INTERNAL(launch_oz(s->gf, *vo.P, p, SLOT_VG_MIXED, s->stream, 40));
   } else {
     // Z^Q_{ib}(k,t) = sum_a V^{k,k-q}_ia(Q) G^{k-q}_ab(t) -> x64[t][k][Q][i][b]
     GW_TRY_INTERNAL(vg_gemm(s, T_VKKMQ, T_GKMQ, s->gf, q, t0, nt, false, s->x64));
