@@ -498,10 +498,11 @@ def run_ours(args, rank, world, local_rank):
     launches = gw.gw_launch_count(ctx) - launches0
     t_max = max_over_ranks(ms, dist)
 
-    # ---- end to end through the public API with host buffers (pinned): about a minute of steps
+    # ---- end to end through the public API with host buffers (pinned): about half a minute of
+    #      steps (at least one)
     G_host = torch.from_numpy(g).pin_memory()
     S_host = torch.empty(Sig.shape, dtype=Sig.dtype).pin_memory()
-    k_e2e = max(1, min(args.steps, int(np.ceil(60000.0 / max(t_max / args.steps, 1e-3)))))
+    k_e2e = max(1, min(args.steps, int(np.ceil(30000.0 / max(t_max / args.steps, 1e-3)))))
     barrier()
     torch.cuda.synchronize()
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
