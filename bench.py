@@ -626,8 +626,9 @@ def run_ours(args, rank, world, local_rank):
 
 def batched_measure(precision, n_systems=48, steps=3, max_streams=8, tune=True, seed=4):
     """Self-energy evaluations of n Gamma-only systems (nao uniform on {10..120}, naux = 4 nao,
-    80 tau nodes, beta = 100) per second: per-system loop, concurrent streams and one captured
-    graph, then the graph again after the per-system tuner."""
+    80 tau nodes, beta = 100) per second: per-system loop, concurrent streams, one captured
+    graph, the grouped inversion (eager and captured), then the two graph modes again after the
+    per-system tuner."""
     import torch
     from paper_2406_18479_gb300 import gw, inputs as I
     ws = I.batched_molecules(n_systems, seed)
@@ -658,14 +659,16 @@ def batched_measure(precision, n_systems=48, steps=3, max_streams=8, tune=True, 
     out = {"systems": n_systems, "precision": precision, "streams": max_streams, "steps": steps,
            "nao": [w.nao for w in ws], "tflop_per_batch": sum(job_flops(w) for w in ws) / 1e12}
     ms = {}
-    for m in ("serial", "streams", "graph"):
+    for m in ("serial", "streams", "graph", "grouped", "grouped_graph"):
         ms[m] = timed(m)
         print(f"  {m}: {ms[m]:.1f} ms per batch", file=sys.stderr, flush=True)
     if tune:
         t0 = time.perf_counter()
         out["tau_batches"] = b.autotune(G, S)
         out["tune_s"] = time.perf_counter() - t0
-        ms["graph_tuned"] = timed("graph")
+        for m in ("graph", "grouped_graph"):
+            ms[m + "_tuned"] = timed(m)
+            print(f"  {m}_tuned: {ms[m + '_tuned']:.1f} ms per batch", file=sys.stderr, flush=True)
     b.destroy()
     out["ms_per_batch"] = ms
     out["systems_per_s"] = {m: n_systems / (v / 1e3) for m, v in ms.items()}

@@ -512,7 +512,13 @@ int gw_checkpoint_read(const char* path, gw_config* cfg_out, double* mu, int* it
  *   GW_BATCH_STREAMS  all systems enqueued at once on their streams,
  *   GW_BATCH_GRAPH    the same work captured once into a CUDA graph and replayed as one
  *                     graph launch; recaptured when the G or Sigma pointers change (the
- *                     first call after creation or gw_batch_set_coulomb runs uncaptured).
+ *                     first call after creation or gw_batch_set_coulomb runs uncaptured),
+ *   GW_BATCH_GROUPED  every system's evaluation up to the aux Dyson equation (Eq.
+ *                     tilde_P_omega) on its stream, then the inversions of all systems'
+ *                     (I - P0(i Omega)) matrices as one persistent launch over the ragged list
+ *                     of matrices (two launches: n <= 430 and n > 430, largest first), then
+ *                     the rest of every evaluation on its stream,
+ *   GW_BATCH_GROUPED_GRAPH  the grouped work captured into a graph as GW_BATCH_GRAPH does.
  * Every mode computes, per system, exactly what gw_sigma_eval computes alone. Calls are
  * asynchronous: the batch starts after the work queued on cuda_stream and cuda_stream waits
  * for the batch. V, G and Sigma are caller-owned device arrays per system, laid out as for
@@ -520,7 +526,7 @@ int gw_checkpoint_read(const char* path, gw_config* cfg_out, double* mu, int* it
  * the call.
  */
 typedef struct gw_batch gw_batch;
-enum { GW_BATCH_SERIAL = 0, GW_BATCH_STREAMS = 1, GW_BATCH_GRAPH = 2 };
+enum { GW_BATCH_SERIAL = 0, GW_BATCH_STREAMS = 1, GW_BATCH_GRAPH = 2, GW_BATCH_GROUPED = 3, GW_BATCH_GROUPED_GRAPH = 4 };
 
 /*
  * GW_EINVAL for n outside 1..4096 or max_streams outside 1..64. Systems whose tau_chunk is 0

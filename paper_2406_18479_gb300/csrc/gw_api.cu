@@ -135,6 +135,7 @@ struct gw_ctx {
   int* mq_dev = nullptr;
   int* wlist = nullptr;                   // canonical (q, n) matrices of P~(i Omega), as q * nwb + n
   int* wlist_q = nullptr;                 // (q, n) matrices of a q range (gw_sigma_eval_q)
+  std::vector<int> wlist_host;            // host copy of wlist (the items of a grouped inversion)
   int nwlist = 0;
   int* status = nullptr;                  // device flags: [0] singular matrix
   double* maxdiff = nullptr;
@@ -408,8 +409,7 @@ int screened(gw_ctx* c, const double2* P0t, double2* Pt) {
 //
 // With a q range [q0, q1) only the q of the range are transformed and solved; a q whose -q lies
 // outside the range takes every frequency and tau node (its mirror partner is not computed).
-int screened_sym(gw_ctx* c, const double2* P0t, double2* Pt, int q0 = 0, int q1 = -1) {
-  if (q1 < 0) q1 = c->nk;
+int screened_sym_pre(gw_ctx* c, const double2* P0t, int q0, int q1, const int** list_out, int* nlist_out) {
   const long long n2 = c->naux2;
   const bool full = q0 == 0 && q1 == c->nk;
   for (int q = q0; q < q1; ++q) {
@@ -429,15 +429,28 @@ int screened_sym(gw_ctx* c, const double2* P0t, double2* Pt, int q0 = 0, int q1 
       return cuda_check("q-range frequency list");
     list = c->wlist_q;
   }
-  if (nlist > 0) {
-    GW_TRY(add_identity_fp64(c->Pw, c->naux, n2, nlist, -1.0, 1.0, c->stream, list));   // I - P0
-    GW_TRY(batched_inverse_fp64(c->Pw, c->naux, n2, nlist, c->status, c->stream, list));
-    GW_TRY(add_identity_fp64(c->Pw, c->naux, n2, nlist, 1.0, -1.0, c->stream, list));    // (I - P0)^-1 - I
-  }
+  if (nlist > 0) GW_TRY(add_identity_fp64(c->Pw, c->naux, n2, nlist, -1.0, 1.0, c->stream, list));   // I - P0
+  *list_out = list;
+  *nlist_out = nlist;
+  return GW_OK;
+}
+
+int screened_sym_post(gw_ctx* c, double2* Pt, int q0, int q1, const int* list, int nlist) {
+  const long long n2 = c->naux2;
+  if (nlist > 0) GW_TRY(add_identity_fp64(c->Pw, c->naux, n2, nlist, 1.0, -1.0, c->stream, list));   // (I - P0)^-1 - I
   GW_TRY(mirror_fill(c->Pw, c->nk, c->nwb, c->naux, c->mq_dev, c->stream, q0, q1));
   for (int q = q0; q < q1; ++q)
     GW_TRY(transform_q(c, 0, false, c->Pw, Pt, q, 0, canonical_end(c, q, c->ntau, q0, q1), n2));
   return mirror_fill(Pt, c->nk, c->ntau, c->naux, c->mq_dev, c->stream, q0, q1);
+}
+
+int screened_sym(gw_ctx* c, const double2* P0t, double2* Pt, int q0 = 0, int q1 = -1) {
+  if (q1 < 0) q1 = c->nk;
+  const int* list = nullptr;
+  int nlist = 0;
+  GW_TRY(screened_sym_pre(c, P0t, q0, q1, &list, &nlist));
+  if (nlist > 0) GW_TRY(batched_inverse_fp64(c->Pw, c->naux, c->naux2, nlist, c->status, c->stream, list));
+  return screened_sym_post(c, Pt, q0, q1, list, nlist);
 }
 
 }  // namespace
@@ -547,6 +560,7 @@ int ctx_build(gw_ctx* c, const gw_config* cfg) {
       for (int q = 0; q < nk; ++q)
         for (int n = 0; n < canonical_end(c, q, c->nwb); ++n) wl.push_back(q * c->nwb + n);
       c->nwlist = (int)wl.size();
+      c->wlist_host = wl;
       if ((rc = dev_alloc(c, &c->wlist, wl.size())) != GW_OK) break;
       upload(c, c->wlist, wl.data(), wl.size() * sizeof(int));
       // the (q, n) list of a q range (gw_sigma_eval_q): at most every (q, n)
@@ -789,6 +803,34 @@ int gw_sigma_eval(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* Sig_dev) {
   GW_TRY(screened_sym(ctx, ctx->P0t, ctx->Pt));
   return gw_self_energy(ctx, G_dev, reinterpret_cast<const gw_c128*>(ctx->Pt), Sig_dev);
 }
+
+}  // extern "C"
+
+namespace gwi {
+
+int sigma_eval_part(gw_ctx* ctx, const double2* G, double2* Sig, int part) {
+  if (part == 0) {
+    GW_TRY(gw_polarization(ctx, reinterpret_cast<const gw_c128*>(G), reinterpret_cast<gw_c128*>(ctx->P0t)));
+    ProfScope _ps(&ctx->prof);
+    const int* list = nullptr;
+    int nlist = 0;
+    return screened_sym_pre(ctx, ctx->P0t, 0, ctx->nk, &list, &nlist);
+  }
+  {
+    ProfScope _ps(&ctx->prof);
+    GW_TRY(screened_sym_post(ctx, ctx->Pt, 0, ctx->nk, ctx->wlist, ctx->nwlist));
+  }
+  return gw_self_energy(ctx, reinterpret_cast<const gw_c128*>(G), reinterpret_cast<const gw_c128*>(ctx->Pt),
+                        reinterpret_cast<gw_c128*>(Sig));
+}
+
+void inverse_items(gw_ctx* ctx, std::vector<GjItem>* items) {
+  for (int w : ctx->wlist_host) items->push_back(GjItem{ctx->Pw + (long long)w * ctx->naux2, ctx->naux, ctx->status});
+}
+
+}  // namespace gwi
+
+extern "C" {
 
 int gw_sigma_eval_q(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* Sig_dev, int q_begin, int q_end,
                     gw_c128* P0t_dev, gw_c128* Pt_dev) {

@@ -2,8 +2,14 @@
 // k-meshes of uneven size): one gw_ctx per system, the systems spread over a
 // few CUDA streams by predicted cost (longest first onto the least-loaded
 // stream), and the whole batch captured once into a CUDA graph whose branches
-// run concurrently; later evaluations are one graph launch. A per-system
-// serial loop and eager concurrent streams are kept for comparison.
+// run concurrently; later evaluations are one graph launch. In the grouped
+// modes the aux Dyson inversions of all systems (the FP64 stage whose one
+// launch per system fills few SMs: one block per canonical frequency) run as
+// one launch over the ragged list of every system's matrices (one block per
+// matrix, largest first), between the two halves of each system's
+// evaluation; a system whose aux basis exceeds the blocked kernel's limit
+// (800) keeps its own inversion and runs whole in the first half. A
+// per-system serial loop and eager concurrent streams are kept for comparison.
 //
 // Each system computes exactly what a lone gw_sigma_eval computes: the
 // branches share no memory and no kernel depends on timing.
@@ -39,6 +45,13 @@ struct gw_batch {
   cudaGraphExec_t exec = nullptr;
   std::vector<const gw_c128*> gG;
   std::vector<gw_c128*> gS;
+  int graph_grouped = 0;                 // the captured graph is of the grouped flow
+  // grouped inversion: items of every system, split by panel class (n <= 430, n > 430) so that each
+  // matrix gets the panel width of its lone inversion, largest first; in device memory
+  GjItem* items_dev[2] = {nullptr, nullptr};
+  int items_n[2] = {0, 0}, items_maxn[2] = {0, 0};
+  double items_flops[2] = {0.0, 0.0};
+  std::vector<char> whole;               // systems evaluated whole in the grouped flow (naux > 800)
 };
 
 namespace {
@@ -106,6 +119,47 @@ void fit_tau_batches(gw_batch* b, size_t budget) {
   }
 }
 
+void drop_items(gw_batch* b) {
+  for (int c = 0; c < 2; ++c) {
+    if (b->items_dev[c]) cudaFree(b->items_dev[c]);
+    b->items_dev[c] = nullptr;
+    b->items_n[c] = b->items_maxn[c] = 0;
+    b->items_flops[c] = 0.0;
+  }
+}
+
+// the inversion items of every context, by panel class and largest first
+int build_items(gw_batch* b) {
+  drop_items(b);
+  std::vector<GjItem> all;
+  b->whole.assign(b->n, 0);
+  for (int i = 0; i < b->n; ++i) {
+    if (b->cfg[i].naux > kGjBlockedMaxN8)
+      b->whole[i] = 1;
+    else
+      inverse_items(b->ctx[i], &all);
+  }
+  std::stable_sort(all.begin(), all.end(), [](const GjItem& x, const GjItem& y) { return x.n > y.n; });
+  std::vector<GjItem> cls[2];
+  for (const GjItem& it : all) cls[it.n > kGjBlockedMaxN16 ? 1 : 0].push_back(it);
+  for (int c = 0; c < 2; ++c) {
+    if (cls[c].empty()) continue;
+    if (cudaMalloc(reinterpret_cast<void**>(&b->items_dev[c]), cls[c].size() * sizeof(GjItem)) != cudaSuccess ||
+        cudaMemcpy(b->items_dev[c], cls[c].data(), cls[c].size() * sizeof(GjItem), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      drop_items(b);
+      return fail(GW_ENOMEM, "gw_batch: inversion item list");
+    }
+    b->items_n[c] = (int)cls[c].size();
+    for (const GjItem& it : cls[c]) {
+      b->items_maxn[c] = std::max(b->items_maxn[c], it.n);
+      b->items_flops[c] += 8.0 * (double)it.n * it.n * it.n;
+    }
+  }
+  return GW_OK;
+}
+
 void drop_graph(gw_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   b->exec = nullptr;
@@ -121,7 +175,7 @@ int create_contexts(gw_batch* b) {
     if (b->V[i]) GW_TRY_BATCH(gw_set_coulomb(b->ctx[i], b->V[i]));
   }
   drop_graph(b);
-  return GW_OK;
+  return build_items(b);
 }
 
 // every system on its stream, eager; the streams fork from and join into main
@@ -136,6 +190,41 @@ int enqueue_concurrent(gw_batch* b, const gw_c128* const* G, gw_c128* const* S) 
     if (cudaStreamWaitEvent(b->main, b->ev[1 + l], 0) != cudaSuccess) return fail(GW_ECUDA, "gw_batch: join wait");
   }
   return GW_OK;
+}
+
+int fork_lanes(gw_batch* b) {
+  if (cudaEventRecord(b->ev[0], b->main) != cudaSuccess) return fail(GW_ECUDA, "gw_batch: fork record");
+  for (cudaStream_t s : b->streams)
+    if (cudaStreamWaitEvent(s, b->ev[0], 0) != cudaSuccess) return fail(GW_ECUDA, "gw_batch: fork wait");
+  return GW_OK;
+}
+
+int join_lanes(gw_batch* b) {
+  for (size_t l = 0; l < b->streams.size(); ++l) {
+    if (cudaEventRecord(b->ev[1 + l], b->streams[l]) != cudaSuccess) return fail(GW_ECUDA, "gw_batch: join record");
+    if (cudaStreamWaitEvent(b->main, b->ev[1 + l], 0) != cudaSuccess) return fail(GW_ECUDA, "gw_batch: join wait");
+  }
+  return GW_OK;
+}
+
+// every system's first half on its stream; all aux Dyson inversions as one launch per panel class
+// on main; every system's second half on its stream
+int enqueue_grouped(gw_batch* b, const gw_c128* const* G, gw_c128* const* S) {
+  GW_TRY_BATCH(fork_lanes(b));
+  const std::vector<int> order = by_cost(b);
+  for (int i : order)
+    GW_TRY_BATCH(b->whole[i] ? gw_sigma_eval(b->ctx[i], G[i], S[i])
+                             : sigma_eval_part(b->ctx[i], reinterpret_cast<const double2*>(G[i]),
+                                               reinterpret_cast<double2*>(S[i]), 0));
+  GW_TRY_BATCH(join_lanes(b));
+  for (int c = 0; c < 2; ++c)
+    GW_TRY_BATCH(batched_inverse_group_fp64(b->items_dev[c], b->items_n[c], b->items_maxn[c], b->items_flops[c],
+                                            b->main));
+  GW_TRY_BATCH(fork_lanes(b));
+  for (int i : order)
+    if (!b->whole[i])
+      GW_TRY_BATCH(sigma_eval_part(b->ctx[i], reinterpret_cast<const double2*>(G[i]), reinterpret_cast<double2*>(S[i]), 1));
+  return join_lanes(b);
 }
 
 // one system after another, each waiting for the previous one
@@ -153,11 +242,11 @@ int enqueue_serial(gw_batch* b, const gw_c128* const* G, gw_c128* const* S) {
   return GW_OK;
 }
 
-int capture(gw_batch* b, const gw_c128* const* G, gw_c128* const* S) {
+int capture(gw_batch* b, const gw_c128* const* G, gw_c128* const* S, bool grouped) {
   drop_graph(b);
   if (cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     return fail(GW_ECUDA, "gw_batch: begin capture failed");
-  const int rc = enqueue_concurrent(b, G, S);
+  const int rc = grouped ? enqueue_grouped(b, G, S) : enqueue_concurrent(b, G, S);
   cudaGraph_t graph = nullptr;
   const cudaError_t e = cudaStreamEndCapture(b->main, &graph);
   if (rc != GW_OK) {
@@ -173,6 +262,7 @@ int capture(gw_batch* b, const gw_c128* const* G, gw_c128* const* S) {
   }
   b->gG.assign(G, G + b->n);
   b->gS.assign(S, S + b->n);
+  b->graph_grouped = grouped ? 1 : 0;
   return GW_OK;
 }
 
@@ -180,12 +270,13 @@ int capture(gw_batch* b, const gw_c128* const* G, gw_c128* const* S) {
 // The first evaluation after (re)creating the contexts runs uncaptured: one-time kernel
 // attribute and tensor-map setup happen outside the capture, and that call's results come
 // from it; the graph serves the calls that follow.
-int graph_eval(gw_batch* b, const gw_c128* const* G, gw_c128* const* S) {
-  const bool same = b->exec && std::equal(b->gG.begin(), b->gG.end(), G) && std::equal(b->gS.begin(), b->gS.end(), S);
+int graph_eval(gw_batch* b, const gw_c128* const* G, gw_c128* const* S, bool grouped) {
+  const bool same = b->exec && b->graph_grouped == (grouped ? 1 : 0) && std::equal(b->gG.begin(), b->gG.end(), G) &&
+                    std::equal(b->gS.begin(), b->gS.end(), S);
   if (!same) {
     const bool first = !b->exec;
-    if (first) GW_TRY_BATCH(enqueue_concurrent(b, G, S));
-    GW_TRY_BATCH(capture(b, G, S));
+    if (first) GW_TRY_BATCH(grouped ? enqueue_grouped(b, G, S) : enqueue_concurrent(b, G, S));
+    GW_TRY_BATCH(capture(b, G, S, grouped));
     if (first) return GW_OK;
   }
   if (cudaGraphLaunch(b->exec, b->main) != cudaSuccess) return fail(GW_ECUDA, "gw_batch: graph launch failed");
@@ -262,6 +353,7 @@ int gw_batch_destroy(gw_batch* b) {
     if (s) cudaStreamSynchronize(s);
   if (b->main) cudaStreamSynchronize(b->main);
   drop_graph(b);
+  drop_items(b);
   for (gw_ctx* c : b->ctx)
     if (c) gw_destroy(c);
   for (cudaEvent_t e : b->ev)
@@ -291,15 +383,17 @@ int gw_batch_set_coulomb(gw_batch* b, const gw_c128* const* V_dev) {
 int gw_batch_sigma_eval(gw_batch* b, const gw_c128* const* G_dev, gw_c128* const* Sig_dev, int mode) {
   if (!b || !G_dev || !Sig_dev) return fail(GW_EINVAL, "gw_batch_sigma_eval: null argument");
   if (!all_set(b, G_dev, Sig_dev)) return fail(GW_EINVAL, "gw_batch_sigma_eval: a system has no V, G or Sigma");
-  if (mode < GW_BATCH_SERIAL || mode > GW_BATCH_GRAPH)
+  if (mode < GW_BATCH_SERIAL || mode > GW_BATCH_GROUPED_GRAPH)
     return fail(GW_EINVAL, "gw_batch_sigma_eval: unknown mode %d", mode);
   GW_TRY_BATCH(fork_from_user(b, false));
   if (mode == GW_BATCH_SERIAL)
     GW_TRY_BATCH(enqueue_serial(b, G_dev, Sig_dev));
   else if (mode == GW_BATCH_STREAMS)
     GW_TRY_BATCH(enqueue_concurrent(b, G_dev, Sig_dev));
+  else if (mode == GW_BATCH_GROUPED)
+    GW_TRY_BATCH(enqueue_grouped(b, G_dev, Sig_dev));
   else
-    GW_TRY_BATCH(graph_eval(b, G_dev, Sig_dev));
+    GW_TRY_BATCH(graph_eval(b, G_dev, Sig_dev, mode == GW_BATCH_GROUPED_GRAPH));
   return join_to_user(b);
 }
 

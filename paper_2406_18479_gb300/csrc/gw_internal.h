@@ -97,6 +97,23 @@ int zgemm_fp64(const ZGemm& g, void* stream);
 int batched_inverse_fp64(double2* base, int n, long long stride, int nbatch, int* status_dev,
                          void* stream, const int* list = nullptr);
 
+// One matrix of a grouped inversion: its pointer (n x n, row-major), size and status word.
+// largest matrix the blocked Gauss-Jordan inversion takes with a 16-column panel and with an
+// 8-column panel (its shared-memory footprint); larger ones take the unblocked kernel
+constexpr int kGjBlockedMaxN16 = 430;
+constexpr int kGjBlockedMaxN8 = 800;
+struct GjItem {
+  double2* M;
+  int n;
+  int* status;
+};
+// Gauss-Jordan inversion of a ragged list of matrices (items in device memory, count of them,
+// the largest n at most 800) in one launch, one block per item in list order; flops for the
+// profile. The panel width follows max_n (16 up to 430, else 8), as batched_inverse_fp64's does
+// for one n, so a matrix gets bit for bit what a lone inversion of its size gives when both
+// take the same panel width.
+int batched_inverse_group_fp64(const GjItem* items_dev, int count, int max_n, double flops, void* stream);
+
 // Aux Dyson pieces: M <- I - M; and after inversion M <- M - I.
 int add_identity_fp64(double2* base, int n, long long stride, int nbatch, double scale_m,
                       double shift, void* stream, const int* list = nullptr);
@@ -147,6 +164,14 @@ int trace_fp64(const double2* gamma, const double2* S, int nk, int nao, double* 
 int add_fp64(const double2* a, const double2* b, double2* c, long long n, void* stream);
 int dot_re_fp64(const double2* x, const double2* y, long long n, double* partial_dev, double* out_dev, void* stream);
 int lincomb_fp64(const double2* const* v, const double* c, int m, double2* out, long long n, void* stream);
+
+// gw_sigma_eval in two parts around the aux Dyson inversions (for batches that invert the
+// matrices of many systems in one launch): part 0 is P0, the forward transforms and I - P0 of
+// the canonical (q, n); then the caller inverts the matrices inverse_items lists (in place, as
+// batched_inverse_fp64 does); part 1 is (I - P0)^{-1} - I, the mirror fills, the back transforms
+// and Sigma. Together they issue exactly the launches of gw_sigma_eval, in its order.
+int sigma_eval_part(gw_ctx* ctx, const double2* G, double2* Sig, int part);
+void inverse_items(gw_ctx* ctx, std::vector<GjItem>* items);
 
 // sizes, stream and mu of a context (for host code outside the file that defines gw_ctx)
 struct CtxInfo {

@@ -215,35 +215,47 @@ __global__ void __launch_bounds__(256) gj_inverse_kernel(double2* base, int n, l
 }
 
 // Blocked form of the same inversion (same pivots, same result up to rounding order), for
-// n <= kGjBlockedMaxN. Columns are taken in panels of kGjPanel: the panel (n x kGjPanel) is
+// n <= kGjBlockedMaxN[B]. Columns are taken in panels of B (16, or 8 for larger n, where two
+// 16-column panels no longer fit in shared memory): the panel (n x B) is
 // eliminated in shared memory with partial pivoting (explicit row swaps), written back, the
 // panel's row swaps are applied to the other columns, and those columns receive the panel's
-// effect as one rank-kGjPanel update,
+// effect as one rank-B update,
 //   A[i][c] <- (i in the panel's pivot rows ? 0 : A[i][c]) + sum_t P[i][t] A_old[k0 + t][c],
 // so the matrix is read and written once per panel instead of once per column. The column
 // swaps that undo the row interchanges are applied at the end through one permutation.
-constexpr int kGjPanel = 16;
-constexpr int kGjBlockedMaxN = 430;   // dynamic shared memory n * (2 * 16 * 16 + 16 + 8) bytes, plus the
-                                      // kernel's static shared memory, within 227 KB
+// The size limits (kGjBlockedMaxN16, kGjBlockedMaxN8) keep the dynamic shared memory,
+// n * (2 * B * 16 + 16 + 8) bytes, plus the kernel's static shared memory within 227 KB.
 
+template <int B>
 size_t gj_blocked_smem(int n) {
-  return (size_t)n * (2 * kGjPanel * sizeof(double2) + sizeof(double2) + 2 * sizeof(int));
+  return (size_t)n * (2 * B * sizeof(double2) + sizeof(double2) + 2 * sizeof(int));
 }
 
+// One matrix per block: matrix blockIdx.x of base (through list when given), or, with items,
+// the item blockIdx.x (its own pointer, size and status word: a ragged list of matrices from
+// several systems in one launch; the dynamic shared memory is sized for the largest).
+template <int B>
 __global__ void __launch_bounds__(256) gj_inverse_blocked_kernel(double2* base, int n, long long stride,
-                                                                 const int* list, int* status) {
-  constexpr int B = kGjPanel;
+                                                                 const int* list, int* status,
+                                                                 const GjItem* items) {
   extern __shared__ double2 sm[];
+  __shared__ double red_v[8];
+  __shared__ int red_i[8];
+  __shared__ int s_p, s_bad;
+  __shared__ double2 rowc[B];
+  double2* M;
+  if (items) {
+    M = items[blockIdx.x].M;
+    n = items[blockIdx.x].n;
+    status = items[blockIdx.x].status;
+  } else {
+    M = base + (long long)(list ? list[blockIdx.x] : (int)blockIdx.x) * stride;
+  }
   double2* P = sm;                         // [n][B]  panel
   double2* AK = P + (size_t)n * B;         // [B][n]  pivot rows at the panel start; staging at the end
   double2* fcol = AK + (size_t)n * B;      // [n]     pivot column of one step
   int* swp = reinterpret_cast<int*>(fcol + n);   // [n] row swapped with row c at step c
   int* pi = swp + n;                       // [n]     final column permutation
-  __shared__ double red_v[8];
-  __shared__ int red_i[8];
-  __shared__ int s_p, s_bad;
-  __shared__ double2 rowc[B];
-  double2* M = base + (long long)(list ? list[blockIdx.x] : (int)blockIdx.x) * stride;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) s_bad = 0;
   __syncthreads();
@@ -778,25 +790,41 @@ int zgemm_fp64(const ZGemm& g, void* stream) {
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "zgemm_fp64 launch: %s", cudaGetErrorString(e));
 }
 
+namespace {
+template <int B>
+bool gj_blocked_attr() {
+  static const bool ok = [] {
+    const int maxn = B == 16 ? kGjBlockedMaxN16 : kGjBlockedMaxN8;
+    const bool r = cudaFuncSetAttribute(gj_inverse_blocked_kernel<B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)gj_blocked_smem<B>(maxn)) == cudaSuccess;
+    cudaGetLastError();
+    return r;
+  }();
+  return ok;
+}
+
+template <int B>
+int launch_gj_blocked(double2* base, int n, long long stride, int nblocks, int* status_dev, cudaStream_t st,
+                      const int* list, const GjItem* items, double flops, double bytes) {
+  if (!gj_blocked_attr<B>()) return fail(GW_ECUDA, "gj_inverse_blocked: shared memory attribute refused");
+  prof_begin(SLOT_INVERSE_FP64, st);
+  gj_inverse_blocked_kernel<B><<<nblocks, 256, gj_blocked_smem<B>(n), st>>>(base, n, stride, list, status_dev, items);
+  prof_end(SLOT_INVERSE_FP64, st, flops, bytes);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "gj_inverse_blocked launch: %s", cudaGetErrorString(e));
+}
+}  // namespace
+
 int batched_inverse_fp64(double2* base, int n, long long stride, int nbatch, int* status_dev,
                          void* stream, const int* list) {
   if (nbatch <= 0) return GW_OK;
-  if (n <= kGjBlockedMaxN) {
-    static const bool blocked_attr = [] {
-      const bool ok = cudaFuncSetAttribute(gj_inverse_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)gj_blocked_smem(kGjBlockedMaxN)) == cudaSuccess;
-      cudaGetLastError();
-      return ok;
-    }();
-    if (!blocked_attr) return fail(GW_ECUDA, "gj_inverse_blocked: shared memory attribute refused");
-    prof_begin(SLOT_INVERSE_FP64, (cudaStream_t)stream);
-    gj_inverse_blocked_kernel<<<nbatch, 256, gj_blocked_smem(n), (cudaStream_t)stream>>>(base, n, stride, list,
-                                                                                         status_dev);
-    prof_end(SLOT_INVERSE_FP64, (cudaStream_t)stream, 8.0 * (double)n * n * n * nbatch,
-             32.0 * (double)n * n * nbatch);
-    const cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "gj_inverse_blocked launch: %s", cudaGetErrorString(e));
-  }
+  const double flops = 8.0 * (double)n * n * n * nbatch, bytes = 32.0 * (double)n * n * nbatch;
+  if (n <= kGjBlockedMaxN16)
+    return launch_gj_blocked<16>(base, n, stride, nbatch, status_dev, (cudaStream_t)stream, list, nullptr, flops,
+                                 bytes);
+  if (n <= kGjBlockedMaxN8)
+    return launch_gj_blocked<8>(base, n, stride, nbatch, status_dev, (cudaStream_t)stream, list, nullptr, flops,
+                                bytes);
   const size_t smem = 2 * (size_t)n * sizeof(double2) + (size_t)n * sizeof(int);
   if (smem > 200 * 1024) return fail(GW_EINVAL, "batched_inverse_fp64: n=%d too large", n);
   static const bool attr_set = [] {   // once, also when several threads launch
@@ -1003,6 +1031,21 @@ int lincomb_fp64(const double2* const* v, const double* c, int m, double2* out, 
   prof_end(SLOT_ELEMENTWISE, (cudaStream_t)stream, 4.0 * n * m, 16.0 * n * (m + 1));
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GW_OK : fail(GW_ECUDA, "lincomb launch: %s", cudaGetErrorString(e));
+}
+
+}  // namespace gwi
+
+namespace gwi {
+
+int batched_inverse_group_fp64(const GjItem* items_dev, int count, int max_n, double flops, void* stream) {
+  if (count <= 0) return GW_OK;
+  if (max_n > kGjBlockedMaxN8) return fail(GW_EINVAL, "batched_inverse_group_fp64: n = %d above %d", max_n, kGjBlockedMaxN8);
+  const double bytes = 32.0 * (double)max_n * max_n * count;
+  if (max_n <= kGjBlockedMaxN16)
+    return launch_gj_blocked<16>(nullptr, max_n, 0, count, nullptr, (cudaStream_t)stream, nullptr, items_dev, flops,
+                                 bytes);
+  return launch_gj_blocked<8>(nullptr, max_n, 0, count, nullptr, (cudaStream_t)stream, nullptr, items_dev, flops,
+                              bytes);
 }
 
 }  // namespace gwi

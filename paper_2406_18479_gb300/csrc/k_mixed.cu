@@ -644,6 +644,14 @@ __global__ void __launch_bounds__(352, 1)
     const int quarter = warp & 3;
     const int half = (warp - 2) >> 2;
     constexpr int kCols = BN / 2;
+    static_assert(kCols % 4 == 0, "the chunk merge takes columns in groups of 4");
+    constexpr int kNG4 = kCols / 4;
+    // groups whose running sum stays in registers; the rest go through the per-CTA scratch. At the
+    // 168-register limit of 352 threads more groups spill: 3 (48 registers) where the kernel has
+    // no slice output, 2 for the wide slice-output tiles, none for the narrow ones (the V.G
+    // products, whose one-chunk path slows down with any more live registers)
+    constexpr int kRGWant = !SO ? 3 : (BN >= 72 ? 2 : 0);
+    constexpr int kRG = kNG4 < kRGWant ? kNG4 : kRGWant;
     const int lrow = quarter * 32 + lane;            // TMEM lane = row within the tile
     // per-CTA scratch, column-major so that a warp's 32 rows of one column are contiguous:
     // ws holds the running sum, cw the newest chunk value
@@ -777,6 +785,8 @@ __global__ void __launch_bounds__(352, 1)
         }
         __syncwarp();
       };
+      // running sums of the first kRG groups of 4 columns of this warp (chunked contractions)
+      float4 rs[kRG > 0 ? kRG : 1][4];
       for (int c = 0; c < nchunks; ++c, ++chunk) {
         const uint32_t buf = chunk % S::kBufs;
         if (!mbar_wait(&acc_full[buf], (chunk / S::kBufs) & 1, abort_flag, p.status, 14)) { ok = false; break; }
@@ -837,54 +847,113 @@ __global__ void __launch_bounds__(352, 1)
           if (lane == 0) mbar_arrive(&acc_empty[buf]);
           continue;
         }
-        // ---- drain: TMEM -> chunk value (an exact FP32 pair per part) -> output or scratch
-#pragma unroll 1
-        for (int g = 0; g < kCols / G; ++g) {
-          const int cb = half * kCols + g * G;
-          float v[3][2][G];                           // [order][im, re][column]
-          const uint32_t taddr = tbase + (uint32_t)cb;
-#pragma unroll
-          for (int o = 0; o < 3; ++o) {
-            tmem_ldg<G>(taddr + o * S::kOrderCols, v[o][0]);
-            tmem_ldg<G>(taddr + o * S::kOrderCols + BN, v[o][1]);
-          }
-          tmem_wait_ld();
-          if (g == kCols / G - 1) {
-            // this warp's accumulator columns are in registers: release TMEM
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[buf]);
-          }
-#pragma unroll
-          for (int u = 0; u < G; ++u) {
-            const int cl = cb + u;
-            if (!col_ok(cl)) continue;
-            // orders 0 and 1 are exact, so their sum is exact as a pair
-            float rh, rl, ih, il;
-            two_sum(v[0][1][u], v[1][1][u], rh, rl);
-            rl = __fadd_rn(rl, v[2][1][u]);
-            two_sum(v[0][0][u], v[1][0][u], ih, il);
-            il = __fadd_rn(il, v[2][0][u]);
-            if (single) out_write(cl, rh, rl, ih, il);
-            else (c == 0 ? ws : cw)[(size_t)cl * kBM] = make_float4(rh, rl, ih, il);
-          }
-        }
-        // ---- merge into the running sum (overlaps the next chunk's MMAs)
-        if (!single && c > 0) {
-          const bool last = c == nchunks - 1;
+        if (single) {
+          // ---- one-chunk contraction: TMEM -> value (an exact FP32 pair per part) -> output
 #pragma unroll 1
           for (int g = 0; g < kCols / G; ++g) {
             const int cb = half * kCols + g * G;
-            float4 a[G], x[G];
+            float v[3][2][G];                         // [order][im, re][column]
+            const uint32_t taddr = tbase + (uint32_t)cb;
+#pragma unroll
+            for (int o = 0; o < 3; ++o) {
+              tmem_ldg<G>(taddr + o * S::kOrderCols, v[o][0]);
+              tmem_ldg<G>(taddr + o * S::kOrderCols + BN, v[o][1]);
+            }
+            tmem_wait_ld();
+            if (g == kCols / G - 1) {
+              // this warp's accumulator columns are in registers: release TMEM
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&acc_empty[buf]);
+            }
 #pragma unroll
             for (int u = 0; u < G; ++u) {
+              const int cl = cb + u;
+              if (!col_ok(cl)) continue;
+              // orders 0 and 1 are exact, so their sum is exact as a pair
+              float rh, rl, ih, il;
+              two_sum(v[0][1][u], v[1][1][u], rh, rl);
+              rl = __fadd_rn(rl, v[2][1][u]);
+              two_sum(v[0][0][u], v[1][0][u], ih, il);
+              il = __fadd_rn(il, v[2][0][u]);
+              out_write(cl, rh, rl, ih, il);
+            }
+          }
+          continue;
+        }
+        const bool last = c == nchunks - 1;
+        // chunk value of one column (an exact FP32 pair per part: orders 0 and 1 are exact)
+        auto chunk_value = [](const float (&v)[3][2][4], int u) {
+          float rh, rl, ih, il;
+          two_sum(v[0][1][u], v[1][1][u], rh, rl);
+          rl = __fadd_rn(rl, v[2][1][u]);
+          two_sum(v[0][0][u], v[1][0][u], ih, il);
+          il = __fadd_rn(il, v[2][0][u]);
+          return make_float4(rh, rl, ih, il);
+        };
+        auto tmem_group = [&](int cb, float (&v)[3][2][4]) {
+          const uint32_t taddr = tbase + (uint32_t)cb;
+#pragma unroll
+          for (int o = 0; o < 3; ++o) {
+            tmem_ld4(taddr + o * S::kOrderCols, v[o][0]);
+            tmem_ld4(taddr + o * S::kOrderCols + BN, v[o][1]);
+          }
+          tmem_wait_ld();
+        };
+        auto release = [&]() {                        // this warp's columns are out of TMEM
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        };
+        // ---- resident columns: the running sum stays in registers from chunk to chunk
+#pragma unroll
+        for (int g = 0; g < kRG; ++g) {
+          const int cb = half * kCols + 4 * g;
+          float v[3][2][4];
+          tmem_group(cb, v);
+          if (g == kNG4 - 1) release();
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4 x = chunk_value(v, u);
+            float4& a = rs[g][u];
+            if (c == 0) {
+              a = x;
+            } else {
+              df_add(a.x, a.y, x.x, x.y);
+              df_add(a.z, a.w, x.z, x.w);
+            }
+            if (last && col_ok(cb + u)) {
+              if (SO) so_mx = max(so_mx, max(__float_as_uint(a.x) & 0x7FFFFFFFu, __float_as_uint(a.z) & 0x7FFFFFFFu));
+              out_write(cb + u, a.x, a.y, a.z, a.w);
+            }
+          }
+        }
+        // ---- the other columns: chunk value to the per-CTA scratch, then TMEM is released
+#pragma unroll 1
+        for (int g = kRG; g < kNG4; ++g) {
+          const int cb = half * kCols + 4 * g;
+          float v[3][2][4];
+          tmem_group(cb, v);
+          if (g == kNG4 - 1) release();
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (col_ok(cb + u)) (c == 0 ? ws : cw)[(size_t)(cb + u) * kBM] = chunk_value(v, u);
+        }
+        // ---- and merged into their running sum there (overlaps the next chunk's MMAs)
+        if (c > 0) {
+#pragma unroll 1
+          for (int g = kRG; g < kNG4; ++g) {
+            const int cb = half * kCols + 4 * g;
+            float4 a[4], x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
               if (col_ok(cb + u)) {
                 a[u] = ws[(size_t)(cb + u) * kBM];
                 x[u] = cw[(size_t)(cb + u) * kBM];
               }
             }
 #pragma unroll
-            for (int u = 0; u < G; ++u) {
+            for (int u = 0; u < 4; ++u) {
               const int cl = cb + u;
               if (!col_ok(cl)) continue;
               df_add(a[u].x, a[u].y, x[u].x, x[u].y);

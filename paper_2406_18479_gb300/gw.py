@@ -36,8 +36,9 @@ ABI_SYMBOLS = [
     "gw_diis_destroy", "gw_diis_push", "gw_diis_extrapolate", "gw_scgw_bytes", "gw_scgw", "gw_diis_push_residual",
     "gw_commutator_residual", "gw_gf2_self_energy", "gw_gf2_exchange", "gw_k_interpolate", "gw_ir_grids", "gw_set_overlap", "gw_checkpoint_write", "gw_checkpoint_read", "gw_selftest_bounded_wait", "gw_check_guards", "gw_debug_mark_guard",
 ]
-GW_BATCH_SERIAL, GW_BATCH_STREAMS, GW_BATCH_GRAPH = 0, 1, 2
-BATCH_MODES = {"serial": GW_BATCH_SERIAL, "streams": GW_BATCH_STREAMS, "graph": GW_BATCH_GRAPH}
+GW_BATCH_SERIAL, GW_BATCH_STREAMS, GW_BATCH_GRAPH, GW_BATCH_GROUPED, GW_BATCH_GROUPED_GRAPH = 0, 1, 2, 3, 4
+BATCH_MODES = {"serial": GW_BATCH_SERIAL, "streams": GW_BATCH_STREAMS, "graph": GW_BATCH_GRAPH,
+               "grouped": GW_BATCH_GROUPED, "grouped_graph": GW_BATCH_GROUPED_GRAPH}
 
 
 class GWError(RuntimeError):

@@ -1,6 +1,7 @@
 """Batched evaluation of independent systems (gw_batch_*): every mode (per-system loop,
-concurrent streams, captured graph) gives, per system, the oracle's self-energy and
-exactly what a lone gw_sigma_eval gives; graph replays and the tuner keep that."""
+concurrent streams, captured graph, grouped inversion eager and captured) gives, per system,
+the oracle's self-energy and exactly what a lone gw_sigma_eval gives; graph replays and the
+tuner keep that."""
 import ctypes
 
 import numpy as np
@@ -67,7 +68,8 @@ def test_batch_modes_match_oracle_and_lone_runs(systems, precision, tol):
     G = [torch.from_numpy(g).cuda() for _, _, g, _ in systems]
     results = {}
     S = out_buffers(systems, float("nan"))
-    for mode in ("serial", "streams", "graph", "graph"):      # the second graph call replays
+    # the second call of each graph mode replays its capture
+    for mode in ("serial", "streams", "graph", "graph", "grouped", "grouped_graph", "grouped_graph"):
         for s in S:
             s.fill_(float("nan"))
         b.sigma_eval(G, S, mode)
@@ -112,4 +114,31 @@ def test_autotune_keeps_results(systems):
     b.synchronize()
     for s, (w, v, g, ref) in zip(S, systems):
         assert rel(s.cpu().numpy(), ref) < 1e-7
+    b.destroy()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", ["fp64", "bf16x4"])
+def test_grouped_inversion_spans_both_panel_widths(precision):
+    """A batch whose aux bases straddle 430 (the widest matrix of the 16-column panel): the
+    grouped modes invert both size classes in their own launches and still give, bit for bit,
+    what lone evaluations give."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ws = [I.molecule("small", 6, ntau=8, beta=20.0, seed=70),
+          I.molecule("naux440", 110, ntau=8, beta=20.0, seed=71),
+          I.molecule("naux432", 108, ntau=8, beta=20.0, seed=72),
+          I.molecule("naux428", 107, ntau=8, beta=20.0, seed=73)]
+    data = [I.make_inputs(w)[1:] for w in ws]
+    cfgs = [gw.make_config(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision=precision) for w in ws]
+    b = gw.gw_batch(cfgs, max_streams=3)
+    b.set_coulomb([torch.from_numpy(v).cuda() for v, _ in data])
+    G = [torch.from_numpy(g).cuda() for _, g in data]
+    lone = [alone(w, v, g, precision) for w, (v, g) in zip(ws, data)]
+    for mode in ("grouped", "grouped_graph", "grouped_graph"):
+        S = out_buffers([(w,) for w in ws], float("nan"))
+        b.sigma_eval(G, S, mode)
+        b.synchronize()
+        for i, s in enumerate(S):
+            assert np.array_equal(s.cpu().numpy(), lone[i]), (mode, ws[i].name)
     b.destroy()
