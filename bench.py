@@ -12,7 +12,7 @@ The Si-like 3x3x3 solid (nk=27, nao=26, naux=200) runs with
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x4|fp64]
     python bench.py --impl reference      # the FP64 CPU oracle on a bounded sample
     python bench.py --serving [--serving-jobs N] [--precision P]   # scGW job stream alone
-    python bench.py --batched [--precision P] [--steps K]          # 48 molecules: loop vs graph
+    python bench.py --batched [--precision P] [--steps K]          # 48 molecules: every batch mode
 
 Under torchrun (N > 1) every rank evaluates its own seeded system (weak
 scaling, no collective on the data path); the time is the maximum over ranks.
@@ -614,6 +614,11 @@ def run_ours(args, rank, world, local_rank):
         line["fp64"] = fp64
     if serving is not None:
         line["serving"] = serving
+    if world == 1 and args.batched_default:
+        # the 48-molecule batch: per-system loop against concurrent streams and the captured grouped
+        # flow (one step each; bench.py --batched times every mode and the tuner)
+        line["batched"] = batched_measure(args.precision, steps=1, max_streams=args.batch_streams, tune=False,
+                                          modes=("serial", "streams", "grouped_graph"))
     if keep_v:
         with CpuMeter() as cpu:
             val, sample, spent = oracle_sample(w, h, v, g, budget_s=args.ref_budget)
@@ -624,7 +629,8 @@ def run_ours(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
-def batched_measure(precision, n_systems=48, steps=3, max_streams=8, tune=True, seed=4):
+def batched_measure(precision, n_systems=48, steps=3, max_streams=8, tune=True, seed=4,
+                    modes=("serial", "streams", "graph", "grouped", "grouped_graph")):
     """Self-energy evaluations of n Gamma-only systems (nao uniform on {10..120}, naux = 4 nao,
     80 tau nodes, beta = 100) per second: per-system loop, concurrent streams, one captured
     graph, the grouped inversion (eager and captured), then the two graph modes again after the
@@ -659,7 +665,7 @@ def batched_measure(precision, n_systems=48, steps=3, max_streams=8, tune=True, 
     out = {"systems": n_systems, "precision": precision, "streams": max_streams, "steps": steps,
            "nao": [w.nao for w in ws], "tflop_per_batch": sum(job_flops(w) for w in ws) / 1e12}
     ms = {}
-    for m in ("serial", "streams", "graph", "grouped", "grouped_graph"):
+    for m in modes:
         ms[m] = timed(m)
         print(f"  {m}: {ms[m]:.1f} ms per batch", file=sys.stderr, flush=True)
     if tune:
@@ -876,6 +882,8 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="measure only the 48-molecule batch (loop vs streams vs graph) and print its own line")
     ap.add_argument("--batch-streams", type=int, default=8)
+    ap.add_argument("--no-batched", dest="batched_default", action="store_false",
+                    help="leave the 48-molecule batch out of the default line")
     ap.add_argument("--v-packed", action="store_true",
                     help="pass V packed (pairs k1 <= k2 only) to the library")
     ap.add_argument("--ir-lambda", type=float, default=0.0,

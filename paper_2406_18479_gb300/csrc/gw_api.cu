@@ -584,8 +584,10 @@ int ctx_build(gw_ctx* c, const gw_config* cfg) {
     if ((rc = dev_alloc(c, &c->gamma, (size_t)nk * c->nao2)) != GW_OK) break;
     if ((rc = dev_alloc(c, &c->rho, (size_t)c->naux)) != GW_OK) break;
     // exchange partials of the fused kernel, or the per-k intermediate of the GEMM path (nao above its limit)
+    // (plus, with only the packed V resident, room for the two unpacked blocks V^{kk'} and V^{k'k})
+    const bool unpack_exchange = cfg->v_packed && cfg->precision != GW_FP64;
     const size_t nxinf = c->nao <= kExchangeMaxNao ? (size_t)nk * nk * exchange_chunks(nk, c->naux) * c->nao2
-                                                   : (size_t)nk * c->pair;
+                                                   : (size_t)(unpack_exchange ? nk + 2 : nk) * c->pair;
     if ((rc = dev_alloc(c, &c->xinf, nxinf)) != GW_OK) break;
     if ((rc = dev_alloc(c, &c->scal, (size_t)kDotBlocks + 8)) != GW_OK) break;
     if ((rc = dev_alloc(c, &c->gw_w, (size_t)nk * c->nwf * c->nao2)) != GW_OK) break;
@@ -898,51 +900,73 @@ int gw_sigma_inf(gw_ctx* ctx, const gw_c128* G_dev, gw_c128* SigInf_dev) {
   // exchange: -(1 / N_k) sum_{k'} sum_{Q b} X^{k'}_{Q i b} V^{k'k}_bj(Q), X^{k'}_{Q i b} = sum_a V^{kk'}_ia(Q) gamma^{k'}_ab
   if (nao <= kExchangeMaxNao)
     return exchange_fp64(Vs, ctx->gamma, ctx->xinf, S, nk, naux, nao, -1.0 / nk, packed, ctx->stream);
-  if (packed)
-    return fail(GW_ENOTIMPL, "gw_sigma_inf: nao above %d with a packed V needs FP64 precision", kExchangeMaxNao);
-  for (int k = 0; k < nk; ++k) {
+  // per k: X^{k'} = V^{kk'} gamma^{k'} for every k' (one batched product), then S^k -= X^{k'} V^{k'k}
+  // summed over k' in order. With only the packed V resident, V^{kk'} and V^{k'k} are unpacked
+  // into two scratch blocks per (k, k') and the first product runs one k' at a time (the same
+  // arithmetic per element as the batched product).
+  double2* vx = ctx->xinf + (long long)nk * ctx->pair;
+  auto first = [&](const double2* A, long long a_stride, const double2* B, double2* C, int nbatch) {
     ZGemm a;
     a.M = naux * nao;
     a.N = nao;
     a.K = nao;
-    a.nbatch = nk;
-    a.A = ctx->V + (long long)k * nk * ctx->pair;
-    a.ba.bs_in = ctx->pair;
+    a.nbatch = nbatch;
+    a.A = A;
+    a.ba.bs_in = a_stride;
     a.va.rs_in = nao;
     a.va.ks_in = 1;
-    a.B = ctx->gamma;
+    a.B = B;
     a.bb.bs_in = ctx->nao2;
     a.vb.rs_in = 1;
     a.vb.ks_in = nao;
-    a.C = ctx->xinf;
+    a.C = C;
     a.bc.bs_in = ctx->pair;
     a.vc.rs_in = nao;
     a.vc.ks_in = 1;
     a.slot = SLOT_STATIC_FP64;
-    GW_TRY(zgemm_fp64(a, ctx->stream));
-    for (int kp = 0; kp < nk; ++kp) {
-      ZGemm b;
-      b.M = nao;
-      b.N = nao;
-      b.K = naux * nao;
-      b.A = ctx->xinf + (long long)kp * ctx->pair;
-      b.va.rs_in = nao;
-      b.va.kin = nao;
-      b.va.ks_in = 1;
-      b.va.ks_out = ctx->nao2;
-      b.B = ctx->V + ((long long)kp * nk + k) * ctx->pair;
-      b.vb.rs_in = 1;
-      b.vb.kin = nao;
-      b.vb.ks_in = nao;
-      b.vb.ks_out = ctx->nao2;
-      b.C = S + (long long)k * ctx->nao2;
-      b.vc.rs_in = nao;
-      b.vc.ks_in = 1;
-      b.alpha = -1.0 / nk;
-      b.accumulate = 1;
-      b.slot = SLOT_STATIC_FP64;
-      GW_TRY(zgemm_fp64(b, ctx->stream));
-    }
+    return zgemm_fp64(a, ctx->stream);
+  };
+  auto second = [&](const double2* X, const double2* Vb, int k) {
+    ZGemm b;
+    b.M = nao;
+    b.N = nao;
+    b.K = naux * nao;
+    b.A = X;
+    b.va.rs_in = nao;
+    b.va.kin = nao;
+    b.va.ks_in = 1;
+    b.va.ks_out = ctx->nao2;
+    b.B = Vb;
+    b.vb.rs_in = 1;
+    b.vb.kin = nao;
+    b.vb.ks_in = nao;
+    b.vb.ks_out = ctx->nao2;
+    b.C = S + (long long)k * ctx->nao2;
+    b.vc.rs_in = nao;
+    b.vc.ks_in = 1;
+    b.alpha = -1.0 / nk;
+    b.accumulate = 1;
+    b.slot = SLOT_STATIC_FP64;
+    return zgemm_fp64(b, ctx->stream);
+  };
+  if (packed) {
+    for (int k = 0; k < nk; ++k)
+      for (int kp = 0; kp < nk; ++kp) {
+        VPairs L;
+        L.k1[0] = k;
+        L.k2[0] = kp;
+        L.k1[1] = kp;
+        L.k2[1] = k;
+        GW_TRY(unpack_v_fp64(ctx->Vp, nk, nao, ctx->pair, L, 2, vx, ctx->stream));
+        GW_TRY(first(vx, 0, ctx->gamma + (long long)kp * ctx->nao2, ctx->xinf, 1));
+        GW_TRY(second(ctx->xinf, vx + ctx->pair, k));
+      }
+    return GW_OK;
+  }
+  for (int k = 0; k < nk; ++k) {
+    GW_TRY(first(ctx->V + (long long)k * nk * ctx->pair, ctx->pair, ctx->gamma, ctx->xinf, nk));
+    for (int kp = 0; kp < nk; ++kp)
+      GW_TRY(second(ctx->xinf + (long long)kp * ctx->pair, ctx->V + ((long long)kp * nk + k) * ctx->pair, k));
   }
   return GW_OK;
 }

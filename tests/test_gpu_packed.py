@@ -66,6 +66,25 @@ def test_sigma_eval_and_static_part(G, prec, v_slices, nk3):
     packed.destroy()
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16x4"])
+def test_static_part_above_the_fused_exchange_limit(G, prec):
+    """nao = 56 is above the fused exchange kernel's limit (52): the exchange takes the GEMM path,
+    which with only the packed V resident unpacks V^{kk'} and V^{k'k} per (k, k')."""
+    w, h, v, g = case((2, 1, 1), 56, 8, 4, 5)
+    full, packed = pair_of_contexts(G, w, precision=prec)
+    G.gw_set_coulomb(full, dev(v))
+    G.gw_set_coulomb(packed, dev(I.pack_v(v)))
+    gd = dev(g)
+    i1 = torch.empty((w.nk, w.nao, w.nao), dtype=torch.complex128, device="cuda")
+    i2 = torch.empty_like(i1)
+    G.gw_sigma_inf(full, gd, i1)
+    G.gw_sigma_inf(packed, gd, i2)
+    torch.cuda.synchronize()
+    assert torch.equal(i1, i2)
+    full.destroy()
+    packed.destroy()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
 def test_gf2(G, prec):
     w, h, v, g = case((2, 1, 1), 4, 6, 4, 5)
