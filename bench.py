@@ -900,7 +900,16 @@ def main():
     if args.precision is None or args.precision == "bf16x3":
         args.precision = "bf16x4"
     if args.steps is None:
-        args.steps = 2 if args.precision == "fp64" else (3 if (args.batched or args.loop or args.gf2) else 10)
+        if args.precision == "fp64":
+            args.steps = 2
+        elif args.batched or args.loop or args.gf2:
+            args.steps = 3
+        else:
+            # about a minute of timed work: 2 steps of a 4x4x4 solid (~43 s each), 10 of smaller ones
+            from paper_2406_18479_gb300 import inputs as I
+            w = I.WORKLOADS.get(args.workload)
+            big = w is not None and sum(stage_flops(w.nk3, w.nao, w.naux, w.ntau).values()) > 1e15
+            args.steps = 2 if big else 10
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
