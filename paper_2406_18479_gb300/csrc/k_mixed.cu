@@ -116,17 +116,24 @@ __device__ __forceinline__ long long fixed31_f64(unsigned long long bits, int E)
 }
 
 // Slices of the double-float value h + l (|h + l| < 2^E): s_i, a multiple of q_i with
-// |s_i| <= 128 q_i, for i = 0..3 (magic[i] = 1.5 * 2^23 * q_i).
+// |s_i| <= 128 q_i, for i = 0..3 (magic[i] = 1.5 * 2^23 * q_i; q_i = 2^(E-7-8i)).
+// The pair is normalised once (an exact two-sum: the epilogue's pairs are not normalised, l
+// holding the order 2-3 sum), after which |l| <= 2^(E-25). s_0 and s_1 are cut from h (each
+// remainder exact, |h| <= q_1 / 2 = 2^(E-16) after s_1); l joins before s_2, the one rounding
+// on the way (at most 2^(E-40), far below q_3 = 2^(E-31)); |remainder| <= q_2 / 2 = 128 q_3
+// before s_3. Residual: q_3 / 2 plus that rounding.
 __device__ __forceinline__ void df_slices(float h, float l, const float magic[4], float s[4]) {
+  {
+    const float t = __fadd_rn(h, l);
+    const float hv = __fsub_rn(t, l);
+    l = __fadd_rn(__fsub_rn(h, hv), __fsub_rn(l, __fsub_rn(t, hv)));
+    h = t;
+  }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
+    if (i == 2) h = __fadd_rn(h, l);
     s[i] = __fsub_rn(__fadd_rn(h, magic[i]), magic[i]);   // h rounded to a multiple of q_i
-    h = __fsub_rn(h, s[i]);                               // exact
-    // renormalise; the epilogue's pairs are not normalised (l holds the order 2-3 sum, up to
-    // 2^-16 of the chunk maximum), so t may round, by at most 2^(E-39), far below q_3 = 2^(E-31)
-    const float t = __fadd_rn(h, l);
-    l = __fsub_rn(l, __fsub_rn(t, h));
-    h = t;
+    if (i < 3) h = __fsub_rn(h, s[i]);                    // exact
   }
 }
 
@@ -288,6 +295,7 @@ struct OzParams {
   __nv_bfloat16* so_dst = nullptr;
   long long so_rows = 0;
   int so_ksteps = 0, so_cb = 0, so_ch_cb = 0, so_mdiv = 1, so_ndiv = 1 << 30;
+  FastDiv so_ndivf, so_cbf;            // so_ndiv and so_cb as multiply-high divisors (set at launch)
   long long so_rm = 0, so_rn = 0, so_row_bs_in = 0, so_row_bs_out = 0, so_ch_bs_in = 0, so_ch_bs_out = 0;
 };
 
@@ -710,6 +718,10 @@ __global__ void __launch_bounds__(352, 1)
       //      |hi| of its re and im parts, as in slice_kernel.
       const int m_so = mt * kBM + lrow;               // producer row within the batch
       const bool mok = m_so < p.M;
+      // the row's part of the consumer position (the column part varies per 4-column group)
+      const int so_mhi = SO ? m_so / p.so_mdiv : 0, so_mlo = m_so - so_mhi * p.so_mdiv;
+      const long long so_row0 = bo * p.so_row_bs_out + bi * p.so_row_bs_in + (long long)so_mhi * p.so_rm;
+      const long long so_ch0 = bo * p.so_ch_bs_out + bi * p.so_ch_bs_in + so_mlo / 4;
       uint32_t so_mx = 0;                             // largest |hi| of this thread's values (bits)
       // alignment of this lane group's chunk from the thread maxima; returns true for a chunk
       // taken as zero (largest value below 2^-90: its slices would be subnormal)
@@ -763,13 +775,11 @@ __global__ void __launch_bounds__(352, 1)
         }
         __syncwarp();
         if (gok) {
-          const int m_hi = m_so / p.so_mdiv, m_lo = m_so - m_hi * p.so_mdiv;
-          const int n_hi = n0 / p.so_ndiv, n_lo = n0 - n_hi * p.so_ndiv;
-          const long long crow = bo * p.so_row_bs_out + bi * p.so_row_bs_in + (long long)m_hi * p.so_rm +
-                                 (long long)n_hi * p.so_rn;
-          const long long ch = bo * p.so_ch_bs_out + bi * p.so_ch_bs_in + (long long)(n_lo / p.so_cb) * p.so_ch_cb +
-                               m_lo / 4;
-          const long long kstep = ch * (p.so_cb / 4) + (n_lo % p.so_cb) / 4;
+          const int n_hi = fdiv(n0, p.so_ndivf), n_lo = n0 - n_hi * p.so_ndiv;
+          const int c_hi = fdiv(n_lo, p.so_cbf), c_lo = n_lo - c_hi * p.so_cb;
+          const long long crow = so_row0 + (long long)n_hi * p.so_rn;
+          const long long ch = so_ch0 + (long long)c_hi * p.so_ch_cb;
+          const long long kstep = ch * (p.so_cb >> 2) + (c_lo >> 2);
           if (crow < 0 || crow >= p.so_rows || kstep < 0 || kstep >= p.so_ksteps) {
             atomicExch(p.status + 1, 17);            // a layout outside the planes: recorded, not written
           } else {
@@ -800,10 +810,10 @@ __global__ void __launch_bounds__(352, 1)
 #pragma unroll 1
           for (int g = 0; g < kCols / G; ++g) {
             const int cb = half * kCols + g * G;
-            float v[3][2][G];
+            float v[2][2][G];                         // orders 0 and 1: the maximum takes the hi word
             const uint32_t taddr = tbase + (uint32_t)cb;
 #pragma unroll
-            for (int o = 0; o < 3; ++o) {
+            for (int o = 0; o < 2; ++o) {
               tmem_ldg<G>(taddr + o * S::kOrderCols, v[o][0]);
               tmem_ldg<G>(taddr + o * S::kOrderCols + BN, v[o][1]);
             }
@@ -1111,6 +1121,8 @@ int launch_oz_bn(const Planes& A, const Planes& B, OzParams p, int slot, cudaStr
     if (p.dblock || !p.so_dst || p.so_mdiv % 4 || p.so_cb % 4 || p.so_cb <= 0 || p.M % 4 || p.N % 4 ||
         nstride % 4 || !halves_ok || p.so_ksteps <= 0 || p.so_rows <= 0)
       return fail(GW_EINVAL, "oz_gemm: slice output layout not supported");
+    p.so_ndivf = make_fastdiv(p.so_ndiv);
+    p.so_cbf = make_fastdiv(p.so_cb);
   }
   p.mtiles = (p.M + kBM - 1) / kBM;
   p.ntiles = (p.N + nstride - 1) / nstride;
