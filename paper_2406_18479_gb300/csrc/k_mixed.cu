@@ -286,9 +286,11 @@ struct OzParams {
   // and n = n_hi so_ndiv + n_lo, goes to
   //   row   = bo so_row_bs_out + bi so_row_bs_in + m_hi so_rm + n_hi so_rn,
   //   chunk = bo so_ch_bs_out + bi so_ch_bs_in + (n_lo / so_cb) so_ch_cb + m_lo / 4,
-  //   k     = chunk (4 so_cb) + 4 (n_lo % so_cb) + m_lo % 4,
+  //   k     = chunk (4 so_cb) + 16 ((n_lo % so_cb) / 4) + 4 (m_lo % 4) + n_lo % 4,
   // so that one chunk (4 consecutive rows m_lo x so_cb consecutive columns n_lo) lies in one
-  // tile and shares one slice alignment, the largest |value| of the chunk. so_xhalf: a chunk
+  // tile and shares one slice alignment, the largest |value| of the chunk; within a k-step of 16
+  // (4 rows x 4 columns) each row's 4 values are contiguous, so that a lane writes its own
+  // 8 bytes per slice (every producer of a consumer's two operands uses this order). so_xhalf: a chunk
   // spans both column halves of the tile (their maxima are exchanged). Requires so_mdiv % 4 == 0,
   // so_cb % 4 == 0, 4-aligned column ranges, and no block-diagonal batching.
   int so = 0, so_xhalf = 0;
@@ -435,7 +437,7 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 template <int BN_>
 struct OzShape {
   static constexpr int kBN = BN_;                      // output columns per tile (40, 56, 72 or 80)
-  static constexpr int kStages = kBN <= 40 ? 4 : 3;
+  static constexpr int kStages = kBN <= 56 ? 4 : 3;
   static constexpr int kRowBytes = 128;                // four slices x 16 k x bf16
   static constexpr int kAGroup = kBM * kRowBytes;      // bytes of one A group tile
   static constexpr int kBBlock = kBN * kRowBytes;      // bytes of one B group block
@@ -449,11 +451,9 @@ struct OzShape {
   static constexpr int kBufCols = 3 * kOrderCols;
   static constexpr int kBufs = 2 * kBufCols <= kTmemCols ? 2 : 1;
   // slice output: maxima exchanged between column halves (two tiles in flight x 4 lane quarters x
-  // 2 halves x 32 lanes) and per-warp line staging (8 warps x 8 line groups x 272 bytes)
+  // 2 halves x 32 lanes)
   static constexpr int kXmaxBytes = 2 * 4 * 2 * 32 * 4;
-  static constexpr int kLineBytes = 272;
-  static constexpr int kStageOutBytes = 8 * 8 * kLineBytes;
-  static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + 256 + kXmaxBytes + kStageOutBytes;
+  static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes + 256 + kXmaxBytes;
   static_assert(3 * kOrderCols <= kTmemCols, "three orders must fit in TMEM");
   static_assert(kStageBytes % 1024 == 0, "stages must keep the 1024-byte swizzle alignment");
   static_assert(kSmem <= 232448, "stages exceed shared memory");
@@ -500,7 +500,6 @@ __global__ void __launch_bounds__(352, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_full + 6);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   uint32_t* xmax = reinterpret_cast<uint32_t*>(smem + (size_t)S::kStages * S::kStageBytes + 256);
-  uint8_t* stage_out = reinterpret_cast<uint8_t*>(xmax) + S::kXmaxBytes;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -750,50 +749,43 @@ __global__ void __launch_bounds__(352, 1)
         for (int sl = 0; sl < 4; ++sl) magic[sl] = ldexpf(3.0f, E + 15 - 8 * sl);   // 1.5 * 2^23 * q_sl
         return eb == 0 || E < -90;
       };
-      // line staging of this warp's 8 lane groups: [re | im] x 4 slices x 16 values (+16 bytes of
-      // padding, so that the 2-byte stores of one instruction fall in distinct banks)
-      uint8_t* line = stage_out + ((size_t)(warp - 2) * 8 + (lane >> 2)) * S::kLineBytes;
       // slices of 4 columns c0..c0+3 of this row (double-float values f) -> one 16-wide line of the
-      // consumer's planes, written by the 4 lanes of the group (128 bytes per part)
+      // consumer's planes (128 bytes per part), of which this lane writes its row's 8 bytes per slice
       auto so_line = [&](int c0, const float4* f, bool zero, const float* magic) {
         const int n0 = nt * nstride + c0;
         const bool gok = ok && mok && c0 < nstride && n0 < p.N;   // the same for all 4 columns and lanes
-        __nv_bfloat16* lb = reinterpret_cast<__nv_bfloat16*>(line);
+        if (!gok) return;
+        const int n_hi = fdiv(n0, p.so_ndivf), n_lo = n0 - n_hi * p.so_ndiv;
+        const int c_hi = fdiv(n_lo, p.so_cbf), c_lo = n_lo - c_hi * p.so_cb;
+        const long long crow = so_row0 + (long long)n_hi * p.so_rn;
+        const long long ch = so_ch0 + (long long)c_hi * p.so_ch_cb;
+        const long long kstep = ch * (p.so_cb >> 2) + (c_lo >> 2);
+        if (crow < 0 || crow >= p.so_rows || kstep < 0 || kstep >= p.so_ksteps) {
+          atomicExch(p.status + 1, 17);              // a layout outside the planes: recorded, not written
+          return;
+        }
         const int j4 = lane & 3;
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-          float sr[4] = {0.f, 0.f, 0.f, 0.f}, si[4] = {0.f, 0.f, 0.f, 0.f};
-          if (gok && !zero) {
-            df_slices(f[cc].x, f[cc].y, magic, sr);
-            df_slices(f[cc].z, f[cc].w, magic, si);
+        for (int gr = 0; gr < 2; ++gr) {              // real part, then imaginary part
+          float sv[4][4];                             // [column][slice]
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+#pragma unroll
+            for (int sl = 0; sl < 4; ++sl) sv[cc][sl] = 0.f;
+            if (!zero) df_slices(gr ? f[cc].z : f[cc].x, gr ? f[cc].w : f[cc].y, magic, sv[cc]);
           }
+          __nv_bfloat16* dst = p.so_dst + (((long long)gr * p.so_ksteps + kstep) * p.so_rows + crow) * 64 + 4 * j4;
 #pragma unroll
           for (int sl = 0; sl < 4; ++sl) {
-            lb[sl * 16 + cc * 4 + j4] = __float2bfloat16_rn(sr[sl]);        // exact: digit x 2^(E-7-8 sl)
-            lb[64 + sl * 16 + cc * 4 + j4] = __float2bfloat16_rn(si[sl]);
+            // exact: digit x 2^(E-7-8 sl)
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(sv[0][sl], sv[1][sl]);
+            const __nv_bfloat162 hi = __floats2bfloat162_rn(sv[2][sl], sv[3][sl]);
+            uint2 w;
+            w.x = *reinterpret_cast<const uint32_t*>(&lo);
+            w.y = *reinterpret_cast<const uint32_t*>(&hi);
+            *reinterpret_cast<uint2*>(dst + 16 * sl) = w;
           }
         }
-        __syncwarp();
-        if (gok) {
-          const int n_hi = fdiv(n0, p.so_ndivf), n_lo = n0 - n_hi * p.so_ndiv;
-          const int c_hi = fdiv(n_lo, p.so_cbf), c_lo = n_lo - c_hi * p.so_cb;
-          const long long crow = so_row0 + (long long)n_hi * p.so_rn;
-          const long long ch = so_ch0 + (long long)c_hi * p.so_ch_cb;
-          const long long kstep = ch * (p.so_cb >> 2) + (c_lo >> 2);
-          if (crow < 0 || crow >= p.so_rows || kstep < 0 || kstep >= p.so_ksteps) {
-            atomicExch(p.status + 1, 17);            // a layout outside the planes: recorded, not written
-          } else {
-#pragma unroll
-            for (int gr = 0; gr < 2; ++gr) {
-              const uint4* src = reinterpret_cast<const uint4*>(line + gr * 128);
-              uint4* dst =
-                  reinterpret_cast<uint4*>(p.so_dst + (((long long)gr * p.so_ksteps + kstep) * p.so_rows + crow) * 64);
-              dst[j4] = src[j4];
-              dst[j4 + 4] = src[j4 + 4];
-            }
-          }
-        }
-        __syncwarp();
       };
       // running sums of the first kRG groups of 4 columns of this warp (chunked contractions)
       float4 rs[kRG > 0 ? kRG : 1][4];
