@@ -140,11 +140,11 @@ def test_invalid_arguments_rejected(G):
     ctx.destroy()
 
 
-@pytest.mark.parametrize("n", [1, 15, 16, 17, 33, 200, 430, 431])
+@pytest.mark.parametrize("n", [1, 15, 16, 17, 33, 200, 430, 431, 519, 800, 801])
 def test_aux_dyson_inverse_with_pivoting(G, n):
     """gw_aux_dyson = (I - P0)^{-1} - I per (q, n) (Eq. tilde_P_omega) against numpy, with unit
     diagonals in P0 so that I - P0 has a zero diagonal and every step must pivot; sizes around
-    the 16-column panels of the blocked inversion and beyond its 430 limit."""
+    the panels of the blocked inversion (16 columns up to n = 430, 8 up to 800) and beyond."""
     ntau = 4
     ctx = G.gw_create((1, 1, 1), 1, n, ntau, 10.0, precision="fp64")
     nw = ctx.nwb
