@@ -120,15 +120,17 @@ def test_autotune_keeps_results(systems):
 @pytest.mark.gpu
 @pytest.mark.parametrize("precision", ["fp64", "bf16x4"])
 def test_grouped_inversion_spans_both_panel_widths(precision):
-    """A batch whose aux bases straddle 430 (the widest matrix of the 16-column panel): the
-    grouped modes invert both size classes in their own launches and still give, bit for bit,
-    what lone evaluations give."""
+    """A batch whose aux bases straddle 430 (the widest matrix of the 16-column panel) and one
+    above 800 (the widest of the 8-column panel): the grouped modes invert both panel classes in
+    their own launches, leave the largest system's inversion to its own evaluation, and still
+    give, bit for bit, what lone evaluations give."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     ws = [I.molecule("small", 6, ntau=8, beta=20.0, seed=70),
           I.molecule("naux440", 110, ntau=8, beta=20.0, seed=71),
           I.molecule("naux432", 108, ntau=8, beta=20.0, seed=72),
-          I.molecule("naux428", 107, ntau=8, beta=20.0, seed=73)]
+          I.molecule("naux428", 107, ntau=8, beta=20.0, seed=73),
+          I.molecule("naux804", 201, ntau=4, beta=20.0, seed=74)]   # above 800: inverted on its own
     data = [I.make_inputs(w)[1:] for w in ws]
     cfgs = [gw.make_config(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision=precision) for w in ws]
     b = gw.gw_batch(cfgs, max_streams=3)
