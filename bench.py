@@ -671,6 +671,7 @@ def batched_measure(precision, n_systems=48, steps=3, max_streams=8, tune=True, 
     if tune:
         t0 = time.perf_counter()
         out["tau_batches"] = b.autotune(G, S)
+        out["tile_widths"] = [wd for _, wd in b.tuned()]
         out["tune_s"] = time.perf_counter() - t0
         for m in ("graph", "grouped_graph"):
             ms[m + "_tuned"] = timed(m)

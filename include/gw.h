@@ -111,6 +111,10 @@ typedef struct {
                            (nao % 4 == 0, nao <= 56, naux % 40 == 0), 1 = always through FP64-range
                            intermediates and a separate slicing pass. Both meet the same error
                            bound; their results differ by rounding order (the chunks differ). */
+  int tile_n;           /* mixed precisions: output columns per tile of the P0, R and V.G GEMMs
+                           whose width the slice-output layout does not fix: 0 = automatic (72
+                           where that pads the columns less than 80, else 80), or 56, 72 or 80.
+                           Results are the same for every width (gw_batch_autotune times them). */
 } gw_config;
 
 /* Library version string. */
@@ -542,10 +546,16 @@ int gw_batch_sigma_eval(gw_batch* batch, const gw_c128* const* G_dev, gw_c128* c
 /*
  * Per-system tuner: times one evaluation of each system for equal tau batches of
  * ntau / {1, 2, 3, 4, 6, 8} nodes (the grid of the GEMM launches) that fit the system's
- * budget share, keeps the fastest, and rebuilds the contexts. chosen (optional, n ints)
- * receives the batch sizes. Blocks until done; Sigma_dev is used as scratch.
+ * budget share, keeps the fastest; then, in the mixed precisions, times the tile widths
+ * 0 (automatic), 56, 72 and 80 of gw_config.tile_n at that batch and keeps the fastest.
+ * Systems of the same shape (mesh, nao, naux, ntau, precision, V layout, budget share) take
+ * the choice of the first one tuned. Rebuilds the contexts. chosen (optional, n ints) receives
+ * the tau batch sizes; gw_batch_tuned reports both choices. Blocks until done; Sigma_dev is
+ * used as scratch. Every choice gives the same results.
  */
 int gw_batch_autotune(gw_batch* batch, const gw_c128* const* G_dev, gw_c128* const* Sig_dev, int* chosen);
+/* The tau batch and tile width system i runs with (after gw_batch_autotune: the tuned ones). */
+int gw_batch_tuned(const gw_batch* batch, int i, int* tau_chunk, int* tile_n);
 /* Waits for the batch and reports any device-side failure of its contexts. */
 int gw_batch_synchronize(gw_batch* batch);
 

@@ -150,6 +150,7 @@ int gw_checkpoint_read(const char* path, gw_config* cfg_out, double* mu, int* it
     cfg_out->v_slices = keep.v_slices;
     cfg_out->v_packed = keep.v_packed;
     cfg_out->slice_pass = keep.slice_pass;
+    cfg_out->tile_n = keep.tile_n;
   }
   if (mu) *mu = m;
   if (iteration) *iteration = (int)it;

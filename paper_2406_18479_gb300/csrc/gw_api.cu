@@ -482,7 +482,8 @@ bool config_ok(const gw_config* cfg) {
            cfg->naux < 1 || cfg->naux > 4096 || cfg->ntau < 1 || cfg->ntau > 512 || !(cfg->beta > 0) ||
            cfg->precision < GW_FP64 || cfg->precision > GW_MIXED_BF16X4 || cfg->v_slices < GW_V_AUTO ||
            cfg->v_slices > GW_V_PER_Q || cfg->v_packed < 0 || cfg->v_packed > 1 || cfg->slice_pass < 0 ||
-           cfg->slice_pass > 1);
+           cfg->slice_pass > 1 ||
+           !(cfg->tile_n == 0 || cfg->tile_n == 56 || cfg->tile_n == 72 || cfg->tile_n == 80));
 }
 
 // Weights w_j with p(beta) = sum_j w_j f(tau_j) for the polynomial p of degree n - 1 through the
@@ -611,6 +612,7 @@ int ctx_build(gw_ctx* c, const gw_config* cfg) {
       d.v_slices = cfg->v_slices;
       d.v_packed = cfg->v_packed;
       d.fuse = cfg->slice_pass == 0;
+      d.tile_n = cfg->tile_n;
       d.mq = c->mq;
       if ((rc = mixed_create(&c->mixed, d, c->stream, c->status, &c->bytes, c->dry)) != GW_OK) break;
     }

@@ -404,47 +404,84 @@ int gw_batch_autotune(gw_batch* b, const gw_c128* const* G_dev, gw_c128* const* 
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return fail(GW_ECUDA, "gw_batch_autotune: events");
+  // device time of the second of two evaluations of system i under cfg (1e30 if cfg does not fit)
+  auto time_cfg = [&](int i, const gw_config& cfg, float* ms) -> int {
+    *ms = 1e30f;
+    cudaStream_t s = b->streams[b->lane[i]];
+    gw_ctx* ctx = nullptr;
+    if (gw_create(&ctx, &cfg, s) != GW_OK) return GW_OK;   // a candidate that does not fit is skipped
+    if (gw_set_coulomb(ctx, b->V[i]) == GW_OK && gw_sigma_eval(ctx, G_dev[i], Sig_dev[i]) == GW_OK &&
+        cudaEventRecord(e0, s) == cudaSuccess && gw_sigma_eval(ctx, G_dev[i], Sig_dev[i]) == GW_OK &&
+        cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess)
+      cudaEventElapsedTime(ms, e0, e1);
+    const int sync_rc = gw_synchronize(ctx);
+    gw_destroy(ctx);
+    return sync_rc;
+  };
+  // systems of one shape (sizes, precision, V layout, budget share) share one tuning
+  auto same_shape = [&](int i, int j) {
+    const gw_config &x = b->cfg[i], &y = b->cfg[j];
+    return std::equal(x.nk, x.nk + 3, y.nk) && x.nao == y.nao && x.naux == y.naux && x.ntau == y.ntau &&
+           x.precision == y.precision && x.v_slices == y.v_slices && x.v_packed == y.v_packed &&
+           x.slice_pass == y.slice_pass && b->max_chunk[i] == b->max_chunk[j];
+  };
+  std::vector<int> done;
   int rc = GW_OK;
   for (int i = 0; i < b->n && rc == GW_OK; ++i) {
-    // candidates: equal batches of ntau / {1, 2, 3, 4, 6, 8} nodes within the system's budget share
-    const int T = b->cfg[i].ntau;
-    std::vector<int> cand;
-    for (int d : {1, 2, 3, 4, 6, 8}) {
-      const int c = (T + d - 1) / d;
-      if (c <= b->max_chunk[i] && std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
-    }
-    if (cand.empty()) cand.push_back(b->max_chunk[i]);
-    float best_ms = 1e30f;
-    int best = b->cfg[i].tau_chunk;
-    cudaStream_t s = b->streams[b->lane[i]];
-    for (int c : cand) {
-      gw_config cfg = b->cfg[i];
-      cfg.tau_chunk = c;
-      gw_ctx* ctx = nullptr;
-      if (gw_create(&ctx, &cfg, s) != GW_OK) continue;   // a candidate that does not fit is skipped
-      float ms = 1e30f;
-      if (gw_set_coulomb(ctx, b->V[i]) == GW_OK && gw_sigma_eval(ctx, G_dev[i], Sig_dev[i]) == GW_OK &&
-          cudaEventRecord(e0, s) == cudaSuccess && gw_sigma_eval(ctx, G_dev[i], Sig_dev[i]) == GW_OK &&
-          cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess)
-        cudaEventElapsedTime(&ms, e0, e1);
-      const int sync_rc = gw_synchronize(ctx);
-      gw_destroy(ctx);
-      if (sync_rc != GW_OK) {
-        rc = sync_rc;
+    bool reused = false;
+    for (int j : done)
+      if (same_shape(i, j)) {
+        b->cfg[i].tau_chunk = b->cfg[j].tau_chunk;
+        b->cfg[i].tile_n = b->cfg[j].tile_n;
+        reused = true;
         break;
       }
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = c;
+    if (!reused) {
+      // tau batch: equal batches of ntau / {1, 2, 3, 4, 6, 8} nodes within the system's budget share
+      const int T = b->cfg[i].ntau;
+      std::vector<int> cand;
+      for (int d : {1, 2, 3, 4, 6, 8}) {
+        const int c = (T + d - 1) / d;
+        if (c <= b->max_chunk[i] && std::find(cand.begin(), cand.end(), c) == cand.end()) cand.push_back(c);
       }
+      if (cand.empty()) cand.push_back(b->max_chunk[i]);
+      float best_ms = 1e30f;
+      gw_config best = b->cfg[i];
+      for (int c : cand) {
+        gw_config cfg = b->cfg[i];
+        cfg.tau_chunk = c;
+        float ms;
+        if ((rc = time_cfg(i, cfg, &ms)) != GW_OK) break;
+        if (ms < best_ms) best_ms = ms, best = cfg;
+      }
+      // then the tile width of the free-width GEMMs (mixed precisions), at that tau batch
+      if (rc == GW_OK && b->cfg[i].precision != GW_FP64) {
+        for (int w : {0, 56, 72, 80}) {
+          if (w == best.tile_n) continue;
+          gw_config cfg = best;
+          cfg.tile_n = w;
+          float ms;
+          if ((rc = time_cfg(i, cfg, &ms)) != GW_OK) break;
+          if (ms < best_ms) best_ms = ms, best = cfg;
+        }
+      }
+      b->cfg[i].tau_chunk = best.tau_chunk;
+      b->cfg[i].tile_n = best.tile_n;
+      done.push_back(i);
     }
-    b->cfg[i].tau_chunk = best;
-    if (chosen) chosen[i] = best;
+    if (chosen) chosen[i] = b->cfg[i].tau_chunk;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc == GW_OK) rc = create_contexts(b);
   return rc;
+}
+
+int gw_batch_tuned(const gw_batch* b, int i, int* tau_chunk, int* tile_n) {
+  if (!b || i < 0 || i >= b->n) return fail(GW_EINVAL, "gw_batch_tuned: no system %d", i);
+  if (tau_chunk) *tau_chunk = b->cfg[i].tau_chunk;
+  if (tile_n) *tile_n = b->cfg[i].tile_n;
+  return GW_OK;
 }
 
 int gw_batch_synchronize(gw_batch* b) {

@@ -10,7 +10,8 @@ namespace gwi {
 struct MixedDims {
   int nk3[3] = {1, 1, 1};
   int nk = 1, nao = 0, naux = 0, ntau = 0, precision = 0, tau_chunk = 0, v_slices = 0, v_packed = 0;
-  int fuse = 1;           // 1: slice-output epilogues where the sizes allow (nao % 4 == 0, nao <= 56, naux % 40 == 0)
+  int fuse = 1;
+  int tile_n = 0;                 // tile width of the free-width GEMMs (0: automatic)           // 1: slice-output epilogues where the sizes allow (nao % 4 == 0, nao <= 56, naux % 40 == 0)
   std::vector<int> mq;    // index of -q for every q
 };
 

@@ -1435,7 +1435,7 @@ int vg_gemm(MixedState* s, int pair_tab, int g_tab, const Planes& Gp, int q, int
     p.vc.rs_in = 1;
     p.vc.rs_out = (long long)nk * s->pair;
     p.vc.ks_in = nao;
-    return launch_oz(Gp, *vo.P, p, SLOT_VG_MIXED, s->stream);
+    return launch_oz(Gp, *vo.P, p, SLOT_VG_MIXED, s->stream, s->d.tile_n);
   }
   p.M = naux * nao;                       // (Q', b)
   p.N = nt * nao;                         // (t, d)
@@ -1448,7 +1448,7 @@ int vg_gemm(MixedState* s, int pair_tab, int g_tab, const Planes& Gp, int q, int
   p.vc.kin = nao;
   p.vc.ks_in = nao;
   p.vc.ks_out = (long long)nk * s->pair;
-  return launch_oz(*vo.P, Gp, p, SLOT_VG_MIXED, s->stream);
+  return launch_oz(*vo.P, Gp, p, SLOT_VG_MIXED, s->stream, s->d.tile_n);
 }
 
 // Fused path, P0 operands. The contraction index of P0 runs over (k, d, b) in chunks of 4 b x all
@@ -1531,7 +1531,7 @@ int polarization_chunk(MixedState* s, const double2* G, double2* P0t, double spi
   p.status = s->status;
   p.ws = s->ws;
   (void)nao;
-  return launch_oz(xs, ys, p, SLOT_P0_TC, s->stream);
+  return launch_oz(xs, ys, p, SLOT_P0_TC, s->stream, s->d.tile_n);
 }
 
 int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double2* Sig, int q, int t0, int nt) {
@@ -1574,7 +1574,7 @@ int self_energy_chunk(MixedState* s, const double2* G, const double2* Pt, double
       p.so_row_bs_out = (long long)nk * nao;
     }
     // the fused chunks are halves of an 80-wide tile
-    GW_TRY_INTERNAL(launch_oz(*vo.P, s->ps, p, SLOT_R_TC, s->stream, s->fused ? 80 : 0));
+    GW_TRY_INTERNAL(launch_oz(*vo.P, s->ps, p, SLOT_R_TC, s->stream, s->fused ? 80 : s->d.tile_n));
   }
   if (s->fused) {
     // Z^Q_{ib}(k,t) = sum_a G^{k-q}_ab(t) V^{k,k-q}_ia(Q): rows (t, b) of G^T, columns (i, Q) of V,

@@ -31,7 +31,7 @@ ABI_SYMBOLS = [
     "gw_mix", "gw_synchronize", "gw_profile_enable", "gw_launch_count", "gw_profile_slots",
     "gw_profile_read", "gw_polarization_noalloc", "gw_job_bytes", "gw_server_create",
     "gw_server_destroy", "gw_submit", "gw_poll", "gw_batch_create", "gw_batch_destroy",
-    "gw_batch_set_coulomb", "gw_batch_sigma_eval", "gw_batch_autotune", "gw_batch_synchronize",
+    "gw_batch_set_coulomb", "gw_batch_sigma_eval", "gw_batch_autotune", "gw_batch_tuned", "gw_batch_synchronize",
     "gw_density", "gw_sigma_inf", "gw_set_mu", "gw_particle_number", "gw_find_mu", "gw_diis_create",
     "gw_diis_destroy", "gw_diis_push", "gw_diis_extrapolate", "gw_scgw_bytes", "gw_scgw", "gw_diis_push_residual",
     "gw_commutator_residual", "gw_gf2_self_energy", "gw_gf2_exchange", "gw_k_interpolate", "gw_ir_grids", "gw_set_overlap", "gw_checkpoint_write", "gw_checkpoint_read", "gw_selftest_bounded_wait", "gw_check_guards", "gw_debug_mark_guard",
@@ -52,7 +52,7 @@ class gw_config(ctypes.Structure):
         ("nk", ctypes.c_int * 3), ("nao", ctypes.c_int), ("naux", ctypes.c_int), ("ntau", ctypes.c_int),
         ("beta", ctypes.c_double), ("mu", ctypes.c_double), ("spin_factor", ctypes.c_double),
         ("precision", ctypes.c_int), ("tau_chunk", ctypes.c_int), ("v_slices", ctypes.c_int),
-        ("v_packed", ctypes.c_int), ("slice_pass", ctypes.c_int),
+        ("v_packed", ctypes.c_int), ("slice_pass", ctypes.c_int), ("tile_n", ctypes.c_int),
     ]
 
 
@@ -144,6 +144,7 @@ def lib():
     L.gw_batch_set_coulomb.argtypes = [vp, ctypes.POINTER(vp)]
     L.gw_batch_sigma_eval.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), i]
     L.gw_batch_autotune.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(i)]
+    L.gw_batch_tuned.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]
     L.gw_batch_synchronize.argtypes = [vp]
     L.gw_density.argtypes = [vp, vp, vp]
     L.gw_sigma_inf.argtypes = [vp, vp, vp]
@@ -216,7 +217,7 @@ class gw_ctx:
     """Owner of one gw_ctx* (gw_create ... gw_destroy)."""
 
     def __init__(self, nk3, nao, naux, ntau, beta, mu=0.0, spin_factor=2.0, precision="fp64",
-                 tau_chunk=0, v_slices=0, stream=None, v_packed=False, slice_pass=False):
+                 tau_chunk=0, v_slices=0, stream=None, v_packed=False, slice_pass=False, tile_n=0):
         import torch
         self.nk3 = tuple(int(x) for x in nk3)
         self.nk = int(np.prod(self.nk3))
@@ -228,7 +229,7 @@ class gw_ctx:
         self.v_packed = int(v_packed)
         cfg = gw_config((ctypes.c_int * 3)(*self.nk3), self.nao, self.naux, self.ntau, self.beta,
                         self.mu, float(spin_factor), prec, int(tau_chunk), int(v_slices), self.v_packed,
-                        int(bool(slice_pass)))
+                        int(bool(slice_pass)), int(tile_n))
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         h = ctypes.c_void_p()
         _check(lib().gw_create(ctypes.byref(h), ctypes.byref(cfg), ctypes.c_void_p(self.stream.cuda_stream)))
@@ -410,11 +411,11 @@ def gw_polarization_noalloc(nk3, nao, naux, ntau, spin_factor, V, G, P0t, stream
 
 
 def make_config(nk3, nao, naux, ntau, beta, mu=0.0, spin_factor=2.0, precision="fp64", tau_chunk=0,
-                v_slices=0, v_packed=False, slice_pass=False):
+                v_slices=0, v_packed=False, slice_pass=False, tile_n=0):
     prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     return gw_config((ctypes.c_int * 3)(*[int(x) for x in nk3]), int(nao), int(naux), int(ntau), float(beta),
                      float(mu), float(spin_factor), prec, int(tau_chunk), int(v_slices), int(bool(v_packed)),
-                     int(bool(slice_pass)))
+                     int(bool(slice_pass)), int(tile_n))
 
 
 def gw_job_bytes(cfg: gw_config) -> int:
@@ -537,6 +538,15 @@ class gw_batch:
         chosen = (ctypes.c_int * self.n)()
         _check(lib().gw_batch_autotune(self._h, self._ptrs(G, "G"), self._ptrs(Sig, "Sig"), chosen))
         return list(chosen)
+
+    def tuned(self):
+        """[(tau batch, tile width)] of every system (gw_batch_tuned)."""
+        out = []
+        for i in range(self.n):
+            t, w = ctypes.c_int(0), ctypes.c_int(0)
+            _check(lib().gw_batch_tuned(self._h, i, ctypes.byref(t), ctypes.byref(w)))
+            out.append((t.value, w.value))
+        return out
 
     def synchronize(self):
         _check(lib().gw_batch_synchronize(self._h))

@@ -38,7 +38,8 @@ def test_null_and_out_of_range_arguments(L):
 
 
 @pytest.mark.parametrize("field,value", [("nao", 0), ("naux", 5000), ("ntau", 0), ("beta", -1.0), ("precision", 7),
-                                         ("precision", 2), ("v_slices", 3), ("v_packed", 2), ("slice_pass", 2)])
+                                         ("precision", 2), ("v_slices", 3), ("v_packed", 2), ("slice_pass", 2),
+                                         ("tile_n", 64), ("tile_n", -1)])
 def test_bad_configurations(L, field, value):
     cfg = gw.make_config((2, 1, 1), 3, 4, 5, 2.0)
     setattr(cfg, field, value)

@@ -110,6 +110,9 @@ def test_autotune_keeps_results(systems):
     chosen = b.autotune(G, S)
     assert len(chosen) == len(systems)
     assert all(1 <= c <= w.ntau for c, (w, *_) in zip(chosen, systems))
+    tuned = b.tuned()
+    assert [t for t, _ in tuned] == chosen
+    assert all(wd in (0, 56, 72, 80) for _, wd in tuned)
     b.sigma_eval(G, S, "graph")
     b.synchronize()
     for s, (w, v, g, ref) in zip(S, systems):
@@ -144,3 +147,18 @@ def test_grouped_inversion_spans_both_panel_widths(precision):
         for i, s in enumerate(S):
             assert np.array_equal(s.cpu().numpy(), lone[i]), (mode, ws[i].name)
     b.destroy()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("tile_n", [56, 72, 80])
+def test_tile_width_keeps_results(systems, tile_n):
+    """Every tile width of the free-width GEMMs gives the oracle's self-energy (and the tuner's
+    candidates are exactly these contexts)."""
+    for w, v, g, ref in systems:
+        ctx = gw.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision="bf16x4", tile_n=tile_n)
+        gw.gw_set_coulomb(ctx, torch.from_numpy(v).cuda())
+        S = torch.empty(ctx.shapes()["Sig"], dtype=torch.complex128, device="cuda")
+        gw.gw_sigma_eval(ctx, torch.from_numpy(g).cuda(), S)
+        gw.gw_synchronize(ctx)
+        assert rel(S.cpu().numpy(), ref) < 1e-7, (w.name, tile_n)
+        ctx.destroy()

@@ -98,10 +98,12 @@ def test_self_energy_sampled_from_gpu_pt(gpu, inputs, samples, precision, tol):
 
 def test_sigma_eval_equals_staged_calls(gpu):
     # gw_sigma_eval solves the aux Dyson equation at canonical (q, n) only and mirrors the rest,
-    # the staged gw_screened_interaction solves every (q, n): equal up to FP64 rounding order
-    for prec in ("fp64", "bf16x3"):
+    # the staged gw_screened_interaction solves every (q, n): equal up to FP64 rounding order.
+    # In the mixed precision P~ is then cut into slices whose last digit is 2^-32 of the chunk
+    # maximum, so a rounding-order difference in P~ can move Sigma by up to that: 5e-10.
+    for prec, tol in (("fp64", 1e-11), ("bf16x3", 5e-10)):
         out = gpu[prec]
-        assert rel(out["Sig_eval"], out["Sig"]) < 1e-11
+        assert rel(out["Sig_eval"], out["Sig"]) < tol
 
 
 def test_mixed_target_against_fp64(gpu):
