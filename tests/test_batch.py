@@ -152,13 +152,18 @@ def test_grouped_inversion_spans_both_panel_widths(precision):
 @pytest.mark.gpu
 @pytest.mark.parametrize("tile_n", [56, 72, 80])
 def test_tile_width_keeps_results(systems, tile_n):
-    """Every tile width of the free-width GEMMs gives the oracle's self-energy (and the tuner's
-    candidates are exactly these contexts)."""
+    """Every tile width of the free-width GEMMs gives the oracle's self-energy, and bit for bit
+    what the automatic width gives (a tile's width does not change how any one output element
+    is summed); the tuner's candidates are exactly these contexts."""
     for w, v, g, ref in systems:
-        ctx = gw.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision="bf16x4", tile_n=tile_n)
-        gw.gw_set_coulomb(ctx, torch.from_numpy(v).cuda())
-        S = torch.empty(ctx.shapes()["Sig"], dtype=torch.complex128, device="cuda")
-        gw.gw_sigma_eval(ctx, torch.from_numpy(g).cuda(), S)
-        gw.gw_synchronize(ctx)
-        assert rel(S.cpu().numpy(), ref) < 1e-7, (w.name, tile_n)
-        ctx.destroy()
+        out = []
+        for width in (0, tile_n):
+            ctx = gw.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision="bf16x4", tile_n=width)
+            gw.gw_set_coulomb(ctx, torch.from_numpy(v).cuda())
+            S = torch.empty(ctx.shapes()["Sig"], dtype=torch.complex128, device="cuda")
+            gw.gw_sigma_eval(ctx, torch.from_numpy(g).cuda(), S)
+            gw.gw_synchronize(ctx)
+            out.append(S.cpu().numpy())
+            ctx.destroy()
+        assert rel(out[1], ref) < 1e-7, (w.name, tile_n)
+        assert np.array_equal(out[0], out[1]), (w.name, tile_n)
