@@ -519,9 +519,10 @@ int gw_checkpoint_read(const char* path, gw_config* cfg_out, double* mu, int* it
  *                     first call after creation or gw_batch_set_coulomb runs uncaptured),
  *   GW_BATCH_GROUPED  every system's evaluation up to the aux Dyson equation (Eq.
  *                     tilde_P_omega) on its stream, then the inversions of all systems'
- *                     (I - P0(i Omega)) matrices as one persistent launch over the ragged list
- *                     of matrices (two launches: n <= 430 and n > 430, largest first), then
- *                     the rest of every evaluation on its stream,
+ *                     (I - P0(i Omega)) matrices as launches over the ragged list of matrices,
+ *                     one block per matrix, largest first (one launch for n <= 430, one for
+ *                     430 < n <= 800; a system with naux > 800 inverts its own matrices
+ *                     within its evaluation), then the rest of every evaluation on its stream,
  *   GW_BATCH_GROUPED_GRAPH  the grouped work captured into a graph as GW_BATCH_GRAPH does.
  * Every mode computes, per system, exactly what gw_sigma_eval computes alone. Calls are
  * asynchronous: the batch starts after the work queued on cuda_stream and cuda_stream waits
