@@ -253,6 +253,17 @@ def ncu_traffic(kernel, algorithmic_bytes_per_launch):
     return rec["dram_per_algorithmic_byte"] * algorithmic_bytes_per_launch
 
 
+def in_turns(rank, world, fn, barrier, per_turn=2):
+    """fn() on every rank, per_turn ranks at a time (turn rank // per_turn), a barrier after each
+    turn; returns this rank's fn()."""
+    out = None
+    for turn in range((world + per_turn - 1) // per_turn):
+        if rank // per_turn == turn:
+            out = fn()
+        barrier()
+    return out
+
+
 def max_over_ranks(value, dist=None):
     """The largest value over all ranks (the timing rule for a multi-rank run)."""
     if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
@@ -447,20 +458,25 @@ def run_ours(args, rank, world, local_rank):
     w = I.Workload(base.name, base.nk3, base.nao, base.naux, base.ntau, base.nomega, base.beta, base.mu,
                    base.decay, base.seed + rank, base.solid)
     t_in = time.perf_counter()
-    h, v, g = I.make_inputs(w)
-    grid = None
-    if args.ir_lambda > 0:
-        # the same system on an IR grid (the tau node count follows from Lambda and eps)
-        grid = gw.gw_ir_grids(w.beta, args.ir_lambda, args.ir_eps)
-        w = I.Workload(f"{w.name}_ir{args.ir_lambda:g}", w.nk3, w.nao, w.naux, len(grid[0]), len(grid[0]), w.beta,
-                       w.mu, w.decay, w.seed, w.solid)
-        g = I.g0_tau(h, w.mu, w.beta, grid[0])
-    V = torch.from_numpy(I.pack_v(v) if args.v_packed else v).cuda()
-    G = torch.from_numpy(g).cuda()
+    keep_v = rank == 0 and world == 1 and not args.no_cpu_baseline and args.ir_lambda <= 0
+
+    def make_inputs():
+        h, v, g = I.make_inputs(w)
+        grid, wr = None, w
+        if args.ir_lambda > 0:
+            # the same system on an IR grid (the tau node count follows from Lambda and eps)
+            grid = gw.gw_ir_grids(w.beta, args.ir_lambda, args.ir_eps)
+            wr = I.Workload(f"{w.name}_ir{args.ir_lambda:g}", w.nk3, w.nao, w.naux, len(grid[0]), len(grid[0]),
+                            w.beta, w.mu, w.decay, w.seed, w.solid)
+            g = I.g0_tau(h, w.mu, w.beta, grid[0])
+        V = torch.from_numpy(I.pack_v(v) if args.v_packed else v).cuda()
+        G = torch.from_numpy(g).cuda()
+        return h, (v if keep_v else None), g, grid, wr, V, G
+
+    # the host copy of a 4x4x4 solid's V is 71 GB: ranks on one node build their inputs two at a
+    # time, each freeing its host V once it is on the device
+    h, v, g, grid, w, V, G = in_turns(rank, world, make_inputs, barrier)
     v_bytes = V.numel() * 16
-    keep_v = rank == 0 and world == 1 and not args.no_cpu_baseline and grid is None
-    if not keep_v:
-        del v
     input_s = time.perf_counter() - t_in
     ctx = gw.gw_create(w.nk3, w.nao, w.naux, w.ntau, w.beta, precision=args.precision, tau_chunk=args.tau_chunk,
                        v_packed=args.v_packed, slice_pass=args.slice_pass)

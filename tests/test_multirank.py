@@ -68,3 +68,40 @@ def test_q_sharded_sigma_and_timing_reduction():
         err, tmax = out[r]
         assert err < 1e-12
         assert tmax == 20.0
+
+
+def _turns_worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import sys
+        import time
+        sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+        import bench
+
+        def work():
+            t0 = time.monotonic()
+            time.sleep(0.3)
+            return (t0, time.monotonic())
+
+        out[rank] = bench.in_turns(rank, world, work, dist.barrier)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_inputs_are_built_in_turns_of_two_ranks():
+    """bench.py builds each rank's inputs (the host copy of V is 71 GB on the 4x4x4 solid) two
+    ranks at a time: every rank builds exactly once, and a later turn starts only after every
+    rank of the earlier turns has finished."""
+    world = 5
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_turns_worker, args=(world, port, out), nprocs=world, join=True, start_method="spawn")
+    spans = {r: out[r] for r in range(world)}
+    assert sorted(spans) == list(range(world))
+    for a in range(world):
+        for b in range(world):
+            if a // 2 < b // 2:
+                assert spans[a][1] <= spans[b][0], (a, b)
